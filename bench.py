@@ -1,0 +1,366 @@
+"""Benchmark of the DJ-TLED time step on GB300 (element-updates per second).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gdj|reference] [--workload W]
+
+One step = one DJ-TLED time step of the whole mesh: element forces (Table 3),
+deterministic gather and central-difference update with prescribed
+displacements (Eq. 13).  Default workload: unit cube, 59^3 voxels x 6 Kuhn
+tets = 1,232,274 T4 / 216,000 nodes, neo-Hookean E = 3 kPa, nu = 0.49, base
+fixed, top face sheared 10 % on a smooth ramp over 5000 steps (the 1.2M-tet
+variant of the hex-cube shear workload).  The working set (~215 MB) is larger
+than the 129 MB L2, so no flush is needed between steps.
+
+N > 1 (torchrun): every rank advances its own replica of the workload (the
+method has no exchange step: replicas only, weak scaling); rank 0 prints the
+line with value = all ranks' element-updates / max-over-ranks time.
+
+--impl reference runs the FP64 oracle on the host cores as the reference arm
+(rank 0 only), each step on a bounded sub-cube of the same workload.
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2106_14189_gb300 import workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per element-update, T4 neo-Hookean (FP32 / int32), from the
+# per-term model of the design: element side and node side of each kernel.
+#   force kernel : connectivity 16 + element table 68 (0J 36, P 24, kappa 0V 4,
+#                  1/det 0J 4) + element-force write 48 (4 nodes x 12 B)
+#                  + u^n read once per node 16 N/E
+#   update kernel: element-force read 48 + gather index 16 (4 B per slot)
+#                  + node state 64 N/E (U^n, U^n-U^n-1 read and written, 16 B each)
+BYTES_FORCE_T4_NH = dict(elem=16 + 68 + 48, node=16)
+BYTES_UPDATE_T4_NH = dict(elem=48 + 16, node=64)
+
+
+def workload(name):
+    if name == "tet4_cube59":
+        p = W.cube_shear(W.TET4, 59, n_steps=5000, shear=0.1)
+        desc = ("tet4 unit cube 59^3 x 6 Kuhn (1,232,274 T4, 216,000 nodes), neo-Hookean "
+                "E=3kPa nu=0.49 rho=1000, base fixed, top shear 10% smooth ramp over 5000 steps, "
+                "dt=0.9 dt_crit")
+    elif name == "hex8_cube64":
+        p = W.cube_shear(W.HEX8, 64, n_steps=5000, shear=0.1)
+        desc = ("hex8 unit cube 64^3 (262,144 H8, 274,625 nodes), 1-point + hourglass 0.1, "
+                "neo-Hookean E=3kPa nu=0.49, base fixed, top shear 10% smooth ramp over 5000 "
+                "steps, dt=0.9 dt_crit")
+    elif name == "tet4_cube10":
+        p = W.cube_compression_tet4(10, 2000)
+        desc = "tet4 cube 10^3 x 6 (6000 T4), NH, -20% z smooth ramp, 2000 steps"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return p, desc
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2106_14189_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        d = json.load(open(PEAKS_FILE))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(p_small, n_steps, dt=None):
+    """Oracle element-updates/s on a problem, timed over n_steps (after set-up)."""
+    from oracle import dynamics
+    s = dynamics.ExplicitSolver.from_problem(p_small, dt=dt)
+    s.step()
+    t = time.perf_counter()
+    for _ in range(n_steps):
+        s.step()
+    el = time.perf_counter() - t
+    return p_small.n_elems * n_steps / el, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    # bounded sample: a smaller cube of the same workload family, sized so that
+    # (warmup + steps) oracle steps take about a minute
+    budget_s = float(os.environ.get("DJ_REF_BUDGET_S", "60"))
+    probe = W.cube_shear(W.TET4, 8, n_steps=5000) if args.workload.startswith("tet4") else \
+        W.cube_shear(W.HEX8, 12, n_steps=5000)
+    rate, _ = oracle_rate(probe, 5)
+    per_step_elems = rate * budget_s / max(1, args.steps + args.warmup)
+    if args.workload.startswith("tet4"):
+        n = max(2, int(round((per_step_elems / 6.0) ** (1 / 3))))
+        sample = W.cube_shear(W.TET4, n, n_steps=5000)
+    else:
+        n = max(2, int(round(per_step_elems ** (1 / 3))))
+        sample = W.cube_shear(W.HEX8, n, n_steps=5000)
+    from oracle import dynamics
+    s = dynamics.ExplicitSolver.from_problem(sample)
+    for _ in range(args.warmup):
+        s.step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    el = time.perf_counter() - t
+    value = sample.n_elems * args.steps / el
+    _, desc = workload(args.workload)
+    line = {"impl": "reference", "metric": "element-updates/s", "value": value,
+            "unit": "element-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": "element-updates/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"FP64 numpy oracle, {sample.name} ({sample.n_elems} elements) "
+                                       f"per step, same element type/material/boundary recipe"},
+            "e2e": {"value": value, "unit": "element-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="gdj", choices=["gdj", "reference"])
+    ap.add_argument("--workload", default="tet4_cube59",
+                    choices=["tet4_cube59", "hex8_cube64", "tet4_cube10"])
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-also", action="store_true", help="skip the secondary hex8 workload")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_2106_14189_gb300 import binding as B
+
+    p, desc = workload(args.workload)
+    mesh = B.Mesh(p)
+    stream = torch.cuda.current_stream()
+    # warm-up
+    mesh.run(args.warmup, stream)
+    mesh.sync(stream)
+    # timed region
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    mesh.run(args.steps, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else None
+    mesh.sync(stream)
+    ms = ev0.elapsed_time(ev1)
+    # per-kernel device time over the same number of steps (events between kernels)
+    ms_force, ms_update = B.dj_run_n_profiled(mesh.h, args.steps, stream)
+    mesh.sync(stream)
+    t_max = torch.tensor([ms], device="cuda")
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    E, N = p.n_elems, p.n_nodes
+    value = world * E * args.steps / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel
+    peak, peak_kind = measured_peak()
+    ne_ratio = N / E
+    force_bytes = (BYTES_FORCE_T4_NH["elem"] + BYTES_FORCE_T4_NH["node"] * ne_ratio) * E
+    update_bytes = (BYTES_UPDATE_T4_NH["elem"] + BYTES_UPDATE_T4_NH["node"] * ne_ratio) * E
+    t_force = ms_force * 1e-3 / args.steps
+    t_update = ms_update * 1e-3 / args.steps
+    dominant = "force" if t_force >= t_update else "update"
+    bytes_dom = force_bytes if dominant == "force" else update_bytes
+    t_dom = t_force if dominant == "force" else t_update
+    achieved = bytes_dom / t_dom / 1e9
+    traffic = None
+    try:
+        tr = json.load(open(TRAFFIC_FILE))
+        if tr.get("source_hash") == kernel_source_hash() and tr.get("workload") == args.workload:
+            traffic = tr.get(f"{dominant}_bytes_per_launch")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"force_tet4 (NH)" if dominant == "force" else "node gather-update",
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_dom,
+                "step": {"bytes_per_element_update": (force_bytes + update_bytes) / E,
+                         "achieved_gbs": (force_bytes + update_bytes) / (ms_max * 1e-3 / args.steps) / 1e9},
+                "kernel_us": {"force": t_force * 1e6, "update": t_update * 1e6}}
+
+    # end to end through the public C ABI with host buffers: every step uploads
+    # the prescribed-displacement targets of that step and reads U back
+    e2e = None
+    if args.e2e_steps > 0:
+        targets = np.array(p.bc_target, dtype=np.float64)
+        n_e2e = args.e2e_steps
+        U_host = np.empty((N, 3))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(n_e2e):
+            B.dj_mesh_update_bc_targets(mesh.h, targets)
+            B.dj_step(mesh.h, stream)
+            U_host = B.dj_get_displacements(mesh.h, N)
+        t1 = time.perf_counter()
+        info = mesh.info()
+        n_bc_nodes = len(np.unique(p.bc_dof // 3))
+        e2e = {"value": E * n_e2e / (t1 - t0), "unit": "element-updates/s",
+               "h2d_bytes_per_step": int(n_bc_nodes * 16), "d2h_bytes_per_step": int(N * 16),
+               "steps": n_e2e}
+
+    # secondary workload: the hex8 cube (same metric)
+    also = None
+    if args.workload == "tet4_cube59" and world == 1 and not args.no_also:
+        ph, desch = workload("hex8_cube64")
+        mh = B.Mesh(ph)
+        mh.run(args.warmup, stream)
+        mh.sync(stream)
+        kh = max(1000, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mh.run(kh, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mh.sync(stream)
+        msh = e0.elapsed_time(e1)
+        also = {"workload": desch, "value": ph.n_elems * kh / (msh * 1e-3),
+                "unit": "element-updates/s", "ms_per_step": msh / kh, "steps": kh}
+        mh.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = W.cube_shear(W.TET4, 24, n_steps=5000)
+        rate, el = oracle_rate(sample, 8)
+        cpu = {"value": rate, "unit": "element-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle, 8 steps of the same recipe on a 24^3 x 6 cube "
+                         f"({sample.n_elems} T4), {el:.1f} s"}
+    mesh.close()
+    if rank == 0:
+        line = {"metric": "element-updates/s", "value": value, "unit": "element-updates/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": desc, "elements": E, "nodes": N,
+                           "parallelism": f"replicas x{world}",
+                           "l2": "working set ~215 MB > 129 MB L2 (no flush needed)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 2 * args.steps, "also": also,
+                "source_hash": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * dj_tled.h -- C ABI of the GB300 DJ-TLED time-step library.
+ *
+ * The library advances a hyperelastic finite element mesh in time with the
+ * direct Jacobian total Lagrangian explicit dynamics (DJ-TLED) method of
+ * J. Zhang, "A direct Jacobian total Lagrangian explicit dynamics finite
+ * element algorithm for real-time simulation of hyperelastic materials"
+ * (arXiv 2106.14189):
+ *
+ *   per element   tJ = 0J + H_xi u_e (Eq. 11), J (Eq. 12), g_hat (Eq. 18),
+ *                 invariants (Table 1), nodal forces (Table 3)
+ *   per node      deterministic gather of the element forces (sum in Eq. 13),
+ *                 central-difference update with lumped mass and
+ *                 mass-proportional damping (Eq. 13), prescribed displacements
+ *
+ * Elements: 4-node tetrahedra (volume coordinates) and 8-node bricks with
+ * 1-point integration and hourglass control.  Materials (Table 3): neo-Hookean
+ * (NH), transversely isotropic NH (TI), orthotropic NH (OT), Mooney-Rivlin (MR).
+ *
+ * Conventions shared by every call
+ *   - Units are SI (m, Pa, kg/m^3, s).
+ *   - Node ids and element ids are the caller's, 0-based.  The library
+ *     renumbers internally for memory locality; every array passed in or out is
+ *     in the caller's order.
+ *   - Host pointers (plain C arrays) are copied during the call; the caller
+ *     keeps ownership.  Pointers documented as "device" must point to memory of
+ *     the current CUDA device.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls taking a stream only enqueue work unless documented otherwise.
+ *   - Every call returns a dj_status and never throws or aborts.  On failure
+ *     dj_last_error(mesh) holds a one-line description.
+ *   - A dj_mesh owns all device memory it allocates until dj_mesh_destroy.
+ *     A dj_mesh is not thread safe: one host thread at a time.
+ */
+#ifndef DJ_TLED_H
+#define DJ_TLED_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DJ_OK = 0,
+  DJ_ERR_INVALID_ARG = 1,       /* bad pointer, size, parameter or call order */
+  DJ_ERR_BAD_MESH = 2,          /* empty mesh or connectivity out of range */
+  DJ_ERR_INVERTED_ELEMENT = 3,  /* det 0J <= 0 at set-up, or det tJ <= 0 while stepping */
+  DJ_ERR_NOT_PRECOMPUTED = 4,   /* stepping before dj_precompute */
+  DJ_ERR_NONFINITE = 5,         /* NaN/Inf produced by an element force */
+  DJ_ERR_NOT_CONVERGED = 6,     /* dj_relax_to_tol hit max_steps */
+  DJ_ERR_CUDA = 7,              /* a CUDA runtime call failed */
+  DJ_ERR_OOM = 8,               /* device or host allocation failed */
+  DJ_ERR_UNSUPPORTED = 9        /* combination not built (e.g. no device) */
+} dj_status;
+
+enum { DJ_TET4 = 4, DJ_HEX8 = 8 };                    /* element types */
+enum { DJ_NH = 0, DJ_TI = 1, DJ_OT = 2, DJ_MR = 3 };  /* Table 3 models */
+enum { DJ_RAMP_LINEAR = 0, DJ_RAMP_SMOOTH = 1 };      /* prescribed-value ramps */
+
+typedef struct dj_mesh dj_mesh;
+
+/* Run parameters (Sec. 2.2, Eq. 13-14).
+ *   dt                time step [s]; <= 0 selects dt_scale * dt_crit.  A value
+ *                     above dt_crit is rejected (DJ_ERR_INVALID_ARG).
+ *   dt_scale          fraction of the critical step (default 0.9).
+ *   alpha             mass-proportional damping D = alpha M [1/s] (default 0).
+ *   hg_coeff          H8 hourglass coefficient kappa_hg (default 0.1).
+ *   ramp_steps        prescribed values follow target * s(min(n / ramp_steps, 1))
+ *                     at step n; <= 0 applies the targets at once.
+ *   ramp_kind         DJ_RAMP_LINEAR: s = tau (Sec. 5.1);
+ *                     DJ_RAMP_SMOOTH: s = 10 tau^3 - 15 tau^4 + 6 tau^5.
+ *   relax_check_every residual check interval of dj_relax_to_tol (default 100).
+ *   renumber          1 (default): reorder nodes and elements along a Morton
+ *                     curve for locality; 0: keep the caller's order. */
+typedef struct {
+  double dt;
+  double dt_scale;
+  double alpha;
+  double hg_coeff;
+  long long ramp_steps;
+  int ramp_kind;
+  int relax_check_every;
+  int renumber;
+  int reserved;
+} dj_params;
+
+/* Read-only description of a mesh after dj_precompute. */
+typedef struct {
+  long long n_nodes, n_elems, n_bc_dofs, step;
+  int elem_type;            /* DJ_TET4 or DJ_HEX8 */
+  int model_flags;          /* bit m set when some element uses model m */
+  double dt, dt_crit;       /* time step in use and the critical step (Eq. 14) */
+  double total_mass;        /* sum of the lumped nodal masses [kg] */
+  long long device_bytes;   /* device memory held by the mesh */
+  long long elem_table_bytes_per_elem;  /* bytes of per-element tables read per step */
+  long long slot_bytes_per_elem;        /* bytes of element-force slots written per step */
+  long long gather_index_bytes;         /* bytes of the node gather index */
+  long long node_bytes_per_node;        /* bytes of node state read + written per step */
+} dj_info;
+
+/* Fill *p with the defaults listed above. */
+void dj_params_default(dj_params* p);
+
+/* Create a mesh (Sec. 2.1.2: isoparametric T4 / H8 elements).
+ *   elem_type  DJ_TET4 or DJ_HEX8
+ *   X          host, n_nodes * 3 doubles, row-major reference coordinates 0x
+ *   conn       host, n_elems * elem_type ints, 0-based node ids.  T4: any order
+ *              with det 0J > 0 (0J = H_xi X_e, Eq. 3, volume coordinates);
+ *              H8: bottom face counter-clockwise seen from above, then top face.
+ *   out        receives the handle (NULL on failure)
+ * Errors: DJ_ERR_INVALID_ARG (null pointer, bad type, non-finite X),
+ *         DJ_ERR_BAD_MESH (n_nodes <= 0, n_elems <= 0, id out of range). */
+dj_status dj_mesh_create(int elem_type, const double* X, long long n_nodes,
+                         const int* conn, long long n_elems, dj_mesh** out);
+
+/* Per-element material (Table 3), all host arrays of n_elems entries:
+ *   model   DJ_NH / DJ_TI / DJ_OT / DJ_MR
+ *   mu      shear modulus (MR: mu = 2 C10), kappa bulk modulus, rho density
+ *   eta_a, eta_b  fibre stiffnesses (TI uses eta_a, OT both; NULL = 0)
+ *   c01     Mooney-Rivlin C01 (NULL = 0)
+ *   a_dir, b_dir  n_elems * 3 fibre directions 0a, 0b (normalised here;
+ *           NULL = x and y axes)
+ * Every element defaults to NH with mu = kappa = rho = 0 until this is called.
+ * Errors: DJ_ERR_INVALID_ARG (mu, kappa, rho <= 0; eta, c01 < 0; zero fibre
+ *         direction on a fibre element; unknown model). */
+dj_status dj_mesh_set_materials(dj_mesh* mesh, const unsigned char* model, const double* mu,
+                                const double* kappa, const double* rho, const double* eta_a,
+                                const double* eta_b, const double* c01, const double* a_dir,
+                                const double* b_dir);
+
+/* Prescribed displacements (Sec. 5.1, Sec. 6: fixed and ramped DOFs).
+ *   dof     host, n entries, dof = 3 * node + component (0 x, 1 y, 2 z)
+ *   target  host, n final values [m]; 0 = fixed DOF
+ * Replaces any earlier list; n = 0 clears it.  Duplicate DOFs are rejected.
+ * Must be called before dj_precompute. */
+dj_status dj_mesh_set_bcs(dj_mesh* mesh, const long long* dof, const double* target, long long n);
+
+/* Replace the target values of the current prescribed-DOF list (same order as
+ * the last dj_mesh_set_bcs).  Allowed after dj_precompute; takes effect on the
+ * next step.  Host array of n_bc_dofs doubles. */
+dj_status dj_mesh_update_bc_targets(dj_mesh* mesh, const double* target);
+
+/* External nodal forces R (Eq. 13), host n_nodes * 3 doubles, constant in
+ * time; NULL clears them.  Must be called before dj_precompute. */
+dj_status dj_mesh_set_loads(dj_mesh* mesh, const double* R);
+
+/* One-time set-up on the current CUDA device (Algorithm 1, pre-computation):
+ * FP64 evaluation of 0J, det 0J, 0V, I1m, I4m, I6m (Table 2), hourglass
+ * constants, lumped mass and the critical step (Eq. 14), then FP32 tables.
+ * Resets the state to rest (U^0 = U^-1 = 0, step 0).  Synchronous.
+ *   dt_out  optional, receives the time step in use
+ * Errors: DJ_ERR_INVERTED_ELEMENT (det 0J <= 0, message names the element),
+ *         DJ_ERR_INVALID_ARG (dt above the critical step), DJ_ERR_CUDA, DJ_ERR_OOM. */
+dj_status dj_precompute(dj_mesh* mesh, const dj_params* params, double* dt_out);
+
+/* Advance one time step (Algorithm 1 runtime loop + central difference, Eq. 13)
+ * on `stream`.  Asynchronous: element inversion or non-finite forces raised
+ * during the step are reported by the next dj_sync / dj_get_displacements. */
+dj_status dj_step(dj_mesh* mesh, void* stream);
+
+/* Advance n >= 0 steps on `stream` (replays of a captured CUDA graph). Async. */
+dj_status dj_run_n(dj_mesh* mesh, long long n, void* stream);
+
+/* Advance n steps with one launch per kernel and a CUDA event between kernels;
+ * synchronous.  ms_force / ms_update (optional) receive the summed device time
+ * of the element-force kernels and of the gather-update kernels. */
+dj_status dj_run_n_profiled(dj_mesh* mesh, long long n, void* stream, double* ms_force,
+                            double* ms_update);
+
+/* Wait for `stream` and report device-side errors of earlier steps
+ * (DJ_ERR_INVERTED_ELEMENT / DJ_ERR_NONFINITE). */
+dj_status dj_sync(dj_mesh* mesh, void* stream);
+
+/* Dynamic relaxation (Sec. 6): step with the current damping until the
+ * residual r = ||F - R||_free / ||F - R||_prescribed (FP64, every
+ * relax_check_every steps) is <= tol, or max_steps steps were taken.  On
+ * success the state is one step past the checked one.  Synchronous.
+ *   steps_out, residual_out  optional
+ * Errors: DJ_ERR_NOT_CONVERGED, DJ_ERR_INVERTED_ELEMENT, DJ_ERR_NONFINITE. */
+dj_status dj_relax_to_tol(dj_mesh* mesh, double tol, long long max_steps, long long* steps_out,
+                          double* residual_out, void* stream);
+
+/* Warm start: U^0 = U^-1 = U0 (host, n_nodes * 3 doubles); step counter kept.
+ * Synchronous. */
+dj_status dj_set_displacements(dj_mesh* mesh, const double* U0);
+
+/* Current displacements U^n, host n_nodes * 3 doubles.  Synchronizes the
+ * device and reports pending device-side errors. */
+dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
+
+/* Current displacements into device memory, n_nodes * 3 floats in caller
+ * order, enqueued on `stream`. */
+dj_status dj_get_displacements_device(dj_mesh* mesh, float* d_U_out, void* stream);
+
+/* Assembled internal forces F(U) = sum_e F^(e) (Eq. 13) for host displacements
+ * U (n_nodes * 3 doubles), written to host F_out (n_nodes * 3).  The stepping
+ * state is left unchanged.  Synchronous. */
+dj_status dj_internal_forces(dj_mesh* mesh, const double* U, double* F_out);
+
+/* Checkpoint: opaque, bit-exact copy of the stepping state (U^n, U^n - U^n-1,
+ * step counter).  dj_set_state on the same mesh resumes bit-identically. */
+dj_status dj_state_size(const dj_mesh* mesh, size_t* bytes);
+dj_status dj_get_state(dj_mesh* mesh, void* buf, size_t bytes);
+dj_status dj_set_state(dj_mesh* mesh, const void* buf, size_t bytes);
+
+dj_status dj_get_info(const dj_mesh* mesh, dj_info* info);
+const char* dj_status_string(dj_status s);
+const char* dj_last_error(const dj_mesh* mesh);
+void dj_mesh_destroy(dj_mesh* mesh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DJ_TLED_H */

@@ -1,0 +1,347 @@
+"""ctypes binding of libdjtled.so (C ABI in include/dj_tled.h).
+
+Argument marshalling only: every step of the DJ-TLED path runs in the CUDA
+library.  Functions carry the C names; ``Mesh`` wraps a handle for convenience.
+If the library has not been built the import of this module still works, but
+any call raises ``RuntimeError`` (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libdjtled.so")
+
+DJ_OK = 0
+STATUS = {0: "DJ_OK", 1: "DJ_ERR_INVALID_ARG", 2: "DJ_ERR_BAD_MESH", 3: "DJ_ERR_INVERTED_ELEMENT",
+          4: "DJ_ERR_NOT_PRECOMPUTED", 5: "DJ_ERR_NONFINITE", 6: "DJ_ERR_NOT_CONVERGED",
+          7: "DJ_ERR_CUDA", 8: "DJ_ERR_OOM", 9: "DJ_ERR_UNSUPPORTED"}
+DJ_TET4, DJ_HEX8 = 4, 8
+DJ_NH, DJ_TI, DJ_OT, DJ_MR = 0, 1, 2, 3
+
+# every exported entry point of include/dj_tled.h
+EXPORTS = [
+    "dj_params_default", "dj_mesh_create", "dj_mesh_set_materials", "dj_mesh_set_bcs",
+    "dj_mesh_update_bc_targets", "dj_mesh_set_loads", "dj_precompute", "dj_step", "dj_run_n",
+    "dj_run_n_profiled", "dj_sync", "dj_relax_to_tol", "dj_set_displacements",
+    "dj_get_displacements", "dj_get_displacements_device", "dj_internal_forces",
+    "dj_state_size", "dj_get_state", "dj_set_state", "dj_get_info", "dj_status_string",
+    "dj_last_error", "dj_mesh_destroy",
+]
+
+
+class dj_params(C.Structure):
+    _fields_ = [("dt", C.c_double), ("dt_scale", C.c_double), ("alpha", C.c_double),
+                ("hg_coeff", C.c_double), ("ramp_steps", C.c_longlong), ("ramp_kind", C.c_int),
+                ("relax_check_every", C.c_int), ("renumber", C.c_int), ("reserved", C.c_int)]
+
+
+class dj_info(C.Structure):
+    _fields_ = [("n_nodes", C.c_longlong), ("n_elems", C.c_longlong), ("n_bc_dofs", C.c_longlong),
+                ("step", C.c_longlong), ("elem_type", C.c_int), ("model_flags", C.c_int),
+                ("dt", C.c_double), ("dt_crit", C.c_double), ("total_mass", C.c_double),
+                ("device_bytes", C.c_longlong), ("elem_table_bytes_per_elem", C.c_longlong),
+                ("slot_bytes_per_elem", C.c_longlong), ("gather_index_bytes", C.c_longlong),
+                ("node_bytes_per_node", C.c_longlong)]
+
+
+class DJError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.name}" + (f" ({detail})" if detail else ""))
+
+
+_lib = None
+_P = C.c_void_p
+_D = C.POINTER(C.c_double)
+_LL = C.POINTER(C.c_longlong)
+
+
+def lib():
+    """Load libdjtled.so; raises RuntimeError if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} not built: run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "dj_params_default": (None, [C.POINTER(dj_params)]),
+        "dj_mesh_create": (C.c_int, [C.c_int, _D, C.c_longlong, C.POINTER(C.c_int), C.c_longlong,
+                                     C.POINTER(_P)]),
+        "dj_mesh_set_materials": (C.c_int, [_P, C.POINTER(C.c_ubyte), _D, _D, _D, _D, _D, _D, _D, _D]),
+        "dj_mesh_set_bcs": (C.c_int, [_P, _LL, _D, C.c_longlong]),
+        "dj_mesh_update_bc_targets": (C.c_int, [_P, _D]),
+        "dj_mesh_set_loads": (C.c_int, [_P, _D]),
+        "dj_precompute": (C.c_int, [_P, C.POINTER(dj_params), _D]),
+        "dj_step": (C.c_int, [_P, _P]),
+        "dj_run_n": (C.c_int, [_P, C.c_longlong, _P]),
+        "dj_run_n_profiled": (C.c_int, [_P, C.c_longlong, _P, _D, _D]),
+        "dj_sync": (C.c_int, [_P, _P]),
+        "dj_relax_to_tol": (C.c_int, [_P, C.c_double, C.c_longlong, _LL, _D, _P]),
+        "dj_set_displacements": (C.c_int, [_P, _D]),
+        "dj_get_displacements": (C.c_int, [_P, _D]),
+        "dj_get_displacements_device": (C.c_int, [_P, _P, _P]),
+        "dj_internal_forces": (C.c_int, [_P, _D, _D]),
+        "dj_state_size": (C.c_int, [_P, C.POINTER(C.c_size_t)]),
+        "dj_get_state": (C.c_int, [_P, _P, C.c_size_t]),
+        "dj_set_state": (C.c_int, [_P, _P, C.c_size_t]),
+        "dj_get_info": (C.c_int, [_P, C.POINTER(dj_info)]),
+        "dj_status_string": (C.c_char_p, [C.c_int]),
+        "dj_last_error": (C.c_char_p, [_P]),
+        "dj_mesh_destroy": (None, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _dptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _stream(s) -> Optional[int]:
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return int(s.cuda_stream)
+    return int(s)
+
+
+def _check(st: int, where: str, handle=None):
+    if st != DJ_OK:
+        detail = ""
+        if handle:
+            msg = lib().dj_last_error(handle)
+            detail = msg.decode() if msg else ""
+        raise DJError(st, where, detail)
+
+
+def default_params(**kw) -> dj_params:
+    p = dj_params()
+    lib().dj_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ----------------------------------------------------------------- C names --
+def dj_mesh_create(elem_type: int, X, conn):
+    X = _f64(X)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    h = _P()
+    n_nodes = X.shape[0] if X.ndim == 2 else X.size // 3
+    n_elems = conn.shape[0] if conn.ndim == 2 else conn.size // max(int(elem_type), 1)
+    st = lib().dj_mesh_create(int(elem_type), _dptr(X), n_nodes,
+                              conn.ctypes.data_as(C.POINTER(C.c_int)), n_elems, C.byref(h))
+    _check(st, "dj_mesh_create")
+    return h
+
+
+def dj_mesh_set_materials(h, model, mu, kappa, rho, eta_a=None, eta_b=None, c01=None, a_dir=None,
+                          b_dir=None):
+    model = np.ascontiguousarray(model, dtype=np.uint8)
+    arrs = [_f64(x) for x in (mu, kappa, rho, eta_a, eta_b, c01, a_dir, b_dir)]
+    st = lib().dj_mesh_set_materials(h, model.ctypes.data_as(C.POINTER(C.c_ubyte)),
+                                     *[_dptr(a) for a in arrs])
+    _check(st, "dj_mesh_set_materials", h)
+
+
+def dj_mesh_set_bcs(h, dof, target):
+    dof = np.ascontiguousarray(dof, dtype=np.int64)
+    target = _f64(target)
+    st = lib().dj_mesh_set_bcs(h, dof.ctypes.data_as(_LL), _dptr(target), dof.size)
+    _check(st, "dj_mesh_set_bcs", h)
+
+
+def dj_mesh_update_bc_targets(h, target):
+    target = _f64(target)
+    _check(lib().dj_mesh_update_bc_targets(h, _dptr(target)), "dj_mesh_update_bc_targets", h)
+
+
+def dj_mesh_set_loads(h, R):
+    R = _f64(R)
+    _check(lib().dj_mesh_set_loads(h, _dptr(R)), "dj_mesh_set_loads", h)
+
+
+def dj_precompute(h, params: Optional[dj_params] = None) -> float:
+    dt = C.c_double(0.0)
+    st = lib().dj_precompute(h, C.byref(params) if params is not None else None, C.byref(dt))
+    _check(st, "dj_precompute", h)
+    return dt.value
+
+
+def dj_step(h, stream=None):
+    _check(lib().dj_step(h, _stream(stream)), "dj_step", h)
+
+
+def dj_run_n(h, n: int, stream=None):
+    _check(lib().dj_run_n(h, int(n), _stream(stream)), "dj_run_n", h)
+
+
+def dj_run_n_profiled(h, n: int, stream=None):
+    a, b = C.c_double(0), C.c_double(0)
+    _check(lib().dj_run_n_profiled(h, int(n), _stream(stream), C.byref(a), C.byref(b)),
+           "dj_run_n_profiled", h)
+    return a.value, b.value
+
+
+def dj_sync(h, stream=None):
+    _check(lib().dj_sync(h, _stream(stream)), "dj_sync", h)
+
+
+def dj_relax_to_tol(h, tol: float, max_steps: int, stream=None, raise_on_fail=True):
+    steps, r = C.c_longlong(0), C.c_double(0)
+    st = lib().dj_relax_to_tol(h, float(tol), int(max_steps), C.byref(steps), C.byref(r),
+                               _stream(stream))
+    if raise_on_fail:
+        _check(st, "dj_relax_to_tol", h)
+    return st, steps.value, r.value
+
+
+def dj_set_displacements(h, U0):
+    U0 = _f64(U0)
+    _check(lib().dj_set_displacements(h, _dptr(U0)), "dj_set_displacements", h)
+
+
+def dj_get_displacements(h, n_nodes: int) -> np.ndarray:
+    out = np.empty((n_nodes, 3), dtype=np.float64)
+    _check(lib().dj_get_displacements(h, _dptr(out)), "dj_get_displacements", h)
+    return out
+
+
+def dj_get_displacements_device(h, d_ptr: int, stream=None):
+    _check(lib().dj_get_displacements_device(h, d_ptr, _stream(stream)),
+           "dj_get_displacements_device", h)
+
+
+def dj_internal_forces(h, U) -> np.ndarray:
+    U = _f64(U)
+    out = np.empty(U.shape, dtype=np.float64)
+    _check(lib().dj_internal_forces(h, _dptr(U), _dptr(out)), "dj_internal_forces", h)
+    return out
+
+
+def dj_state_size(h) -> int:
+    n = C.c_size_t(0)
+    _check(lib().dj_state_size(h, C.byref(n)), "dj_state_size", h)
+    return n.value
+
+
+def dj_get_state(h) -> bytes:
+    n = dj_state_size(h)
+    buf = C.create_string_buffer(n)
+    _check(lib().dj_get_state(h, C.cast(buf, _P), n), "dj_get_state", h)
+    return buf.raw
+
+
+def dj_set_state(h, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(lib().dj_set_state(h, C.cast(buf, _P), len(blob)), "dj_set_state", h)
+
+
+def dj_get_info(h) -> dj_info:
+    info = dj_info()
+    _check(lib().dj_get_info(h, C.byref(info)), "dj_get_info", h)
+    return info
+
+
+def dj_status_string(s: int) -> str:
+    return lib().dj_status_string(int(s)).decode()
+
+
+def dj_last_error(h) -> str:
+    r = lib().dj_last_error(h)
+    return r.decode() if r else ""
+
+
+def dj_mesh_destroy(h):
+    lib().dj_mesh_destroy(h)
+
+
+# ------------------------------------------------------------- convenience --
+class Mesh:
+    """Owning wrapper of a dj_mesh handle built from a workloads.Problem."""
+
+    def __init__(self, problem, params: Optional[dj_params] = None, precompute: bool = True,
+                 **param_kw):
+        p = problem
+        self.problem = p
+        self.n_nodes = p.n_nodes
+        self.h = dj_mesh_create(p.elem_type, p.X, p.conn)
+        try:
+            dj_mesh_set_materials(self.h, p.model, p.mu, p.kappa, p.rho, p.eta_a, p.eta_b, p.c01,
+                                  p.a_dir, p.b_dir)
+            dj_mesh_set_bcs(self.h, p.bc_dof, p.bc_target)
+            if params is None:
+                kw = dict(dt_scale=p.dt_scale, alpha=p.alpha, hg_coeff=p.hg_coeff,
+                          ramp_steps=p.ramp_steps, ramp_kind=p.ramp_kind)
+                kw.update(param_kw)
+                params = default_params(**kw)
+            self.params = params
+            self.dt = dj_precompute(self.h, params) if precompute else None
+        except Exception:
+            dj_mesh_destroy(self.h)
+            self.h = None
+            raise
+
+    def step(self, stream=None):
+        dj_step(self.h, stream)
+
+    def run(self, n, stream=None):
+        dj_run_n(self.h, n, stream)
+
+    def sync(self, stream=None):
+        dj_sync(self.h, stream)
+
+    def displacements(self) -> np.ndarray:
+        return dj_get_displacements(self.h, self.n_nodes)
+
+    def set_displacements(self, U0):
+        dj_set_displacements(self.h, U0)
+
+    def internal_forces(self, U) -> np.ndarray:
+        return dj_internal_forces(self.h, U)
+
+    def relax(self, tol, max_steps, stream=None, raise_on_fail=True):
+        return dj_relax_to_tol(self.h, tol, max_steps, stream, raise_on_fail)
+
+    def info(self) -> dj_info:
+        return dj_get_info(self.h)
+
+    def close(self):
+        if self.h:
+            dj_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,1033 @@
+// Host implementation of the C ABI declared in include/dj_tled.h.
+//
+// Data layout in device memory (E_pad = E rounded up to 128, internal order):
+//   conn      int4[E_pad] (T4) or int4[2 E_pad] (H8)                16 / 32 B per element
+//   consts    float[n_consts * E_pad], structure of arrays (dj_internal.h)
+//   slots     float4[n_e * E_pad], element force of local node a at a * E_pad + e
+//   sell      int[...] node -> slot ids, sliced ELL with chunks of 32 nodes
+//   U, V      float4[N]: U^n (w = update coefficient a_i) and U^n - U^{n-1}
+//             (w = index into the prescribed-node table, -1 if free)
+//   bct       float4[n_bc_nodes]: target displacement, w = component mask
+//   state     DevState (step counter, ramp value, error flags, residual sums)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "dj_internal.h"
+
+using namespace dj;
+
+struct dj_mesh {
+  int elem_type = 0, ne = 0;
+  long long N = 0, E = 0;
+  std::vector<double> X;
+  std::vector<int> conn;
+  bool materials_set = false;
+  std::vector<unsigned char> model;
+  std::vector<double> mu, kappa, rho, eta_a, eta_b, c01, adir, bdir;
+  std::vector<long long> bc_dof;
+  std::vector<double> bc_target;
+  std::vector<double> R;
+  dj_params params{};
+  // renumbering
+  std::vector<int> node_new_of_old, node_old_of_new, elem_old_of_new;
+  // device data
+  bool precomputed = false;
+  int device = -1;
+  int E_pad = 0, n_consts = 0, off_fa = -1, off_fb = -1, off_mr = -1, off_hg = -1;
+  int variant = VAR_NH, model_flags = 0;
+  int4* d_conn = nullptr;
+  float* d_consts = nullptr;
+  float4* d_slots = nullptr;
+  int* d_sell = nullptr;
+  int* d_chunk_ptr = nullptr;
+  float4* d_U = nullptr;
+  float4* d_V = nullptr;
+  float4* d_bct = nullptr;
+  float4* d_R = nullptr;
+  float4* d_fout = nullptr;
+  int* d_perm = nullptr;  // node_new_of_old on device
+  DevState* d_state = nullptr;
+  double2* d_partials = nullptr;
+  DevState* h_state = nullptr;  // pinned
+  int n_node_blocks = 0;
+  int n_bc_nodes = 0;
+  std::vector<int> bc_node_of_entry;  // per bc entry: prescribed-node row
+  std::vector<int> bc_comp_of_entry;
+  std::vector<float4> h_bct;
+  std::vector<float> h_ai;
+  std::vector<int> h_bcidx;
+  double dt = 0, dt_crit = 0, total_mass = 0;
+  float bm1 = 1.f;
+  int threads_force = 256;
+  long long device_bytes = 0;
+  long long sell_entries = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t run_exec = nullptr;
+  int run_chunk = 0;
+  cudaGraphExec_t relax_exec = nullptr;
+  int relax_k = 0;
+  std::string last_error;
+};
+
+namespace {
+
+inline float bits_to_float(int v) {
+  float f;
+  std::memcpy(&f, &v, 4);
+  return f;
+}
+inline int float_to_bits(float f) {
+  int v;
+  std::memcpy(&v, &f, 4);
+  return v;
+}
+
+dj_status fail(dj_mesh* m, dj_status s, const char* fmt, ...) {
+  if (m) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    m->last_error = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t _e = (call);                                                                  \
+    if (_e != cudaSuccess)                                                                    \
+      return fail(m, _e == cudaErrorMemoryAllocation ? DJ_ERR_OOM : DJ_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(_e), __FILE__, __LINE__);                          \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(dj_mesh* m, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T) + 16);
+  if (e == cudaSuccess) m->device_bytes += (long long)(count * sizeof(T));
+  return e;
+}
+
+void release_device(dj_mesh* m) {
+  if (m->run_exec) cudaGraphExecDestroy(m->run_exec);
+  if (m->relax_exec) cudaGraphExecDestroy(m->relax_exec);
+  m->run_exec = m->relax_exec = nullptr;
+  m->run_chunk = m->relax_k = 0;
+  void* ptrs[] = {m->d_conn, m->d_consts, m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U, m->d_V,
+                  m->d_bct,  m->d_R,      m->d_fout,  m->d_perm, m->d_state,     m->d_partials};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (m->h_state) cudaFreeHost(m->h_state);
+  if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+  m->d_conn = nullptr;
+  m->d_consts = nullptr;
+  m->d_slots = nullptr;
+  m->d_sell = nullptr;
+  m->d_chunk_ptr = nullptr;
+  m->d_U = m->d_V = m->d_bct = m->d_R = m->d_fout = nullptr;
+  m->d_perm = nullptr;
+  m->d_state = nullptr;
+  m->d_partials = nullptr;
+  m->h_state = nullptr;
+  m->cap_stream = nullptr;
+  m->device_bytes = 0;
+  m->precomputed = false;
+}
+
+// Morton key of a point in the unit cube, 21 bits per axis
+uint64_t spread21(uint64_t x) {
+  x &= 0x1fffff;
+  x = (x | x << 32) & 0x1f00000000ffffULL;
+  x = (x | x << 16) & 0x1f0000ff0000ffULL;
+  x = (x | x << 8) & 0x100f00f00f00f00fULL;
+  x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+  x = (x | x << 2) & 0x1249249249249249ULL;
+  return x;
+}
+
+std::vector<int> morton_order(const std::vector<double>& P, long long n) {
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (long long i = 0; i < n; ++i)
+    for (int j = 0; j < 3; ++j) {
+      lo[j] = std::min(lo[j], P[3 * i + j]);
+      hi[j] = std::max(hi[j], P[3 * i + j]);
+    }
+  double ext = 0;
+  for (int j = 0; j < 3; ++j) ext = std::max(ext, hi[j] - lo[j]);
+  if (!(ext > 0)) ext = 1;
+  std::vector<uint64_t> key(n);
+  for (long long i = 0; i < n; ++i) {
+    uint64_t k = 0;
+    for (int j = 0; j < 3; ++j) {
+      double t = (P[3 * i + j] - lo[j]) / ext;
+      uint64_t q = (uint64_t)std::min(2097151.0, std::max(0.0, t * 2097151.0));
+      k |= spread21(q) << j;
+    }
+    key[i] = k;
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key[a] < key[b]; });
+  return order;
+}
+
+int count_bits(int v) {
+  int c = 0;
+  while (v) {
+    c += v & 1;
+    v >>= 1;
+  }
+  return c;
+}
+
+dj_status read_state(dj_mesh* m, cudaStream_t s) {
+  CK(cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return DJ_OK;
+}
+
+dj_status check_flags(dj_mesh* m) {
+  const DevState& st = *m->h_state;
+  if (st.err_flags) {
+    const int be = st.bad_elem;
+    const int caller = (be >= 0 && be < (int)m->E) ? m->elem_old_of_new[be] : -1;
+    if (st.err_flags & ERR_INVERTED)
+      return fail(m, DJ_ERR_INVERTED_ELEMENT, "element %d inverted (det tJ <= 0) by step %lld",
+                  caller, st.step);
+    return fail(m, DJ_ERR_NONFINITE, "non-finite force in element %d by step %lld", caller,
+                st.step);
+  }
+  return DJ_OK;
+}
+
+ForceArgs force_args(dj_mesh* m, int advance) {
+  ForceArgs a;
+  a.conn = m->d_conn;
+  a.consts = m->d_consts;
+  a.U = m->d_U;
+  a.slots = m->d_slots;
+  a.E = (int)m->E;
+  a.E_pad = m->E_pad;
+  a.off_fa = m->off_fa;
+  a.off_fb = m->off_fb;
+  a.off_mr = m->off_mr;
+  a.off_hg = m->off_hg;
+  a.st = m->d_state;
+  a.advance = advance;
+  a.ramp_steps = m->params.ramp_steps;
+  a.ramp_kind = m->params.ramp_kind;
+  return a;
+}
+
+NodeArgs node_args(dj_mesh* m) {
+  NodeArgs a;
+  a.sell = m->d_sell;
+  a.chunk_ptr = m->d_chunk_ptr;
+  a.slots = m->d_slots;
+  a.U = m->d_U;
+  a.V = m->d_V;
+  a.bct = m->d_bct;
+  a.R = m->d_R;
+  a.fout = m->d_fout;
+  a.partials = m->d_partials;
+  a.st = m->d_state;
+  a.N = (int)m->N;
+  a.bm1 = m->bm1;
+  return a;
+}
+
+cudaError_t launch_step(dj_mesh* m, cudaStream_t s, int mode) {
+  cudaError_t e = launch_force(m->elem_type, m->variant, force_args(m, 1), m->threads_force, s);
+  if (e != cudaSuccess) return e;
+  e = launch_node(mode, node_args(m), s);
+  if (e != cudaSuccess) return e;
+  if (mode == NODE_UPDATE_RESID) e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, s);
+  return e;
+}
+
+dj_status need_ready(dj_mesh* m) {
+  if (!m) return DJ_ERR_INVALID_ARG;
+  if (!m->precomputed) return fail(m, DJ_ERR_NOT_PRECOMPUTED, "call dj_precompute first");
+  CK(cudaSetDevice(m->device));
+  return DJ_OK;
+}
+
+// Capture `body` on the mesh's capture stream into an executable graph.
+template <class F>
+dj_status capture(dj_mesh* m, cudaGraphExec_t* out, F body) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t be = body(m->cap_stream);
+  cudaError_t ee = cudaStreamEndCapture(m->cap_stream, &g);
+  if (be != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(m, DJ_ERR_CUDA, "graph capture: %s", cudaGetErrorString(be));
+  }
+  CK(ee);
+  cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  CK(ie);
+  return DJ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dj_params_default(dj_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->dt = 0.0;
+  p->dt_scale = 0.9;
+  p->alpha = 0.0;
+  p->hg_coeff = 0.1;
+  p->ramp_steps = 0;
+  p->ramp_kind = DJ_RAMP_SMOOTH;
+  p->relax_check_every = 100;
+  p->renumber = 1;
+}
+
+const char* dj_status_string(dj_status s) {
+  switch (s) {
+    case DJ_OK: return "ok";
+    case DJ_ERR_INVALID_ARG: return "invalid argument";
+    case DJ_ERR_BAD_MESH: return "bad mesh";
+    case DJ_ERR_INVERTED_ELEMENT: return "inverted element";
+    case DJ_ERR_NOT_PRECOMPUTED: return "not precomputed";
+    case DJ_ERR_NONFINITE: return "non-finite value";
+    case DJ_ERR_NOT_CONVERGED: return "not converged";
+    case DJ_ERR_CUDA: return "CUDA error";
+    case DJ_ERR_OOM: return "out of memory";
+    case DJ_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* dj_last_error(const dj_mesh* m) { return m ? m->last_error.c_str() : "null mesh"; }
+
+dj_status dj_mesh_create(int elem_type, const double* X, long long n_nodes, const int* conn,
+                         long long n_elems, dj_mesh** out) {
+  if (!out) return DJ_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (elem_type != DJ_TET4 && elem_type != DJ_HEX8) return DJ_ERR_INVALID_ARG;
+  if (n_nodes <= 0 || n_elems <= 0) return DJ_ERR_BAD_MESH;
+  if (!X || !conn) return DJ_ERR_INVALID_ARG;
+  if (n_nodes >= INT_MAX / 2 || (long long)elem_type * (n_elems + 128) >= INT_MAX)
+    return DJ_ERR_UNSUPPORTED;
+  for (long long i = 0; i < 3 * n_nodes; ++i)
+    if (!std::isfinite(X[i])) return DJ_ERR_INVALID_ARG;
+  for (long long i = 0; i < elem_type * n_elems; ++i)
+    if (conn[i] < 0 || conn[i] >= n_nodes) return DJ_ERR_BAD_MESH;
+  dj_mesh* m = new (std::nothrow) dj_mesh();
+  if (!m) return DJ_ERR_OOM;
+  m->elem_type = elem_type;
+  m->ne = elem_type;
+  m->N = n_nodes;
+  m->E = n_elems;
+  m->X.assign(X, X + 3 * n_nodes);
+  m->conn.assign(conn, conn + elem_type * n_elems);
+  dj_params_default(&m->params);
+  *out = m;
+  return DJ_OK;
+}
+
+dj_status dj_mesh_set_materials(dj_mesh* m, const unsigned char* model, const double* mu,
+                                const double* kappa, const double* rho, const double* eta_a,
+                                const double* eta_b, const double* c01, const double* a_dir,
+                                const double* b_dir) {
+  if (!m) return DJ_ERR_INVALID_ARG;
+  if (!model || !mu || !kappa || !rho)
+    return fail(m, DJ_ERR_INVALID_ARG, "model, mu, kappa and rho are required");
+  const long long E = m->E;
+  for (long long e = 0; e < E; ++e) {
+    if (model[e] > DJ_MR) return fail(m, DJ_ERR_INVALID_ARG, "element %lld: unknown model", e);
+    if (!(mu[e] > 0) || !(kappa[e] > 0) || !(rho[e] > 0) || !std::isfinite(mu[e]) ||
+        !std::isfinite(kappa[e]) || !std::isfinite(rho[e]))
+      return fail(m, DJ_ERR_INVALID_ARG, "element %lld: mu, kappa, rho must be finite and > 0", e);
+    const double ea = eta_a ? eta_a[e] : 0.0, eb = eta_b ? eta_b[e] : 0.0, c = c01 ? c01[e] : 0.0;
+    if (!(ea >= 0) || !(eb >= 0) || !(c >= 0) || !std::isfinite(ea + eb + c))
+      return fail(m, DJ_ERR_INVALID_ARG, "element %lld: eta and c01 must be finite and >= 0", e);
+    if ((model[e] == DJ_TI || model[e] == DJ_OT) && ea > 0) {
+      const double* d = a_dir ? a_dir + 3 * e : nullptr;
+      if (d && !(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > 0))
+        return fail(m, DJ_ERR_INVALID_ARG, "element %lld: zero fibre direction a", e);
+    }
+    if (model[e] == DJ_OT && eb > 0) {
+      const double* d = b_dir ? b_dir + 3 * e : nullptr;
+      if (d && !(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > 0))
+        return fail(m, DJ_ERR_INVALID_ARG, "element %lld: zero fibre direction b", e);
+    }
+  }
+  m->model.assign(model, model + E);
+  m->mu.assign(mu, mu + E);
+  m->kappa.assign(kappa, kappa + E);
+  m->rho.assign(rho, rho + E);
+  m->eta_a.assign(E, 0.0);
+  m->eta_b.assign(E, 0.0);
+  m->c01.assign(E, 0.0);
+  if (eta_a) m->eta_a.assign(eta_a, eta_a + E);
+  if (eta_b) m->eta_b.assign(eta_b, eta_b + E);
+  if (c01) m->c01.assign(c01, c01 + E);
+  m->adir.resize(3 * E);
+  m->bdir.resize(3 * E);
+  for (long long e = 0; e < E; ++e) {
+    for (int j = 0; j < 3; ++j) {
+      m->adir[3 * e + j] = a_dir ? a_dir[3 * e + j] : (j == 0 ? 1.0 : 0.0);
+      m->bdir[3 * e + j] = b_dir ? b_dir[3 * e + j] : (j == 1 ? 1.0 : 0.0);
+    }
+  }
+  m->materials_set = true;
+  m->precomputed = false;
+  return DJ_OK;
+}
+
+dj_status dj_mesh_set_bcs(dj_mesh* m, const long long* dof, const double* target, long long n) {
+  if (!m) return DJ_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!dof || !target))) return fail(m, DJ_ERR_INVALID_ARG, "bad bc arrays");
+  std::vector<char> seen(3 * m->N, 0);
+  for (long long k = 0; k < n; ++k) {
+    if (dof[k] < 0 || dof[k] >= 3 * m->N)
+      return fail(m, DJ_ERR_INVALID_ARG, "bc entry %lld: dof %lld out of range", k, dof[k]);
+    if (seen[dof[k]]) return fail(m, DJ_ERR_INVALID_ARG, "bc entry %lld: duplicate dof %lld", k, dof[k]);
+    if (!std::isfinite(target[k])) return fail(m, DJ_ERR_INVALID_ARG, "bc entry %lld: non-finite", k);
+    seen[dof[k]] = 1;
+  }
+  m->bc_dof.assign(dof, dof + n);
+  m->bc_target.assign(target, target + n);
+  m->precomputed = false;
+  return DJ_OK;
+}
+
+dj_status dj_mesh_set_loads(dj_mesh* m, const double* R) {
+  if (!m) return DJ_ERR_INVALID_ARG;
+  if (!R) {
+    m->R.clear();
+  } else {
+    for (long long i = 0; i < 3 * m->N; ++i)
+      if (!std::isfinite(R[i])) return fail(m, DJ_ERR_INVALID_ARG, "non-finite load");
+    m->R.assign(R, R + 3 * m->N);
+  }
+  m->precomputed = false;
+  return DJ_OK;
+}
+
+dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
+  if (!m) return DJ_ERR_INVALID_ARG;
+  if (!m->materials_set) return fail(m, DJ_ERR_INVALID_ARG, "call dj_mesh_set_materials first");
+  dj_params prm;
+  if (p)
+    prm = *p;
+  else
+    dj_params_default(&prm);
+  if (!(prm.dt_scale > 0) || !(prm.alpha >= 0) || !(prm.hg_coeff >= 0) || prm.relax_check_every <= 0 ||
+      (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt))
+    return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  release_device(m);
+  m->device = dev;
+  m->params = prm;
+  const long long N = m->N, E = m->E;
+  const int ne = m->ne;
+  // ---- renumbering (caller -> internal) --------------------------------
+  m->node_old_of_new.resize(N);
+  m->elem_old_of_new.resize(E);
+  if (prm.renumber) {
+    m->node_old_of_new = morton_order(m->X, N);
+  } else {
+    std::iota(m->node_old_of_new.begin(), m->node_old_of_new.end(), 0);
+  }
+  m->node_new_of_old.assign(N, 0);
+  for (long long i = 0; i < N; ++i) m->node_new_of_old[m->node_old_of_new[i]] = (int)i;
+  if (prm.renumber) {
+    std::vector<double> cen(3 * E, 0.0);
+    for (long long e = 0; e < E; ++e)
+      for (int b = 0; b < ne; ++b)
+        for (int j = 0; j < 3; ++j) cen[3 * e + j] += m->X[3 * (size_t)m->conn[e * ne + b] + j] / ne;
+    m->elem_old_of_new = morton_order(cen, E);
+  } else {
+    std::iota(m->elem_old_of_new.begin(), m->elem_old_of_new.end(), 0);
+  }
+  std::vector<double> Xn(3 * N);
+  for (long long i = 0; i < N; ++i)
+    for (int j = 0; j < 3; ++j) Xn[3 * i + j] = m->X[3 * (size_t)m->node_old_of_new[i] + j];
+  std::vector<int> cn((size_t)E * ne);
+  for (long long e = 0; e < E; ++e)
+    for (int b = 0; b < ne; ++b)
+      cn[e * ne + b] = m->node_new_of_old[m->conn[(size_t)m->elem_old_of_new[e] * ne + b]];
+  // ---- table layout ---------------------------------------------------------
+  m->E_pad = (int)((E + 127) / 128 * 128);
+  const int E_pad = m->E_pad;
+  m->model_flags = 0;
+  for (long long e = 0; e < E; ++e) m->model_flags |= 1 << m->model[e];
+  bool fa = false, fb = false, mr = (m->model_flags >> DJ_MR) & 1;
+  for (long long e = 0; e < E; ++e) {
+    if ((m->model[e] == DJ_TI || m->model[e] == DJ_OT) && m->eta_a[e] > 0) fa = true;
+    if (m->model[e] == DJ_OT && m->eta_b[e] > 0) fb = true;
+  }
+  // kernel variant, then the table blocks it reads (unused fibre blocks hold zeros)
+  if (fb) fa = true;
+  if (mr && fa) {
+    m->variant = VAR_ALL;
+    fb = true;
+  } else if (mr) {
+    m->variant = VAR_MR;
+  } else if (fb) {
+    m->variant = VAR_OT;
+  } else if (fa) {
+    m->variant = VAR_TI;
+  } else {
+    m->variant = VAR_NH;
+  }
+  int nc = K_COMMON;
+  m->off_fa = m->off_fb = m->off_mr = m->off_hg = -1;
+  if (fa) { m->off_fa = nc; nc += 7; }
+  if (fb) { m->off_fb = nc; nc += 7; }
+  if (mr) { m->off_mr = nc; nc += 1; }
+  if (ne == 8) { m->off_hg = nc; nc += 13; }
+  m->n_consts = nc;
+  m->threads_force = ne == 4 ? 256 : 128;
+  // ---- gather index: node -> slots (ascending element, local node) ---------
+  std::vector<int> cnt(N + 1, 0);
+  for (size_t k = 0; k < cn.size(); ++k) cnt[cn[k] + 1]++;
+  for (long long i = 0; i < N; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> csr(cn.size()), fillp(cnt.begin(), cnt.end() - 1);
+  for (long long e = 0; e < E; ++e)
+    for (int b = 0; b < ne; ++b) csr[fillp[cn[e * ne + b]]++] = b * E_pad + (int)e;
+  const long long n_chunks = (N + SELL_C - 1) / SELL_C;
+  std::vector<int> chunk_ptr(n_chunks + 1, 0);
+  for (long long c = 0; c < n_chunks; ++c) {
+    int w = 0;
+    for (long long i = c * SELL_C; i < std::min(N, (c + 1) * SELL_C); ++i) w = std::max(w, cnt[i + 1] - cnt[i]);
+    chunk_ptr[c + 1] = chunk_ptr[c] + w * SELL_C;
+  }
+  std::vector<int> sell(chunk_ptr[n_chunks], -1);
+  for (long long i = 0; i < N; ++i) {
+    const long long c = i / SELL_C, lane = i % SELL_C;
+    for (int j = 0; j < cnt[i + 1] - cnt[i]; ++j) sell[chunk_ptr[c] + j * SELL_C + lane] = csr[cnt[i] + j];
+  }
+  m->sell_entries = (long long)sell.size();
+  // ---- prescribed nodes ----------------------------------------------------
+  std::vector<int> bcidx(N, -1);
+  m->h_bct.clear();
+  m->bc_node_of_entry.assign(m->bc_dof.size(), 0);
+  m->bc_comp_of_entry.assign(m->bc_dof.size(), 0);
+  for (size_t k = 0; k < m->bc_dof.size(); ++k) {
+    const int node = m->node_new_of_old[m->bc_dof[k] / 3];
+    const int comp = (int)(m->bc_dof[k] % 3);
+    if (bcidx[node] < 0) {
+      bcidx[node] = (int)m->h_bct.size();
+      m->h_bct.push_back(make_float4(0.f, 0.f, 0.f, bits_to_float(0)));
+    }
+    float4& t = m->h_bct[bcidx[node]];
+    int mask = float_to_bits(t.w) | (1 << comp);
+    if (comp == 0) t.x = (float)m->bc_target[k];
+    if (comp == 1) t.y = (float)m->bc_target[k];
+    if (comp == 2) t.z = (float)m->bc_target[k];
+    t.w = bits_to_float(mask);
+    m->bc_node_of_entry[k] = bcidx[node];
+    m->bc_comp_of_entry[k] = comp;
+  }
+  m->n_bc_nodes = (int)m->h_bct.size();
+  m->h_bcidx = bcidx;
+  // ---- device buffers --------------------------------------------------------
+  const size_t conn4_count = (size_t)E_pad * (ne / 4);
+  CK(dalloc(m, &m->d_conn, conn4_count));
+  CK(cudaMemset(m->d_conn, 0, conn4_count * sizeof(int4)));
+  CK(dalloc(m, &m->d_consts, (size_t)nc * E_pad));
+  CK(cudaMemset(m->d_consts, 0, (size_t)nc * E_pad * sizeof(float)));
+  CK(dalloc(m, &m->d_slots, (size_t)ne * E_pad));
+  CK(cudaMemset(m->d_slots, 0, (size_t)ne * E_pad * sizeof(float4)));
+  CK(dalloc(m, &m->d_sell, sell.size() + 1));
+  CK(cudaMemcpy(m->d_sell, sell.data(), sell.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(dalloc(m, &m->d_chunk_ptr, chunk_ptr.size()));
+  CK(cudaMemcpy(m->d_chunk_ptr, chunk_ptr.data(), chunk_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(dalloc(m, &m->d_U, N));
+  CK(dalloc(m, &m->d_V, N));
+  CK(dalloc(m, &m->d_fout, N));
+  CK(dalloc(m, &m->d_bct, std::max(1, m->n_bc_nodes)));
+  if (m->n_bc_nodes)
+    CK(cudaMemcpy(m->d_bct, m->h_bct.data(), m->h_bct.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  CK(dalloc(m, &m->d_perm, N));
+  CK(cudaMemcpy(m->d_perm, m->node_new_of_old.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+  if (!m->R.empty()) {
+    std::vector<float4> Rn(N);
+    for (long long i = 0; i < N; ++i) {
+      const size_t o = 3 * (size_t)m->node_old_of_new[i];
+      Rn[i] = make_float4((float)m->R[o], (float)m->R[o + 1], (float)m->R[o + 2], 0.f);
+    }
+    CK(dalloc(m, &m->d_R, N));
+    CK(cudaMemcpy(m->d_R, Rn.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  }
+  m->n_node_blocks = (int)((N + NODE_THREADS - 1) / NODE_THREADS);
+  CK(dalloc(m, &m->d_partials, m->n_node_blocks));
+  CK(dalloc(m, &m->d_state, 1));
+  CK(cudaMallocHost((void**)&m->h_state, sizeof(DevState)));
+  CK(cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+  // ---- FP64 pre-computation on the device ------------------------------------
+  {
+    std::vector<unsigned char> mo(E);
+    std::vector<double> mu(E), ka(E), rh(E), ea(E), eb(E), c1(E), ad(3 * E), bd(3 * E);
+    for (long long e = 0; e < E; ++e) {
+      const int o = m->elem_old_of_new[e];
+      mo[e] = m->model[o];
+      mu[e] = m->mu[o];
+      ka[e] = m->kappa[o];
+      rh[e] = m->rho[o];
+      ea[e] = m->eta_a[o];
+      eb[e] = m->eta_b[o];
+      c1[e] = m->c01[o];
+      for (int j = 0; j < 3; ++j) {
+        ad[3 * e + j] = m->adir[3 * (size_t)o + j];
+        bd[3 * e + j] = m->bdir[3 * (size_t)o + j];
+      }
+    }
+    double *dX = nullptr, *dmu = nullptr, *dka = nullptr, *drh = nullptr, *dea = nullptr, *deb = nullptr,
+           *dc1 = nullptr, *dad = nullptr, *dbd = nullptr, *dem = nullptr, *ddt = nullptr, *dmass = nullptr,
+           *dred = nullptr;
+    unsigned char* dmo = nullptr;
+    int *dcn = nullptr, *dbad = nullptr, *dbc = nullptr;
+    auto cleanup = [&]() {
+      void* ps[] = {dX, dmu, dka, drh, dea, deb, dc1, dad, dbd, dem, ddt, dmass, dred, dmo, dcn, dbad, dbc};
+      for (void* q : ps)
+        if (q) cudaFree(q);
+    };
+#define CKP(call)                                                                   \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      cleanup();                                                                    \
+      release_device(m);                                                            \
+      return fail(m, _e == cudaErrorMemoryAllocation ? DJ_ERR_OOM : DJ_ERR_CUDA,    \
+                  "precompute: %s: %s", #call, cudaGetErrorString(_e));             \
+    }                                                                               \
+  } while (0)
+    CKP(cudaMalloc(&dX, 3 * N * sizeof(double)));
+    CKP(cudaMalloc(&dcn, (size_t)E * ne * sizeof(int)));
+    CKP(cudaMalloc(&dmo, E));
+    CKP(cudaMalloc(&dmu, E * sizeof(double)));
+    CKP(cudaMalloc(&dka, E * sizeof(double)));
+    CKP(cudaMalloc(&drh, E * sizeof(double)));
+    CKP(cudaMalloc(&dea, E * sizeof(double)));
+    CKP(cudaMalloc(&deb, E * sizeof(double)));
+    CKP(cudaMalloc(&dc1, E * sizeof(double)));
+    CKP(cudaMalloc(&dad, 3 * E * sizeof(double)));
+    CKP(cudaMalloc(&dbd, 3 * E * sizeof(double)));
+    CKP(cudaMalloc(&dem, E * sizeof(double)));
+    CKP(cudaMalloc(&ddt, E * sizeof(double)));
+    CKP(cudaMalloc(&dmass, N * sizeof(double)));
+    CKP(cudaMalloc(&dred, 256 * sizeof(double)));
+    CKP(cudaMalloc(&dbad, sizeof(int)));
+    CKP(cudaMalloc(&dbc, N * sizeof(int)));
+    CKP(cudaMemcpy(dX, Xn.data(), 3 * N * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dcn, cn.data(), (size_t)E * ne * sizeof(int), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dmo, mo.data(), E, cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dmu, mu.data(), E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dka, ka.data(), E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(drh, rh.data(), E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dea, ea.data(), E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(deb, eb.data(), E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dc1, c1.data(), E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dad, ad.data(), 3 * E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dbd, bd.data(), 3 * E * sizeof(double), cudaMemcpyHostToDevice));
+    CKP(cudaMemcpy(dbc, bcidx.data(), N * sizeof(int), cudaMemcpyHostToDevice));
+    const int big = INT_MAX;
+    CKP(cudaMemcpy(dbad, &big, sizeof(int), cudaMemcpyHostToDevice));
+    PreArgs pa;
+    pa.X = dX;
+    pa.conn = dcn;
+    pa.model = dmo;
+    pa.mu = dmu;
+    pa.kappa = dka;
+    pa.rho = drh;
+    pa.eta_a = dea;
+    pa.eta_b = deb;
+    pa.c01 = dc1;
+    pa.adir = dad;
+    pa.bdir = dbd;
+    pa.consts = m->d_consts;
+    pa.conn4 = m->d_conn;
+    pa.elem_mass = dem;
+    pa.dt_elem = ddt;
+    pa.bad = dbad;
+    pa.E = (int)E;
+    pa.E_pad = E_pad;
+    pa.ne = ne;
+    pa.off_fa = m->off_fa;
+    pa.off_fb = m->off_fb;
+    pa.off_mr = m->off_mr;
+    pa.off_hg = m->off_hg;
+    pa.hg_coeff = prm.hg_coeff;
+    CKP(launch_precompute_elements(pa, 0));
+    int bad = 0;
+    CKP(cudaMemcpy(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad != INT_MAX) {
+      const int caller = m->elem_old_of_new[bad];
+      cleanup();
+      release_device(m);
+      return fail(m, DJ_ERR_INVERTED_ELEMENT, "element %d has det 0J <= 0", caller);
+    }
+    CKP(launch_min_reduce(ddt, (int)E, dred, 0));
+    std::vector<double> red(256);
+    CKP(cudaMemcpy(red.data(), dred, 256 * sizeof(double), cudaMemcpyDeviceToHost));
+    m->dt_crit = *std::min_element(red.begin(), red.end());
+    if (prm.dt > 0) {
+      if (prm.dt > m->dt_crit * (1.0 + 1e-12)) {
+        const double dc = m->dt_crit;
+        cleanup();
+        release_device(m);
+        return fail(m, DJ_ERR_INVALID_ARG, "dt %.6g exceeds the critical step %.6g", prm.dt, dc);
+      }
+      m->dt = prm.dt;
+    } else {
+      m->dt = prm.dt_scale * m->dt_crit;
+      if (prm.dt_scale > 1.0) {
+        cleanup();
+        release_device(m);
+        return fail(m, DJ_ERR_INVALID_ARG, "dt_scale above 1 exceeds the critical step");
+      }
+    }
+    const double adt = prm.alpha * m->dt;
+    m->bm1 = (float)((2.0 - adt) / (2.0 + adt));
+    CKP(launch_node_mass(m->d_sell, m->d_chunk_ptr, dem, E_pad, (int)N, m->dt, prm.alpha, dbc, dmass, m->d_U,
+                         m->d_V, 0));
+    std::vector<double> mass(N);
+    CKP(cudaMemcpy(mass.data(), dmass, N * sizeof(double), cudaMemcpyDeviceToHost));
+    m->total_mass = 0;
+    for (double v : mass) m->total_mass += v;
+    std::vector<float4> U0(N);
+    CKP(cudaMemcpy(U0.data(), m->d_U, N * sizeof(float4), cudaMemcpyDeviceToHost));
+    m->h_ai.resize(N);
+    for (long long i = 0; i < N; ++i) m->h_ai[i] = U0[i].w;
+    cleanup();
+#undef CKP
+  }
+  DevState st0{};
+  st0.step = 0;
+  st0.ramp_s = 0.f;
+  st0.err_flags = 0;
+  st0.bad_elem = INT_MAX;
+  CK(cudaMemcpy(m->d_state, &st0, sizeof(DevState), cudaMemcpyHostToDevice));
+  CK(cudaDeviceSynchronize());
+  m->precomputed = true;
+  if (dt_out) *dt_out = m->dt;
+  return DJ_OK;
+}
+
+dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
+  if (!m || !target) return DJ_ERR_INVALID_ARG;
+  for (size_t k = 0; k < m->bc_dof.size(); ++k) {
+    if (!std::isfinite(target[k])) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
+    m->bc_target[k] = target[k];
+  }
+  if (!m->precomputed) return DJ_OK;
+  CK(cudaSetDevice(m->device));
+  for (size_t k = 0; k < m->bc_dof.size(); ++k) {
+    float4& t = m->h_bct[m->bc_node_of_entry[k]];
+    const float v = (float)target[k];
+    if (m->bc_comp_of_entry[k] == 0) t.x = v;
+    if (m->bc_comp_of_entry[k] == 1) t.y = v;
+    if (m->bc_comp_of_entry[k] == 2) t.z = v;
+  }
+  if (m->n_bc_nodes)
+    CK(cudaMemcpy(m->d_bct, m->h_bct.data(), m->h_bct.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  return DJ_OK;
+}
+
+dj_status dj_step(dj_mesh* m, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  CK(launch_step(m, (cudaStream_t)stream, NODE_UPDATE));
+  return DJ_OK;
+}
+
+dj_status dj_run_n(dj_mesh* m, long long n, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (n < 0) return fail(m, DJ_ERR_INVALID_ARG, "n < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = 32;
+  if (n >= chunk && !m->run_exec) {
+    s = capture(m, &m->run_exec, [&](cudaStream_t cs) {
+      for (int k = 0; k < chunk; ++k) {
+        cudaError_t e = launch_step(m, cs, NODE_UPDATE);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    });
+    if (s) return s;
+    m->run_chunk = chunk;
+  }
+  long long left = n;
+  while (m->run_exec && left >= m->run_chunk) {
+    CK(cudaGraphLaunch(m->run_exec, st));
+    left -= m->run_chunk;
+  }
+  for (; left > 0; --left) CK(launch_step(m, st, NODE_UPDATE));
+  return DJ_OK;
+}
+
+dj_status dj_run_n_profiled(dj_mesh* m, long long n, void* stream, double* ms_force, double* ms_update) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (n < 0) return fail(m, DJ_ERR_INVALID_ARG, "n < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<cudaEvent_t> ev(2 * n + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  dj_status rs = DJ_OK;
+  cudaError_t err = cudaEventRecord(ev[0], st);
+  for (long long k = 0; k < n && err == cudaSuccess; ++k) {
+    err = launch_force(m->elem_type, m->variant, force_args(m, 1), m->threads_force, st);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], st);
+    if (err == cudaSuccess) err = launch_node(NODE_UPDATE, node_args(m), st);
+    if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], st);
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  double tf = 0, tu = 0;
+  for (long long k = 0; k < n && err == cudaSuccess; ++k) {
+    float a = 0, b = 0;
+    err = cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]);
+    tf += a;
+    tu += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (err != cudaSuccess) rs = fail(m, DJ_ERR_CUDA, "profiled run: %s", cudaGetErrorString(err));
+  if (ms_force) *ms_force = tf;
+  if (ms_update) *ms_update = tu;
+  return rs;
+}
+
+dj_status dj_sync(dj_mesh* m, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  s = read_state(m, (cudaStream_t)stream);
+  if (s) return s;
+  return check_flags(m);
+}
+
+dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long* steps_out,
+                          double* residual_out, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!(tol >= 0) || max_steps < 0) return fail(m, DJ_ERR_INVALID_ARG, "bad tol or max_steps");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int k = m->params.relax_check_every;
+  if (!m->relax_exec || m->relax_k != k) {
+    if (m->relax_exec) cudaGraphExecDestroy(m->relax_exec);
+    m->relax_exec = nullptr;
+    s = capture(m, &m->relax_exec, [&](cudaStream_t cs) {
+      for (int j = 0; j < k - 1; ++j) {
+        cudaError_t e = launch_step(m, cs, NODE_UPDATE);
+        if (e != cudaSuccess) return e;
+      }
+      cudaError_t e = launch_step(m, cs, NODE_UPDATE_RESID);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, cs);
+    });
+    if (s) return s;
+    m->relax_k = k;
+  }
+  long long done = 0;
+  double r = INFINITY;
+  while (done + k <= max_steps) {
+    CK(cudaGraphLaunch(m->relax_exec, st));
+    CK(cudaStreamSynchronize(st));
+    done += k;
+    s = check_flags(m);
+    if (s) {
+      if (steps_out) *steps_out = done;
+      return s;
+    }
+    const double num = std::sqrt(m->h_state->resid_num2), den = std::sqrt(m->h_state->resid_den2);
+    r = den > 0 ? num / den : num;
+    if (r <= tol) {
+      if (steps_out) *steps_out = done;
+      if (residual_out) *residual_out = r;
+      return DJ_OK;
+    }
+  }
+  // remaining steps that do not complete a check interval
+  for (; done < max_steps; ++done) CK(launch_step(m, st, NODE_UPDATE));
+  s = read_state(m, st);
+  if (s) return s;
+  s = check_flags(m);
+  if (steps_out) *steps_out = done;
+  if (residual_out) *residual_out = r;
+  if (s) return s;
+  return fail(m, DJ_ERR_NOT_CONVERGED, "residual %.3e above tol %.3e after %lld steps", r, tol, done);
+}
+
+dj_status dj_set_displacements(dj_mesh* m, const double* U0) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!U0) return fail(m, DJ_ERR_INVALID_ARG, "null U0");
+  const long long N = m->N;
+  std::vector<float4> U(N), V(N);
+  for (long long i = 0; i < N; ++i) {
+    const size_t o = 3 * (size_t)m->node_old_of_new[i];
+    if (!std::isfinite(U0[o]) || !std::isfinite(U0[o + 1]) || !std::isfinite(U0[o + 2]))
+      return fail(m, DJ_ERR_INVALID_ARG, "non-finite displacement");
+    U[i] = make_float4((float)U0[o], (float)U0[o + 1], (float)U0[o + 2], m->h_ai[i]);
+    V[i] = make_float4(0.f, 0.f, 0.f, bits_to_float(m->h_bcidx[i]));
+  }
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(m->d_U, U.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->d_V, V.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  return DJ_OK;
+}
+
+dj_status dj_get_displacements(dj_mesh* m, double* U_out) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!U_out) return fail(m, DJ_ERR_INVALID_ARG, "null U_out");
+  CK(cudaDeviceSynchronize());
+  const long long N = m->N;
+  std::vector<float4> U(N);
+  CK(cudaMemcpy(U.data(), m->d_U, N * sizeof(float4), cudaMemcpyDeviceToHost));
+  for (long long i = 0; i < N; ++i) {
+    const size_t o = 3 * (size_t)m->node_old_of_new[i];
+    U_out[o] = U[i].x;
+    U_out[o + 1] = U[i].y;
+    U_out[o + 2] = U[i].z;
+  }
+  s = read_state(m, 0);
+  if (s) return s;
+  return check_flags(m);
+}
+
+dj_status dj_get_displacements_device(dj_mesh* m, float* d_U_out, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!d_U_out) return fail(m, DJ_ERR_INVALID_ARG, "null output");
+  CK(launch_to_caller_order(m->d_U, m->d_perm, (int)m->N, d_U_out, (cudaStream_t)stream));
+  return DJ_OK;
+}
+
+dj_status dj_internal_forces(dj_mesh* m, const double* U, double* F_out) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!U || !F_out) return fail(m, DJ_ERR_INVALID_ARG, "null array");
+  const long long N = m->N;
+  CK(cudaDeviceSynchronize());
+  std::vector<float4> save(N), Un(N), F(N);
+  CK(cudaMemcpy(save.data(), m->d_U, N * sizeof(float4), cudaMemcpyDeviceToHost));
+  for (long long i = 0; i < N; ++i) {
+    const size_t o = 3 * (size_t)m->node_old_of_new[i];
+    Un[i] = make_float4((float)U[o], (float)U[o + 1], (float)U[o + 2], save[i].w);
+  }
+  CK(cudaMemcpy(m->d_U, Un.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  CK(launch_force(m->elem_type, m->variant, force_args(m, 0), m->threads_force, 0));
+  NodeArgs na = node_args(m);
+  na.R = nullptr;
+  CK(launch_node(NODE_FORCE_ONLY, na, 0));
+  CK(cudaMemcpy(F.data(), m->d_fout, N * sizeof(float4), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(m->d_U, save.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  for (long long i = 0; i < N; ++i) {
+    const size_t o = 3 * (size_t)m->node_old_of_new[i];
+    F_out[o] = F[i].x;
+    F_out[o + 1] = F[i].y;
+    F_out[o + 2] = F[i].z;
+  }
+  s = read_state(m, 0);
+  if (s) return s;
+  return check_flags(m);
+}
+
+namespace {
+struct StateHeader {
+  unsigned long long magic;
+  long long N;
+  long long step;
+  long long pad;
+};
+const unsigned long long kStateMagic = 0x444a544c45440001ULL;
+}  // namespace
+
+dj_status dj_state_size(const dj_mesh* m, size_t* bytes) {
+  if (!m || !bytes) return DJ_ERR_INVALID_ARG;
+  *bytes = sizeof(StateHeader) + 2 * (size_t)m->N * sizeof(float4);
+  return DJ_OK;
+}
+
+dj_status dj_get_state(dj_mesh* m, void* buf, size_t bytes) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  size_t need = 0;
+  dj_state_size(m, &need);
+  if (!buf || bytes < need) return fail(m, DJ_ERR_INVALID_ARG, "state buffer too small");
+  CK(cudaDeviceSynchronize());
+  s = read_state(m, 0);
+  if (s) return s;
+  StateHeader h{kStateMagic, m->N, m->h_state->step, 0};
+  char* p = (char*)buf;
+  std::memcpy(p, &h, sizeof(h));
+  CK(cudaMemcpy(p + sizeof(h), m->d_U, m->N * sizeof(float4), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(p + sizeof(h) + m->N * sizeof(float4), m->d_V, m->N * sizeof(float4), cudaMemcpyDeviceToHost));
+  return DJ_OK;
+}
+
+dj_status dj_set_state(dj_mesh* m, const void* buf, size_t bytes) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  size_t need = 0;
+  dj_state_size(m, &need);
+  if (!buf || bytes < need) return fail(m, DJ_ERR_INVALID_ARG, "state buffer too small");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.N != m->N) return fail(m, DJ_ERR_INVALID_ARG, "state from another mesh");
+  const char* p = (const char*)buf;
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(m->d_U, p + sizeof(h), m->N * sizeof(float4), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(m->d_V, p + sizeof(h) + m->N * sizeof(float4), m->N * sizeof(float4), cudaMemcpyHostToDevice));
+  DevState st{};
+  st.step = h.step;
+  st.bad_elem = INT_MAX;
+  CK(cudaMemcpy(m->d_state, &st, sizeof(st), cudaMemcpyHostToDevice));
+  return DJ_OK;
+}
+
+dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
+  dj_mesh* m = const_cast<dj_mesh*>(mc);
+  if (!m || !info) return DJ_ERR_INVALID_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->n_nodes = m->N;
+  info->n_elems = m->E;
+  info->n_bc_dofs = (long long)m->bc_dof.size();
+  info->elem_type = m->elem_type;
+  if (!m->precomputed) return DJ_OK;
+  CK(cudaSetDevice(m->device));
+  CK(cudaDeviceSynchronize());
+  dj_status s = read_state(m, 0);
+  if (s) return s;
+  info->step = m->h_state->step;
+  info->model_flags = m->model_flags;
+  info->dt = m->dt;
+  info->dt_crit = m->dt_crit;
+  info->total_mass = m->total_mass;
+  info->device_bytes = m->device_bytes;
+  info->elem_table_bytes_per_elem = (long long)m->n_consts * 4 + 4 * m->ne;
+  info->slot_bytes_per_elem = 16LL * m->ne;
+  info->gather_index_bytes = m->sell_entries * 4;
+  info->node_bytes_per_node = 64;
+  return DJ_OK;
+}
+
+void dj_mesh_destroy(dj_mesh* m) {
+  if (!m) return;
+  if (m->device >= 0) cudaSetDevice(m->device);
+  release_device(m);
+  delete m;
+}
+
+}  // extern "C"

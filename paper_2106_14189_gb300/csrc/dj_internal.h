@@ -1,0 +1,115 @@
+// Internal declarations of the DJ-TLED library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dj_tled.h"
+
+namespace dj {
+
+// ---------------------------------------------------------------------------
+// per-element FP32 table (structure of arrays, stride E_pad), built by the FP64
+// pre-computation.  Common part (19 floats):
+//   0..8   0J row-major, 0J[i][j] = d x_j / d xi_i               (Eq. 3)
+//   9..14  P = (mu / 2) I1m = mu 0V 0J^-T 0J^-1, as P00 P11 P22 P01 P02 P12
+//          (Eq. 37 scaled by dPsi/dI1 of NH / TI / OT; C10 I1m for MR)
+//   15     kappa 0V                                               (Table 3)
+//   16     r0 = 1 / det 0J                                        (Eq. 12)
+// optional blocks (offset -1 when absent):
+//   fibre a: Q_a = eta_a I4m (6 floats, Eq. 45), s_a = 1 / (2 eta_a 0V)
+//   fibre b: Q_b = eta_b I6m (6 floats, Eq. 46), s_b = 1 / (2 eta_b 0V)
+//   MR:      c01 / c10 ratio, 1 / (2 0V)            (Eq. 39-42 rewritten)
+//   H8 hourglass: c_{alpha j} = h_alpha . X_{:,j} (12 floats, alpha-major), k
+// ---------------------------------------------------------------------------
+enum { K_J0 = 0, K_P = 9, K_KV = 15, K_R0 = 16, K_COMMON = 17 };
+
+// Device-resident stepping state, one per mesh.
+struct DevState {
+  long long step;     // n of the current displacement U^n
+  float ramp_s;       // s(tau) for the step being computed (U^{n+1})
+  int err_flags;      // bit 0: det tJ <= 0, bit 1: non-finite force
+  int bad_elem;       // smallest internal element id with an error
+  int pad0;
+  double resid_num2;  // sum of squared residual over free DOFs
+  double resid_den2;  // sum of squared reaction over prescribed DOFs
+};
+
+enum { ERR_INVERTED = 1, ERR_NONFINITE = 2 };
+
+struct ForceArgs {
+  const int4* conn;      // tet: E_pad int4; hex: 2 E_pad int4 (nodes 0-3, 4-7)
+  const float* consts;   // n_consts * E_pad
+  const float4* U;       // U^n (xyz), w = node update coefficient
+  float4* slots;         // element-force slots, slot = a * E_pad + e
+  int E, E_pad;
+  int off_fa, off_fb, off_mr, off_hg;
+  DevState* st;
+  int advance;           // 1: this launch is a time step (bump step, ramp)
+  long long ramp_steps;
+  int ramp_kind;
+};
+
+struct NodeArgs {
+  const int* sell;        // sliced-ELL slot ids, chunks of 32 nodes, column-major
+  const int* chunk_ptr;   // n_chunks + 1 offsets into sell
+  const float4* slots;
+  float4* U;              // in/out: U^n -> U^{n+1}; w = a_i
+  float4* V;              // in/out: U^n - U^{n-1} -> U^{n+1} - U^n; w = bc index bits
+  const float4* bct;      // per prescribed node: target xyz, w = component mask bits
+  const float4* R;        // external loads or nullptr
+  float4* fout;           // force-only mode output
+  double2* partials;      // residual partial sums per block
+  const DevState* st;
+  int N;
+  float bm1;              // b - 1 = (2 - alpha dt) / (2 + alpha dt)
+};
+
+enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2 };
+
+constexpr int NODE_THREADS = 256;
+constexpr int SELL_C = 32;
+
+// kernels_step.cu
+cudaError_t launch_force(int elem_type, int variant, const ForceArgs& a, int threads,
+                         cudaStream_t s);
+cudaError_t launch_node(int mode, const NodeArgs& a, cudaStream_t s);
+cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
+
+// force kernel variants
+enum { VAR_NH = 0, VAR_TI = 1, VAR_OT = 2, VAR_MR = 3, VAR_ALL = 4 };
+
+// kernels_pre.cu
+struct PreArgs {
+  const double* X;          // internal order, N * 3
+  const int* conn;          // internal order, E * ne
+  const unsigned char* model;
+  const double* mu;
+  const double* kappa;
+  const double* rho;
+  const double* eta_a;
+  const double* eta_b;
+  const double* c01;
+  const double* adir;       // E * 3
+  const double* bdir;
+  float* consts;
+  int4* conn4;
+  double* elem_mass;        // rho 0V / n_e
+  double* dt_elem;
+  int* bad;                 // first inverted element (atomicMin), init E
+  int E, E_pad, ne;
+  int off_fa, off_fb, off_mr, off_hg;
+  double hg_coeff;
+};
+cudaError_t launch_precompute_elements(const PreArgs& a, cudaStream_t s);
+cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double* elem_mass,
+                             int E_pad, int N, double dt, double alpha, const int* bc_index,
+                             double* mass_out, float4* U, float4* V, cudaStream_t s);
+cudaError_t launch_min_reduce(const double* v, int n, double* out, cudaStream_t s);
+cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, int N, float* out,
+                                   cudaStream_t s);
+
+}  // namespace dj

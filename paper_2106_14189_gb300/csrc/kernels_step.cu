@@ -1,0 +1,480 @@
+// DJ-TLED time-step kernels for sm_103a.
+//
+//  force_kernel<ELEM, FA, FB, MR>   one thread per element: Algorithm 1 runtime
+//      steps 1-4 (tJ, J, g_hat, invariants, Table 3 force), written to the
+//      element-force slots (slot = a * E_pad + e, so each store instruction of a
+//      warp is one contiguous 512-byte run).
+//  node_kernel<MODE>                one thread per node: deterministic gather of
+//      the node's slots (sliced ELL, fixed order), central-difference update
+//      with mass-proportional damping (Eq. 13) and prescribed displacements;
+//      optional FP64 residual partial sums for dynamic relaxation.
+//
+// FP32 arithmetic throughout the step.  The force is evaluated in this
+// algebraically equivalent form of Table 3 (P = dPsi/dI1 I1m, adj = det(tJ) tJ^-1):
+//
+//   F = [ J^-2/3 tJ^T (P + psi_a Q_a + psi_b Q_b + MR term)
+//         + ( -J^-2/3 (P:g + psi_a Q_a:g + psi_b Q_b:g) / 3 - MR vol term ) adj / det tJ
+//         + kappa 0V (J - 1) r0 adj ] H_xi
+//
+// using  I1 = g_hat^T m1 = g:P / (mu 0V)  (m1 from I1m, Eq. 22/37),
+//        I4 = g:Q_a / (2 eta_a 0V), psi_a = I4bar - 1, and
+//        J tJ^-1 / det tJ ... = r0 adj  (Eq. 12).
+#include <cuda_runtime.h>
+
+#include "dj_internal.h"
+
+namespace dj {
+
+namespace {
+
+__device__ __forceinline__ float ldg_stream(const float* p) { return __ldcs(p); }
+
+struct M3 {
+  float m[3][3];
+};
+
+__device__ __forceinline__ float det3(const M3& a) {
+  return a.m[0][0] * (a.m[1][1] * a.m[2][2] - a.m[1][2] * a.m[2][1]) -
+         a.m[0][1] * (a.m[1][0] * a.m[2][2] - a.m[1][2] * a.m[2][0]) +
+         a.m[0][2] * (a.m[1][0] * a.m[2][1] - a.m[1][1] * a.m[2][0]);
+}
+
+// adjugate: adj(a) = det(a) a^-1
+__device__ __forceinline__ M3 adj3(const M3& a) {
+  M3 r;
+  r.m[0][0] = a.m[1][1] * a.m[2][2] - a.m[1][2] * a.m[2][1];
+  r.m[0][1] = a.m[0][2] * a.m[2][1] - a.m[0][1] * a.m[2][2];
+  r.m[0][2] = a.m[0][1] * a.m[1][2] - a.m[0][2] * a.m[1][1];
+  r.m[1][0] = a.m[1][2] * a.m[2][0] - a.m[1][0] * a.m[2][2];
+  r.m[1][1] = a.m[0][0] * a.m[2][2] - a.m[0][2] * a.m[2][0];
+  r.m[1][2] = a.m[0][2] * a.m[1][0] - a.m[0][0] * a.m[1][2];
+  r.m[2][0] = a.m[1][0] * a.m[2][1] - a.m[1][1] * a.m[2][0];
+  r.m[2][1] = a.m[0][1] * a.m[2][0] - a.m[0][0] * a.m[2][1];
+  r.m[2][2] = a.m[0][0] * a.m[1][1] - a.m[0][1] * a.m[1][0];
+  return r;
+}
+
+// symmetric 3x3 stored as s[6] = {00, 11, 22, 01, 02, 12}
+__device__ __forceinline__ float sym_at(const float* s, int i, int j) {
+  if (i == j) return s[i];
+  int k = i + j;  // (0,1)->1, (0,2)->2, (1,2)->3
+  return s[2 + k];
+}
+
+__device__ __forceinline__ void load_sym(const float* c, int off, int E_pad, int e, float* s) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) s[k] = ldg_stream(c + (size_t)(off + k) * E_pad + e);
+}
+
+// g : S  (Frobenius product of symmetric g with symmetric S)
+__device__ __forceinline__ float frob_sym(const float* g, const float* s) {
+  return g[0] * s[0] + g[1] * s[1] + g[2] * s[2] + 2.f * (g[3] * s[3] + g[4] * s[4] + g[5] * s[5]);
+}
+
+// acc += w * tJ^T S  (S symmetric)
+__device__ __forceinline__ void add_tJT_sym(M3& acc, const M3& tJ, const float* s, float w) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float v = tJ.m[0][i] * sym_at(s, 0, j) + tJ.m[1][i] * sym_at(s, 1, j) +
+                tJ.m[2][i] * sym_at(s, 2, j);
+      acc.m[i][j] = fmaf(w, v, acc.m[i][j]);
+    }
+}
+
+template <bool FA, bool FB, bool MR>
+__device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const float* __restrict__ c, int E_pad,
+                                              int e, const ForceArgs& a, bool& bad) {
+  const float D = det3(tJ);
+  const float r0 = ldg_stream(c + (size_t)K_R0 * E_pad + e);
+  const float kV = ldg_stream(c + (size_t)K_KV * E_pad + e);
+  const float J = D * r0;  // Eq. 12
+  bad = !(D > 0.f);
+  const float rc = rcbrtf(J);
+  const float Jm23 = rc * rc;  // J^-2/3
+  // g = tJ tJ^T (Eq. 17), symmetric
+  float g[6];
+  g[0] = tJ.m[0][0] * tJ.m[0][0] + tJ.m[0][1] * tJ.m[0][1] + tJ.m[0][2] * tJ.m[0][2];
+  g[1] = tJ.m[1][0] * tJ.m[1][0] + tJ.m[1][1] * tJ.m[1][1] + tJ.m[1][2] * tJ.m[1][2];
+  g[2] = tJ.m[2][0] * tJ.m[2][0] + tJ.m[2][1] * tJ.m[2][1] + tJ.m[2][2] * tJ.m[2][2];
+  g[3] = tJ.m[0][0] * tJ.m[1][0] + tJ.m[0][1] * tJ.m[1][1] + tJ.m[0][2] * tJ.m[1][2];
+  g[4] = tJ.m[0][0] * tJ.m[2][0] + tJ.m[0][1] * tJ.m[2][1] + tJ.m[0][2] * tJ.m[2][2];
+  g[5] = tJ.m[1][0] * tJ.m[2][0] + tJ.m[1][1] * tJ.m[2][1] + tJ.m[1][2] * tJ.m[2][2];
+
+  float P[6];
+  load_sym(c, K_P, E_pad, e, P);
+  const float gP = frob_sym(g, P);  // = mu 0V I1
+  M3 T;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
+  float Sdev = 1.f;                 // weight of tJ^T P
+  float vol_over_D = -gP / 3.f;     // multiplies Jm23 adj / D
+  if (FA) {
+    float Q[6];
+    load_sym(c, a.off_fa, E_pad, e, Q);
+    const float sa = ldg_stream(c + (size_t)(a.off_fa + 6) * E_pad + e);
+    const float gQ = frob_sym(g, Q);
+    const float psi = Jm23 * gQ * sa - 1.f;  // I4bar - 1 (Eq. 31, Table 1)
+    add_tJT_sym(T, tJ, Q, psi);
+    vol_over_D -= psi * gQ / 3.f;
+  }
+  if (FB) {
+    float Q[6];
+    load_sym(c, a.off_fb, E_pad, e, Q);
+    const float sb = ldg_stream(c + (size_t)(a.off_fb + 6) * E_pad + e);
+    const float gQ = frob_sym(g, Q);
+    const float psi = Jm23 * gQ * sb - 1.f;  // I6bar - 1 (Eq. 32)
+    add_tJT_sym(T, tJ, Q, psi);
+    vol_over_D -= psi * gQ / 3.f;
+  }
+  add_tJT_sym(T, tJ, P, Sdev);
+  float mr_vol = 0.f;
+  if (MR) {
+    // C01 g_hat^T I2m = gm (g:P P - P g P), gm = C01 / (2 C10^2 0V)   (Eq. 39-42)
+    const float gm = ldg_stream(c + (size_t)a.off_mr * E_pad + e);
+    float Pg[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Pg[i][j] = sym_at(P, i, 0) * sym_at(g, 0, j) + sym_at(P, i, 1) * sym_at(g, 1, j) +
+                   sym_at(P, i, 2) * sym_at(g, 2, j);
+    float S2[6];
+    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const int i = ii[k], j = jj[k];
+      const float PgP = Pg[i][0] * sym_at(P, 0, j) + Pg[i][1] * sym_at(P, 1, j) +
+                        Pg[i][2] * sym_at(P, 2, j);
+      S2[k] = gm * (gP * sym_at(P, i, j) - PgP);
+    }
+    float trPgPg = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
+    add_tJT_sym(T, tJ, S2, Jm23);                      // extra J^-2/3 of Eq. 39
+    mr_vol = -Jm23 * Jm23 * gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
+  }
+  const M3 A = adj3(tJ);
+  const float invD = 1.f / D;
+  const float ca = (Jm23 * vol_over_D + mr_vol) * invD + kV * (J - 1.f) * r0;
+  M3 F;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) F.m[i][j] = fmaf(Jm23, T.m[i][j], ca * A.m[i][j]);
+  return F;
+}
+
+__device__ __forceinline__ void flag_error(DevState* st, int e, bool inverted, bool nonfinite) {
+  int f = (inverted ? ERR_INVERTED : 0) | (nonfinite ? ERR_NONFINITE : 0);
+  if (f) {
+    atomicOr(&st->err_flags, f);
+    atomicMin(&st->bad_elem, e);
+  }
+}
+
+__device__ __forceinline__ void advance_clock(const ForceArgs& a) {
+  if (a.advance && blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long n1 = a.st->step + 1;
+    double s = 1.0;
+    if (a.ramp_steps > 0) {
+      double tau = (double)n1 / (double)a.ramp_steps;
+      tau = tau > 1.0 ? 1.0 : tau;
+      s = a.ramp_kind == DJ_RAMP_LINEAR ? tau : tau * tau * tau * (10.0 - 15.0 * tau + 6.0 * tau * tau);
+    }
+    a.st->ramp_s = (float)s;
+    a.st->step = n1;
+  }
+}
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+  return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+template <bool FA, bool FB, bool MR>
+__global__ void __launch_bounds__(256) force_tet4_kernel(ForceArgs a) {
+  advance_clock(a);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  const int E_pad = a.E_pad;
+  const float* __restrict__ c = a.consts;
+  const int4 nd = __ldcs(a.conn + e);
+  const float4 u0 = __ldg(a.U + nd.x), u1 = __ldg(a.U + nd.y), u2 = __ldg(a.U + nd.z),
+               u3 = __ldg(a.U + nd.w);
+  // tJ = 0J + H_xi u_e (Eq. 11, Eq. 3 orientation): rows u_b - u_0
+  M3 tJ;
+  const float du[3][3] = {{u1.x - u0.x, u1.y - u0.y, u1.z - u0.z},
+                          {u2.x - u0.x, u2.y - u0.y, u2.z - u0.z},
+                          {u3.x - u0.x, u3.y - u0.y, u3.z - u0.z}};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) tJ.m[i][j] = ldg_stream(c + (size_t)(K_J0 + 3 * i + j) * E_pad + e) + du[i][j];
+  bool inv;
+  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, c, E_pad, e, a, inv);
+  // nodal forces = F H_xi: node b (1..3) gets column b-1, node 0 minus their sum (Sec. 7)
+  const float4 f1 = make_float4(F.m[0][0], F.m[1][0], F.m[2][0], 0.f);
+  const float4 f2 = make_float4(F.m[0][1], F.m[1][1], F.m[2][1], 0.f);
+  const float4 f3 = make_float4(F.m[0][2], F.m[1][2], F.m[2][2], 0.f);
+  const float4 f0 = make_float4(-(f1.x + f2.x + f3.x), -(f1.y + f2.y + f3.y), -(f1.z + f2.z + f3.z), 0.f);
+  const bool nonfinite = !finite3(f0.x, f0.y, f0.z) || !finite3(f1.x, f1.y, f1.z) ||
+                         !finite3(f2.x, f2.y, f2.z) || !finite3(f3.x, f3.y, f3.z);
+  flag_error(a.st, e, inv, nonfinite && !inv);
+  a.slots[e] = f0;
+  a.slots[(size_t)E_pad + e] = f1;
+  a.slots[(size_t)2 * E_pad + e] = f2;
+  a.slots[(size_t)3 * E_pad + e] = f3;
+}
+
+// natural coordinates of the brick nodes (bottom face CCW, then top face)
+__device__ constexpr float XI8[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                        {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+// hourglass base vectors h1 = xi eta, h2 = eta zeta, h3 = zeta xi, h4 = xi eta zeta
+__device__ constexpr float H8[4][8] = {{1, -1, 1, -1, 1, -1, 1, -1},
+                                       {1, 1, -1, -1, -1, -1, 1, 1},
+                                       {1, -1, -1, 1, -1, 1, 1, -1},
+                                       {-1, 1, -1, 1, 1, -1, 1, -1}};
+
+template <bool FA, bool FB, bool MR>
+__global__ void __launch_bounds__(128) force_hex8_kernel(ForceArgs a) {
+  advance_clock(a);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  const int E_pad = a.E_pad;
+  const float* __restrict__ c = a.consts;
+  const int4 n0 = __ldcs(a.conn + 2 * (size_t)e), n1 = __ldcs(a.conn + 2 * (size_t)e + 1);
+  const int nid[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+  float u[8][3];
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const float4 v = __ldg(a.U + nid[b]);
+    u[b][0] = v.x;
+    u[b][1] = v.y;
+    u[b][2] = v.z;
+  }
+  // s_i = (H_xi u)_i = sum_b xi_{b,i} u_b / 8
+  float s[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float acc = 0.f;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc += XI8[b][i] * u[b][j];
+      s[i][j] = 0.125f * acc;
+    }
+  M3 J0, tJ;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      J0.m[i][j] = ldg_stream(c + (size_t)(K_J0 + 3 * i + j) * E_pad + e);
+      tJ.m[i][j] = J0.m[i][j] + s[i][j];  // Eq. 11
+    }
+  bool inv;
+  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, c, E_pad, e, a, inv);
+  // hourglass (1-point H8): q_alpha = gamma_alpha . u, gamma_alpha = h_alpha - sum_j c_aj 0B_j
+  const float r0 = ldg_stream(c + (size_t)K_R0 * E_pad + e);
+  const M3 J0a = adj3(J0);  // 0J^-1 = adj r0
+  float cc[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cc[q][j] = ldg_stream(c + (size_t)(a.off_hg + 3 * q + j) * E_pad + e);
+  const float khg = ldg_stream(c + (size_t)(a.off_hg + 12) * E_pad + e);
+  // e_{alpha,i} = sum_j c_{alpha j} (0J^-1)_{j i}
+  float eq[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      eq[q][i] = r0 * (cc[q][0] * J0a.m[0][i] + cc[q][1] * J0a.m[1][i] + cc[q][2] * J0a.m[2][i]);
+  float H[4][3];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float hu = 0.f;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) hu += H8[q][b] * u[b][j];
+      H[q][j] = khg * (hu - (eq[q][0] * s[0][j] + eq[q][1] * s[1][j] + eq[q][2] * s[2][j]));
+    }
+  // G_i = F[:, i] / 8 - (1/8) sum_alpha e_{alpha,i} H_alpha
+  float G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      G[i][j] = 0.125f * (F.m[j][i] - (eq[0][i] * H[0][j] + eq[1][i] * H[1][j] +
+                                       eq[2][i] * H[2][j] + eq[3][i] * H[3][j]));
+  bool nonfinite = false;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    float f[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float v = XI8[b][0] * G[0][j] + XI8[b][1] * G[1][j] + XI8[b][2] * G[2][j];
+      v += H8[0][b] * H[0][j] + H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
+      f[j] = v;
+    }
+    nonfinite |= !finite3(f[0], f[1], f[2]);
+    a.slots[(size_t)b * E_pad + e] = make_float4(f[0], f[1], f[2], 0.f);
+  }
+  flag_error(a.st, e, inv, nonfinite && !inv);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int chunk = i / SELL_C, lane = i % SELL_C;
+  double num2 = 0.0, den2 = 0.0;
+  if (i < a.N) {
+    const int beg = __ldg(a.chunk_ptr + chunk), end = __ldg(a.chunk_ptr + chunk + 1);
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int p = beg + lane; p < end; p += SELL_C) {
+      const int sid = __ldcs(a.sell + p);
+      if (sid >= 0) {
+        const float4 f = __ldcs(a.slots + sid);
+        fx += f.x;
+        fy += f.y;
+        fz += f.z;
+      }
+    }
+    if (a.R) {
+      const float4 r = __ldg(a.R + i);
+      fx -= r.x;
+      fy -= r.y;
+      fz -= r.z;
+    }
+    // now f = F_int - R
+    const float4 V = a.V[i];
+    const int bc = __float_as_int(V.w);
+    if (MODE == NODE_FORCE_ONLY) {
+      a.fout[i] = make_float4(fx, fy, fz, 0.f);
+    } else {
+      const float4 U = a.U[i];
+      const float ai = U.w;
+      // velocity form of the central difference: D^{n+1} = a (R - F) + (b - 1) D^n
+      float dx = fmaf(-ai, fx, a.bm1 * V.x);
+      float dy = fmaf(-ai, fy, a.bm1 * V.y);
+      float dz = fmaf(-ai, fz, a.bm1 * V.z);
+      float nx = U.x + dx, ny = U.y + dy, nz = U.z + dz;
+      int mask = 0;
+      if (bc >= 0) {
+        const float4 t = __ldg(a.bct + bc);
+        mask = __float_as_int(t.w);
+        const float rs = a.st->ramp_s;
+        if (mask & 1) { nx = t.x * rs; dx = nx - U.x; }
+        if (mask & 2) { ny = t.y * rs; dy = ny - U.y; }
+        if (mask & 4) { nz = t.z * rs; dz = nz - U.z; }
+      }
+      a.U[i] = make_float4(nx, ny, nz, ai);
+      a.V[i] = make_float4(dx, dy, dz, V.w);
+      if (MODE == NODE_UPDATE_RESID) {
+        const double f3[3] = {fx, fy, fz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (mask & (1 << k)) den2 += f3[k] * f3[k];
+          else num2 += f3[k] * f3[k];
+        }
+      }
+    }
+  }
+  if (MODE == NODE_UPDATE_RESID) {
+    __shared__ double sn[NODE_THREADS / 32], sd[NODE_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      num2 += __shfl_down_sync(0xffffffffu, num2, o);
+      den2 += __shfl_down_sync(0xffffffffu, den2, o);
+    }
+    const int w = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0) {
+      sn[w] = num2;
+      sd[w] = den2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tn = 0.0, td = 0.0;
+      for (int k = 0; k < NODE_THREADS / 32; ++k) {
+        tn += sn[k];
+        td += sd[k];
+      }
+      a.partials[blockIdx.x] = make_double2(tn, td);
+    }
+  }
+}
+
+__global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevState* st) {
+  __shared__ double sn[256], sd[256];
+  double tn = 0.0, td = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    tn += p[k].x;
+    td += p[k].y;
+  }
+  sn[threadIdx.x] = tn;
+  sd[threadIdx.x] = td;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sn[threadIdx.x] += sn[threadIdx.x + o];
+      sd[threadIdx.x] += sd[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    st->resid_num2 = sn[0];
+    st->resid_den2 = sd[0];
+  }
+}
+
+template <int ELEM, bool FA, bool FB, bool MR>
+cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
+  const int grid = (a.E + threads - 1) / threads;
+  if (ELEM == DJ_TET4)
+    force_tet4_kernel<FA, FB, MR><<<grid, threads, 0, s>>>(a);
+  else
+    force_hex8_kernel<FA, FB, MR><<<grid, threads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int ELEM>
+cudaError_t launch_force_e(int variant, const ForceArgs& a, int threads, cudaStream_t s) {
+  switch (variant) {
+    case VAR_NH: return launch_force_t<ELEM, false, false, false>(a, threads, s);
+    case VAR_TI: return launch_force_t<ELEM, true, false, false>(a, threads, s);
+    case VAR_OT: return launch_force_t<ELEM, true, true, false>(a, threads, s);
+    case VAR_MR: return launch_force_t<ELEM, false, false, true>(a, threads, s);
+    default: return launch_force_t<ELEM, true, true, true>(a, threads, s);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_force(int elem_type, int variant, const ForceArgs& a, int threads,
+                         cudaStream_t s) {
+  if (elem_type == DJ_TET4) return launch_force_e<DJ_TET4>(variant, a, threads, s);
+  return launch_force_e<DJ_HEX8>(variant, a, threads, s);
+}
+
+cudaError_t launch_node(int mode, const NodeArgs& a, cudaStream_t s) {
+  const int grid = (a.N + NODE_THREADS - 1) / NODE_THREADS;
+  if (mode == NODE_UPDATE)
+    node_kernel<NODE_UPDATE><<<grid, NODE_THREADS, 0, s>>>(a);
+  else if (mode == NODE_UPDATE_RESID)
+    node_kernel<NODE_UPDATE_RESID><<<grid, NODE_THREADS, 0, s>>>(a);
+  else
+    node_kernel<NODE_FORCE_ONLY><<<grid, NODE_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s) {
+  resid_finalize_kernel<<<1, 256, 0, s>>>(partials, n, st);
+  return cudaGetLastError();
+}
+
+}  // namespace dj

@@ -1,0 +1,99 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, and rejects bad input in host code before any device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2106_14189_gb300 import binding, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dj_tled.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    return binding.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dj_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(binding.EXPORTS) == names
+
+
+def test_params_default(lib):
+    p = binding.default_params()
+    assert p.dt_scale == 0.9 and p.hg_coeff == 0.1 and p.relax_check_every == 100
+    assert p.renumber == 1 and p.ramp_kind == 1
+
+
+def test_status_strings(lib):
+    for s, name in binding.STATUS.items():
+        assert binding.dj_status_string(s)
+    assert binding.dj_status_string(3) == "inverted element"
+
+
+def test_host_validation_errors(lib):
+    X, conn = workloads.cube_tet4(2)
+    with pytest.raises(binding.DJError) as e:
+        binding.dj_mesh_create(5, X, conn)
+    assert e.value.status == 1
+    bad = conn.copy()
+    bad[0, 0] = X.shape[0]
+    with pytest.raises(binding.DJError) as e:
+        binding.dj_mesh_create(4, X, bad)
+    assert e.value.status == 2
+    with pytest.raises(binding.DJError) as e:
+        binding.dj_mesh_create(4, X, conn[:0])
+    assert e.value.status == 2
+    Xn = X.copy()
+    Xn[3, 1] = np.nan
+    with pytest.raises(binding.DJError) as e:
+        binding.dj_mesh_create(4, Xn, conn)
+    assert e.value.status == 1
+    h = binding.dj_mesh_create(4, X, conn)
+    try:
+        E = conn.shape[0]
+        ones = np.ones(E)
+        with pytest.raises(binding.DJError) as e:
+            binding.dj_mesh_set_materials(h, np.zeros(E), -ones, ones, ones)
+        assert e.value.status == 1 and "mu" in binding.dj_last_error(h)
+        with pytest.raises(binding.DJError) as e:
+            binding.dj_mesh_set_materials(h, np.full(E, 7), ones, ones, ones)
+        assert e.value.status == 1
+        binding.dj_mesh_set_materials(h, np.zeros(E), ones, ones, ones)
+        with pytest.raises(binding.DJError) as e:
+            binding.dj_mesh_set_bcs(h, [0, 0], [0.0, 1.0])
+        assert "duplicate" in binding.dj_last_error(h)
+        with pytest.raises(binding.DJError):
+            binding.dj_mesh_set_bcs(h, [3 * X.shape[0]], [0.0])
+        binding.dj_mesh_set_bcs(h, [0, 1, 2], [0.0, 0.0, 0.1])
+        with pytest.raises(binding.DJError) as e:
+            binding.dj_step(h)
+        assert e.value.status == 4
+    finally:
+        binding.dj_mesh_destroy(h)
+
+
+def test_state_size_is_known_before_device_work(lib):
+    X, conn = workloads.cube_hex8(2)
+    h = binding.dj_mesh_create(8, X, conn)
+    try:
+        assert binding.dj_state_size(h) == 32 + 2 * 16 * X.shape[0]
+        info = binding.dj_get_info(h)
+        assert info.n_nodes == X.shape[0] and info.n_elems == conn.shape[0] and info.elem_type == 8
+    finally:
+        binding.dj_mesh_destroy(h)

@@ -1,0 +1,256 @@
+"""GPU parity of the DJ-TLED step (CUDA library through the C ABI) against the
+FP64 oracle.
+
+Tolerances (stated once, used everywhere below):
+* forces:        max |F_gpu - F_ref| <= 1e-4 max |F_ref|   (FP32 element arithmetic)
+* displacements: rel-Linf = max |U_gpu - U_ref| / max |U_ref| <= 1e-4 after N steps
+  (the tolerance the build targets for FP32 against FP64).
+"""
+import numpy as np
+import pytest
+
+from oracle import dynamics
+from paper_2106_14189_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4
+DISP_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_14189_gb300 import binding
+    return binding
+
+
+def rel_linf(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+MODELS = [W.NH, W.TI, W.OT, W.MR]
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("renumber", [1, 0])
+def test_tet4_forces_match_oracle(B, model, renumber):
+    # 6 * 7^3 = 2058 elements: several 256-thread tiles plus a ragged tail
+    p = W.random_tet_mesh_problem(2058, seed=11 + model, model=model)
+    rng = np.random.default_rng(5)
+    U = rng.normal(size=(p.n_nodes, 3)) * 0.02
+    with B.Mesh(p, renumber=renumber) as m:
+        F = m.internal_forces(U)
+    ref = dynamics.Model.from_problem(p).internal_forces(U)
+    assert rel_linf(F, ref) < FORCE_TOL
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_hex8_forces_match_oracle(B, model):
+    p = W.random_hex_mesh_problem(9, seed=21 + model, model=model)  # 729 bricks, ragged
+    p.hg_coeff = 0.15
+    rng = np.random.default_rng(6)
+    U = rng.normal(size=(p.n_nodes, 3)) * 0.01
+    with B.Mesh(p) as m:
+        F = m.internal_forces(U)
+    ref = dynamics.Model.from_problem(p).internal_forces(U)
+    assert rel_linf(F, ref) < FORCE_TOL
+
+
+@pytest.mark.parametrize("et", [4, 8])
+def test_single_element_mesh(B, et):
+    X, conn = W.single_element(et, seed=4)
+    E = 1
+    mat = dict(model=np.full(E, W.TI, dtype=np.uint8), mu=np.full(E, 1000.0),
+               kappa=np.full(E, 30000.0), rho=np.full(E, 1000.0), eta_a=np.full(E, 2000.0),
+               eta_b=np.zeros(E), c01=np.zeros(E), a_dir=np.array([[1.0, 2.0, 0.5]]),
+               b_dir=np.array([[0.0, 1.0, 0.0]]))
+    p = W.Problem(name="one", elem_type=et, X=X, conn=conn, bc_dof=np.array([0, 1, 2], dtype=np.int64),
+                  bc_target=np.array([0.0, 0.0, 0.05]), ramp_steps=50, **mat)
+    with B.Mesh(p) as m:
+        m.run(120)
+        U = m.displacements()
+    ref = dynamics.ExplicitSolver.from_problem(p).run(120)
+    assert rel_linf(U, ref) < DISP_TOL
+
+
+@pytest.fixture(scope="module")
+def cfg1_reference():
+    p = W.cube_compression_tet4(10, 2000)
+    s = dynamics.ExplicitSolver.from_problem(p)
+    out = {}
+    for n in (500, 2000):
+        s.run(n - s.n)
+        out[n] = s.U.copy()
+    return p, s.dt, out
+
+
+def test_cfg1_trajectory_2000_steps(B, cfg1_reference):
+    """Tet4 cube 10^3 x 6 (6000 T4), NH, E = 3 kPa, nu = 0.49, -20 % z on a smooth ramp."""
+    p, dt_ref, ref = cfg1_reference
+    with B.Mesh(p) as m:
+        assert abs(m.dt - dt_ref) < 1e-12 * dt_ref
+        m.run(500)
+        U500 = m.displacements()
+        m.run(1500)
+        U2000 = m.displacements()
+        info = m.info()
+    assert info.step == 2000
+    assert rel_linf(U500, ref[500]) < DISP_TOL
+    e = rel_linf(U2000, ref[2000])
+    rmse = float(np.sqrt(np.mean((U2000 - ref[2000]) ** 2)))  # Eq. 52
+    print(f"cfg1 rel-Linf {e:.3e} RMSE {rmse:.3e} m")
+    assert e < DISP_TOL
+
+
+def test_hex8_trajectory_shear(B):
+    p = W.cube_shear(W.HEX8, 8, n_steps=1500, shear=0.1)
+    with B.Mesh(p) as m:
+        m.run(1500)
+        U = m.displacements()
+        dt = m.dt
+    s = dynamics.ExplicitSolver.from_problem(p)
+    assert abs(s.dt - dt) < 1e-12 * dt
+    ref = s.run(1500)
+    assert rel_linf(U, ref) < DISP_TOL
+
+
+def test_anisotropic_ellipsoid_damped(B):
+    p = W.ellipsoid_tet4(h=7e-3, seed=3)
+    p.alpha = 5.0
+    p.ramp_steps = 400
+    with B.Mesh(p) as m:
+        m.run(600)
+        U = m.displacements()
+    ref = dynamics.ExplicitSolver.from_problem(p).run(600)
+    assert rel_linf(U, ref) < DISP_TOL
+
+
+def test_orthotropic_and_mooney_rivlin_trajectories(B):
+    for model in (W.OT, W.MR):
+        p = W.random_tet_mesh_problem(750, seed=40 + model, model=model)
+        p.ramp_steps = 300
+        p.alpha = 2.0
+        with B.Mesh(p) as m:
+            m.run(400)
+            U = m.displacements()
+        ref = dynamics.ExplicitSolver.from_problem(p).run(400)
+        assert rel_linf(U, ref) < DISP_TOL, model
+
+
+def test_external_loads(B):
+    p = W.random_hex_mesh_problem(4, seed=8)
+    p.ramp_steps = 100
+    rng = np.random.default_rng(1)
+    R = rng.normal(size=(p.n_nodes, 3)) * 0.05
+    m = B.Mesh(p, precompute=False)
+    B.dj_mesh_set_loads(m.h, R)
+    m.dt = B.dj_precompute(m.h, m.params)
+    m.run(200)
+    U = m.displacements()
+    m.close()
+    ref = dynamics.ExplicitSolver.from_problem(p, R=R).run(200)
+    assert rel_linf(U, ref) < DISP_TOL
+
+
+def test_deterministic_and_checkpoint_resume_bit_identical(B):
+    p = W.cube_compression_tet4(6, 300)
+    with B.Mesh(p) as a, B.Mesh(p) as b:
+        a.run(300)
+        b.run(150)
+        blob = B.dj_get_state(b.h)
+        b.run(150)
+        Ua, Ub = a.displacements(), b.displacements()
+        assert np.array_equal(Ua, Ub)
+        B.dj_set_state(b.h, blob)
+        assert B.dj_get_info(b.h).step == 150
+        b.run(150)
+        assert np.array_equal(b.displacements(), Ua)
+
+
+def test_graph_and_direct_launch_agree(B):
+    p = W.cube_shear(W.HEX8, 5, n_steps=100)
+    with B.Mesh(p) as a, B.Mesh(p) as b:
+        a.run(100)  # graph replays of 32 steps + 4 direct steps
+        for _ in range(100):
+            b.step()
+        assert np.array_equal(a.displacements(), b.displacements())
+        fa, fu = B.dj_run_n_profiled(b.h, 10)
+        assert fa > 0 and fu > 0
+
+
+def test_inverted_reference_element_is_reported(B):
+    X, conn = W.cube_tet4(3)
+    conn = conn.copy()
+    conn[17, [1, 2]] = conn[17, [2, 1]]
+    p = W.cube_compression_tet4(3, 10)
+    p.conn = conn
+    with pytest.raises(B.DJError) as e:
+        B.Mesh(p)
+    assert e.value.status == 3 and "element 17" in str(e.value)
+
+
+def test_inversion_while_stepping_is_reported(B):
+    p = W.cube_compression_tet4(3, 10, strain=-3.0)   # crush to -300 % in 10 steps
+    with B.Mesh(p) as m:
+        m.run(40)
+        with pytest.raises(B.DJError) as e:
+            m.sync()
+        assert e.value.status in (3, 5)
+
+
+def test_dt_above_critical_rejected(B):
+    p = W.cube_compression_tet4(3, 10)
+    with pytest.raises(B.DJError) as e:
+        B.Mesh(p, dt=1.0)
+    assert e.value.status == 1
+
+
+def test_relaxation_matches_oracle(B):
+    p = W.cube_shear(W.HEX8, 4, shear=0.1)
+    p.alpha, p.ramp_steps = 4.0, 200
+    with B.Mesh(p, relax_check_every=50) as m:
+        st, steps, r = m.relax(1e-5, 40000)
+        U = m.displacements()
+    s = dynamics.ExplicitSolver.from_problem(p)
+    n_ref, r_ref, ok = s.relax(1e-5, 40000, check_every=50)
+    assert ok and r <= 1e-5
+    assert abs(steps - n_ref) <= 100
+    assert rel_linf(U, s.U) < 1e-3
+
+
+def test_full_size_cfg2b_sampled_nodes(B):
+    """1.23M-tet cube (59^3 x 6) as timed by the benchmark: forces and one update at
+    sampled nodes against the oracle, which evaluates only their incident elements."""
+    p = W.cube_shear(W.TET4, 59, n_steps=5000)
+    rng = np.random.default_rng(0)
+    with B.Mesh(p) as m:
+        m.run(200)
+        U0 = m.displacements()
+        m.step()
+        U1 = m.displacements()
+        m.step()
+        U2 = m.displacements()
+        dt = m.dt
+    assert np.abs(U2).max() > 0
+    sample = rng.choice(p.n_nodes, size=64, replace=False)
+    for i in sample:
+        els = np.nonzero((p.conn == i).any(axis=1))[0]
+        sub = W.Problem(name="sub", elem_type=4, X=p.X, conn=p.conn[els], model=p.model[els],
+                        mu=p.mu[els], kappa=p.kappa[els], rho=p.rho[els], eta_a=p.eta_a[els],
+                        eta_b=p.eta_b[els], c01=p.c01[els], a_dir=p.a_dir[els], b_dir=p.b_dir[els],
+                        bc_dof=np.zeros(0, dtype=np.int64), bc_target=np.zeros(0))
+        mdl = dynamics.Model.from_problem(sub)
+        F = mdl.internal_forces(U1)[i]
+        a_i = 2 * dt * dt / (2 * mdl.mass[i])
+        U2_ref = -a_i * F + 2 * U1[i] - U0[i]
+        pres = np.isin(3 * i + np.arange(3), p.bc_dof)
+        if pres.all():
+            continue
+        scale = np.abs(U2 - U1).max()
+        err = np.abs(U2[i] - U2_ref)[~pres].max()
+        assert err <= 1e-4 * scale + 1e-6 * np.abs(U2).max(), (i, err, scale)
