@@ -42,7 +42,8 @@ def test_tet4_forces_match_oracle(B, model, renumber):
     # 6 * 7^3 = 2058 elements: several 256-thread tiles plus a ragged tail
     p = W.random_tet_mesh_problem(2058, seed=11 + model, model=model)
     rng = np.random.default_rng(5)
-    U = rng.normal(size=(p.n_nodes, 3)) * 0.02
+    # nodal noise of 0.5 % of the box size: strains of a few percent, no inversion
+    U = rng.normal(size=(p.n_nodes, 3)) * 0.005
     with B.Mesh(p, renumber=renumber) as m:
         F = m.internal_forces(U)
     ref = dynamics.Model.from_problem(p).internal_forces(U)
@@ -54,7 +55,7 @@ def test_hex8_forces_match_oracle(B, model):
     p = W.random_hex_mesh_problem(9, seed=21 + model, model=model)  # 729 bricks, ragged
     p.hg_coeff = 0.15
     rng = np.random.default_rng(6)
-    U = rng.normal(size=(p.n_nodes, 3)) * 0.01
+    U = rng.normal(size=(p.n_nodes, 3)) * 0.004
     with B.Mesh(p) as m:
         F = m.internal_forces(U)
     ref = dynamics.Model.from_problem(p).internal_forces(U)
@@ -120,13 +121,15 @@ def test_hex8_trajectory_shear(B):
 
 
 def test_anisotropic_ellipsoid_damped(B):
-    p = W.ellipsoid_tet4(h=7e-3, seed=3)
+    # coarse (7 mm) version of the brain-sized ellipsoid: surface patches cover only a
+    # few nodes, so the patch displacements are scaled down to keep elements valid
+    p = W.ellipsoid_tet4(h=7e-3, seed=3, disp_range=(1e-3, 3e-3))
     p.alpha = 5.0
-    p.ramp_steps = 400
+    p.ramp_steps = 500
     with B.Mesh(p) as m:
-        m.run(600)
+        m.run(700)
         U = m.displacements()
-    ref = dynamics.ExplicitSolver.from_problem(p).run(600)
+    ref = dynamics.ExplicitSolver.from_problem(p).run(700)
     assert rel_linf(U, ref) < DISP_TOL
 
 
