@@ -41,15 +41,30 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
 
-# Algorithmic bytes per element-update, T4 neo-Hookean (FP32 / int32), from the
-# per-term model of the design: element side and node side of each kernel.
-#   force kernel : connectivity 16 + element table 68 (0J 36, P 24, kappa 0V 4,
-#                  1/det 0J 4) + element-force write 48 (4 nodes x 12 B)
-#                  + u^n read once per node 16 N/E
-#   update kernel: element-force read 48 + gather index 16 (4 B per slot)
-#                  + node state 64 N/E (U^n, U^n-U^n-1 read and written, 16 B each)
-BYTES_FORCE_T4_NH = dict(elem=16 + 68 + 48, node=16)
-BYTES_UPDATE_T4_NH = dict(elem=48 + 16, node=64)
+# Algorithmic bytes per element-update (FP32 / int32 / uint16), from the per-term
+# model of the design.  Forces count 12 useful bytes per
+# (x, y, z) record; node state is U^n and U^n - U^n-1, read and written (64 B).
+#   tiled assembly (default)
+#     force kernel : local connectivity 2 n_e + element table 4 n_consts
+#                    + local slot index 2 n_e
+#                    + per partial (P / E): node id 4 + local offsets 2 + force 12
+#                    + u^n read once per node 16 N / E
+#     update kernel: per partial: gather index 4 + force 12; node state 64 N / E
+#   slot assembly
+#     force kernel : connectivity 4 n_e + table 4 n_consts + forces 12 n_e + u^n 16 N / E
+#     update kernel: forces 12 n_e + gather index 4 n_e + node state 64 N / E
+def algorithmic_bytes(info, n_nodes):
+    E = float(info.n_elems)
+    ne = info.elem_type
+    nE = n_nodes / E
+    if info.assembly == 1:
+        pE = info.n_parts / E
+        force = 2 * ne + 4 * info.n_consts + 2 * ne + (4 + 2 + 12) * pE + 16 * nE
+        update = (4 + 12) * pE + 64 * nE
+    else:
+        force = 4 * ne + 4 * info.n_consts + 12 * ne + 16 * nE
+        update = 12 * ne + 4 * ne + 64 * nE
+    return force * E, update * E
 
 
 def workload(name):
@@ -216,6 +231,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-also", action="store_true", help="skip the secondary hex8 workload")
+    ap.add_argument("--assembly", type=int, default=1, help="1 tiles (default), 0 element slots")
+    ap.add_argument("--tile-size", type=int, default=0)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -239,7 +256,8 @@ def main():
     from paper_2106_14189_gb300 import binding as B
 
     p, desc = workload(args.workload)
-    mesh = B.Mesh(p)
+    mesh = B.Mesh(p, assembly=args.assembly, tile_size=args.tile_size)
+    minfo = mesh.info()
     stream = torch.cuda.current_stream()
     # warm-up
     mesh.run(args.warmup, stream)
@@ -273,9 +291,7 @@ def main():
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peak()
-    ne_ratio = N / E
-    force_bytes = (BYTES_FORCE_T4_NH["elem"] + BYTES_FORCE_T4_NH["node"] * ne_ratio) * E
-    update_bytes = (BYTES_UPDATE_T4_NH["elem"] + BYTES_UPDATE_T4_NH["node"] * ne_ratio) * E
+    force_bytes, update_bytes = algorithmic_bytes(minfo, N)
     t_force = ms_force * 1e-3 / args.steps
     t_update = ms_update * 1e-3 / args.steps
     dominant = "force" if t_force >= t_update else "update"
@@ -291,7 +307,8 @@ def main():
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"force_tet4 (NH)" if dominant == "force" else "node gather-update",
+                "kernel": ("element force (" + ("tiles" if minfo.assembly == 1 else "slots") + ")")
+                if dominant == "force" else "node gather-update",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_dom,
                 "step": {"bytes_per_element_update": (force_bytes + update_bytes) / E,
@@ -322,7 +339,7 @@ def main():
     also = None
     if args.workload == "tet4_cube59" and world == 1 and not args.no_also:
         ph, desch = workload("hex8_cube64")
-        mh = B.Mesh(ph)
+        mh = B.Mesh(ph, assembly=args.assembly)
         mh.run(args.warmup, stream)
         mh.sync(stream)
         kh = max(1000, args.steps // 2)
@@ -353,6 +370,8 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": desc, "elements": E, "nodes": N,
                            "parallelism": f"replicas x{world}",
+                           "assembly": "tiles" if minfo.assembly == 1 else "slots",
+                           "tile_size": minfo.tile_size,
                            "l2": "working set ~215 MB > 129 MB L2 (no flush needed)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps, "also": also,

@@ -72,7 +72,15 @@ typedef struct dj_mesh dj_mesh;
  *                     DJ_RAMP_SMOOTH: s = 10 tau^3 - 15 tau^4 + 6 tau^5.
  *   relax_check_every residual check interval of dj_relax_to_tol (default 100).
  *   renumber          1 (default): reorder nodes and elements along a Morton
- *                     curve for locality; 0: keep the caller's order. */
+ *                     curve for locality; 0: keep the caller's order.
+ *   assembly          how element forces reach the nodes (sum in Eq. 13), both
+ *                     deterministic: 1 (default) tiles -- each block of
+ *                     tile_size consecutive elements sums its forces per node in
+ *                     shared memory and the node update gathers one partial per
+ *                     (tile, node); 0 slots -- every element writes one force per
+ *                     node and the node update gathers all of them.
+ *   tile_size         elements per tile, a multiple of 32 (T4 <= 512, H8 <= 256);
+ *                     0 selects 256 (T4) / 128 (H8). */
 typedef struct {
   double dt;
   double dt_scale;
@@ -82,6 +90,8 @@ typedef struct {
   int ramp_kind;
   int relax_check_every;
   int renumber;
+  int assembly;
+  int tile_size;
   int reserved;
 } dj_params;
 
@@ -97,6 +107,11 @@ typedef struct {
   long long slot_bytes_per_elem;        /* bytes of element-force slots written per step */
   long long gather_index_bytes;         /* bytes of the node gather index */
   long long node_bytes_per_node;        /* bytes of node state read + written per step */
+  long long n_parts;        /* tiled assembly: number of (tile, node) partial forces */
+  int assembly;             /* assembly in use (see dj_params) */
+  int tile_size;            /* elements per tile (tiled assembly) */
+  int n_consts;             /* floats per element in the element table */
+  int reserved;
 } dj_info;
 
 /* Fill *p with the defaults listed above. */

@@ -70,6 +70,15 @@ struct dj_mesh {
   int threads_force = 256;
   long long device_bytes = 0;
   long long sell_entries = 0;
+  // tiled assembly
+  int assembly = ASSEMBLY_TILES, T = 0, n_tiles = 0, smem_nodes = 0;
+  long long n_parts = 0;
+  int* d_tile_ptr = nullptr;
+  int* d_tile_nodes = nullptr;
+  unsigned short* d_lconn = nullptr;
+  unsigned short* d_lptr = nullptr;
+  unsigned short* d_lidx = nullptr;
+  float4* d_parts = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t run_exec = nullptr;
   int run_chunk = 0;
@@ -123,10 +132,15 @@ void release_device(dj_mesh* m) {
   if (m->relax_exec) cudaGraphExecDestroy(m->relax_exec);
   m->run_exec = m->relax_exec = nullptr;
   m->run_chunk = m->relax_k = 0;
-  void* ptrs[] = {m->d_conn, m->d_consts, m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U, m->d_V,
-                  m->d_bct,  m->d_R,      m->d_fout,  m->d_perm, m->d_state,     m->d_partials};
+  void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
+                  m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
+                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx,
+                  m->d_parts};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  m->d_tile_ptr = m->d_tile_nodes = nullptr;
+  m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
+  m->d_parts = nullptr;
   if (m->h_state) cudaFreeHost(m->h_state);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   m->d_conn = nullptr;
@@ -210,6 +224,23 @@ dj_status check_flags(dj_mesh* m) {
   return DJ_OK;
 }
 
+// Sliced ELL (chunks of SELL_C rows, column-major, -1 padding) of CSR lists.
+void build_sell(const std::vector<int>& ptr, const std::vector<int>& idx, long long N,
+                std::vector<int>& chunk_ptr, std::vector<int>& sell) {
+  const long long n_chunks = (N + SELL_C - 1) / SELL_C;
+  chunk_ptr.assign(n_chunks + 1, 0);
+  for (long long c = 0; c < n_chunks; ++c) {
+    int w = 0;
+    for (long long i = c * SELL_C; i < std::min(N, (c + 1) * SELL_C); ++i) w = std::max(w, ptr[i + 1] - ptr[i]);
+    chunk_ptr[c + 1] = chunk_ptr[c] + w * SELL_C;
+  }
+  sell.assign(chunk_ptr[n_chunks], -1);
+  for (long long i = 0; i < N; ++i) {
+    const long long c = i / SELL_C, lane = i % SELL_C;
+    for (int j = 0; j < ptr[i + 1] - ptr[i]; ++j) sell[chunk_ptr[c] + j * SELL_C + lane] = idx[ptr[i] + j];
+  }
+}
+
 ForceArgs force_args(dj_mesh* m, int advance) {
   ForceArgs a;
   a.conn = m->d_conn;
@@ -229,11 +260,30 @@ ForceArgs force_args(dj_mesh* m, int advance) {
   return a;
 }
 
+TileArgs tile_args(dj_mesh* m) {
+  TileArgs t;
+  t.tile_ptr = m->d_tile_ptr;
+  t.tile_nodes = m->d_tile_nodes;
+  t.lconn = m->d_lconn;
+  t.lptr = m->d_lptr;
+  t.lidx = m->d_lidx;
+  t.partials = m->d_parts;
+  t.T = m->T;
+  t.smem_nodes = m->smem_nodes;
+  return t;
+}
+
+cudaError_t launch_force_any(dj_mesh* m, int advance, cudaStream_t s) {
+  if (m->assembly == ASSEMBLY_TILES)
+    return launch_force_tiled(m->elem_type, m->variant, force_args(m, advance), tile_args(m), m->n_tiles, s);
+  return launch_force(m->elem_type, m->variant, force_args(m, advance), m->threads_force, s);
+}
+
 NodeArgs node_args(dj_mesh* m) {
   NodeArgs a;
   a.sell = m->d_sell;
   a.chunk_ptr = m->d_chunk_ptr;
-  a.slots = m->d_slots;
+  a.slots = m->assembly == ASSEMBLY_TILES ? m->d_parts : m->d_slots;
   a.U = m->d_U;
   a.V = m->d_V;
   a.bct = m->d_bct;
@@ -247,7 +297,7 @@ NodeArgs node_args(dj_mesh* m) {
 }
 
 cudaError_t launch_step(dj_mesh* m, cudaStream_t s, int mode) {
-  cudaError_t e = launch_force(m->elem_type, m->variant, force_args(m, 1), m->threads_force, s);
+  cudaError_t e = launch_force_any(m, 1, s);
   if (e != cudaSuccess) return e;
   e = launch_node(mode, node_args(m), s);
   if (e != cudaSuccess) return e;
@@ -295,6 +345,8 @@ void dj_params_default(dj_params* p) {
   p->ramp_kind = DJ_RAMP_SMOOTH;
   p->relax_check_every = 100;
   p->renumber = 1;
+  p->assembly = ASSEMBLY_TILES;
+  p->tile_size = 0;
 }
 
 const char* dj_status_string(dj_status s) {
@@ -430,8 +482,14 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   else
     dj_params_default(&prm);
   if (!(prm.dt_scale > 0) || !(prm.alpha >= 0) || !(prm.hg_coeff >= 0) || prm.relax_check_every <= 0 ||
-      (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt))
+      (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt) ||
+      (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES))
     return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
+  {
+    const int tmax = m->ne == 4 ? 512 : 256;
+    if (prm.tile_size < 0 || prm.tile_size % 32 != 0 || prm.tile_size > tmax)
+      return fail(m, DJ_ERR_INVALID_ARG, "tile_size must be a multiple of 32 and <= %d", tmax);
+  }
   int dev = 0;
   CK(cudaGetDevice(&dev));
   release_device(m);
@@ -504,17 +562,55 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   std::vector<int> csr(cn.size()), fillp(cnt.begin(), cnt.end() - 1);
   for (long long e = 0; e < E; ++e)
     for (int b = 0; b < ne; ++b) csr[fillp[cn[e * ne + b]]++] = b * E_pad + (int)e;
-  const long long n_chunks = (N + SELL_C - 1) / SELL_C;
-  std::vector<int> chunk_ptr(n_chunks + 1, 0);
-  for (long long c = 0; c < n_chunks; ++c) {
-    int w = 0;
-    for (long long i = c * SELL_C; i < std::min(N, (c + 1) * SELL_C); ++i) w = std::max(w, cnt[i + 1] - cnt[i]);
-    chunk_ptr[c + 1] = chunk_ptr[c] + w * SELL_C;
-  }
-  std::vector<int> sell(chunk_ptr[n_chunks], -1);
-  for (long long i = 0; i < N; ++i) {
-    const long long c = i / SELL_C, lane = i % SELL_C;
-    for (int j = 0; j < cnt[i + 1] - cnt[i]; ++j) sell[chunk_ptr[c] + j * SELL_C + lane] = csr[cnt[i] + j];
+  std::vector<int> chunk_ptr, sell;
+  build_sell(cnt, csr, N, chunk_ptr, sell);  // node -> element slots (lumped mass, slot assembly)
+  m->assembly = prm.assembly;
+  std::vector<int> tile_ptr, tile_nodes, part_chunk_ptr, part_sell;
+  std::vector<unsigned short> lconn, lptr, lidx;
+  if (m->assembly == ASSEMBLY_TILES) {
+    const int T = prm.tile_size > 0 ? prm.tile_size : (ne == 4 ? 256 : 128);
+    m->T = T;
+    m->n_tiles = (int)((E + T - 1) / T);
+    tile_ptr.assign(m->n_tiles + 1, 0);
+    lconn.assign((size_t)E_pad * ne, 0);
+    lidx.assign((size_t)m->n_tiles * T * ne, 0);
+    int smax = 0;
+    std::vector<int> loc;
+    for (int t = 0; t < m->n_tiles; ++t) {
+      const long long e0 = (long long)t * T, e1 = std::min(E, e0 + T);
+      loc.assign(cn.begin() + e0 * ne, cn.begin() + e1 * ne);
+      std::sort(loc.begin(), loc.end());
+      loc.erase(std::unique(loc.begin(), loc.end()), loc.end());
+      const int n_t = (int)loc.size();
+      smax = std::max(smax, n_t);
+      tile_ptr[t + 1] = tile_ptr[t] + n_t;
+      tile_nodes.insert(tile_nodes.end(), loc.begin(), loc.end());
+      // local connectivity and the per-node slot lists (ascending element, then local node)
+      std::vector<int> kcnt(n_t + 1, 0);
+      for (long long e = e0; e < e1; ++e)
+        for (int b = 0; b < ne; ++b) {
+          const int k = (int)(std::lower_bound(loc.begin(), loc.end(), cn[e * ne + b]) - loc.begin());
+          lconn[e * ne + b] = (unsigned short)k;
+          kcnt[k + 1]++;
+        }
+      for (int k = 0; k < n_t; ++k) kcnt[k + 1] += kcnt[k];
+      for (int k = 0; k <= n_t; ++k) lptr.push_back((unsigned short)kcnt[k]);
+      std::vector<int> fillk(kcnt.begin(), kcnt.end() - 1);
+      for (long long e = e0; e < e1; ++e)
+        for (int b = 0; b < ne; ++b) {
+          const int k = lconn[e * ne + b];
+          lidx[(size_t)t * T * ne + fillk[k]++] = (unsigned short)(b * T + (int)(e - e0));
+        }
+    }
+    m->smem_nodes = smax;
+    m->n_parts = tile_ptr[m->n_tiles];
+    // node -> partial ids, ascending tile
+    std::vector<int> pc(N + 1, 0);
+    for (int v : tile_nodes) pc[v + 1]++;
+    for (long long i = 0; i < N; ++i) pc[i + 1] += pc[i];
+    std::vector<int> plist(tile_nodes.size()), pf(pc.begin(), pc.end() - 1);
+    for (size_t q = 0; q < tile_nodes.size(); ++q) plist[pf[tile_nodes[q]]++] = (int)q;
+    build_sell(pc, plist, N, part_chunk_ptr, part_sell);
   }
   m->sell_entries = (long long)sell.size();
   // ---- prescribed nodes ----------------------------------------------------
@@ -546,12 +642,41 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   CK(cudaMemset(m->d_conn, 0, conn4_count * sizeof(int4)));
   CK(dalloc(m, &m->d_consts, (size_t)nc * E_pad));
   CK(cudaMemset(m->d_consts, 0, (size_t)nc * E_pad * sizeof(float)));
-  CK(dalloc(m, &m->d_slots, (size_t)ne * E_pad));
-  CK(cudaMemset(m->d_slots, 0, (size_t)ne * E_pad * sizeof(float4)));
-  CK(dalloc(m, &m->d_sell, sell.size() + 1));
-  CK(cudaMemcpy(m->d_sell, sell.data(), sell.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CK(dalloc(m, &m->d_chunk_ptr, chunk_ptr.size()));
-  CK(cudaMemcpy(m->d_chunk_ptr, chunk_ptr.data(), chunk_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  int* d_mass_sell = nullptr;  // node -> element slots, for the lumped mass (tiled mode)
+  int* d_mass_chunk = nullptr;
+  if (m->assembly == ASSEMBLY_SLOTS) {
+    CK(dalloc(m, &m->d_slots, (size_t)ne * E_pad));
+    CK(cudaMemset(m->d_slots, 0, (size_t)ne * E_pad * sizeof(float4)));
+    CK(dalloc(m, &m->d_sell, sell.size() + 1));
+    CK(cudaMemcpy(m->d_sell, sell.data(), sell.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_chunk_ptr, chunk_ptr.size()));
+    CK(cudaMemcpy(m->d_chunk_ptr, chunk_ptr.data(), chunk_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    d_mass_sell = m->d_sell;
+    d_mass_chunk = m->d_chunk_ptr;
+  } else {
+    CK(dalloc(m, &m->d_tile_ptr, tile_ptr.size()));
+    CK(cudaMemcpy(m->d_tile_ptr, tile_ptr.data(), tile_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_tile_nodes, tile_nodes.size()));
+    CK(cudaMemcpy(m->d_tile_nodes, tile_nodes.data(), tile_nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_lconn, lconn.size()));
+    CK(cudaMemcpy(m->d_lconn, lconn.data(), lconn.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_lptr, lptr.size()));
+    CK(cudaMemcpy(m->d_lptr, lptr.data(), lptr.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_lidx, lidx.size()));
+    CK(cudaMemcpy(m->d_lidx, lidx.data(), lidx.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_parts, (size_t)m->n_parts));
+    CK(cudaMemset(m->d_parts, 0, (size_t)m->n_parts * sizeof(float4)));
+    CK(dalloc(m, &m->d_sell, part_sell.size() + 1));
+    CK(cudaMemcpy(m->d_sell, part_sell.data(), part_sell.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_chunk_ptr, part_chunk_ptr.size()));
+    CK(cudaMemcpy(m->d_chunk_ptr, part_chunk_ptr.data(), part_chunk_ptr.size() * sizeof(int),
+                  cudaMemcpyHostToDevice));
+    m->sell_entries = (long long)part_sell.size();
+    CK(cudaMalloc(&d_mass_sell, (sell.size() + 1) * sizeof(int)));
+    CK(cudaMemcpy(d_mass_sell, sell.data(), sell.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&d_mass_chunk, chunk_ptr.size() * sizeof(int)));
+    CK(cudaMemcpy(d_mass_chunk, chunk_ptr.data(), chunk_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
   CK(dalloc(m, &m->d_U, N));
   CK(dalloc(m, &m->d_V, N));
   CK(dalloc(m, &m->d_fout, N));
@@ -601,6 +726,11 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
       void* ps[] = {dX, dmu, dka, drh, dea, deb, dc1, dad, dbd, dem, ddt, dmass, dred, dmo, dcn, dbad, dbc};
       for (void* q : ps)
         if (q) cudaFree(q);
+      if (m->assembly == ASSEMBLY_TILES) {
+        if (d_mass_sell) cudaFree(d_mass_sell);
+        if (d_mass_chunk) cudaFree(d_mass_chunk);
+        d_mass_sell = d_mass_chunk = nullptr;
+      }
     };
 #define CKP(call)                                                                   \
   do {                                                                              \
@@ -699,7 +829,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     }
     const double adt = prm.alpha * m->dt;
     m->bm1 = (float)((2.0 - adt) / (2.0 + adt));
-    CKP(launch_node_mass(m->d_sell, m->d_chunk_ptr, dem, E_pad, (int)N, m->dt, prm.alpha, dbc, dmass, m->d_U,
+    CKP(launch_node_mass(d_mass_sell, d_mass_chunk, dem, E_pad, (int)N, m->dt, prm.alpha, dbc, dmass, m->d_U,
                          m->d_V, 0));
     std::vector<double> mass(N);
     CKP(cudaMemcpy(mass.data(), dmass, N * sizeof(double), cudaMemcpyDeviceToHost));
@@ -782,27 +912,41 @@ dj_status dj_run_n_profiled(dj_mesh* m, long long n, void* stream, double* ms_fo
   if (s) return s;
   if (n < 0) return fail(m, DJ_ERR_INVALID_ARG, "n < 0");
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<cudaEvent_t> ev(2 * n + 1);
+  // steps captured into graphs of up to 256 steps with an event between every
+  // two kernels, so that launch gaps do not enter the per-kernel times
+  const long long chunk = 256;
+  std::vector<cudaEvent_t> ev(2 * chunk + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
-  dj_status rs = DJ_OK;
-  cudaError_t err = cudaEventRecord(ev[0], st);
-  for (long long k = 0; k < n && err == cudaSuccess; ++k) {
-    err = launch_force(m->elem_type, m->variant, force_args(m, 1), m->threads_force, st);
-    if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 1], st);
-    if (err == cudaSuccess) err = launch_node(NODE_UPDATE, node_args(m), st);
-    if (err == cudaSuccess) err = cudaEventRecord(ev[2 * k + 2], st);
-  }
-  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
   double tf = 0, tu = 0;
-  for (long long k = 0; k < n && err == cudaSuccess; ++k) {
-    float a = 0, b = 0;
-    err = cudaEventElapsedTime(&a, ev[2 * k], ev[2 * k + 1]);
-    if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[2 * k + 1], ev[2 * k + 2]);
-    tf += a;
-    tu += b;
+  dj_status rs = DJ_OK;
+  for (long long done = 0; done < n && rs == DJ_OK;) {
+    const long long k = std::min(chunk, n - done);
+    cudaGraphExec_t exec = nullptr;
+    rs = capture(m, &exec, [&](cudaStream_t cs) {
+      cudaError_t err = cudaEventRecord(ev[0], cs);
+      for (long long j = 0; j < k && err == cudaSuccess; ++j) {
+        err = launch_force_any(m, 1, cs);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * j + 1], cs);
+        if (err == cudaSuccess) err = launch_node(NODE_UPDATE, node_args(m), cs);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * j + 2], cs);
+      }
+      return err;
+    });
+    if (rs) break;
+    cudaError_t err = cudaGraphLaunch(exec, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    for (long long j = 0; j < k && err == cudaSuccess; ++j) {
+      float a = 0, b = 0;
+      err = cudaEventElapsedTime(&a, ev[2 * j], ev[2 * j + 1]);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[2 * j + 1], ev[2 * j + 2]);
+      tf += a;
+      tu += b;
+    }
+    cudaGraphExecDestroy(exec);
+    if (err != cudaSuccess) rs = fail(m, DJ_ERR_CUDA, "profiled run: %s", cudaGetErrorString(err));
+    done += k;
   }
   for (auto& e : ev) cudaEventDestroy(e);
-  if (err != cudaSuccess) rs = fail(m, DJ_ERR_CUDA, "profiled run: %s", cudaGetErrorString(err));
   if (ms_force) *ms_force = tf;
   if (ms_update) *ms_update = tu;
   return rs;
@@ -927,7 +1071,7 @@ dj_status dj_internal_forces(dj_mesh* m, const double* U, double* F_out) {
     Un[i] = make_float4((float)U[o], (float)U[o + 1], (float)U[o + 2], save[i].w);
   }
   CK(cudaMemcpy(m->d_U, Un.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
-  CK(launch_force(m->elem_type, m->variant, force_args(m, 0), m->threads_force, 0));
+  CK(launch_force_any(m, 0, 0));
   NodeArgs na = node_args(m);
   na.R = nullptr;
   CK(launch_node(NODE_FORCE_ONLY, na, 0));
@@ -1016,10 +1160,19 @@ dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
   info->dt_crit = m->dt_crit;
   info->total_mass = m->total_mass;
   info->device_bytes = m->device_bytes;
-  info->elem_table_bytes_per_elem = (long long)m->n_consts * 4 + 4 * m->ne;
-  info->slot_bytes_per_elem = 16LL * m->ne;
+  if (m->assembly == ASSEMBLY_TILES) {
+    info->elem_table_bytes_per_elem = (long long)m->n_consts * 4 + 2 * m->ne;
+    info->slot_bytes_per_elem = 16 * m->n_parts / std::max(1LL, m->E);
+  } else {
+    info->elem_table_bytes_per_elem = (long long)m->n_consts * 4 + 4 * m->ne;
+    info->slot_bytes_per_elem = 16LL * m->ne;
+  }
   info->gather_index_bytes = m->sell_entries * 4;
   info->node_bytes_per_node = 64;
+  info->n_parts = m->n_parts;
+  info->assembly = m->assembly;
+  info->tile_size = m->T;
+  info->n_consts = m->n_consts;
   return DJ_OK;
 }
 

@@ -68,7 +68,23 @@ struct NodeArgs {
   float bm1;              // b - 1 = (2 - alpha dt) / (2 + alpha dt)
 };
 
+// Tiled assembly: a tile is the T consecutive (Morton-ordered) elements of one
+// block.  Its unique nodes are staged in shared memory, the element forces are
+// summed per unique node inside the tile in a fixed order, and one partial force
+// per (tile, node) is written; the node kernel gathers those partials.
+struct TileArgs {
+  const int* tile_ptr;          // n_tiles + 1: first partial of each tile
+  const int* tile_nodes;        // per partial: internal node id
+  const unsigned short* lconn;  // per element n_e local node indices (element-major)
+  const unsigned short* lptr;   // per tile n_t + 1 offsets (tile t starts at tile_ptr[t] + t)
+  const unsigned short* lidx;   // per tile T n_e local slots a * T + e_local, grouped by node
+  float4* partials;             // per (tile, node) force
+  int T;
+  int smem_nodes;               // capacity of the staged-node array
+};
+
 enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2 };
+enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1 };
 
 constexpr int NODE_THREADS = 256;
 constexpr int SELL_C = 32;
@@ -76,6 +92,8 @@ constexpr int SELL_C = 32;
 // kernels_step.cu
 cudaError_t launch_force(int elem_type, int variant, const ForceArgs& a, int threads,
                          cudaStream_t s);
+cudaError_t launch_force_tiled(int elem_type, int variant, const ForceArgs& a, const TileArgs& t,
+                               int n_tiles, cudaStream_t s);
 cudaError_t launch_node(int mode, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
 

@@ -83,13 +83,56 @@ __device__ __forceinline__ void add_tJT_sym(M3& acc, const M3& tJ, const float* 
     }
 }
 
+// Per-element constants of the table, loaded once into registers.
 template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const float* __restrict__ c, int E_pad,
-                                              int e, const ForceArgs& a, bool& bad) {
+struct ElemConsts {
+  float J0[3][3];
+  float P[6];
+  float kV, r0;
+  float Qa[FA ? 6 : 1], sa;
+  float Qb[FB ? 6 : 1], sb;
+  float gm;
+
+  __device__ __forceinline__ void load(const float* __restrict__ c, int E_pad, int e,
+                                       const ForceArgs& a) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) J0[i][j] = ldg_stream(c + (size_t)(K_J0 + 3 * i + j) * E_pad + e);
+    load_sym(c, K_P, E_pad, e, P);
+    kV = ldg_stream(c + (size_t)K_KV * E_pad + e);
+    r0 = ldg_stream(c + (size_t)K_R0 * E_pad + e);
+    if (FA) {
+      load_sym(c, a.off_fa, E_pad, e, Qa);
+      sa = ldg_stream(c + (size_t)(a.off_fa + 6) * E_pad + e);
+    }
+    if (FB) {
+      load_sym(c, a.off_fb, E_pad, e, Qb);
+      sb = ldg_stream(c + (size_t)(a.off_fb + 6) * E_pad + e);
+    }
+    if (MR) gm = ldg_stream(c + (size_t)a.off_mr * E_pad + e);
+  }
+};
+
+// Hourglass constants of a brick: c_{alpha j} = h_alpha . X_j and k.
+struct HgConsts {
+  float cc[4][3];
+  float k;
+  __device__ __forceinline__ void load(const float* __restrict__ c, int E_pad, int e, int off) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cc[q][j] = ldg_stream(c + (size_t)(off + 3 * q + j) * E_pad + e);
+    k = ldg_stream(c + (size_t)(off + 12) * E_pad + e);
+  }
+};
+
+// F = J^-2/3 tJ^T (P + psi_a Q_a + psi_b Q_b + MR) + coefficient * adj(tJ)   (Table 3)
+template <bool FA, bool FB, bool MR>
+__device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA, FB, MR>& k,
+                                              bool& bad) {
   const float D = det3(tJ);
-  const float r0 = ldg_stream(c + (size_t)K_R0 * E_pad + e);
-  const float kV = ldg_stream(c + (size_t)K_KV * E_pad + e);
-  const float J = D * r0;  // Eq. 12
+  const float J = D * k.r0;  // Eq. 12
   bad = !(D > 0.f);
   const float rc = rcbrtf(J);
   const float Jm23 = rc * rc;  // J^-2/3
@@ -102,66 +145,56 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const float* __restr
   g[4] = tJ.m[0][0] * tJ.m[2][0] + tJ.m[0][1] * tJ.m[2][1] + tJ.m[0][2] * tJ.m[2][2];
   g[5] = tJ.m[1][0] * tJ.m[2][0] + tJ.m[1][1] * tJ.m[2][1] + tJ.m[1][2] * tJ.m[2][2];
 
-  float P[6];
-  load_sym(c, K_P, E_pad, e, P);
-  const float gP = frob_sym(g, P);  // = mu 0V I1
+  const float gP = frob_sym(g, k.P);  // = mu 0V I1
   M3 T;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
-  float Sdev = 1.f;                 // weight of tJ^T P
-  float vol_over_D = -gP / 3.f;     // multiplies Jm23 adj / D
+  float vol_over_D = -gP / 3.f;  // multiplies Jm23 adj / D
   if (FA) {
-    float Q[6];
-    load_sym(c, a.off_fa, E_pad, e, Q);
-    const float sa = ldg_stream(c + (size_t)(a.off_fa + 6) * E_pad + e);
-    const float gQ = frob_sym(g, Q);
-    const float psi = Jm23 * gQ * sa - 1.f;  // I4bar - 1 (Eq. 31, Table 1)
-    add_tJT_sym(T, tJ, Q, psi);
+    const float gQ = frob_sym(g, k.Qa);
+    const float psi = Jm23 * gQ * k.sa - 1.f;  // I4bar - 1 (Eq. 31, Table 1)
+    add_tJT_sym(T, tJ, k.Qa, psi);
     vol_over_D -= psi * gQ / 3.f;
   }
   if (FB) {
-    float Q[6];
-    load_sym(c, a.off_fb, E_pad, e, Q);
-    const float sb = ldg_stream(c + (size_t)(a.off_fb + 6) * E_pad + e);
-    const float gQ = frob_sym(g, Q);
-    const float psi = Jm23 * gQ * sb - 1.f;  // I6bar - 1 (Eq. 32)
-    add_tJT_sym(T, tJ, Q, psi);
+    const float gQ = frob_sym(g, k.Qb);
+    const float psi = Jm23 * gQ * k.sb - 1.f;  // I6bar - 1 (Eq. 32)
+    add_tJT_sym(T, tJ, k.Qb, psi);
     vol_over_D -= psi * gQ / 3.f;
   }
-  add_tJT_sym(T, tJ, P, Sdev);
+  add_tJT_sym(T, tJ, k.P, 1.f);
   float mr_vol = 0.f;
   if (MR) {
     // C01 g_hat^T I2m = gm (g:P P - P g P), gm = C01 / (2 C10^2 0V)   (Eq. 39-42)
-    const float gm = ldg_stream(c + (size_t)a.off_mr * E_pad + e);
     float Pg[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        Pg[i][j] = sym_at(P, i, 0) * sym_at(g, 0, j) + sym_at(P, i, 1) * sym_at(g, 1, j) +
-                   sym_at(P, i, 2) * sym_at(g, 2, j);
+        Pg[i][j] = sym_at(k.P, i, 0) * sym_at(g, 0, j) + sym_at(k.P, i, 1) * sym_at(g, 1, j) +
+                   sym_at(k.P, i, 2) * sym_at(g, 2, j);
     float S2[6];
     const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const int i = ii[k], j = jj[k];
-      const float PgP = Pg[i][0] * sym_at(P, 0, j) + Pg[i][1] * sym_at(P, 1, j) +
-                        Pg[i][2] * sym_at(P, 2, j);
-      S2[k] = gm * (gP * sym_at(P, i, j) - PgP);
+    for (int q = 0; q < 6; ++q) {
+      const int i = ii[q], j = jj[q];
+      const float PgP = Pg[i][0] * sym_at(k.P, 0, j) + Pg[i][1] * sym_at(k.P, 1, j) +
+                        Pg[i][2] * sym_at(k.P, 2, j);
+      S2[q] = k.gm * (gP * sym_at(k.P, i, j) - PgP);
     }
     float trPgPg = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
-    add_tJT_sym(T, tJ, S2, Jm23);                      // extra J^-2/3 of Eq. 39
-    mr_vol = -Jm23 * Jm23 * gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
+    add_tJT_sym(T, tJ, S2, Jm23);                               // extra J^-2/3 of Eq. 39
+    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
   }
   const M3 A = adj3(tJ);
   const float invD = 1.f / D;
-  const float ca = (Jm23 * vol_over_D + mr_vol) * invD + kV * (J - 1.f) * r0;
+  const float ca = (Jm23 * vol_over_D + mr_vol) * invD + k.kV * (J - 1.f) * k.r0;
   M3 F;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -196,41 +229,6 @@ __device__ __forceinline__ bool finite3(float x, float y, float z) {
   return isfinite(x) && isfinite(y) && isfinite(z);
 }
 
-template <bool FA, bool FB, bool MR>
-__global__ void __launch_bounds__(256) force_tet4_kernel(ForceArgs a) {
-  advance_clock(a);
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.E) return;
-  const int E_pad = a.E_pad;
-  const float* __restrict__ c = a.consts;
-  const int4 nd = __ldcs(a.conn + e);
-  const float4 u0 = __ldg(a.U + nd.x), u1 = __ldg(a.U + nd.y), u2 = __ldg(a.U + nd.z),
-               u3 = __ldg(a.U + nd.w);
-  // tJ = 0J + H_xi u_e (Eq. 11, Eq. 3 orientation): rows u_b - u_0
-  M3 tJ;
-  const float du[3][3] = {{u1.x - u0.x, u1.y - u0.y, u1.z - u0.z},
-                          {u2.x - u0.x, u2.y - u0.y, u2.z - u0.z},
-                          {u3.x - u0.x, u3.y - u0.y, u3.z - u0.z}};
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) tJ.m[i][j] = ldg_stream(c + (size_t)(K_J0 + 3 * i + j) * E_pad + e) + du[i][j];
-  bool inv;
-  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, c, E_pad, e, a, inv);
-  // nodal forces = F H_xi: node b (1..3) gets column b-1, node 0 minus their sum (Sec. 7)
-  const float4 f1 = make_float4(F.m[0][0], F.m[1][0], F.m[2][0], 0.f);
-  const float4 f2 = make_float4(F.m[0][1], F.m[1][1], F.m[2][1], 0.f);
-  const float4 f3 = make_float4(F.m[0][2], F.m[1][2], F.m[2][2], 0.f);
-  const float4 f0 = make_float4(-(f1.x + f2.x + f3.x), -(f1.y + f2.y + f3.y), -(f1.z + f2.z + f3.z), 0.f);
-  const bool nonfinite = !finite3(f0.x, f0.y, f0.z) || !finite3(f1.x, f1.y, f1.z) ||
-                         !finite3(f2.x, f2.y, f2.z) || !finite3(f3.x, f3.y, f3.z);
-  flag_error(a.st, e, inv, nonfinite && !inv);
-  a.slots[e] = f0;
-  a.slots[(size_t)E_pad + e] = f1;
-  a.slots[(size_t)2 * E_pad + e] = f2;
-  a.slots[(size_t)3 * E_pad + e] = f3;
-}
-
 // natural coordinates of the brick nodes (bottom face CCW, then top face)
 __device__ constexpr float XI8[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
                                         {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
@@ -240,23 +238,39 @@ __device__ constexpr float H8[4][8] = {{1, -1, 1, -1, 1, -1, 1, -1},
                                        {1, -1, -1, 1, -1, 1, 1, -1},
                                        {-1, 1, -1, 1, 1, -1, 1, -1}};
 
+template <int NE>
+struct ElemExtra;
+template <>
+struct ElemExtra<4> {
+  __device__ __forceinline__ void load(const float*, int, int, int) {}
+};
+template <>
+struct ElemExtra<8> : HgConsts {};
+
+// Nodal forces of one T4 element: tJ = 0J + H_xi u (rows u_b - u_0, Eq. 11),
+// F H_xi: node b = 1..3 takes column b-1, node 0 minus their sum (Sec. 7).
 template <bool FA, bool FB, bool MR>
-__global__ void __launch_bounds__(128) force_hex8_kernel(ForceArgs a) {
-  advance_clock(a);
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.E) return;
-  const int E_pad = a.E_pad;
-  const float* __restrict__ c = a.consts;
-  const int4 n0 = __ldcs(a.conn + 2 * (size_t)e), n1 = __ldcs(a.conn + 2 * (size_t)e + 1);
-  const int nid[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
-  float u[8][3];
+__device__ __forceinline__ void tet4_forces(const float (&u)[4][3], const ElemConsts<FA, FB, MR>& k,
+                                            const ElemExtra<4>&, float (&f)[4][3], bool& inv) {
+  M3 tJ;
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    const float4 v = __ldg(a.U + nid[b]);
-    u[b][0] = v.x;
-    u[b][1] = v.y;
-    u[b][2] = v.z;
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) tJ.m[i][j] = k.J0[i][j] + (u[i + 1][j] - u[0][j]);
+  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, k, inv);
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    f[1][j] = F.m[j][0];
+    f[2][j] = F.m[j][1];
+    f[3][j] = F.m[j][2];
+    f[0][j] = -(F.m[j][0] + F.m[j][1] + F.m[j][2]);
   }
+}
+
+// Nodal forces of one 1-point H8 element with hourglass control.
+template <bool FA, bool FB, bool MR>
+__device__ __forceinline__ void hex8_forces(const float (&u)[8][3], const ElemConsts<FA, FB, MR>& k,
+                                            const ElemExtra<8>& hg, float (&f)[8][3], bool& inv) {
   // s_i = (H_xi u)_i = sum_b xi_{b,i} u_b / 8
   float s[3][3];
 #pragma unroll
@@ -273,28 +287,20 @@ __global__ void __launch_bounds__(128) force_hex8_kernel(ForceArgs a) {
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      J0.m[i][j] = ldg_stream(c + (size_t)(K_J0 + 3 * i + j) * E_pad + e);
-      tJ.m[i][j] = J0.m[i][j] + s[i][j];  // Eq. 11
+      J0.m[i][j] = k.J0[i][j];
+      tJ.m[i][j] = k.J0[i][j] + s[i][j];  // Eq. 11
     }
-  bool inv;
-  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, c, E_pad, e, a, inv);
-  // hourglass (1-point H8): q_alpha = gamma_alpha . u, gamma_alpha = h_alpha - sum_j c_aj 0B_j
-  const float r0 = ldg_stream(c + (size_t)K_R0 * E_pad + e);
-  const M3 J0a = adj3(J0);  // 0J^-1 = adj r0
-  float cc[4][3];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) cc[q][j] = ldg_stream(c + (size_t)(a.off_hg + 3 * q + j) * E_pad + e);
-  const float khg = ldg_stream(c + (size_t)(a.off_hg + 12) * E_pad + e);
-  // e_{alpha,i} = sum_j c_{alpha j} (0J^-1)_{j i}
-  float eq[4][3];
+  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, k, inv);
+  // hourglass: q_alpha = gamma_alpha . u, gamma_alpha = h_alpha - sum_j c_aj 0B_j,
+  // 0B = 0J^-1 H_xi with 0J^-1 = adj(0J) / det 0J
+  const M3 J0a = adj3(J0);
+  float eq[4][3];  // e_{alpha,i} = sum_j c_{alpha j} (0J^-1)_{j i}
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
-      eq[q][i] = r0 * (cc[q][0] * J0a.m[0][i] + cc[q][1] * J0a.m[1][i] + cc[q][2] * J0a.m[2][i]);
-  float H[4][3];
+      eq[q][i] = k.r0 * (hg.cc[q][0] * J0a.m[0][i] + hg.cc[q][1] * J0a.m[1][i] + hg.cc[q][2] * J0a.m[2][i]);
+  float H[4][3];  // k q_alpha
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -302,30 +308,143 @@ __global__ void __launch_bounds__(128) force_hex8_kernel(ForceArgs a) {
       float hu = 0.f;
 #pragma unroll
       for (int b = 0; b < 8; ++b) hu += H8[q][b] * u[b][j];
-      H[q][j] = khg * (hu - (eq[q][0] * s[0][j] + eq[q][1] * s[1][j] + eq[q][2] * s[2][j]));
+      H[q][j] = hg.k * (hu - (eq[q][0] * s[0][j] + eq[q][1] * s[1][j] + eq[q][2] * s[2][j]));
     }
-  // G_i = F[:, i] / 8 - (1/8) sum_alpha e_{alpha,i} H_alpha
+  // G_i = F[:, i] / 8 - (1/8) sum_alpha e_{alpha,i} H_alpha;  f_b = sum_i xi_{b,i} G_i + sum_alpha h_{alpha,b} H_alpha
   float G[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j)
-      G[i][j] = 0.125f * (F.m[j][i] - (eq[0][i] * H[0][j] + eq[1][i] * H[1][j] +
-                                       eq[2][i] * H[2][j] + eq[3][i] * H[3][j]));
-  bool nonfinite = false;
+      G[i][j] = 0.125f * (F.m[j][i] - (eq[0][i] * H[0][j] + eq[1][i] * H[1][j] + eq[2][i] * H[2][j] +
+                                       eq[3][i] * H[3][j]));
 #pragma unroll
-  for (int b = 0; b < 8; ++b) {
-    float f[3];
+  for (int b = 0; b < 8; ++b)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float v = XI8[b][0] * G[0][j] + XI8[b][1] * G[1][j] + XI8[b][2] * G[2][j];
-      v += H8[0][b] * H[0][j] + H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
-      f[j] = v;
+    for (int j = 0; j < 3; ++j)
+      f[b][j] = XI8[b][0] * G[0][j] + XI8[b][1] * G[1][j] + XI8[b][2] * G[2][j] + H8[0][b] * H[0][j] +
+                H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
+}
+
+template <int NE, bool FA, bool FB, bool MR>
+__device__ __forceinline__ void elem_forces(const float (&u)[NE][3], const ElemConsts<FA, FB, MR>& k,
+                                            const ElemExtra<NE>& x, float (&f)[NE][3], bool& inv) {
+  if constexpr (NE == 4)
+    tet4_forces<FA, FB, MR>(u, k, x, f, inv);
+  else
+    hex8_forces<FA, FB, MR>(u, k, x, f, inv);
+}
+
+template <int NE>
+__device__ __forceinline__ bool all_finite(const float (&f)[NE][3]) {
+  bool ok = true;
+#pragma unroll
+  for (int b = 0; b < NE; ++b) ok &= finite3(f[b][0], f[b][1], f[b][2]);
+  return ok;
+}
+
+// Element-slot assembly: one thread per element, forces to slot a * E_pad + e.
+template <int NE, bool FA, bool FB, bool MR>
+__global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceArgs a) {
+  advance_clock(a);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.E) return;
+  const int E_pad = a.E_pad;
+  const float* __restrict__ c = a.consts;
+  ElemConsts<FA, FB, MR> k;
+  k.load(c, E_pad, e, a);
+  ElemExtra<NE> x;
+  if constexpr (NE == 8) x.load(c, E_pad, e, a.off_hg);
+  int nid[NE];
+  {
+    const int4 n0 = __ldcs(a.conn + (NE / 4) * (size_t)e);
+    nid[0] = n0.x; nid[1] = n0.y; nid[2] = n0.z; nid[3] = n0.w;
+    if constexpr (NE == 8) {
+      const int4 n1 = __ldcs(a.conn + 2 * (size_t)e + 1);
+      nid[4] = n1.x; nid[5] = n1.y; nid[6] = n1.z; nid[7] = n1.w;
     }
-    nonfinite |= !finite3(f[0], f[1], f[2]);
-    a.slots[(size_t)b * E_pad + e] = make_float4(f[0], f[1], f[2], 0.f);
   }
-  flag_error(a.st, e, inv, nonfinite && !inv);
+  float u[NE][3];
+#pragma unroll
+  for (int b = 0; b < NE; ++b) {
+    const float4 v = __ldg(a.U + nid[b]);
+    u[b][0] = v.x; u[b][1] = v.y; u[b][2] = v.z;
+  }
+  float f[NE][3];
+  bool inv;
+  elem_forces<NE, FA, FB, MR>(u, k, x, f, inv);
+  flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
+#pragma unroll
+  for (int b = 0; b < NE; ++b) a.slots[(size_t)b * E_pad + e] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
+}
+
+// Tiled assembly: block = tile of T elements.  The tile's unique nodes are
+// staged in shared memory, element forces go to shared memory (slot a * T + e),
+// and each unique node sums its slots in the fixed order of the local index.
+template <int NE, bool FA, bool FB, bool MR>
+__global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceArgs a, TileArgs t) {
+  extern __shared__ float4 smem4[];
+  advance_clock(a);
+  const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
+  float4* su = smem4;                                   // staged u of the tile's nodes
+  float* sf = reinterpret_cast<float*>(smem4 + t.smem_nodes);  // 3 x (NE T) slot forces
+  const int base = __ldg(t.tile_ptr + tile);
+  const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
+  const int e = tile * T + tid;
+  const bool valid = e < a.E;
+  const float* __restrict__ c = a.consts;
+  ElemConsts<FA, FB, MR> k;
+  ElemExtra<NE> x;
+  unsigned short lc[NE];
+  if (valid) {
+    k.load(c, a.E_pad, e, a);
+    if constexpr (NE == 8) x.load(c, a.E_pad, e, a.off_hg);
+    if constexpr (NE == 4) {
+      const ushort4 v = __ldcs(reinterpret_cast<const ushort4*>(t.lconn) + e);
+      lc[0] = v.x; lc[1] = v.y; lc[2] = v.z; lc[3] = v.w;
+    } else {
+      const ushort4 v0 = __ldcs(reinterpret_cast<const ushort4*>(t.lconn) + 2 * (size_t)e);
+      const ushort4 v1 = __ldcs(reinterpret_cast<const ushort4*>(t.lconn) + 2 * (size_t)e + 1);
+      lc[0] = v0.x; lc[1] = v0.y; lc[2] = v0.z; lc[3] = v0.w;
+      lc[4] = v1.x; lc[5] = v1.y; lc[6] = v1.z; lc[7] = v1.w;
+    }
+  }
+  for (int q = tid; q < n_t; q += T) su[q] = __ldg(a.U + __ldg(t.tile_nodes + base + q));
+  __syncthreads();
+  if (valid) {
+    float u[NE][3];
+#pragma unroll
+    for (int b = 0; b < NE; ++b) {
+      const float4 v = su[lc[b]];
+      u[b][0] = v.x; u[b][1] = v.y; u[b][2] = v.z;
+    }
+    float f[NE][3];
+    bool inv;
+    elem_forces<NE, FA, FB, MR>(u, k, x, f, inv);
+    flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
+    const int S = NE * T;
+#pragma unroll
+    for (int b = 0; b < NE; ++b) {
+      sf[b * T + tid] = f[b][0];
+      sf[S + b * T + tid] = f[b][1];
+      sf[2 * S + b * T + tid] = f[b][2];
+    }
+  }
+  __syncthreads();
+  const int S = NE * T;
+  const unsigned short* lp = t.lptr + base + tile;
+  const unsigned short* li = t.lidx + (size_t)tile * S;
+  for (int q = tid; q < n_t; q += T) {
+    const int p0 = lp[q], p1 = lp[q + 1];
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    for (int p = p0; p < p1; ++p) {
+      const int l = li[p];
+      fx += sf[l];
+      fy += sf[S + l];
+      fz += sf[2 * S + l];
+    }
+    t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
+  }
 }
 
 template <int MODE>
@@ -432,24 +551,46 @@ __global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevS
   }
 }
 
-template <int ELEM, bool FA, bool FB, bool MR>
+template <int NE, bool FA, bool FB, bool MR>
 cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
   const int grid = (a.E + threads - 1) / threads;
-  if (ELEM == DJ_TET4)
-    force_tet4_kernel<FA, FB, MR><<<grid, threads, 0, s>>>(a);
-  else
-    force_hex8_kernel<FA, FB, MR><<<grid, threads, 0, s>>>(a);
+  force_slots_kernel<NE, FA, FB, MR><<<grid, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int ELEM>
+template <int NE, bool FA, bool FB, bool MR>
+cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
+  const size_t smem = (size_t)t.smem_nodes * sizeof(float4) + (size_t)3 * NE * t.T * sizeof(float);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         96 * 1024);
+    attr_set = true;
+  }
+  force_tiles_kernel<NE, FA, FB, MR><<<n_tiles, t.T, smem, s>>>(a, t);
+  return cudaGetLastError();
+}
+
+template <int NE>
 cudaError_t launch_force_e(int variant, const ForceArgs& a, int threads, cudaStream_t s) {
   switch (variant) {
-    case VAR_NH: return launch_force_t<ELEM, false, false, false>(a, threads, s);
-    case VAR_TI: return launch_force_t<ELEM, true, false, false>(a, threads, s);
-    case VAR_OT: return launch_force_t<ELEM, true, true, false>(a, threads, s);
-    case VAR_MR: return launch_force_t<ELEM, false, false, true>(a, threads, s);
-    default: return launch_force_t<ELEM, true, true, true>(a, threads, s);
+    case VAR_NH: return launch_force_t<NE, false, false, false>(a, threads, s);
+    case VAR_TI: return launch_force_t<NE, true, false, false>(a, threads, s);
+    case VAR_OT: return launch_force_t<NE, true, true, false>(a, threads, s);
+    case VAR_MR: return launch_force_t<NE, false, false, true>(a, threads, s);
+    default: return launch_force_t<NE, true, true, true>(a, threads, s);
+  }
+}
+
+template <int NE>
+cudaError_t launch_tiles_e(int variant, const ForceArgs& a, const TileArgs& t, int n_tiles,
+                           cudaStream_t s) {
+  switch (variant) {
+    case VAR_NH: return launch_tiles_t<NE, false, false, false>(a, t, n_tiles, s);
+    case VAR_TI: return launch_tiles_t<NE, true, false, false>(a, t, n_tiles, s);
+    case VAR_OT: return launch_tiles_t<NE, true, true, false>(a, t, n_tiles, s);
+    case VAR_MR: return launch_tiles_t<NE, false, false, true>(a, t, n_tiles, s);
+    default: return launch_tiles_t<NE, true, true, true>(a, t, n_tiles, s);
   }
 }
 
@@ -457,8 +598,14 @@ cudaError_t launch_force_e(int variant, const ForceArgs& a, int threads, cudaStr
 
 cudaError_t launch_force(int elem_type, int variant, const ForceArgs& a, int threads,
                          cudaStream_t s) {
-  if (elem_type == DJ_TET4) return launch_force_e<DJ_TET4>(variant, a, threads, s);
-  return launch_force_e<DJ_HEX8>(variant, a, threads, s);
+  if (elem_type == DJ_TET4) return launch_force_e<4>(variant, a, threads, s);
+  return launch_force_e<8>(variant, a, threads, s);
+}
+
+cudaError_t launch_force_tiled(int elem_type, int variant, const ForceArgs& a, const TileArgs& t,
+                               int n_tiles, cudaStream_t s) {
+  if (elem_type == DJ_TET4) return launch_tiles_e<4>(variant, a, t, n_tiles, s);
+  return launch_tiles_e<8>(variant, a, t, n_tiles, s);
 }
 
 cudaError_t launch_node(int mode, const NodeArgs& a, cudaStream_t s) {

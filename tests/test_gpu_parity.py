@@ -37,26 +37,28 @@ MODELS = [W.NH, W.TI, W.OT, W.MR]
 
 
 @pytest.mark.parametrize("model", MODELS)
-@pytest.mark.parametrize("renumber", [1, 0])
-def test_tet4_forces_match_oracle(B, model, renumber):
-    # 6 * 7^3 = 2058 elements: several 256-thread tiles plus a ragged tail
+@pytest.mark.parametrize("renumber,assembly,tile", [(1, 1, 0), (0, 1, 96), (1, 0, 0), (0, 0, 0),
+                                                    (1, 1, 512), (1, 1, 32)])
+def test_tet4_forces_match_oracle(B, model, renumber, assembly, tile):
+    # 6 * 7^3 = 2058 elements: several tiles plus a ragged tail
     p = W.random_tet_mesh_problem(2058, seed=11 + model, model=model)
     rng = np.random.default_rng(5)
     # nodal noise of 0.5 % of the box size: strains of a few percent, no inversion
     U = rng.normal(size=(p.n_nodes, 3)) * 0.005
-    with B.Mesh(p, renumber=renumber) as m:
+    with B.Mesh(p, renumber=renumber, assembly=assembly, tile_size=tile) as m:
         F = m.internal_forces(U)
     ref = dynamics.Model.from_problem(p).internal_forces(U)
     assert rel_linf(F, ref) < FORCE_TOL
 
 
 @pytest.mark.parametrize("model", MODELS)
-def test_hex8_forces_match_oracle(B, model):
+@pytest.mark.parametrize("assembly,tile", [(1, 0), (0, 0), (1, 256), (1, 64)])
+def test_hex8_forces_match_oracle(B, model, assembly, tile):
     p = W.random_hex_mesh_problem(9, seed=21 + model, model=model)  # 729 bricks, ragged
     p.hg_coeff = 0.15
     rng = np.random.default_rng(6)
     U = rng.normal(size=(p.n_nodes, 3)) * 0.004
-    with B.Mesh(p) as m:
+    with B.Mesh(p, assembly=assembly, tile_size=tile) as m:
         F = m.internal_forces(U)
     ref = dynamics.Model.from_problem(p).internal_forces(U)
     assert rel_linf(F, ref) < FORCE_TOL
@@ -175,9 +177,10 @@ def test_deterministic_and_checkpoint_resume_bit_identical(B):
         assert np.array_equal(b.displacements(), Ua)
 
 
-def test_graph_and_direct_launch_agree(B):
+@pytest.mark.parametrize("assembly", [1, 0])
+def test_graph_and_direct_launch_agree(B, assembly):
     p = W.cube_shear(W.HEX8, 5, n_steps=100)
-    with B.Mesh(p) as a, B.Mesh(p) as b:
+    with B.Mesh(p, assembly=assembly) as a, B.Mesh(p, assembly=assembly) as b:
         a.run(100)  # graph replays of 32 steps + 4 direct steps
         for _ in range(100):
             b.step()
@@ -211,6 +214,19 @@ def test_dt_above_critical_rejected(B):
     with pytest.raises(B.DJError) as e:
         B.Mesh(p, dt=1.0)
     assert e.value.status == 1
+    for bad_tile in (48, 1024):
+        with pytest.raises(B.DJError) as e:
+            B.Mesh(p, tile_size=bad_tile)
+        assert e.value.status == 1
+
+
+def test_slot_and_tile_assembly_trajectories_agree(B):
+    p = W.cube_compression_tet4(8, 400)
+    with B.Mesh(p, assembly=0) as a, B.Mesh(p, assembly=1) as b:
+        a.run(400)
+        b.run(400)
+        Ua, Ub = a.displacements(), b.displacements()
+    assert rel_linf(Ub, Ua) < 1e-5
 
 
 def test_relaxation_matches_oracle(B):
