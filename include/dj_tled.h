@@ -80,7 +80,13 @@ typedef struct dj_mesh dj_mesh;
  *                     (tile, node); 0 slots -- every element writes one force per
  *                     node and the node update gathers all of them.
  *   tile_size         elements per tile, a multiple of 32 (T4 <= 512, H8 <= 256);
- *                     0 selects 256 (T4) / 128 (H8). */
+ *                     0 selects 256 (T4) / 128 (H8).
+ *   precision         0 (default): FP32 nodal state and forces.  1: compensated
+ *                     FP32 -- the displacement is kept as an unevaluated sum of
+ *                     two floats and the element force is evaluated from the
+ *                     increment tJ - 0J so that J - 1 and the deviatoric stress
+ *                     keep FP32 relative accuracy at small strain; needed to
+ *                     relax stiff (kappa / mu ~ 50) meshes to residuals ~1e-5. */
 typedef struct {
   double dt;
   double dt_scale;
@@ -92,7 +98,7 @@ typedef struct {
   int renumber;
   int assembly;
   int tile_size;
-  int reserved;
+  int precision;
 } dj_params;
 
 /* Read-only description of a mesh after dj_precompute. */
@@ -111,7 +117,7 @@ typedef struct {
   int assembly;             /* assembly in use (see dj_params) */
   int tile_size;            /* elements per tile (tiled assembly) */
   int n_consts;             /* floats per element in the element table */
-  int reserved;
+  int precision;            /* precision mode in use (see dj_params) */
 } dj_info;
 
 /* Fill *p with the defaults listed above. */
@@ -177,9 +183,12 @@ dj_status dj_step(dj_mesh* mesh, void* stream);
 /* Advance n >= 0 steps on `stream` (replays of a captured CUDA graph). Async. */
 dj_status dj_run_n(dj_mesh* mesh, long long n, void* stream);
 
-/* Advance n steps with one launch per kernel and a CUDA event between kernels;
- * synchronous.  ms_force / ms_update (optional) receive the summed device time
- * of the element-force kernels and of the gather-update kernels. */
+/* Advance n steps (as dj_run_n), then measure the device time of each kernel
+ * of the step: the element-force kernel and the node update kernel are each
+ * replayed back to back in a CUDA graph (the update on a saved copy of the
+ * state, restored afterwards), for min(n, 64) x max(1, n / 64) launches.
+ * ms_force / ms_update (optional) receive the time per launch times n.
+ * Synchronous. */
 dj_status dj_run_n_profiled(dj_mesh* mesh, long long n, void* stream, double* ms_force,
                             double* ms_update);
 

@@ -38,7 +38,7 @@ class dj_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dt_scale", C.c_double), ("alpha", C.c_double),
                 ("hg_coeff", C.c_double), ("ramp_steps", C.c_longlong), ("ramp_kind", C.c_int),
                 ("relax_check_every", C.c_int), ("renumber", C.c_int), ("assembly", C.c_int),
-                ("tile_size", C.c_int), ("reserved", C.c_int)]
+                ("tile_size", C.c_int), ("precision", C.c_int)]
 
 
 class dj_info(C.Structure):
@@ -49,7 +49,7 @@ class dj_info(C.Structure):
                 ("slot_bytes_per_elem", C.c_longlong), ("gather_index_bytes", C.c_longlong),
                 ("node_bytes_per_node", C.c_longlong), ("n_parts", C.c_longlong),
                 ("assembly", C.c_int), ("tile_size", C.c_int), ("n_consts", C.c_int),
-                ("reserved", C.c_int)]
+                ("precision", C.c_int)]
 
 
 class DJError(RuntimeError):

@@ -54,6 +54,8 @@ struct dj_mesh {
   float4* d_bct = nullptr;
   float4* d_R = nullptr;
   float4* d_fout = nullptr;
+  float4* d_Ulo = nullptr;  // compensated mode: low part of U
+  int cmp = 0;
   int* d_perm = nullptr;  // node_new_of_old on device
   DevState* d_state = nullptr;
   double2* d_partials = nullptr;
@@ -135,12 +137,13 @@ void release_device(dj_mesh* m) {
   void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
                   m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx,
-                  m->d_parts};
+                  m->d_parts,    m->d_Ulo};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_tile_ptr = m->d_tile_nodes = nullptr;
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
   m->d_parts = nullptr;
+  m->d_Ulo = nullptr;
   if (m->h_state) cudaFreeHost(m->h_state);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   m->d_conn = nullptr;
@@ -246,6 +249,7 @@ ForceArgs force_args(dj_mesh* m, int advance) {
   a.conn = m->d_conn;
   a.consts = m->d_consts;
   a.U = m->d_U;
+  a.Ulo = m->d_Ulo;
   a.slots = m->d_slots;
   a.E = (int)m->E;
   a.E_pad = m->E_pad;
@@ -275,8 +279,9 @@ TileArgs tile_args(dj_mesh* m) {
 
 cudaError_t launch_force_any(dj_mesh* m, int advance, cudaStream_t s) {
   if (m->assembly == ASSEMBLY_TILES)
-    return launch_force_tiled(m->elem_type, m->variant, force_args(m, advance), tile_args(m), m->n_tiles, s);
-  return launch_force(m->elem_type, m->variant, force_args(m, advance), m->threads_force, s);
+    return launch_force_tiled(m->elem_type, m->variant, m->cmp, force_args(m, advance), tile_args(m),
+                              m->n_tiles, s);
+  return launch_force(m->elem_type, m->variant, m->cmp, force_args(m, advance), m->threads_force, s);
 }
 
 NodeArgs node_args(dj_mesh* m) {
@@ -285,6 +290,7 @@ NodeArgs node_args(dj_mesh* m) {
   a.chunk_ptr = m->d_chunk_ptr;
   a.slots = m->assembly == ASSEMBLY_TILES ? m->d_parts : m->d_slots;
   a.U = m->d_U;
+  a.Ulo = m->d_Ulo;
   a.V = m->d_V;
   a.bct = m->d_bct;
   a.R = m->d_R;
@@ -299,7 +305,7 @@ NodeArgs node_args(dj_mesh* m) {
 cudaError_t launch_step(dj_mesh* m, cudaStream_t s, int mode) {
   cudaError_t e = launch_force_any(m, 1, s);
   if (e != cudaSuccess) return e;
-  e = launch_node(mode, node_args(m), s);
+  e = launch_node(mode, m->cmp, node_args(m), s);
   if (e != cudaSuccess) return e;
   if (mode == NODE_UPDATE_RESID) e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, s);
   return e;
@@ -309,6 +315,7 @@ dj_status need_ready(dj_mesh* m) {
   if (!m) return DJ_ERR_INVALID_ARG;
   if (!m->precomputed) return fail(m, DJ_ERR_NOT_PRECOMPUTED, "call dj_precompute first");
   CK(cudaSetDevice(m->device));
+  (void)cudaGetLastError();  // drop a non-sticky error left by an earlier failed call
   return DJ_OK;
 }
 
@@ -347,6 +354,7 @@ void dj_params_default(dj_params* p) {
   p->renumber = 1;
   p->assembly = ASSEMBLY_TILES;
   p->tile_size = 0;
+  p->precision = 0;
 }
 
 const char* dj_status_string(dj_status s) {
@@ -483,7 +491,8 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     dj_params_default(&prm);
   if (!(prm.dt_scale > 0) || !(prm.alpha >= 0) || !(prm.hg_coeff >= 0) || prm.relax_check_every <= 0 ||
       (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt) ||
-      (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES))
+      (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES) ||
+      (prm.precision != 0 && prm.precision != 1))
     return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
   {
     const int tmax = m->ne == 4 ? 512 : 256;
@@ -492,6 +501,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   }
   int dev = 0;
   CK(cudaGetDevice(&dev));
+  (void)cudaGetLastError();
   release_device(m);
   m->device = dev;
   m->params = prm;
@@ -679,6 +689,11 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   }
   CK(dalloc(m, &m->d_U, N));
   CK(dalloc(m, &m->d_V, N));
+  m->cmp = prm.precision;
+  if (m->cmp) {
+    CK(dalloc(m, &m->d_Ulo, N));
+    CK(cudaMemset(m->d_Ulo, 0, N * sizeof(float4)));
+  }
   CK(dalloc(m, &m->d_fout, N));
   CK(dalloc(m, &m->d_bct, std::max(1, m->n_bc_nodes)));
   if (m->n_bc_nodes)
@@ -912,44 +927,76 @@ dj_status dj_run_n_profiled(dj_mesh* m, long long n, void* stream, double* ms_fo
   if (s) return s;
   if (n < 0) return fail(m, DJ_ERR_INVALID_ARG, "n < 0");
   cudaStream_t st = (cudaStream_t)stream;
-  // steps captured into graphs of up to 256 steps with an event between every
-  // two kernels, so that launch gaps do not enter the per-kernel times
-  const long long chunk = 256;
-  std::vector<cudaEvent_t> ev(2 * chunk + 1);
-  for (auto& e : ev) CK(cudaEventCreate(&e));
-  double tf = 0, tu = 0;
-  dj_status rs = DJ_OK;
-  for (long long done = 0; done < n && rs == DJ_OK;) {
-    const long long k = std::min(chunk, n - done);
-    cudaGraphExec_t exec = nullptr;
-    rs = capture(m, &exec, [&](cudaStream_t cs) {
-      cudaError_t err = cudaEventRecord(ev[0], cs);
-      for (long long j = 0; j < k && err == cudaSuccess; ++j) {
-        err = launch_force_any(m, 1, cs);
-        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * j + 1], cs);
-        if (err == cudaSuccess) err = launch_node(NODE_UPDATE, node_args(m), cs);
-        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * j + 2], cs);
-      }
-      return err;
-    });
-    if (rs) break;
-    cudaError_t err = cudaGraphLaunch(exec, st);
-    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
-    for (long long j = 0; j < k && err == cudaSuccess; ++j) {
-      float a = 0, b = 0;
-      err = cudaEventElapsedTime(&a, ev[2 * j], ev[2 * j + 1]);
-      if (err == cudaSuccess) err = cudaEventElapsedTime(&b, ev[2 * j + 1], ev[2 * j + 2]);
-      tf += a;
-      tu += b;
+  if (ms_force) *ms_force = 0;
+  if (ms_update) *ms_update = 0;
+  if (n == 0) return DJ_OK;
+  // 1. n time steps (state advances as with dj_run_n)
+  s = dj_run_n(m, n, stream);
+  if (s) return s;
+  // 2. device time of the element-force kernel alone: a graph of up to 64
+  //    back-to-back launches that do not advance the clock, replayed; and of the
+  //    update kernel alone on a saved copy of the state, which is restored after
+  const long long chunk = std::min(64LL, n);
+  cudaGraphExec_t gf = nullptr, gu = nullptr;
+  s = capture(m, &gf, [&](cudaStream_t cs) {
+    for (long long j = 0; j < chunk; ++j) {
+      cudaError_t e = launch_force_any(m, 0, cs);
+      if (e != cudaSuccess) return e;
     }
-    cudaGraphExecDestroy(exec);
-    if (err != cudaSuccess) rs = fail(m, DJ_ERR_CUDA, "profiled run: %s", cudaGetErrorString(err));
-    done += k;
+    return cudaSuccess;
+  });
+  if (s) return s;
+  s = capture(m, &gu, [&](cudaStream_t cs) {
+    for (long long j = 0; j < chunk; ++j) {
+      cudaError_t e = launch_node(NODE_UPDATE, m->cmp, node_args(m), cs);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  });
+  if (s) {
+    cudaGraphExecDestroy(gf);
+    return s;
   }
-  for (auto& e : ev) cudaEventDestroy(e);
-  if (ms_force) *ms_force = tf;
-  if (ms_update) *ms_update = tu;
-  return rs;
+  float4 *sU = nullptr, *sV = nullptr, *sL = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  cudaError_t err = cudaMalloc(&sU, m->N * sizeof(float4));
+  if (err == cudaSuccess) err = cudaMalloc(&sV, m->N * sizeof(float4));
+  if (err == cudaSuccess) err = cudaMemcpyAsync(sU, m->d_U, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(sV, m->d_V, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess && m->cmp) err = cudaMalloc(&sL, m->N * sizeof(float4));
+  if (err == cudaSuccess && m->cmp)
+    err = cudaMemcpyAsync(sL, m->d_Ulo, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  if (err == cudaSuccess) err = cudaEventCreate(&e2);
+  const long long reps = std::max(1LL, n / chunk);
+  if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+  for (long long r = 0; r < reps && err == cudaSuccess; ++r) err = cudaGraphLaunch(gf, st);
+  if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+  for (long long r = 0; r < reps && err == cudaSuccess; ++r) err = cudaGraphLaunch(gu, st);
+  if (err == cudaSuccess) err = cudaEventRecord(e2, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  float tf = 0, tu = 0;
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&tf, e0, e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(&tu, e1, e2);
+  // restore the state and the element forces of the current step
+  if (sU) cudaMemcpyAsync(m->d_U, sU, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (sV) cudaMemcpyAsync(m->d_V, sV, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (sL) cudaMemcpyAsync(m->d_Ulo, sL, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  cudaGraphExecDestroy(gf);
+  cudaGraphExecDestroy(gu);
+  if (sU) cudaFree(sU);
+  if (sV) cudaFree(sV);
+  if (sL) cudaFree(sL);
+  for (cudaEvent_t e : {e0, e1, e2})
+    if (e) cudaEventDestroy(e);
+  if (err != cudaSuccess) return fail(m, DJ_ERR_CUDA, "profiled run: %s", cudaGetErrorString(err));
+  // per-step totals scaled to the n steps that were run
+  const double per = 1.0 / (double)(reps * chunk) * (double)n;
+  if (ms_force) *ms_force = tf * per;
+  if (ms_update) *ms_update = tu * per;
+  return DJ_OK;
 }
 
 dj_status dj_sync(dj_mesh* m, void* stream) {
@@ -1017,16 +1064,18 @@ dj_status dj_set_displacements(dj_mesh* m, const double* U0) {
   if (s) return s;
   if (!U0) return fail(m, DJ_ERR_INVALID_ARG, "null U0");
   const long long N = m->N;
-  std::vector<float4> U(N), V(N);
+  std::vector<float4> U(N), V(N), L(N);
   for (long long i = 0; i < N; ++i) {
     const size_t o = 3 * (size_t)m->node_old_of_new[i];
     if (!std::isfinite(U0[o]) || !std::isfinite(U0[o + 1]) || !std::isfinite(U0[o + 2]))
       return fail(m, DJ_ERR_INVALID_ARG, "non-finite displacement");
     U[i] = make_float4((float)U0[o], (float)U0[o + 1], (float)U0[o + 2], m->h_ai[i]);
     V[i] = make_float4(0.f, 0.f, 0.f, bits_to_float(m->h_bcidx[i]));
+    L[i] = make_float4((float)(U0[o] - U[i].x), (float)(U0[o + 1] - U[i].y), (float)(U0[o + 2] - U[i].z), 0.f);
   }
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(m->d_U, U.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  if (m->cmp) CK(cudaMemcpy(m->d_Ulo, L.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->d_V, V.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   return DJ_OK;
 }
@@ -1037,13 +1086,14 @@ dj_status dj_get_displacements(dj_mesh* m, double* U_out) {
   if (!U_out) return fail(m, DJ_ERR_INVALID_ARG, "null U_out");
   CK(cudaDeviceSynchronize());
   const long long N = m->N;
-  std::vector<float4> U(N);
+  std::vector<float4> U(N), L(N, make_float4(0.f, 0.f, 0.f, 0.f));
   CK(cudaMemcpy(U.data(), m->d_U, N * sizeof(float4), cudaMemcpyDeviceToHost));
+  if (m->cmp) CK(cudaMemcpy(L.data(), m->d_Ulo, N * sizeof(float4), cudaMemcpyDeviceToHost));
   for (long long i = 0; i < N; ++i) {
     const size_t o = 3 * (size_t)m->node_old_of_new[i];
-    U_out[o] = U[i].x;
-    U_out[o + 1] = U[i].y;
-    U_out[o + 2] = U[i].z;
+    U_out[o] = (double)U[i].x + (double)L[i].x;
+    U_out[o + 1] = (double)U[i].y + (double)L[i].y;
+    U_out[o + 2] = (double)U[i].z + (double)L[i].z;
   }
   s = read_state(m, 0);
   if (s) return s;
@@ -1064,19 +1114,23 @@ dj_status dj_internal_forces(dj_mesh* m, const double* U, double* F_out) {
   if (!U || !F_out) return fail(m, DJ_ERR_INVALID_ARG, "null array");
   const long long N = m->N;
   CK(cudaDeviceSynchronize());
-  std::vector<float4> save(N), Un(N), F(N);
+  std::vector<float4> save(N), saveL(N), Un(N), Ln(N), F(N);
   CK(cudaMemcpy(save.data(), m->d_U, N * sizeof(float4), cudaMemcpyDeviceToHost));
+  if (m->cmp) CK(cudaMemcpy(saveL.data(), m->d_Ulo, N * sizeof(float4), cudaMemcpyDeviceToHost));
   for (long long i = 0; i < N; ++i) {
     const size_t o = 3 * (size_t)m->node_old_of_new[i];
     Un[i] = make_float4((float)U[o], (float)U[o + 1], (float)U[o + 2], save[i].w);
+    Ln[i] = make_float4((float)(U[o] - Un[i].x), (float)(U[o + 1] - Un[i].y), (float)(U[o + 2] - Un[i].z), 0.f);
   }
   CK(cudaMemcpy(m->d_U, Un.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  if (m->cmp) CK(cudaMemcpy(m->d_Ulo, Ln.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   CK(launch_force_any(m, 0, 0));
   NodeArgs na = node_args(m);
   na.R = nullptr;
-  CK(launch_node(NODE_FORCE_ONLY, na, 0));
+  CK(launch_node(NODE_FORCE_ONLY, m->cmp, na, 0));
   CK(cudaMemcpy(F.data(), m->d_fout, N * sizeof(float4), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(m->d_U, save.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  if (m->cmp) CK(cudaMemcpy(m->d_Ulo, saveL.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   for (long long i = 0; i < N; ++i) {
     const size_t o = 3 * (size_t)m->node_old_of_new[i];
     F_out[o] = F[i].x;
@@ -1100,7 +1154,7 @@ const unsigned long long kStateMagic = 0x444a544c45440001ULL;
 
 dj_status dj_state_size(const dj_mesh* m, size_t* bytes) {
   if (!m || !bytes) return DJ_ERR_INVALID_ARG;
-  *bytes = sizeof(StateHeader) + 2 * (size_t)m->N * sizeof(float4);
+  *bytes = sizeof(StateHeader) + (m->cmp ? 3 : 2) * (size_t)m->N * sizeof(float4);
   return DJ_OK;
 }
 
@@ -1118,6 +1172,9 @@ dj_status dj_get_state(dj_mesh* m, void* buf, size_t bytes) {
   std::memcpy(p, &h, sizeof(h));
   CK(cudaMemcpy(p + sizeof(h), m->d_U, m->N * sizeof(float4), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(p + sizeof(h) + m->N * sizeof(float4), m->d_V, m->N * sizeof(float4), cudaMemcpyDeviceToHost));
+  if (m->cmp)
+    CK(cudaMemcpy(p + sizeof(h) + 2 * m->N * sizeof(float4), m->d_Ulo, m->N * sizeof(float4),
+                  cudaMemcpyDeviceToHost));
   return DJ_OK;
 }
 
@@ -1134,6 +1191,9 @@ dj_status dj_set_state(dj_mesh* m, const void* buf, size_t bytes) {
   CK(cudaDeviceSynchronize());
   CK(cudaMemcpy(m->d_U, p + sizeof(h), m->N * sizeof(float4), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->d_V, p + sizeof(h) + m->N * sizeof(float4), m->N * sizeof(float4), cudaMemcpyHostToDevice));
+  if (m->cmp)
+    CK(cudaMemcpy(m->d_Ulo, p + sizeof(h) + 2 * m->N * sizeof(float4), m->N * sizeof(float4),
+                  cudaMemcpyHostToDevice));
   DevState st{};
   st.step = h.step;
   st.bad_elem = INT_MAX;
@@ -1173,6 +1233,7 @@ dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
   info->assembly = m->assembly;
   info->tile_size = m->T;
   info->n_consts = m->n_consts;
+  info->precision = m->cmp;
   return DJ_OK;
 }
 

@@ -44,6 +44,7 @@ struct ForceArgs {
   const int4* conn;      // tet: E_pad int4; hex: 2 E_pad int4 (nodes 0-3, 4-7)
   const float* consts;   // n_consts * E_pad
   const float4* U;       // U^n (xyz), w = node update coefficient
+  const float4* Ulo;     // compensated mode: low part of U^n (U = U + Ulo), else unused
   float4* slots;         // element-force slots, slot = a * E_pad + e
   int E, E_pad;
   int off_fa, off_fb, off_mr, off_hg;
@@ -58,6 +59,7 @@ struct NodeArgs {
   const int* chunk_ptr;   // n_chunks + 1 offsets into sell
   const float4* slots;
   float4* U;              // in/out: U^n -> U^{n+1}; w = a_i
+  float4* Ulo;            // compensated mode: low part of U
   float4* V;              // in/out: U^n - U^{n-1} -> U^{n+1} - U^n; w = bc index bits
   const float4* bct;      // per prescribed node: target xyz, w = component mask bits
   const float4* R;        // external loads or nullptr
@@ -90,11 +92,12 @@ constexpr int NODE_THREADS = 256;
 constexpr int SELL_C = 32;
 
 // kernels_step.cu
-cudaError_t launch_force(int elem_type, int variant, const ForceArgs& a, int threads,
+// cmp = 1: compensated precision (double-float U, increment-based forces)
+cudaError_t launch_force(int elem_type, int variant, int cmp, const ForceArgs& a, int threads,
                          cudaStream_t s);
-cudaError_t launch_force_tiled(int elem_type, int variant, const ForceArgs& a, const TileArgs& t,
-                               int n_tiles, cudaStream_t s);
-cudaError_t launch_node(int mode, const NodeArgs& a, cudaStream_t s);
+cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceArgs& a,
+                               const TileArgs& t, int n_tiles, cudaStream_t s);
+cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
 
 // force kernel variants

@@ -247,17 +247,183 @@ struct ElemExtra<4> {
 template <>
 struct ElemExtra<8> : HgConsts {};
 
-// Nodal forces of one T4 element: tJ = 0J + H_xi u (rows u_b - u_0, Eq. 11),
-// F H_xi: node b = 1..3 takes column b-1, node 0 minus their sum (Sec. 7).
+// adj(A + B) - adj(A), expanded so that no O(1) terms cancel
+__device__ __forceinline__ M3 adj_delta(const M3& A, const M3& B) {
+#define DJ_ADJD(p0, p1, q0, q1, r0, r1, s0, s1)                                                  \
+  (A.m[p0][p1] * B.m[q0][q1] + B.m[p0][p1] * A.m[q0][q1] + B.m[p0][p1] * B.m[q0][q1] -           \
+   (A.m[r0][r1] * B.m[s0][s1] + B.m[r0][r1] * A.m[s0][s1] + B.m[r0][r1] * B.m[s0][s1]))
+  M3 r;
+  r.m[0][0] = DJ_ADJD(1, 1, 2, 2, 1, 2, 2, 1);
+  r.m[0][1] = DJ_ADJD(0, 2, 2, 1, 0, 1, 2, 2);
+  r.m[0][2] = DJ_ADJD(0, 1, 1, 2, 0, 2, 1, 1);
+  r.m[1][0] = DJ_ADJD(1, 2, 2, 0, 1, 0, 2, 2);
+  r.m[1][1] = DJ_ADJD(0, 0, 2, 2, 0, 2, 2, 0);
+  r.m[1][2] = DJ_ADJD(0, 2, 1, 0, 0, 0, 1, 2);
+  r.m[2][0] = DJ_ADJD(1, 0, 2, 1, 1, 1, 2, 0);
+  r.m[2][1] = DJ_ADJD(0, 1, 2, 0, 0, 0, 2, 1);
+  r.m[2][2] = DJ_ADJD(0, 0, 1, 1, 0, 1, 1, 0);
+#undef DJ_ADJD
+  return r;
+}
+
+// Compensated form of the same force: with A = 0J and B = tJ - 0J (Eq. 11),
+//   J - 1        = (tr(adj(A) B) + tr(A adj(B)) + det B) / det A          (Eq. 12)
+//   g:P - 3 mu0V = P : (A B^T + B A^T + B B^T),  mu 0V = P : A A^T / 3
+//   tJ^T P - (g:P)/3 tJ^-1
+//                = mu0V (J-1) adj(A) / D + B^T P - mu0V (adj(tJ) - adj(A)) / D
+//                  - (g:P - 3 mu0V) / 3 adj(tJ) / D
+//   I4bar - 1    = (J^-2/3 - 1) + J^-2/3 (P_a : (A B^T + B A^T + B B^T)) s_a
+// Every term is of the order of the increment, so FP32 keeps its relative
+// accuracy at small strain instead of losing it to cancellation.
 template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ void tet4_forces(const float (&u)[4][3], const ElemConsts<FA, FB, MR>& k,
-                                            const ElemExtra<4>&, float (&f)[4][3], bool& inv) {
+__device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, const ElemConsts<FA, FB, MR>& k,
+                                                  bool& bad) {
   M3 tJ;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) tJ.m[i][j] = k.J0[i][j] + (u[i + 1][j] - u[0][j]);
-  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, k, inv);
+    for (int j = 0; j < 3; ++j) tJ.m[i][j] = A.m[i][j] + B.m[i][j];
+  const M3 adjA = adj3(A);
+  const M3 adjB = adj3(B);
+  float dD = det3(B);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dD += adjA.m[i][j] * B.m[j][i] + A.m[i][j] * adjB.m[j][i];
+  const float jm1 = dD * k.r0;  // J - 1
+  const float J = 1.f + jm1;
+  bad = !(J > 0.f);
+  const float D = 1.f / k.r0 + dD;
+  const float invD = 1.f / D;
+  const float lJ = log1pf(jm1);
+  const float Jm23 = expf(-2.f / 3.f * lJ);
+  const float Jm23m1 = expm1f(-2.f / 3.f * lJ);
+  // g0 = A A^T and dg = A B^T + B A^T + B B^T (symmetric, {00,11,22,01,02,12})
+  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+  float g0[6], dg[6], g[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int i = ii[q], j = jj[q];
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      s0 += A.m[i][m] * A.m[j][m];
+      s1 += A.m[i][m] * B.m[j][m] + B.m[i][m] * A.m[j][m] + B.m[i][m] * B.m[j][m];
+    }
+    g0[q] = s0;
+    dg[q] = s1;
+    g[q] = s0 + s1;
+  }
+  const float mV = frob_sym(g0, k.P) / 3.f;  // mu 0V
+  const float dgP = frob_sym(dg, k.P);       // g:P - 3 mu 0V
+  const M3 adjD = adj_delta(A, B);
+  M3 adjT;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) adjT.m[i][j] = adjA.m[i][j] + adjD.m[i][j];
+  M3 T;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
+  add_tJT_sym(T, B, k.P, 1.f);  // B^T P
+  float cT = -dgP / 3.f * invD;  // coefficient of adj(tJ) inside the J^-2/3 bracket
+  if (FA) {
+    const float d4 = frob_sym(dg, k.Qa);
+    const float psi = Jm23m1 + Jm23 * d4 * k.sa;  // I4bar - 1
+    add_tJT_sym(T, tJ, k.Qa, psi);
+    cT -= psi * frob_sym(g, k.Qa) / 3.f * invD;
+  }
+  if (FB) {
+    const float d6 = frob_sym(dg, k.Qb);
+    const float psi = Jm23m1 + Jm23 * d6 * k.sb;  // I6bar - 1
+    add_tJT_sym(T, tJ, k.Qb, psi);
+    cT -= psi * frob_sym(g, k.Qb) / 3.f * invD;
+  }
+  float mr_vol = 0.f;
+  if (MR) {
+    const float gP = 3.f * mV + dgP;
+    float Pg[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        Pg[i][j] = sym_at(k.P, i, 0) * sym_at(g, 0, j) + sym_at(k.P, i, 1) * sym_at(g, 1, j) +
+                   sym_at(k.P, i, 2) * sym_at(g, 2, j);
+    float S2[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int i = ii[q], j = jj[q];
+      const float PgP = Pg[i][0] * sym_at(k.P, 0, j) + Pg[i][1] * sym_at(k.P, 1, j) +
+                        Pg[i][2] * sym_at(k.P, 2, j);
+      S2[q] = k.gm * (gP * sym_at(k.P, i, j) - PgP);
+    }
+    float trPgPg = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
+    add_tJT_sym(T, tJ, S2, Jm23);
+    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;
+  }
+  const float cA = mV * jm1 * invD, cD = -mV * invD;
+  const float cadj = mr_vol * invD + k.kV * jm1 * k.r0;  // volumetric: kappa 0V (J-1) r0 adj(tJ)
+  M3 F;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float br = T.m[i][j] + cA * adjA.m[i][j] + cD * adjD.m[i][j] + cT * adjT.m[i][j];
+      F.m[i][j] = fmaf(Jm23, br, cadj * adjT.m[i][j]);
+    }
+  return F;
+}
+
+template <bool FA, bool FB, bool MR, bool CMP>
+__device__ __forceinline__ M3 force_matrix(const M3& A, const M3& B, const ElemConsts<FA, FB, MR>& k,
+                                           bool& bad) {
+  if constexpr (CMP) {
+    return dj_force_matrix_cmp<FA, FB, MR>(A, B, k, bad);
+  } else {
+    M3 tJ;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) tJ.m[i][j] = A.m[i][j] + B.m[i][j];
+    return dj_force_matrix<FA, FB, MR>(tJ, k, bad);
+  }
+}
+
+// u_b - u_0 of one component; compensated mode: from the (hi, lo) pairs with an
+// error-free difference of the high parts
+template <bool CMP>
+__device__ __forceinline__ float node_diff(float hb, float h0, float lb, float l0) {
+  if constexpr (!CMP) {
+    return hb - h0;
+  } else {
+    const float s = hb - h0;
+    const float bb = s - hb;
+    const float err = (hb - (s - bb)) + (-h0 - bb);
+    return s + (err + (lb - l0));
+  }
+}
+
+// Nodal forces of one T4 element from d_b = u_b - u_0 (b = 1..3):
+// tJ = 0J + H_xi u has rows d_1, d_2, d_3 (Eq. 11); F H_xi gives node b = 1..3
+// column b-1 and node 0 minus their sum (Sec. 7).
+template <bool FA, bool FB, bool MR, bool CMP>
+__device__ __forceinline__ void tet4_forces(const float (&d)[4][3], const ElemConsts<FA, FB, MR>& k,
+                                            const ElemExtra<4>&, float (&f)[4][3], bool& inv) {
+  M3 A, B;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      A.m[i][j] = k.J0[i][j];
+      B.m[i][j] = d[i + 1][j];
+    }
+  const M3 F = force_matrix<FA, FB, MR, CMP>(A, B, k, inv);
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     f[1][j] = F.m[j][0];
@@ -267,11 +433,13 @@ __device__ __forceinline__ void tet4_forces(const float (&u)[4][3], const ElemCo
   }
 }
 
-// Nodal forces of one 1-point H8 element with hourglass control.
-template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ void hex8_forces(const float (&u)[8][3], const ElemConsts<FA, FB, MR>& k,
+// Nodal forces of one 1-point H8 element with hourglass control, from
+// d_b = u_b - u_0 (H_xi and the hourglass vectors annihilate constants, so
+// sums over d_b equal sums over u_b).
+template <bool FA, bool FB, bool MR, bool CMP>
+__device__ __forceinline__ void hex8_forces(const float (&d)[8][3], const ElemConsts<FA, FB, MR>& k,
                                             const ElemExtra<8>& hg, float (&f)[8][3], bool& inv) {
-  // s_i = (H_xi u)_i = sum_b xi_{b,i} u_b / 8
+  // s_i = (H_xi u)_i = sum_b xi_{b,i} d_b / 8
   float s[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -279,21 +447,21 @@ __device__ __forceinline__ void hex8_forces(const float (&u)[8][3], const ElemCo
     for (int j = 0; j < 3; ++j) {
       float acc = 0.f;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc += XI8[b][i] * u[b][j];
+      for (int b = 1; b < 8; ++b) acc += XI8[b][i] * d[b][j];
       s[i][j] = 0.125f * acc;
     }
-  M3 J0, tJ;
+  M3 A, B;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      J0.m[i][j] = k.J0[i][j];
-      tJ.m[i][j] = k.J0[i][j] + s[i][j];  // Eq. 11
+      A.m[i][j] = k.J0[i][j];
+      B.m[i][j] = s[i][j];  // Eq. 11
     }
-  const M3 F = dj_force_matrix<FA, FB, MR>(tJ, k, inv);
+  const M3 F = force_matrix<FA, FB, MR, CMP>(A, B, k, inv);
   // hourglass: q_alpha = gamma_alpha . u, gamma_alpha = h_alpha - sum_j c_aj 0B_j,
   // 0B = 0J^-1 H_xi with 0J^-1 = adj(0J) / det 0J
-  const M3 J0a = adj3(J0);
+  const M3 J0a = adj3(A);
   float eq[4][3];  // e_{alpha,i} = sum_j c_{alpha j} (0J^-1)_{j i}
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -307,7 +475,7 @@ __device__ __forceinline__ void hex8_forces(const float (&u)[8][3], const ElemCo
     for (int j = 0; j < 3; ++j) {
       float hu = 0.f;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) hu += H8[q][b] * u[b][j];
+      for (int b = 1; b < 8; ++b) hu += H8[q][b] * d[b][j];
       H[q][j] = hg.k * (hu - (eq[q][0] * s[0][j] + eq[q][1] * s[1][j] + eq[q][2] * s[2][j]));
     }
   // G_i = F[:, i] / 8 - (1/8) sum_alpha e_{alpha,i} H_alpha;  f_b = sum_i xi_{b,i} G_i + sum_alpha h_{alpha,b} H_alpha
@@ -326,13 +494,13 @@ __device__ __forceinline__ void hex8_forces(const float (&u)[8][3], const ElemCo
                 H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
 }
 
-template <int NE, bool FA, bool FB, bool MR>
-__device__ __forceinline__ void elem_forces(const float (&u)[NE][3], const ElemConsts<FA, FB, MR>& k,
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
+__device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemConsts<FA, FB, MR>& k,
                                             const ElemExtra<NE>& x, float (&f)[NE][3], bool& inv) {
   if constexpr (NE == 4)
-    tet4_forces<FA, FB, MR>(u, k, x, f, inv);
+    tet4_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
   else
-    hex8_forces<FA, FB, MR>(u, k, x, f, inv);
+    hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
 }
 
 template <int NE>
@@ -343,8 +511,20 @@ __device__ __forceinline__ bool all_finite(const float (&f)[NE][3]) {
   return ok;
 }
 
+// d_b = u_b - u_0 from the nodal records (hi, lo)
+template <int NE, bool CMP>
+__device__ __forceinline__ void node_deltas(const float4 (&h)[NE], const float4 (&l)[NE], float (&d)[NE][3]) {
+  d[0][0] = d[0][1] = d[0][2] = 0.f;
+#pragma unroll
+  for (int b = 1; b < NE; ++b) {
+    d[b][0] = node_diff<CMP>(h[b].x, h[0].x, l[b].x, l[0].x);
+    d[b][1] = node_diff<CMP>(h[b].y, h[0].y, l[b].y, l[0].y);
+    d[b][2] = node_diff<CMP>(h[b].z, h[0].z, l[b].z, l[0].z);
+  }
+}
+
 // Element-slot assembly: one thread per element, forces to slot a * E_pad + e.
-template <int NE, bool FA, bool FB, bool MR>
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
 __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceArgs a) {
   advance_clock(a);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -364,15 +544,17 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
       nid[4] = n1.x; nid[5] = n1.y; nid[6] = n1.z; nid[7] = n1.w;
     }
   }
-  float u[NE][3];
+  float4 h[NE], l[NE];
 #pragma unroll
   for (int b = 0; b < NE; ++b) {
-    const float4 v = __ldg(a.U + nid[b]);
-    u[b][0] = v.x; u[b][1] = v.y; u[b][2] = v.z;
+    h[b] = __ldg(a.U + nid[b]);
+    l[b] = CMP ? __ldg(a.Ulo + nid[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
   }
+  float d[NE][3];
+  node_deltas<NE, CMP>(h, l, d);
   float f[NE][3];
   bool inv;
-  elem_forces<NE, FA, FB, MR>(u, k, x, f, inv);
+  elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
   flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
 #pragma unroll
   for (int b = 0; b < NE; ++b) a.slots[(size_t)b * E_pad + e] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
@@ -381,13 +563,14 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
 // Tiled assembly: block = tile of T elements.  The tile's unique nodes are
 // staged in shared memory, element forces go to shared memory (slot a * T + e),
 // and each unique node sums its slots in the fixed order of the local index.
-template <int NE, bool FA, bool FB, bool MR>
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
 __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceArgs a, TileArgs t) {
   extern __shared__ float4 smem4[];
   advance_clock(a);
   const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
-  float4* su = smem4;                                   // staged u of the tile's nodes
-  float* sf = reinterpret_cast<float*>(smem4 + t.smem_nodes);  // 3 x (NE T) slot forces
+  float4* su = smem4;                                          // staged U (high part)
+  float4* sl = smem4 + t.smem_nodes;                           // staged low part (compensated)
+  float* sf = reinterpret_cast<float*>(smem4 + (CMP ? 2 : 1) * t.smem_nodes);  // 3 x (NE T) forces
   const int base = __ldg(t.tile_ptr + tile);
   const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
   const int e = tile * T + tid;
@@ -409,18 +592,24 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
       lc[4] = v1.x; lc[5] = v1.y; lc[6] = v1.z; lc[7] = v1.w;
     }
   }
-  for (int q = tid; q < n_t; q += T) su[q] = __ldg(a.U + __ldg(t.tile_nodes + base + q));
+  for (int q = tid; q < n_t; q += T) {
+    const int gid = __ldg(t.tile_nodes + base + q);
+    su[q] = __ldg(a.U + gid);
+    if (CMP) sl[q] = __ldg(a.Ulo + gid);
+  }
   __syncthreads();
   if (valid) {
-    float u[NE][3];
+    float4 h[NE], l[NE];
 #pragma unroll
     for (int b = 0; b < NE; ++b) {
-      const float4 v = su[lc[b]];
-      u[b][0] = v.x; u[b][1] = v.y; u[b][2] = v.z;
+      h[b] = su[lc[b]];
+      l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    float d[NE][3];
+    node_deltas<NE, CMP>(h, l, d);
     float f[NE][3];
     bool inv;
-    elem_forces<NE, FA, FB, MR>(u, k, x, f, inv);
+    elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
     flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
     const int S = NE * T;
 #pragma unroll
@@ -447,7 +636,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
   }
 }
 
-template <int MODE>
+template <int MODE, bool CMP>
 __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = i / SELL_C, lane = i % SELL_C;
@@ -479,27 +668,52 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       const float4 U = a.U[i];
       const float ai = U.w;
       // velocity form of the central difference: D^{n+1} = a (R - F) + (b - 1) D^n
-      float dx = fmaf(-ai, fx, a.bm1 * V.x);
-      float dy = fmaf(-ai, fy, a.bm1 * V.y);
-      float dz = fmaf(-ai, fz, a.bm1 * V.z);
-      float nx = U.x + dx, ny = U.y + dy, nz = U.z + dz;
+      float dd[3] = {fmaf(-ai, fx, a.bm1 * V.x), fmaf(-ai, fy, a.bm1 * V.y), fmaf(-ai, fz, a.bm1 * V.z)};
+      const float uh[3] = {U.x, U.y, U.z};
+      float nh[3], nl[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
+      if (CMP) {
+        const float4 L = a.Ulo[i];
+        ul[0] = L.x;
+        ul[1] = L.y;
+        ul[2] = L.z;
+      }
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (CMP) {
+          // (hi, lo) + D with an error-free sum of the high parts
+          const float s = uh[q] + dd[q];
+          const float bb = s - uh[q];
+          const float err = (uh[q] - (s - bb)) + (dd[q] - bb);
+          const float lo = ul[q] + err;
+          nh[q] = s + lo;
+          nl[q] = lo - (nh[q] - s);
+        } else {
+          nh[q] = uh[q] + dd[q];
+        }
+      }
       int mask = 0;
       if (bc >= 0) {
         const float4 t = __ldg(a.bct + bc);
         mask = __float_as_int(t.w);
         const float rs = a.st->ramp_s;
-        if (mask & 1) { nx = t.x * rs; dx = nx - U.x; }
-        if (mask & 2) { ny = t.y * rs; dy = ny - U.y; }
-        if (mask & 4) { nz = t.z * rs; dz = nz - U.z; }
+        const float tv[3] = {t.x, t.y, t.z};
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (mask & (1 << q)) {
+            nh[q] = tv[q] * rs;
+            nl[q] = 0.f;
+            dd[q] = (nh[q] - uh[q]) - ul[q];
+          }
       }
-      a.U[i] = make_float4(nx, ny, nz, ai);
-      a.V[i] = make_float4(dx, dy, dz, V.w);
+      a.U[i] = make_float4(nh[0], nh[1], nh[2], ai);
+      if (CMP) a.Ulo[i] = make_float4(nl[0], nl[1], nl[2], 0.f);
+      a.V[i] = make_float4(dd[0], dd[1], dd[2], V.w);
       if (MODE == NODE_UPDATE_RESID) {
         const double f3[3] = {fx, fy, fz};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          if (mask & (1 << k)) den2 += f3[k] * f3[k];
-          else num2 += f3[k] * f3[k];
+        for (int q = 0; q < 3; ++q) {
+          if (mask & (1 << q)) den2 += f3[q] * f3[q];
+          else num2 += f3[q] * f3[q];
         }
       }
     }
@@ -519,9 +733,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
     __syncthreads();
     if (threadIdx.x == 0) {
       double tn = 0.0, td = 0.0;
-      for (int k = 0; k < NODE_THREADS / 32; ++k) {
-        tn += sn[k];
-        td += sd[k];
+      for (int q = 0; q < NODE_THREADS / 32; ++q) {
+        tn += sn[q];
+        td += sd[q];
       }
       a.partials[blockIdx.x] = make_double2(tn, td);
     }
@@ -531,9 +745,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
 __global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevState* st) {
   __shared__ double sn[256], sd[256];
   double tn = 0.0, td = 0.0;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    tn += p[k].x;
-    td += p[k].y;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    tn += p[q].x;
+    td += p[q].y;
   }
   sn[threadIdx.x] = tn;
   sd[threadIdx.x] = td;
@@ -551,72 +765,82 @@ __global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevS
   }
 }
 
-template <int NE, bool FA, bool FB, bool MR>
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
   const int grid = (a.E + threads - 1) / threads;
-  force_slots_kernel<NE, FA, FB, MR><<<grid, threads, 0, s>>>(a);
+  force_slots_kernel<NE, FA, FB, MR, CMP><<<grid, threads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int NE, bool FA, bool FB, bool MR>
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t smem = (size_t)t.smem_nodes * sizeof(float4) + (size_t)3 * NE * t.T * sizeof(float);
+  const size_t smem = (size_t)(CMP ? 2 : 1) * t.smem_nodes * sizeof(float4) +
+                      (size_t)3 * NE * t.T * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         96 * 1024);
+    cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR, CMP>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr_set = true;
   }
-  force_tiles_kernel<NE, FA, FB, MR><<<n_tiles, t.T, smem, s>>>(a, t);
+  force_tiles_kernel<NE, FA, FB, MR, CMP><<<n_tiles, t.T, smem, s>>>(a, t);
   return cudaGetLastError();
 }
 
-template <int NE>
+template <int NE, bool CMP>
 cudaError_t launch_force_e(int variant, const ForceArgs& a, int threads, cudaStream_t s) {
   switch (variant) {
-    case VAR_NH: return launch_force_t<NE, false, false, false>(a, threads, s);
-    case VAR_TI: return launch_force_t<NE, true, false, false>(a, threads, s);
-    case VAR_OT: return launch_force_t<NE, true, true, false>(a, threads, s);
-    case VAR_MR: return launch_force_t<NE, false, false, true>(a, threads, s);
-    default: return launch_force_t<NE, true, true, true>(a, threads, s);
+    case VAR_NH: return launch_force_t<NE, false, false, false, CMP>(a, threads, s);
+    case VAR_TI: return launch_force_t<NE, true, false, false, CMP>(a, threads, s);
+    case VAR_OT: return launch_force_t<NE, true, true, false, CMP>(a, threads, s);
+    case VAR_MR: return launch_force_t<NE, false, false, true, CMP>(a, threads, s);
+    default: return launch_force_t<NE, true, true, true, CMP>(a, threads, s);
   }
 }
 
-template <int NE>
+template <int NE, bool CMP>
 cudaError_t launch_tiles_e(int variant, const ForceArgs& a, const TileArgs& t, int n_tiles,
                            cudaStream_t s) {
   switch (variant) {
-    case VAR_NH: return launch_tiles_t<NE, false, false, false>(a, t, n_tiles, s);
-    case VAR_TI: return launch_tiles_t<NE, true, false, false>(a, t, n_tiles, s);
-    case VAR_OT: return launch_tiles_t<NE, true, true, false>(a, t, n_tiles, s);
-    case VAR_MR: return launch_tiles_t<NE, false, false, true>(a, t, n_tiles, s);
-    default: return launch_tiles_t<NE, true, true, true>(a, t, n_tiles, s);
+    case VAR_NH: return launch_tiles_t<NE, false, false, false, CMP>(a, t, n_tiles, s);
+    case VAR_TI: return launch_tiles_t<NE, true, false, false, CMP>(a, t, n_tiles, s);
+    case VAR_OT: return launch_tiles_t<NE, true, true, false, CMP>(a, t, n_tiles, s);
+    case VAR_MR: return launch_tiles_t<NE, false, false, true, CMP>(a, t, n_tiles, s);
+    default: return launch_tiles_t<NE, true, true, true, CMP>(a, t, n_tiles, s);
   }
 }
 
 }  // namespace
 
-cudaError_t launch_force(int elem_type, int variant, const ForceArgs& a, int threads,
+cudaError_t launch_force(int elem_type, int variant, int cmp, const ForceArgs& a, int threads,
                          cudaStream_t s) {
-  if (elem_type == DJ_TET4) return launch_force_e<4>(variant, a, threads, s);
-  return launch_force_e<8>(variant, a, threads, s);
+  if (elem_type == DJ_TET4)
+    return cmp ? launch_force_e<4, true>(variant, a, threads, s) : launch_force_e<4, false>(variant, a, threads, s);
+  return cmp ? launch_force_e<8, true>(variant, a, threads, s) : launch_force_e<8, false>(variant, a, threads, s);
 }
 
-cudaError_t launch_force_tiled(int elem_type, int variant, const ForceArgs& a, const TileArgs& t,
-                               int n_tiles, cudaStream_t s) {
-  if (elem_type == DJ_TET4) return launch_tiles_e<4>(variant, a, t, n_tiles, s);
-  return launch_tiles_e<8>(variant, a, t, n_tiles, s);
+cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceArgs& a,
+                               const TileArgs& t, int n_tiles, cudaStream_t s) {
+  if (elem_type == DJ_TET4)
+    return cmp ? launch_tiles_e<4, true>(variant, a, t, n_tiles, s)
+               : launch_tiles_e<4, false>(variant, a, t, n_tiles, s);
+  return cmp ? launch_tiles_e<8, true>(variant, a, t, n_tiles, s)
+             : launch_tiles_e<8, false>(variant, a, t, n_tiles, s);
 }
 
-cudaError_t launch_node(int mode, const NodeArgs& a, cudaStream_t s) {
+template <int MODE>
+cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
   const int grid = (a.N + NODE_THREADS - 1) / NODE_THREADS;
-  if (mode == NODE_UPDATE)
-    node_kernel<NODE_UPDATE><<<grid, NODE_THREADS, 0, s>>>(a);
-  else if (mode == NODE_UPDATE_RESID)
-    node_kernel<NODE_UPDATE_RESID><<<grid, NODE_THREADS, 0, s>>>(a);
+  if (cmp)
+    node_kernel<MODE, true><<<grid, NODE_THREADS, 0, s>>>(a);
   else
-    node_kernel<NODE_FORCE_ONLY><<<grid, NODE_THREADS, 0, s>>>(a);
+    node_kernel<MODE, false><<<grid, NODE_THREADS, 0, s>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s) {
+  if (mode == NODE_UPDATE) return launch_node_m<NODE_UPDATE>(cmp, a, s);
+  if (mode == NODE_UPDATE_RESID) return launch_node_m<NODE_UPDATE_RESID>(cmp, a, s);
+  return launch_node_m<NODE_FORCE_ONLY>(cmp, a, s);
 }
 
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s) {
