@@ -281,9 +281,12 @@ def test_cfg1_trajectory_compensated(B, cfg1_reference):
 
 
 def test_full_size_cfg2b_sampled_nodes(B):
-    """1.23M-tet cube (59^3 x 6) as timed by the benchmark: one update at sampled
-    nodes against the oracle, which evaluates only their incident elements.  The
-    FP32 force error is bounded relative to the largest incident element force."""
+    """1.23M-tet cube (59^3 x 6) in the benchmark's configuration (plain FP32, tiled
+    assembly): one update at sampled nodes against the oracle, which evaluates only
+    their incident elements.  FP32 error model of the force at node i: 1e-4 of the
+    largest incident element force, plus the volumetric term's absolute error
+    kappa 0V |0B| dJ with dJ = 8 ulp(1) (J - 1 is formed as det(tJ) / det(0J) - 1)."""
+    from oracle import tled
     p = W.cube_shear(W.TET4, 59, n_steps=5000)
     rng = np.random.default_rng(0)
     with B.Mesh(p) as m:
@@ -297,6 +300,7 @@ def test_full_size_cfg2b_sampled_nodes(B):
     assert np.abs(U2).max() > 0
     sample = rng.choice(p.n_nodes, size=64, replace=False)
     checked = 0
+    eps = float(np.finfo(np.float32).eps)
     for i in sample:
         els = np.nonzero((p.conn == i).any(axis=1))[0]
         sub = W.Problem(name="sub", elem_type=4, X=p.X, conn=p.conn[els], model=p.model[els],
@@ -306,13 +310,16 @@ def test_full_size_cfg2b_sampled_nodes(B):
         mdl = dynamics.Model.from_problem(sub)
         Fe = mdl.element_forces(U1)
         F = mdl.internal_forces(U1)[i]
+        B0, V0 = tled.shape_derivatives(p.X, p.conn[els], 4)
+        vol_scale = np.sum(p.kappa[els] * V0 * np.abs(B0).max(axis=(1, 2)))
         a_i = 2 * dt * dt / (2 * mdl.mass[i])
         U2_ref = -a_i * F + 2 * U1[i] - U0[i]
         pres = np.isin(3 * i + np.arange(3), p.bc_dof)
         if pres.all():
             continue
         err = np.abs(U2[i] - U2_ref)[~pres].max()
-        bound = a_i * 1e-4 * np.abs(Fe).max() + 4 * np.spacing(np.float32(np.abs(U2[i]).max()))
+        bound = a_i * (1e-4 * np.abs(Fe).max() + 8 * eps * vol_scale) \
+            + 4 * np.spacing(np.float32(np.abs(U2[i]).max()))
         assert err <= bound, (i, err, bound)
         checked += 1
     assert checked > 40
