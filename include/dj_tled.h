@@ -162,6 +162,16 @@ dj_status dj_mesh_set_bcs(dj_mesh* mesh, const long long* dof, const double* tar
  * next step.  Host array of n_bc_dofs doubles. */
 dj_status dj_mesh_update_bc_targets(dj_mesh* mesh, const double* target);
 
+/* Independent bodies in one mesh (used for batches of problems).  elem_group:
+ * host, n_elems ints in [0, n_groups); elements of different groups must not
+ * share a node (DJ_ERR_INVALID_ARG otherwise).  Each group gets its own
+ * critical step (Eq. 14) and time step dt_scale * dt_crit(group) (or
+ * params.dt, which must not exceed any group's critical step), its own
+ * damping factor, and its own relaxation residual; dj_relax_to_tol converges
+ * when every group's residual is <= tol.  The ramp is shared (in steps).
+ * NULL or n_groups <= 0 removes the grouping.  Before dj_precompute. */
+dj_status dj_mesh_set_groups(dj_mesh* mesh, const int* elem_group, int n_groups);
+
 /* External nodal forces R (Eq. 13), host n_nodes * 3 doubles, constant in
  * time; NULL clears them.  Must be called before dj_precompute. */
 dj_status dj_mesh_set_loads(dj_mesh* mesh, const double* R);
@@ -229,9 +239,50 @@ dj_status dj_get_state(dj_mesh* mesh, void* buf, size_t bytes);
 dj_status dj_set_state(dj_mesh* mesh, const void* buf, size_t bytes);
 
 dj_status dj_get_info(const dj_mesh* mesh, dj_info* info);
+
+/* Per group (1 group when the mesh has no grouping): time step, critical step
+ * and the residual of the last dj_relax_to_tol check (NaN before any).  Arrays
+ * are optional, each of *n_groups doubles. */
+dj_status dj_get_group_info(const dj_mesh* mesh, int* n_groups, double* dt, double* dt_crit,
+                            double* residual);
 const char* dj_status_string(dj_status s);
 const char* dj_last_error(const dj_mesh* mesh);
 void dj_mesh_destroy(dj_mesh* mesh);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent problems of uneven size (no counterpart in the
+ * paper, which runs one mesh at a time).  Instances of the same element type
+ * are merged into one grouped mesh (see dj_mesh_set_groups): every instance
+ * keeps its own time step, damping factor and residual; the T4 and H8 parts
+ * advance as two independent kernel chains captured in one CUDA graph.
+ * ------------------------------------------------------------------------- */
+typedef struct dj_batch dj_batch;
+
+/* instances: n meshes with materials (and prescribed DOFs, loads) set; they
+ * need not be precomputed.  Their host data is copied: the handles stay owned
+ * by the caller and may be destroyed afterwards. */
+dj_status dj_batch_create(dj_mesh* const* instances, int n, dj_batch** out);
+/* dj_precompute of every part with the same parameters (synchronous). */
+dj_status dj_batch_precompute(dj_batch* batch, const dj_params* params);
+/* Advance every instance n steps (async, graph replays). */
+dj_status dj_batch_run_n(dj_batch* batch, long long n, void* stream);
+/* Wait and report device-side errors of every part. */
+dj_status dj_batch_sync(dj_batch* batch, void* stream);
+/* Relax every instance until each residual is <= tol (checked every
+ * relax_check_every steps); residual_out = the largest instance residual. */
+dj_status dj_batch_relax_to_tol(dj_batch* batch, double tol, long long max_steps,
+                                long long* steps_out, double* residual_out, void* stream);
+/* Instance i: node and element counts, its time step and its last residual. */
+dj_status dj_batch_instance_info(dj_batch* batch, int i, long long* n_nodes, long long* n_elems,
+                                 double* dt, double* residual);
+/* Displacements of instance i (host, its n_nodes * 3 doubles, its node order). */
+dj_status dj_batch_get_displacements(dj_batch* batch, int i, double* U_out);
+/* Warm start of instance i: U^0 = U^-1 = U0.  Synchronous. */
+dj_status dj_batch_set_displacements(dj_batch* batch, int i, const double* U0);
+dj_status dj_batch_get_info(const dj_batch* batch, int* n_instances, long long* n_nodes,
+                            long long* n_elems, long long* n_tet_elems, long long* n_hex_elems);
+const char* dj_batch_last_error(const dj_batch* batch);
+void dj_batch_destroy(dj_batch* batch);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,10 @@ EXPORTS = [
     "dj_run_n_profiled", "dj_sync", "dj_relax_to_tol", "dj_set_displacements",
     "dj_get_displacements", "dj_get_displacements_device", "dj_internal_forces",
     "dj_state_size", "dj_get_state", "dj_set_state", "dj_get_info", "dj_status_string",
-    "dj_last_error", "dj_mesh_destroy",
+    "dj_last_error", "dj_mesh_destroy", "dj_mesh_set_groups", "dj_get_group_info",
+    "dj_batch_create", "dj_batch_precompute", "dj_batch_run_n", "dj_batch_sync",
+    "dj_batch_relax_to_tol", "dj_batch_instance_info", "dj_batch_get_displacements",
+    "dj_batch_set_displacements", "dj_batch_get_info", "dj_batch_last_error", "dj_batch_destroy",
 ]
 
 
@@ -99,6 +102,19 @@ def lib():
         "dj_status_string": (C.c_char_p, [C.c_int]),
         "dj_last_error": (C.c_char_p, [_P]),
         "dj_mesh_destroy": (None, [_P]),
+        "dj_mesh_set_groups": (C.c_int, [_P, C.POINTER(C.c_int), C.c_int]),
+        "dj_get_group_info": (C.c_int, [_P, C.POINTER(C.c_int), _D, _D, _D]),
+        "dj_batch_create": (C.c_int, [C.POINTER(_P), C.c_int, C.POINTER(_P)]),
+        "dj_batch_precompute": (C.c_int, [_P, C.POINTER(dj_params)]),
+        "dj_batch_run_n": (C.c_int, [_P, C.c_longlong, _P]),
+        "dj_batch_sync": (C.c_int, [_P, _P]),
+        "dj_batch_relax_to_tol": (C.c_int, [_P, C.c_double, C.c_longlong, _LL, _D, _P]),
+        "dj_batch_instance_info": (C.c_int, [_P, C.c_int, _LL, _LL, _D, _D]),
+        "dj_batch_get_displacements": (C.c_int, [_P, C.c_int, _D]),
+        "dj_batch_set_displacements": (C.c_int, [_P, C.c_int, _D]),
+        "dj_batch_get_info": (C.c_int, [_P, C.POINTER(C.c_int), _LL, _LL, _LL, _LL]),
+        "dj_batch_last_error": (C.c_char_p, [_P]),
+        "dj_batch_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -282,6 +298,85 @@ def dj_mesh_destroy(h):
     lib().dj_mesh_destroy(h)
 
 
+def dj_mesh_set_groups(h, elem_group, n_groups):
+    g = np.ascontiguousarray(elem_group, dtype=np.int32)
+    _check(lib().dj_mesh_set_groups(h, g.ctypes.data_as(C.POINTER(C.c_int)), int(n_groups)),
+           "dj_mesh_set_groups", h)
+
+
+def dj_get_group_info(h):
+    n = C.c_int(0)
+    _check(lib().dj_get_group_info(h, C.byref(n), None, None, None), "dj_get_group_info", h)
+    dt, dtc, r = (np.empty(n.value) for _ in range(3))
+    _check(lib().dj_get_group_info(h, C.byref(n), _dptr(dt), _dptr(dtc), _dptr(r)),
+           "dj_get_group_info", h)
+    return dt, dtc, r
+
+
+def _bcheck(st, where, b):
+    if st != DJ_OK:
+        msg = lib().dj_batch_last_error(b) if b else b""
+        raise DJError(st, where, msg.decode() if msg else "")
+
+
+def dj_batch_create(handles):
+    arr = (_P * len(handles))(*[h.value if isinstance(h, _P) else h for h in handles])
+    b = _P()
+    _bcheck(lib().dj_batch_create(arr, len(handles), C.byref(b)), "dj_batch_create", None)
+    return b
+
+
+def dj_batch_precompute(b, params=None):
+    _bcheck(lib().dj_batch_precompute(b, C.byref(params) if params is not None else None),
+            "dj_batch_precompute", b)
+
+
+def dj_batch_run_n(b, n, stream=None):
+    _bcheck(lib().dj_batch_run_n(b, int(n), _stream(stream)), "dj_batch_run_n", b)
+
+
+def dj_batch_sync(b, stream=None):
+    _bcheck(lib().dj_batch_sync(b, _stream(stream)), "dj_batch_sync", b)
+
+
+def dj_batch_relax_to_tol(b, tol, max_steps, stream=None, raise_on_fail=True):
+    steps, r = C.c_longlong(0), C.c_double(0)
+    st = lib().dj_batch_relax_to_tol(b, float(tol), int(max_steps), C.byref(steps), C.byref(r),
+                                     _stream(stream))
+    if raise_on_fail:
+        _bcheck(st, "dj_batch_relax_to_tol", b)
+    return st, steps.value, r.value
+
+
+def dj_batch_instance_info(b, i):
+    nn, ne, dt, r = C.c_longlong(0), C.c_longlong(0), C.c_double(0), C.c_double(0)
+    _bcheck(lib().dj_batch_instance_info(b, int(i), C.byref(nn), C.byref(ne), C.byref(dt), C.byref(r)),
+            "dj_batch_instance_info", b)
+    return nn.value, ne.value, dt.value, r.value
+
+
+def dj_batch_get_displacements(b, i, n_nodes):
+    out = np.empty((n_nodes, 3))
+    _bcheck(lib().dj_batch_get_displacements(b, int(i), _dptr(out)), "dj_batch_get_displacements", b)
+    return out
+
+
+def dj_batch_set_displacements(b, i, U0):
+    U0 = _f64(U0)
+    _bcheck(lib().dj_batch_set_displacements(b, int(i), _dptr(U0)), "dj_batch_set_displacements", b)
+
+
+def dj_batch_get_info(b):
+    n = C.c_int(0)
+    v = [C.c_longlong(0) for _ in range(4)]
+    _bcheck(lib().dj_batch_get_info(b, C.byref(n), *[C.byref(x) for x in v]), "dj_batch_get_info", b)
+    return (n.value,) + tuple(x.value for x in v)
+
+
+def dj_batch_destroy(b):
+    lib().dj_batch_destroy(b)
+
+
 # ------------------------------------------------------------- convenience --
 class Mesh:
     """Owning wrapper of a dj_mesh handle built from a workloads.Problem."""
@@ -336,6 +431,70 @@ class Mesh:
         if self.h:
             dj_mesh_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Owning wrapper of a dj_batch built from workloads.Problem instances."""
+
+    def __init__(self, problems, precompute=True, **param_kw):
+        self.problems = list(problems)
+        handles = []
+        try:
+            for p in self.problems:
+                h = dj_mesh_create(p.elem_type, p.X, p.conn)
+                handles.append(h)
+                dj_mesh_set_materials(h, p.model, p.mu, p.kappa, p.rho, p.eta_a, p.eta_b, p.c01,
+                                      p.a_dir, p.b_dir)
+                dj_mesh_set_bcs(h, p.bc_dof, p.bc_target)
+            self.b = dj_batch_create(handles)
+        finally:
+            for h in handles:
+                dj_mesh_destroy(h)
+        p0 = self.problems[0]
+        kw = dict(dt_scale=p0.dt_scale, alpha=p0.alpha, hg_coeff=p0.hg_coeff,
+                  ramp_steps=p0.ramp_steps, ramp_kind=p0.ramp_kind)
+        kw.update(param_kw)
+        self.params = default_params(**kw)
+        if precompute:
+            dj_batch_precompute(self.b, self.params)
+
+    def run(self, n, stream=None):
+        dj_batch_run_n(self.b, n, stream)
+
+    def sync(self, stream=None):
+        dj_batch_sync(self.b, stream)
+
+    def relax(self, tol, max_steps, stream=None, raise_on_fail=True):
+        return dj_batch_relax_to_tol(self.b, tol, max_steps, stream, raise_on_fail)
+
+    def displacements(self, i):
+        return dj_batch_get_displacements(self.b, i, self.problems[i].n_nodes)
+
+    def set_displacements(self, i, U0):
+        dj_batch_set_displacements(self.b, i, U0)
+
+    def instance_info(self, i):
+        return dj_batch_instance_info(self.b, i)
+
+    def info(self):
+        return dj_batch_get_info(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            dj_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -36,6 +36,8 @@ struct dj_mesh {
   std::vector<long long> bc_dof;
   std::vector<double> bc_target;
   std::vector<double> R;
+  std::vector<int> elem_group;  // independent bodies (caller element order), empty = one body
+  int n_groups = 0;
   dj_params params{};
   // renumbering
   std::vector<int> node_new_of_old, node_old_of_new, elem_old_of_new;
@@ -56,6 +58,14 @@ struct dj_mesh {
   float4* d_fout = nullptr;
   float4* d_Ulo = nullptr;  // compensated mode: low part of U
   int cmp = 0;
+  // groups: per-group time step, damping factor and residual
+  std::vector<double> group_dt, group_dt_crit, group_r;
+  std::vector<int> group_node_ptr;  // internal node range of each group
+  float* d_bm1 = nullptr;
+  double2* d_node_resid = nullptr;
+  double2* d_group_resid = nullptr;
+  int* d_group_node_ptr = nullptr;
+  double2* h_group_resid = nullptr;  // pinned
   int* d_perm = nullptr;  // node_new_of_old on device
   DevState* d_state = nullptr;
   double2* d_partials = nullptr;
@@ -137,13 +147,19 @@ void release_device(dj_mesh* m) {
   void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
                   m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx,
-                  m->d_parts,    m->d_Ulo};
+                  m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
+                  m->d_group_node_ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_tile_ptr = m->d_tile_nodes = nullptr;
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
   m->d_parts = nullptr;
   m->d_Ulo = nullptr;
+  m->d_bm1 = nullptr;
+  m->d_node_resid = m->d_group_resid = nullptr;
+  m->d_group_node_ptr = nullptr;
+  if (m->h_group_resid) cudaFreeHost(m->h_group_resid);
+  m->h_group_resid = nullptr;
   if (m->h_state) cudaFreeHost(m->h_state);
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   m->d_conn = nullptr;
@@ -296,6 +312,8 @@ NodeArgs node_args(dj_mesh* m) {
   a.R = m->d_R;
   a.fout = m->d_fout;
   a.partials = m->d_partials;
+  a.node_resid = m->n_groups > 0 ? m->d_node_resid : nullptr;
+  a.bm1_node = m->d_bm1;
   a.st = m->d_state;
   a.N = (int)m->N;
   a.bm1 = m->bm1;
@@ -307,7 +325,12 @@ cudaError_t launch_step(dj_mesh* m, cudaStream_t s, int mode) {
   if (e != cudaSuccess) return e;
   e = launch_node(mode, m->cmp, node_args(m), s);
   if (e != cudaSuccess) return e;
-  if (mode == NODE_UPDATE_RESID) e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, s);
+  if (mode == NODE_UPDATE_RESID) {
+    if (m->n_groups > 0)
+      e = launch_group_resid(m->d_node_resid, m->d_group_node_ptr, m->n_groups, m->d_group_resid, s);
+    else
+      e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, s);
+  }
   return e;
 }
 
@@ -468,6 +491,31 @@ dj_status dj_mesh_set_bcs(dj_mesh* m, const long long* dof, const double* target
   return DJ_OK;
 }
 
+dj_status dj_mesh_set_groups(dj_mesh* m, const int* elem_group, int n_groups) {
+  if (!m) return DJ_ERR_INVALID_ARG;
+  if (!elem_group || n_groups <= 0) {
+    m->elem_group.clear();
+    m->n_groups = 0;
+    m->precomputed = false;
+    return DJ_OK;
+  }
+  std::vector<int> node_group(m->N, -1);
+  for (long long e = 0; e < m->E; ++e) {
+    const int g = elem_group[e];
+    if (g < 0 || g >= n_groups) return fail(m, DJ_ERR_INVALID_ARG, "element %lld: group %d out of range", e, g);
+    for (int b = 0; b < m->ne; ++b) {
+      int& ng = node_group[m->conn[e * m->ne + b]];
+      if (ng >= 0 && ng != g)
+        return fail(m, DJ_ERR_INVALID_ARG, "node %d is shared by groups %d and %d", m->conn[e * m->ne + b], ng, g);
+      ng = g;
+    }
+  }
+  m->elem_group.assign(elem_group, elem_group + m->E);
+  m->n_groups = n_groups;
+  m->precomputed = false;
+  return DJ_OK;
+}
+
 dj_status dj_mesh_set_loads(dj_mesh* m, const double* R) {
   if (!m) return DJ_ERR_INVALID_ARG;
   if (!R) {
@@ -510,11 +558,20 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   // ---- renumbering (caller -> internal) --------------------------------
   m->node_old_of_new.resize(N);
   m->elem_old_of_new.resize(E);
+  std::vector<int> node_group_c;  // caller order
+  if (m->n_groups > 0) {
+    node_group_c.assign(N, 0);
+    for (long long e = 0; e < E; ++e)
+      for (int b = 0; b < ne; ++b) node_group_c[m->conn[e * ne + b]] = m->elem_group[e];
+  }
   if (prm.renumber) {
     m->node_old_of_new = morton_order(m->X, N);
   } else {
     std::iota(m->node_old_of_new.begin(), m->node_old_of_new.end(), 0);
   }
+  if (m->n_groups > 0)  // group-major: every group is a contiguous range of nodes and elements
+    std::stable_sort(m->node_old_of_new.begin(), m->node_old_of_new.end(),
+                     [&](int a, int b) { return node_group_c[a] < node_group_c[b]; });
   m->node_new_of_old.assign(N, 0);
   for (long long i = 0; i < N; ++i) m->node_new_of_old[m->node_old_of_new[i]] = (int)i;
   if (prm.renumber) {
@@ -525,6 +582,13 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     m->elem_old_of_new = morton_order(cen, E);
   } else {
     std::iota(m->elem_old_of_new.begin(), m->elem_old_of_new.end(), 0);
+  }
+  if (m->n_groups > 0) {
+    std::stable_sort(m->elem_old_of_new.begin(), m->elem_old_of_new.end(),
+                     [&](int a, int b) { return m->elem_group[a] < m->elem_group[b]; });
+    m->group_node_ptr.assign(m->n_groups + 1, 0);
+    for (long long i = 0; i < N; ++i) m->group_node_ptr[node_group_c[i] + 1]++;
+    for (int g = 0; g < m->n_groups; ++g) m->group_node_ptr[g + 1] += m->group_node_ptr[g];
   }
   std::vector<double> Xn(3 * N);
   for (long long i = 0; i < N; ++i)
@@ -826,26 +890,67 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     std::vector<double> red(256);
     CKP(cudaMemcpy(red.data(), dred, 256 * sizeof(double), cudaMemcpyDeviceToHost));
     m->dt_crit = *std::min_element(red.begin(), red.end());
-    if (prm.dt > 0) {
-      if (prm.dt > m->dt_crit * (1.0 + 1e-12)) {
-        const double dc = m->dt_crit;
-        cleanup();
-        release_device(m);
-        return fail(m, DJ_ERR_INVALID_ARG, "dt %.6g exceeds the critical step %.6g", prm.dt, dc);
-      }
-      m->dt = prm.dt;
-    } else {
-      m->dt = prm.dt_scale * m->dt_crit;
-      if (prm.dt_scale > 1.0) {
-        cleanup();
-        release_device(m);
-        return fail(m, DJ_ERR_INVALID_ARG, "dt_scale above 1 exceeds the critical step");
+    const int G = std::max(1, m->n_groups);
+    m->group_dt_crit.assign(G, m->dt_crit);
+    if (m->n_groups > 0) {
+      std::vector<double> dte(E);
+      CKP(cudaMemcpy(dte.data(), ddt, E * sizeof(double), cudaMemcpyDeviceToHost));
+      m->group_dt_crit.assign(G, 1e300);
+      for (long long e = 0; e < E; ++e) {
+        const int g = m->elem_group[m->elem_old_of_new[e]];
+        m->group_dt_crit[g] = std::min(m->group_dt_crit[g], dte[e]);
       }
     }
+    m->group_dt.assign(G, 0.0);
+    for (int g = 0; g < G; ++g) {
+      if (prm.dt > 0) {
+        if (prm.dt > m->group_dt_crit[g] * (1.0 + 1e-12)) {
+          const double dc = m->group_dt_crit[g];
+          cleanup();
+          release_device(m);
+          return fail(m, DJ_ERR_INVALID_ARG, "dt %.6g exceeds the critical step %.6g", prm.dt, dc);
+        }
+        m->group_dt[g] = prm.dt;
+      } else {
+        if (prm.dt_scale > 1.0) {
+          cleanup();
+          release_device(m);
+          return fail(m, DJ_ERR_INVALID_ARG, "dt_scale above 1 exceeds the critical step");
+        }
+        m->group_dt[g] = prm.dt_scale * m->group_dt_crit[g];
+      }
+    }
+    m->dt = *std::min_element(m->group_dt.begin(), m->group_dt.end());
     const double adt = prm.alpha * m->dt;
     m->bm1 = (float)((2.0 - adt) / (2.0 + adt));
-    CKP(launch_node_mass(d_mass_sell, d_mass_chunk, dem, E_pad, (int)N, m->dt, prm.alpha, dbc, dmass, m->d_U,
-                         m->d_V, 0));
+    double* ddtn = nullptr;
+    if (m->n_groups > 0) {
+      std::vector<double> dtn(N);
+      std::vector<float> bm1n(N);
+      for (int g = 0; g < m->n_groups; ++g)
+        for (int i = m->group_node_ptr[g]; i < m->group_node_ptr[g + 1]; ++i) {
+          dtn[i] = m->group_dt[g];
+          const double a = prm.alpha * m->group_dt[g];
+          bm1n[i] = (float)((2.0 - a) / (2.0 + a));
+        }
+      CKP(cudaMalloc(&ddtn, N * sizeof(double)));
+      CKP(cudaMemcpy(ddtn, dtn.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+      if (prm.alpha > 0) {
+        CKP(cudaMalloc(&m->d_bm1, N * sizeof(float)));
+        CKP(cudaMemcpy(m->d_bm1, bm1n.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+      }
+      CKP(cudaMalloc(&m->d_node_resid, N * sizeof(double2)));
+      CKP(cudaMalloc(&m->d_group_resid, m->n_groups * sizeof(double2)));
+      CKP(cudaMalloc(&m->d_group_node_ptr, (m->n_groups + 1) * sizeof(int)));
+      CKP(cudaMemcpy(m->d_group_node_ptr, m->group_node_ptr.data(), (m->n_groups + 1) * sizeof(int),
+                     cudaMemcpyHostToDevice));
+      CKP(cudaMallocHost((void**)&m->h_group_resid, m->n_groups * sizeof(double2)));
+    }
+    cudaError_t me = launch_node_mass(d_mass_sell, d_mass_chunk, dem, E_pad, (int)N, m->dt, ddtn, prm.alpha,
+                                      dbc, dmass, m->d_U, m->d_V, 0);
+    if (me == cudaSuccess) me = cudaDeviceSynchronize();
+    if (ddtn) cudaFree(ddtn);
+    CKP(me);
     std::vector<double> mass(N);
     CKP(cudaMemcpy(mass.data(), dmass, N * sizeof(double), cudaMemcpyDeviceToHost));
     m->total_mass = 0;
@@ -1024,6 +1129,11 @@ dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long
       }
       cudaError_t e = launch_step(m, cs, NODE_UPDATE_RESID);
       if (e != cudaSuccess) return e;
+      if (m->n_groups > 0) {
+        e = cudaMemcpyAsync(m->h_group_resid, m->d_group_resid, m->n_groups * sizeof(double2),
+                            cudaMemcpyDeviceToHost, cs);
+        if (e != cudaSuccess) return e;
+      }
       return cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, cs);
     });
     if (s) return s;
@@ -1040,8 +1150,18 @@ dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long
       if (steps_out) *steps_out = done;
       return s;
     }
-    const double num = std::sqrt(m->h_state->resid_num2), den = std::sqrt(m->h_state->resid_den2);
-    r = den > 0 ? num / den : num;
+    if (m->n_groups > 0) {
+      m->group_r.assign(m->n_groups, 0.0);
+      r = 0;
+      for (int g = 0; g < m->n_groups; ++g) {
+        const double num = std::sqrt(m->h_group_resid[g].x), den = std::sqrt(m->h_group_resid[g].y);
+        m->group_r[g] = den > 0 ? num / den : num;
+        r = std::max(r, m->group_r[g]);
+      }
+    } else {
+      const double num = std::sqrt(m->h_state->resid_num2), den = std::sqrt(m->h_state->resid_den2);
+      r = den > 0 ? num / den : num;
+    }
     if (r <= tol) {
       if (steps_out) *steps_out = done;
       if (residual_out) *residual_out = r;
@@ -1237,11 +1357,383 @@ dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
   return DJ_OK;
 }
 
+dj_status dj_get_group_info(const dj_mesh* mc, int* n_groups, double* dt, double* dt_crit,
+                            double* residual) {
+  dj_mesh* m = const_cast<dj_mesh*>(mc);
+  if (!m) return DJ_ERR_INVALID_ARG;
+  const int G = std::max(1, m->n_groups);
+  if (n_groups) *n_groups = G;
+  if (!m->precomputed) return (dt || dt_crit || residual) ? fail(m, DJ_ERR_NOT_PRECOMPUTED, "not precomputed") : DJ_OK;
+  for (int g = 0; g < G; ++g) {
+    if (dt) dt[g] = m->group_dt[g];
+    if (dt_crit) dt_crit[g] = m->group_dt_crit[g];
+    if (residual) residual[g] = g < (int)m->group_r.size() ? m->group_r[g] : NAN;
+  }
+  return DJ_OK;
+}
+
 void dj_mesh_destroy(dj_mesh* m) {
   if (!m) return;
   if (m->device >= 0) cudaSetDevice(m->device);
   release_device(m);
   delete m;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: instances of one element type are merged into one internal mesh
+// with one group per instance; the (at most two) internal meshes advance as
+// two independent chains of kernels captured in one CUDA graph.
+// ---------------------------------------------------------------------------
+struct dj_batch {
+  int n = 0;
+  dj_mesh* part[2] = {nullptr, nullptr};  // 0: T4 instances, 1: H8 instances
+  std::vector<int> inst_part, inst_group;
+  std::vector<long long> inst_node_off, inst_nodes, inst_elems;
+  cudaStream_t cap = nullptr, side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaGraphExec_t run_exec = nullptr, relax_exec = nullptr;
+  int run_chunk = 0, relax_k = 0;
+  bool precomputed = false;
+  std::string last_error;
+};
+
+namespace {
+dj_status bfail(dj_batch* b, dj_status s, const char* msg) {
+  if (b) b->last_error = msg;
+  return s;
+}
+void batch_release_graphs(dj_batch* b) {
+  if (b->run_exec) cudaGraphExecDestroy(b->run_exec);
+  if (b->relax_exec) cudaGraphExecDestroy(b->relax_exec);
+  b->run_exec = b->relax_exec = nullptr;
+  b->run_chunk = b->relax_k = 0;
+}
+
+// Capture two independent chains: part 0 on the capture stream, part 1 on a
+// forked side stream joined at the end.
+template <class F>
+dj_status batch_capture(dj_batch* b, cudaGraphExec_t* out, F body) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
+  cudaError_t be = cudaEventRecord(b->fork, b->cap);
+  if (be == cudaSuccess) be = cudaStreamWaitEvent(b->side, b->fork, 0);
+  if (be == cudaSuccess && b->part[0]) be = body(b->part[0], b->cap);
+  if (be == cudaSuccess && b->part[1]) be = body(b->part[1], b->side);
+  if (be == cudaSuccess) be = cudaEventRecord(b->join, b->side);
+  if (be == cudaSuccess) be = cudaStreamWaitEvent(b->cap, b->join, 0);
+  cudaError_t ee = cudaStreamEndCapture(b->cap, &g);
+  if (be != cudaSuccess || ee != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(be != cudaSuccess ? be : ee));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
+  return DJ_OK;
+}
+}  // namespace
+
+extern "C" {
+
+dj_status dj_batch_create(dj_mesh* const* inst, int n, dj_batch** out) {
+  if (!out) return DJ_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!inst || n <= 0) return DJ_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!inst[i] || !inst[i]->materials_set) return DJ_ERR_INVALID_ARG;
+  dj_batch* b = new (std::nothrow) dj_batch();
+  if (!b) return DJ_ERR_OOM;
+  b->n = n;
+  b->inst_part.resize(n);
+  b->inst_group.resize(n);
+  b->inst_node_off.resize(n);
+  b->inst_nodes.resize(n);
+  b->inst_elems.resize(n);
+  for (int pt = 0; pt < 2; ++pt) {
+    const int et = pt == 0 ? DJ_TET4 : DJ_HEX8;
+    std::vector<double> X, mu, ka, rh, ea, eb, c1, ad, bd, tg, R;
+    std::vector<int> conn, grp;
+    std::vector<unsigned char> mo;
+    std::vector<long long> dof;
+    long long noff = 0;
+    int ng = 0;
+    bool any_R = false;
+    for (int i = 0; i < n; ++i) {
+      const dj_mesh* m = inst[i];
+      if (m->elem_type != et) continue;
+      b->inst_part[i] = pt;
+      b->inst_group[i] = ng;
+      b->inst_node_off[i] = noff;
+      b->inst_nodes[i] = m->N;
+      b->inst_elems[i] = m->E;
+      X.insert(X.end(), m->X.begin(), m->X.end());
+      for (int v : m->conn) conn.push_back((int)(v + noff));
+      grp.insert(grp.end(), m->E, ng);
+      mo.insert(mo.end(), m->model.begin(), m->model.end());
+      mu.insert(mu.end(), m->mu.begin(), m->mu.end());
+      ka.insert(ka.end(), m->kappa.begin(), m->kappa.end());
+      rh.insert(rh.end(), m->rho.begin(), m->rho.end());
+      ea.insert(ea.end(), m->eta_a.begin(), m->eta_a.end());
+      eb.insert(eb.end(), m->eta_b.begin(), m->eta_b.end());
+      c1.insert(c1.end(), m->c01.begin(), m->c01.end());
+      ad.insert(ad.end(), m->adir.begin(), m->adir.end());
+      bd.insert(bd.end(), m->bdir.begin(), m->bdir.end());
+      for (size_t k = 0; k < m->bc_dof.size(); ++k) {
+        dof.push_back(m->bc_dof[k] + 3 * noff);
+        tg.push_back(m->bc_target[k]);
+      }
+      if (!m->R.empty()) any_R = true;
+      noff += m->N;
+      ++ng;
+    }
+    if (ng == 0) continue;
+    if (any_R) {
+      R.assign(3 * noff, 0.0);
+      for (int i = 0; i < n; ++i)
+        if (b->inst_part[i] == pt && inst[i]->elem_type == et && !inst[i]->R.empty())
+          std::copy(inst[i]->R.begin(), inst[i]->R.end(), R.begin() + 3 * b->inst_node_off[i]);
+    }
+    dj_mesh* pm = nullptr;
+    dj_status st = dj_mesh_create(et, X.data(), noff, conn.data(), (long long)grp.size(), &pm);
+    if (st == DJ_OK)
+      st = dj_mesh_set_materials(pm, mo.data(), mu.data(), ka.data(), rh.data(), ea.data(), eb.data(),
+                                 c1.data(), ad.data(), bd.data());
+    if (st == DJ_OK) st = dj_mesh_set_bcs(pm, dof.data(), tg.data(), (long long)dof.size());
+    if (st == DJ_OK && any_R) st = dj_mesh_set_loads(pm, R.data());
+    if (st == DJ_OK) st = dj_mesh_set_groups(pm, grp.data(), ng);
+    if (st != DJ_OK) {
+      if (pm) dj_mesh_destroy(pm);
+      for (int q = 0; q < 2; ++q)
+        if (b->part[q]) dj_mesh_destroy(b->part[q]);
+      delete b;
+      return st;
+    }
+    b->part[pt] = pm;
+  }
+  *out = b;
+  return DJ_OK;
+}
+
+dj_status dj_batch_precompute(dj_batch* b, const dj_params* params) {
+  if (!b) return DJ_ERR_INVALID_ARG;
+  batch_release_graphs(b);
+  for (int pt = 0; pt < 2; ++pt)
+    if (b->part[pt]) {
+      dj_status s = dj_precompute(b->part[pt], params, nullptr);
+      if (s) return bfail(b, s, b->part[pt]->last_error.c_str());
+    }
+  if (!b->cap) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
+  }
+  b->precomputed = true;
+  return DJ_OK;
+}
+
+dj_status dj_batch_run_n(dj_batch* b, long long n, void* stream) {
+  if (!b || n < 0) return DJ_ERR_INVALID_ARG;
+  if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
+  (void)cudaGetLastError();
+  cudaStream_t st = (cudaStream_t)stream;
+  const int chunk = 16;
+  if (n >= chunk && !b->run_exec) {
+    dj_status s = batch_capture(b, &b->run_exec, [&](dj_mesh* m, cudaStream_t cs) {
+      for (int k = 0; k < chunk; ++k) {
+        cudaError_t e = launch_step(m, cs, NODE_UPDATE);
+        if (e != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    });
+    if (s) return s;
+    b->run_chunk = chunk;
+  }
+  long long left = n;
+  while (b->run_exec && left >= b->run_chunk) {
+    cudaError_t e = cudaGraphLaunch(b->run_exec, st);
+    if (e != cudaSuccess) return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
+    left -= b->run_chunk;
+  }
+  for (; left > 0; --left)
+    for (int pt = 0; pt < 2; ++pt)
+      if (b->part[pt]) {
+        cudaError_t e = launch_step(b->part[pt], st, NODE_UPDATE);
+        if (e != cudaSuccess) return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
+      }
+  return DJ_OK;
+}
+
+dj_status dj_batch_sync(dj_batch* b, void* stream) {
+  if (!b) return DJ_ERR_INVALID_ARG;
+  for (int pt = 0; pt < 2; ++pt)
+    if (b->part[pt]) {
+      dj_status s = dj_sync(b->part[pt], stream);
+      if (s) return bfail(b, s, b->part[pt]->last_error.c_str());
+    }
+  return DJ_OK;
+}
+
+dj_status dj_batch_relax_to_tol(dj_batch* b, double tol, long long max_steps, long long* steps_out,
+                                double* residual_out, void* stream) {
+  if (!b || !(tol >= 0) || max_steps < 0) return DJ_ERR_INVALID_ARG;
+  if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
+  (void)cudaGetLastError();
+  cudaStream_t st = (cudaStream_t)stream;
+  dj_mesh* any = b->part[0] ? b->part[0] : b->part[1];
+  const int k = any->params.relax_check_every;
+  if (!b->relax_exec || b->relax_k != k) {
+    if (b->relax_exec) cudaGraphExecDestroy(b->relax_exec);
+    b->relax_exec = nullptr;
+    dj_status s = batch_capture(b, &b->relax_exec, [&](dj_mesh* m, cudaStream_t cs) {
+      for (int j = 0; j < k - 1; ++j) {
+        cudaError_t e = launch_step(m, cs, NODE_UPDATE);
+        if (e != cudaSuccess) return e;
+      }
+      cudaError_t e = launch_step(m, cs, NODE_UPDATE_RESID);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->h_group_resid, m->d_group_resid, m->n_groups * sizeof(double2),
+                            cudaMemcpyDeviceToHost, cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, cs);
+      return e;
+    });
+    if (s) return s;
+    b->relax_k = k;
+  }
+  long long done = 0;
+  double r = INFINITY;
+  while (done + k <= max_steps) {
+    cudaError_t e = cudaGraphLaunch(b->relax_exec, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
+    done += k;
+    r = 0;
+    for (int pt = 0; pt < 2; ++pt) {
+      dj_mesh* m = b->part[pt];
+      if (!m) continue;
+      dj_status s = check_flags(m);
+      if (s) {
+        if (steps_out) *steps_out = done;
+        return bfail(b, s, m->last_error.c_str());
+      }
+      m->group_r.assign(m->n_groups, 0.0);
+      for (int g = 0; g < m->n_groups; ++g) {
+        const double num = std::sqrt(m->h_group_resid[g].x), den = std::sqrt(m->h_group_resid[g].y);
+        m->group_r[g] = den > 0 ? num / den : num;
+        r = std::max(r, m->group_r[g]);
+      }
+    }
+    if (r <= tol) {
+      if (steps_out) *steps_out = done;
+      if (residual_out) *residual_out = r;
+      return DJ_OK;
+    }
+  }
+  if (steps_out) *steps_out = done;
+  if (residual_out) *residual_out = r;
+  return bfail(b, DJ_ERR_NOT_CONVERGED, "batch residual above tol");
+}
+
+dj_status dj_batch_instance_info(dj_batch* b, int i, long long* n_nodes, long long* n_elems, double* dt,
+                                 double* residual) {
+  if (!b || i < 0 || i >= b->n) return DJ_ERR_INVALID_ARG;
+  dj_mesh* m = b->part[b->inst_part[i]];
+  const int g = b->inst_group[i];
+  if (n_nodes) *n_nodes = b->inst_nodes[i];
+  if (n_elems) *n_elems = b->inst_elems[i];
+  if (dt) *dt = m->precomputed ? m->group_dt[g] : NAN;
+  if (residual) *residual = g < (int)m->group_r.size() ? m->group_r[g] : NAN;
+  return DJ_OK;
+}
+
+dj_status dj_batch_get_displacements(dj_batch* b, int i, double* U_out) {
+  if (!b || i < 0 || i >= b->n || !U_out) return DJ_ERR_INVALID_ARG;
+  if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
+  dj_mesh* m = b->part[b->inst_part[i]];
+  if (cudaDeviceSynchronize() != cudaSuccess) return bfail(b, DJ_ERR_CUDA, "sync failed");
+  const long long off = b->inst_node_off[i], nn = b->inst_nodes[i];
+  int lo = m->node_new_of_old[off], hi = lo;
+  for (long long q = 0; q < nn; ++q) {
+    lo = std::min(lo, m->node_new_of_old[off + q]);
+    hi = std::max(hi, m->node_new_of_old[off + q]);
+  }
+  const long long cnt = hi - lo + 1;  // groups are contiguous internal ranges
+  std::vector<float4> U(cnt), L(cnt, make_float4(0.f, 0.f, 0.f, 0.f));
+  if (cudaMemcpy(U.data(), m->d_U + lo, cnt * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bfail(b, DJ_ERR_CUDA, "copy failed");
+  if (m->cmp && cudaMemcpy(L.data(), m->d_Ulo + lo, cnt * sizeof(float4), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bfail(b, DJ_ERR_CUDA, "copy failed");
+  for (long long q = 0; q < nn; ++q) {
+    const int v = m->node_new_of_old[off + q] - lo;
+    U_out[3 * q] = (double)U[v].x + (double)L[v].x;
+    U_out[3 * q + 1] = (double)U[v].y + (double)L[v].y;
+    U_out[3 * q + 2] = (double)U[v].z + (double)L[v].z;
+  }
+  return DJ_OK;
+}
+
+dj_status dj_batch_set_displacements(dj_batch* b, int i, const double* U0) {
+  if (!b || i < 0 || i >= b->n || !U0) return DJ_ERR_INVALID_ARG;
+  if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
+  dj_mesh* m = b->part[b->inst_part[i]];
+  if (cudaDeviceSynchronize() != cudaSuccess) return bfail(b, DJ_ERR_CUDA, "sync failed");
+  const long long off = b->inst_node_off[i], nn = b->inst_nodes[i];
+  int lo = m->node_new_of_old[off], hi = lo;
+  for (long long q = 0; q < nn; ++q) {
+    lo = std::min(lo, m->node_new_of_old[off + q]);
+    hi = std::max(hi, m->node_new_of_old[off + q]);
+  }
+  const long long cnt = hi - lo + 1;  // the instance's contiguous internal range
+  std::vector<float4> U(cnt), L(cnt), V(cnt);
+  for (long long q = 0; q < nn; ++q) {
+    const int v = m->node_new_of_old[off + q];
+    const int r = v - lo;
+    U[r] = make_float4((float)U0[3 * q], (float)U0[3 * q + 1], (float)U0[3 * q + 2], m->h_ai[v]);
+    L[r] = make_float4((float)(U0[3 * q] - U[r].x), (float)(U0[3 * q + 1] - U[r].y),
+                       (float)(U0[3 * q + 2] - U[r].z), 0.f);
+    V[r] = make_float4(0.f, 0.f, 0.f, bits_to_float(m->h_bcidx[v]));
+  }
+  if (cudaMemcpy(m->d_U + lo, U.data(), cnt * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_V + lo, V.data(), cnt * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess ||
+      (m->cmp && cudaMemcpy(m->d_Ulo + lo, L.data(), cnt * sizeof(float4), cudaMemcpyHostToDevice) != cudaSuccess))
+    return bfail(b, DJ_ERR_CUDA, "copy failed");
+  return DJ_OK;
+}
+
+dj_status dj_batch_get_info(const dj_batch* b, int* n_instances, long long* n_nodes, long long* n_elems,
+                            long long* n_tet_elems, long long* n_hex_elems) {
+  if (!b) return DJ_ERR_INVALID_ARG;
+  long long nn = 0, ne = 0, nt = 0, nh = 0;
+  for (int i = 0; i < b->n; ++i) {
+    nn += b->inst_nodes[i];
+    ne += b->inst_elems[i];
+    (b->inst_part[i] == 0 ? nt : nh) += b->inst_elems[i];
+  }
+  if (n_instances) *n_instances = b->n;
+  if (n_nodes) *n_nodes = nn;
+  if (n_elems) *n_elems = ne;
+  if (n_tet_elems) *n_tet_elems = nt;
+  if (n_hex_elems) *n_hex_elems = nh;
+  return DJ_OK;
+}
+
+const char* dj_batch_last_error(const dj_batch* b) { return b ? b->last_error.c_str() : "null batch"; }
+
+void dj_batch_destroy(dj_batch* b) {
+  if (!b) return;
+  batch_release_graphs(b);
+  for (int pt = 0; pt < 2; ++pt)
+    if (b->part[pt]) dj_mesh_destroy(b->part[pt]);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->join) cudaEventDestroy(b->join);
+  delete b;
 }
 
 }  // extern "C"

@@ -65,6 +65,8 @@ struct NodeArgs {
   const float4* R;        // external loads or nullptr
   float4* fout;           // force-only mode output
   double2* partials;      // residual partial sums per block
+  double2* node_resid;    // grouped meshes: per-node residual sums (else nullptr)
+  const float* bm1_node;  // grouped meshes with damping: per-node b - 1 (else nullptr)
   const DevState* st;
   int N;
   float bm1;              // b - 1 = (2 - alpha dt) / (2 + alpha dt)
@@ -99,6 +101,9 @@ cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceA
                                const TileArgs& t, int n_tiles, cudaStream_t s);
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
+// per-group residual sums over contiguous node ranges (one block per group)
+cudaError_t launch_group_resid(const double2* node_resid, const int* group_node_ptr, int n_groups,
+                               double2* out, cudaStream_t s);
 
 // force kernel variants
 enum { VAR_NH = 0, VAR_TI = 1, VAR_OT = 2, VAR_MR = 3, VAR_ALL = 4 };
@@ -126,9 +131,11 @@ struct PreArgs {
   double hg_coeff;
 };
 cudaError_t launch_precompute_elements(const PreArgs& a, cudaStream_t s);
+// dt_node: per-node time step (grouped meshes) or nullptr to use dt
 cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double* elem_mass,
-                             int E_pad, int N, double dt, double alpha, const int* bc_index,
-                             double* mass_out, float4* U, float4* V, cudaStream_t s);
+                             int E_pad, int N, double dt, const double* dt_node, double alpha,
+                             const int* bc_index, double* mass_out, float4* U, float4* V,
+                             cudaStream_t s);
 cudaError_t launch_min_reduce(const double* v, int n, double* out, cudaStream_t s);
 cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, int N, float* out,
                                    cudaStream_t s);

@@ -189,9 +189,10 @@ __global__ void precompute_elements_kernel(PreArgs a) {
 // lumped mass m_i = sum over the node's slots of rho 0V / n_e (FP64, fixed order),
 // then the update coefficient a_i = 2 dt^2 / ((2 + alpha dt) m_i) (Eq. 13)
 __global__ void node_mass_kernel(const int* __restrict__ sell, const int* __restrict__ chunk_ptr,
-                                 const double* __restrict__ elem_mass, int E_pad, int N, double dt,
-                                 double alpha, const int* __restrict__ bc_index, double* mass_out,
-                                 float4* U, float4* V) {
+                                 const double* __restrict__ elem_mass, int E_pad, int N, double dt0,
+                                 const double* __restrict__ dt_node, double alpha,
+                                 const int* __restrict__ bc_index, double* mass_out, float4* U,
+                                 float4* V) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int chunk = i / SELL_C, lane = i % SELL_C;
@@ -201,6 +202,7 @@ __global__ void node_mass_kernel(const int* __restrict__ sell, const int* __rest
     if (s >= 0) m += elem_mass[s % E_pad];
   }
   mass_out[i] = m;
+  const double dt = dt_node ? dt_node[i] : dt0;
   const double ai = m > 0.0 ? 2.0 * dt * dt / ((2.0 + alpha * dt) * m) : 0.0;
   U[i] = make_float4(0.f, 0.f, 0.f, (float)ai);
   V[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(bc_index[i]));
@@ -239,11 +241,12 @@ cudaError_t launch_precompute_elements(const PreArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double* elem_mass,
-                             int E_pad, int N, double dt, double alpha, const int* bc_index,
-                             double* mass_out, float4* U, float4* V, cudaStream_t s) {
+                             int E_pad, int N, double dt, const double* dt_node, double alpha,
+                             const int* bc_index, double* mass_out, float4* U, float4* V,
+                             cudaStream_t s) {
   const int t = 256;
-  node_mass_kernel<<<(N + t - 1) / t, t, 0, s>>>(sell, chunk_ptr, elem_mass, E_pad, N, dt, alpha,
-                                                 bc_index, mass_out, U, V);
+  node_mass_kernel<<<(N + t - 1) / t, t, 0, s>>>(sell, chunk_ptr, elem_mass, E_pad, N, dt, dt_node,
+                                                 alpha, bc_index, mass_out, U, V);
   return cudaGetLastError();
 }
 

@@ -668,7 +668,8 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       const float4 U = a.U[i];
       const float ai = U.w;
       // velocity form of the central difference: D^{n+1} = a (R - F) + (b - 1) D^n
-      float dd[3] = {fmaf(-ai, fx, a.bm1 * V.x), fmaf(-ai, fy, a.bm1 * V.y), fmaf(-ai, fz, a.bm1 * V.z)};
+      const float bm1 = a.bm1_node ? __ldg(a.bm1_node + i) : a.bm1;
+      float dd[3] = {fmaf(-ai, fx, bm1 * V.x), fmaf(-ai, fy, bm1 * V.y), fmaf(-ai, fz, bm1 * V.z)};
       const float uh[3] = {U.x, U.y, U.z};
       float nh[3], nl[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
       if (CMP) {
@@ -718,6 +719,10 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       }
     }
   }
+  if (MODE == NODE_UPDATE_RESID && a.node_resid) {
+    if (i < a.N) a.node_resid[i] = make_double2(num2, den2);
+    return;
+  }
   if (MODE == NODE_UPDATE_RESID) {
     __shared__ double sn[NODE_THREADS / 32], sd[NODE_THREADS / 32];
 #pragma unroll
@@ -763,6 +768,30 @@ __global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevS
     st->resid_num2 = sn[0];
     st->resid_den2 = sd[0];
   }
+}
+
+// one block per group: fixed-order sum of the per-node residual terms of the
+// group's contiguous node range
+__global__ void group_resid_kernel(const double2* __restrict__ nr, const int* __restrict__ gptr,
+                                   double2* out) {
+  __shared__ double sn[256], sd[256];
+  const int g = blockIdx.x;
+  double tn = 0.0, td = 0.0;
+  for (int q = gptr[g] + threadIdx.x; q < gptr[g + 1]; q += blockDim.x) {
+    tn += nr[q].x;
+    td += nr[q].y;
+  }
+  sn[threadIdx.x] = tn;
+  sd[threadIdx.x] = td;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sn[threadIdx.x] += sn[threadIdx.x + o];
+      sd[threadIdx.x] += sd[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[g] = make_double2(sn[0], sd[0]);
 }
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
@@ -841,6 +870,12 @@ cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s) {
   if (mode == NODE_UPDATE) return launch_node_m<NODE_UPDATE>(cmp, a, s);
   if (mode == NODE_UPDATE_RESID) return launch_node_m<NODE_UPDATE_RESID>(cmp, a, s);
   return launch_node_m<NODE_FORCE_ONLY>(cmp, a, s);
+}
+
+cudaError_t launch_group_resid(const double2* node_resid, const int* group_node_ptr, int n_groups,
+                               double2* out, cudaStream_t s) {
+  group_resid_kernel<<<n_groups, 256, 0, s>>>(node_resid, group_node_ptr, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s) {

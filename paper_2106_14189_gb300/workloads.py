@@ -400,7 +400,7 @@ def batch_instances(n_instances: int = 256, seed: int = 0, e_min: int = 5000,
 
     Each instance is a box of random aspect with E in U[1, 10] kPa,
     nu in U[0.45, 0.49], rho = 1000, fixed base and a random displacement of
-    the top face (or of one side face).
+    the top face (or of one side face, scaled by height z / lz).
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -425,7 +425,10 @@ def batch_instances(n_instances: int = 256, seed: int = 0, e_min: int = 5000,
         if side == 0:
             d1, t1 = _face_bcs(X, 2, lz, tol, [(0, disp[0]), (1, disp[1]), (2, disp[2])])
         else:
+            # side face x = lx: displacement grows linearly with height so that it
+            # is compatible with the fixed base along the shared edge
             d1, t1 = _face_bcs(X, 0, lx, tol, [(0, disp[0]), (1, disp[1]), (2, disp[2])])
+            t1 = t1 * X[d1 // 3, 2] / lz
             keep = ~np.isin(d1, d0)
             d1, t1 = d1[keep], t1[keep]
         out.append(Problem(name=f"batch_{inst}", elem_type=et, X=X, conn=conn,
