@@ -227,6 +227,18 @@ dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
  * order, enqueued on `stream`. */
 dj_status dj_get_displacements_device(dj_mesh* mesh, float* d_U_out, void* stream);
 
+/* Warm start from device memory: U^0 = U^-1 = d_U0 (n_nodes * 3 floats, caller
+ * order); enqueued on `stream`; compensated low parts are reset to 0. */
+dj_status dj_set_displacements_device(dj_mesh* mesh, const float* d_U0, void* stream);
+
+/* Evaluate a candidate field d_U (device, n_nodes * 3 floats, caller order)
+ * without changing the stepping state: residual_out receives the relaxation
+ * residual r = ||F - R||_free / ||F - R||_prescribed of that field (largest
+ * group residual for grouped meshes; +inf when an element is inverted) and
+ * inverted_out 1 if some element of the field has det tJ <= 0.  Synchronous. */
+dj_status dj_evaluate_field(dj_mesh* mesh, const float* d_U, double* residual_out, int* inverted_out,
+                            void* stream);
+
 /* Assembled internal forces F(U) = sum_e F^(e) (Eq. 13) for host displacements
  * U (n_nodes * 3 doubles), written to host F_out (n_nodes * 3).  The stepping
  * state is left unchanged.  Synchronous. */
@@ -277,12 +289,61 @@ dj_status dj_batch_instance_info(dj_batch* batch, int i, long long* n_nodes, lon
                                  double* dt, double* residual);
 /* Displacements of instance i (host, its n_nodes * 3 doubles, its node order). */
 dj_status dj_batch_get_displacements(dj_batch* batch, int i, double* U_out);
+/* Displacements of instance i into device memory (its n_nodes * 3 floats, its
+ * node order), enqueued on `stream`. */
+dj_status dj_batch_get_displacements_device(dj_batch* batch, int i, float* d_U_out, void* stream);
 /* Warm start of instance i: U^0 = U^-1 = U0.  Synchronous. */
 dj_status dj_batch_set_displacements(dj_batch* batch, int i, const double* U0);
 dj_status dj_batch_get_info(const dj_batch* batch, int* n_instances, long long* n_nodes,
                             long long* n_elems, long long* n_tet_elems, long long* n_hex_elems);
 const char* dj_batch_last_error(const dj_batch* batch);
 void dj_batch_destroy(dj_batch* batch);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start for dynamic relaxation (no counterpart in the paper, which
+ * names learning only as future work, Sec. 8): proper orthogonal decomposition
+ * of fields and a multilayer perceptron trained with the library's kernels.
+ * All float pointers below are device memory; matrices are row-major unless
+ * stated.
+ * ------------------------------------------------------------------------- */
+typedef struct dj_mlp dj_mlp;
+
+/* MLP with n_layers affine layers of widths[0] -> ... -> widths[n_layers],
+ * tanh between layers, linear output.  Weights Glorot-uniform from `seed`,
+ * biases 0.  Parameters packed as [W_1 (out x in), b_1, W_2, b_2, ...]. */
+dj_status dj_mlp_create(const int* widths, int n_layers, unsigned long long seed, dj_mlp** out);
+long long dj_mlp_num_params(const dj_mlp* mlp);
+dj_status dj_mlp_get_params(dj_mlp* mlp, float* host, long long n);
+/* Replace the parameters (host) and reset the Adam moments. */
+dj_status dj_mlp_set_params(dj_mlp* mlp, const float* host, long long n);
+dj_status dj_mlp_get_grads(dj_mlp* mlp, float* host, long long n);
+/* Y (batch x out) = MLP(X (batch x in)). */
+dj_status dj_mlp_forward(dj_mlp* mlp, const float* d_X, int batch, float* d_Y, void* stream);
+/* Forward + backward of L = 1/(batch n_out) sum_ij w_j (Y_ij - T_ij)^2 (w: n_out
+ * weights or NULL); gradients overwrite the internal gradient buffer.
+ * loss_out (host, optional) synchronizes the stream. */
+dj_status dj_mlp_loss_grad(dj_mlp* mlp, const float* d_X, const float* d_T, const float* d_w, int batch,
+                           double* loss_out, void* stream);
+/* One Adam step with bias correction on the last gradients. */
+dj_status dj_mlp_adam_step(dj_mlp* mlp, float lr, float beta1, float beta2, float eps, void* stream);
+const char* dj_mlp_last_error(const dj_mlp* mlp);
+void dj_mlp_destroy(dj_mlp* mlp);
+
+/* POD of cols snapshots of length rows (d_Y column-major: snapshot c at
+ * d_Y + c * rows; cols <= 4096): d_mean (rows) the snapshot mean, d_modes
+ * (rows x r, row-major) the r leading orthonormal modes of the centred
+ * snapshots (method of snapshots: Gram matrix on the GPU with FP64 slab
+ * accumulation, FP64 Jacobi eigen-decomposition on the host), sigma_out (host,
+ * optional, r) the singular values.  Synchronous. */
+dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d_mean, float* d_modes,
+                     double* sigma_out, void* stream);
+/* d_Q (cols x r) = (X - mean)^T modes for column-major d_X (rows x cols);
+ * d_mean may be NULL.  Synchronous. */
+dj_status dj_pod_project(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_X,
+                         int cols, float* d_Q, void* stream);
+/* d_X (column-major rows x cols) = mean + modes Q^T for d_Q (cols x r). */
+dj_status dj_pod_expand(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_Q,
+                        int cols, float* d_X, void* stream);
 
 #ifdef __cplusplus
 }

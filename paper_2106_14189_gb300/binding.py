@@ -34,6 +34,10 @@ EXPORTS = [
     "dj_batch_create", "dj_batch_precompute", "dj_batch_run_n", "dj_batch_sync",
     "dj_batch_relax_to_tol", "dj_batch_instance_info", "dj_batch_get_displacements",
     "dj_batch_set_displacements", "dj_batch_get_info", "dj_batch_last_error", "dj_batch_destroy",
+    "dj_set_displacements_device", "dj_evaluate_field", "dj_batch_get_displacements_device",
+    "dj_mlp_create", "dj_mlp_num_params", "dj_mlp_get_params", "dj_mlp_set_params",
+    "dj_mlp_get_grads", "dj_mlp_forward", "dj_mlp_loss_grad", "dj_mlp_adam_step",
+    "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
 ]
 
 
@@ -115,6 +119,22 @@ def lib():
         "dj_batch_get_info": (C.c_int, [_P, C.POINTER(C.c_int), _LL, _LL, _LL, _LL]),
         "dj_batch_last_error": (C.c_char_p, [_P]),
         "dj_batch_destroy": (None, [_P]),
+        "dj_set_displacements_device": (C.c_int, [_P, _P, _P]),
+        "dj_evaluate_field": (C.c_int, [_P, _P, _D, C.POINTER(C.c_int), _P]),
+        "dj_batch_get_displacements_device": (C.c_int, [_P, C.c_int, _P, _P]),
+        "dj_mlp_create": (C.c_int, [C.POINTER(C.c_int), C.c_int, C.c_ulonglong, C.POINTER(_P)]),
+        "dj_mlp_num_params": (C.c_longlong, [_P]),
+        "dj_mlp_get_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_longlong]),
+        "dj_mlp_set_params": (C.c_int, [_P, C.POINTER(C.c_float), C.c_longlong]),
+        "dj_mlp_get_grads": (C.c_int, [_P, C.POINTER(C.c_float), C.c_longlong]),
+        "dj_mlp_forward": (C.c_int, [_P, _P, C.c_int, _P, _P]),
+        "dj_mlp_loss_grad": (C.c_int, [_P, _P, _P, _P, C.c_int, _D, _P]),
+        "dj_mlp_adam_step": (C.c_int, [_P, C.c_float, C.c_float, C.c_float, C.c_float, _P]),
+        "dj_mlp_last_error": (C.c_char_p, [_P]),
+        "dj_mlp_destroy": (None, [_P]),
+        "dj_pod_fit": (C.c_int, [_P, C.c_longlong, C.c_int, C.c_int, _P, _P, _D, _P]),
+        "dj_pod_project": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
+        "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -375,6 +395,95 @@ def dj_batch_get_info(b):
 
 def dj_batch_destroy(b):
     lib().dj_batch_destroy(b)
+
+
+def dj_set_displacements_device(h, d_ptr, stream=None):
+    _check(lib().dj_set_displacements_device(h, d_ptr, _stream(stream)), "dj_set_displacements_device", h)
+
+
+def dj_evaluate_field(h, d_ptr, stream=None):
+    r, inv = C.c_double(0), C.c_int(0)
+    _check(lib().dj_evaluate_field(h, d_ptr, C.byref(r), C.byref(inv), _stream(stream)),
+           "dj_evaluate_field", h)
+    return r.value, bool(inv.value)
+
+
+def dj_batch_get_displacements_device(b, i, d_ptr, stream=None):
+    _bcheck(lib().dj_batch_get_displacements_device(b, int(i), d_ptr, _stream(stream)),
+            "dj_batch_get_displacements_device", b)
+
+
+def _mcheck(st, where, m):
+    if st != DJ_OK:
+        msg = lib().dj_mlp_last_error(m) if m else b""
+        raise DJError(st, where, msg.decode() if msg else "")
+
+
+def dj_mlp_create(widths, seed=0):
+    w = (C.c_int * len(widths))(*widths)
+    m = _P()
+    _mcheck(lib().dj_mlp_create(w, len(widths) - 1, int(seed), C.byref(m)), "dj_mlp_create", None)
+    return m
+
+
+def dj_mlp_num_params(m):
+    return int(lib().dj_mlp_num_params(m))
+
+
+def dj_mlp_get_params(m):
+    n = dj_mlp_num_params(m)
+    out = np.empty(n, dtype=np.float32)
+    _mcheck(lib().dj_mlp_get_params(m, out.ctypes.data_as(C.POINTER(C.c_float)), n), "dj_mlp_get_params", m)
+    return out
+
+
+def dj_mlp_set_params(m, p):
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    _mcheck(lib().dj_mlp_set_params(m, p.ctypes.data_as(C.POINTER(C.c_float)), p.size), "dj_mlp_set_params", m)
+
+
+def dj_mlp_get_grads(m):
+    n = dj_mlp_num_params(m)
+    out = np.empty(n, dtype=np.float32)
+    _mcheck(lib().dj_mlp_get_grads(m, out.ctypes.data_as(C.POINTER(C.c_float)), n), "dj_mlp_get_grads", m)
+    return out
+
+
+def dj_mlp_forward(m, d_X, batch, d_Y, stream=None):
+    _mcheck(lib().dj_mlp_forward(m, d_X, int(batch), d_Y, _stream(stream)), "dj_mlp_forward", m)
+
+
+def dj_mlp_loss_grad(m, d_X, d_T, d_w, batch, stream=None, want_loss=True):
+    loss = C.c_double(0)
+    _mcheck(lib().dj_mlp_loss_grad(m, d_X, d_T, d_w, int(batch), C.byref(loss) if want_loss else None,
+                                   _stream(stream)), "dj_mlp_loss_grad", m)
+    return loss.value
+
+
+def dj_mlp_adam_step(m, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _mcheck(lib().dj_mlp_adam_step(m, float(lr), float(beta1), float(beta2), float(eps), _stream(stream)),
+            "dj_mlp_adam_step", m)
+
+
+def dj_mlp_destroy(m):
+    lib().dj_mlp_destroy(m)
+
+
+def dj_pod_fit(d_Y, rows, cols, r, d_mean, d_modes, stream=None):
+    sig = np.empty(r)
+    st = lib().dj_pod_fit(d_Y, int(rows), int(cols), int(r), d_mean, d_modes, _dptr(sig), _stream(stream))
+    _check(st, "dj_pod_fit")
+    return sig
+
+
+def dj_pod_project(d_modes, d_mean, rows, r, d_X, cols, d_Q, stream=None):
+    _check(lib().dj_pod_project(d_modes, d_mean, int(rows), int(r), d_X, int(cols), d_Q, _stream(stream)),
+           "dj_pod_project")
+
+
+def dj_pod_expand(d_modes, d_mean, rows, r, d_Q, cols, d_X, stream=None):
+    _check(lib().dj_pod_expand(d_modes, d_mean, int(rows), int(r), d_Q, int(cols), d_X, _stream(stream)),
+           "dj_pod_expand")
 
 
 # ------------------------------------------------------------- convenience --

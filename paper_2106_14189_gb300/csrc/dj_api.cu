@@ -1228,6 +1228,75 @@ dj_status dj_get_displacements_device(dj_mesh* m, float* d_U_out, void* stream) 
   return DJ_OK;
 }
 
+dj_status dj_set_displacements_device(dj_mesh* m, const float* d_U0, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!d_U0) return fail(m, DJ_ERR_INVALID_ARG, "null field");
+  CK(launch_from_caller_order(d_U0, m->d_perm, (int)m->N, m->d_U, m->d_V, m->d_Ulo, (cudaStream_t)stream));
+  return DJ_OK;
+}
+
+dj_status dj_evaluate_field(dj_mesh* m, const float* d_U, double* residual_out, int* inverted_out, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!d_U) return fail(m, DJ_ERR_INVALID_ARG, "null field");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nb = m->N * sizeof(float4);
+  float4 *sU = nullptr, *sV = nullptr, *sL = nullptr;
+  cudaError_t e = cudaMalloc(&sU, nb);
+  if (e == cudaSuccess) e = cudaMalloc(&sV, nb);
+  if (e == cudaSuccess && m->cmp) e = cudaMalloc(&sL, nb);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sU, m->d_U, nb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sV, m->d_V, nb, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && sL) e = cudaMemcpyAsync(sL, m->d_Ulo, nb, cudaMemcpyDeviceToDevice, st);
+  DevState before{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&before, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  DevState clean = before;  // evaluate with cleared error flags
+  clean.err_flags = 0;
+  clean.bad_elem = INT_MAX;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_state, &clean, sizeof(DevState), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_from_caller_order(d_U, m->d_perm, (int)m->N, m->d_U, m->d_V, m->d_Ulo, st);
+  if (e == cudaSuccess) e = launch_force_any(m, 0, st);
+  if (e == cudaSuccess) e = launch_node(NODE_RESID_ONLY, m->cmp, node_args(m), st);
+  if (e == cudaSuccess) {
+    if (m->n_groups > 0)
+      e = launch_group_resid(m->d_node_resid, m->d_group_node_ptr, m->n_groups, m->d_group_resid, st);
+    else
+      e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, st);
+  }
+  std::vector<double2> gr(std::max(1, m->n_groups));
+  if (e == cudaSuccess && m->n_groups > 0)
+    e = cudaMemcpyAsync(gr.data(), m->d_group_resid, m->n_groups * sizeof(double2), cudaMemcpyDeviceToHost, st);
+  DevState after{};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&after, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // restore the stepping state and its error flags
+  if (sU) cudaMemcpyAsync(m->d_U, sU, nb, cudaMemcpyDeviceToDevice, st);
+  if (sV) cudaMemcpyAsync(m->d_V, sV, nb, cudaMemcpyDeviceToDevice, st);
+  if (sL) cudaMemcpyAsync(m->d_Ulo, sL, nb, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(m->d_state, &before, sizeof(DevState), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+  if (sU) cudaFree(sU);
+  if (sV) cudaFree(sV);
+  if (sL) cudaFree(sL);
+  if (e != cudaSuccess) return fail(m, DJ_ERR_CUDA, "evaluate field: %s", cudaGetErrorString(e));
+  double r = 0;
+  if (m->n_groups > 0) {
+    for (int g = 0; g < m->n_groups; ++g) {
+      const double num = std::sqrt(gr[g].x), den = std::sqrt(gr[g].y);
+      r = std::max(r, den > 0 ? num / den : num);
+    }
+  } else {
+    const double num = std::sqrt(after.resid_num2), den = std::sqrt(after.resid_den2);
+    r = den > 0 ? num / den : num;
+  }
+  const int bad = after.err_flags != 0;
+  if (residual_out) *residual_out = bad ? INFINITY : r;
+  if (inverted_out) *inverted_out = bad;
+  return DJ_OK;
+}
+
 dj_status dj_internal_forces(dj_mesh* m, const double* U, double* F_out) {
   dj_status s = need_ready(m);
   if (s) return s;
@@ -1675,6 +1744,15 @@ dj_status dj_batch_get_displacements(dj_batch* b, int i, double* U_out) {
     U_out[3 * q + 2] = (double)U[v].z + (double)L[v].z;
   }
   return DJ_OK;
+}
+
+dj_status dj_batch_get_displacements_device(dj_batch* b, int i, float* d_out, void* stream) {
+  if (!b || i < 0 || i >= b->n || !d_out) return DJ_ERR_INVALID_ARG;
+  if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
+  dj_mesh* m = b->part[b->inst_part[i]];
+  const cudaError_t e = launch_to_caller_order(m->d_U, m->d_perm + b->inst_node_off[i], (int)b->inst_nodes[i],
+                                               d_out, (cudaStream_t)stream);
+  return e == cudaSuccess ? DJ_OK : bfail(b, DJ_ERR_CUDA, cudaGetErrorString(e));
 }
 
 dj_status dj_batch_set_displacements(dj_batch* b, int i, const double* U0) {

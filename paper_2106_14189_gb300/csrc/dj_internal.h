@@ -87,7 +87,7 @@ struct TileArgs {
   int smem_nodes;               // capacity of the staged-node array
 };
 
-enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2 };
+enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_ONLY = 3 };
 enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1 };
 
 constexpr int NODE_THREADS = 256;
@@ -139,5 +139,9 @@ cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double
 cudaError_t launch_min_reduce(const double* v, int n, double* out, cudaStream_t s);
 cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, int N, float* out,
                                    cudaStream_t s);
+// U (internal) = caller-order field (N x 3 floats); w of U and of V kept,
+// U^n - U^{n-1} = 0, low part = 0
+cudaError_t launch_from_caller_order(const float* src, const int* node_new_of_old, int N, float4* U,
+                                     float4* V, float4* Ulo, cudaStream_t s);
 
 }  // namespace dj

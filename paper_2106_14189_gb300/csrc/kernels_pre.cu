@@ -232,7 +232,26 @@ __global__ void to_caller_order_kernel(const float4* __restrict__ U, const int* 
   out[3 * (size_t)i + 2] = u.z;
 }
 
+__global__ void from_caller_order_kernel(const float* __restrict__ src, const int* __restrict__ perm, int N,
+                                         float4* U, float4* V, float4* Ulo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // caller node id
+  if (i >= N) return;
+  const int v = perm[i];
+  const float4 u = U[v];
+  U[v] = make_float4(src[3 * (size_t)i], src[3 * (size_t)i + 1], src[3 * (size_t)i + 2], u.w);
+  const float4 d = V[v];
+  V[v] = make_float4(0.f, 0.f, 0.f, d.w);
+  if (Ulo) Ulo[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 }  // namespace
+
+cudaError_t launch_from_caller_order(const float* src, const int* node_new_of_old, int N, float4* U,
+                                     float4* V, float4* Ulo, cudaStream_t s) {
+  const int t = 256;
+  from_caller_order_kernel<<<(N + t - 1) / t, t, 0, s>>>(src, node_new_of_old, N, U, V, Ulo);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_precompute_elements(const PreArgs& a, cudaStream_t s) {
   const int t = 128;

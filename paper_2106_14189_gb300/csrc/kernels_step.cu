@@ -664,6 +664,15 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
     const int bc = __float_as_int(V.w);
     if (MODE == NODE_FORCE_ONLY) {
       a.fout[i] = make_float4(fx, fy, fz, 0.f);
+    } else if (MODE == NODE_RESID_ONLY) {
+      int mask = 0;
+      if (bc >= 0) mask = __float_as_int(__ldg(a.bct + bc).w);
+      const double f3[3] = {fx, fy, fz};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (mask & (1 << q)) den2 += f3[q] * f3[q];
+        else num2 += f3[q] * f3[q];
+      }
     } else {
       const float4 U = a.U[i];
       const float ai = U.w;
@@ -719,11 +728,12 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       }
     }
   }
-  if (MODE == NODE_UPDATE_RESID && a.node_resid) {
+  constexpr bool RESID = MODE == NODE_UPDATE_RESID || MODE == NODE_RESID_ONLY;
+  if (RESID && a.node_resid) {
     if (i < a.N) a.node_resid[i] = make_double2(num2, den2);
     return;
   }
-  if (MODE == NODE_UPDATE_RESID) {
+  if (RESID) {
     __shared__ double sn[NODE_THREADS / 32], sd[NODE_THREADS / 32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -869,6 +879,7 @@ cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s) {
   if (mode == NODE_UPDATE) return launch_node_m<NODE_UPDATE>(cmp, a, s);
   if (mode == NODE_UPDATE_RESID) return launch_node_m<NODE_UPDATE_RESID>(cmp, a, s);
+  if (mode == NODE_RESID_ONLY) return launch_node_m<NODE_RESID_ONLY>(cmp, a, s);
   return launch_node_m<NODE_FORCE_ONLY>(cmp, a, s);
 }
 
