@@ -227,6 +227,11 @@ dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
  * order, enqueued on `stream`. */
 dj_status dj_get_displacements_device(dj_mesh* mesh, float* d_U_out, void* stream);
 
+/* Set the step counter n (synchronous).  Prescribed values follow
+ * target * s(min(n / ramp_steps, 1)), so a warm-started relaxation sets
+ * n >= ramp_steps to hold the targets from its first step. */
+dj_status dj_set_step(dj_mesh* mesh, long long step);
+
 /* Warm start from device memory: U^0 = U^-1 = d_U0 (n_nodes * 3 floats, caller
  * order); enqueued on `stream`; compensated low parts are reset to 0. */
 dj_status dj_set_displacements_device(dj_mesh* mesh, const float* d_U0, void* stream);
@@ -289,6 +294,8 @@ dj_status dj_batch_instance_info(dj_batch* batch, int i, long long* n_nodes, lon
                                  double* dt, double* residual);
 /* Displacements of instance i (host, its n_nodes * 3 doubles, its node order). */
 dj_status dj_batch_get_displacements(dj_batch* batch, int i, double* U_out);
+/* dj_set_step on every instance. */
+dj_status dj_batch_set_step(dj_batch* batch, long long step);
 /* Displacements of instance i into device memory (its n_nodes * 3 floats, its
  * node order), enqueued on `stream`. */
 dj_status dj_batch_get_displacements_device(dj_batch* batch, int i, float* d_U_out, void* stream);

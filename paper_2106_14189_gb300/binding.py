@@ -38,6 +38,7 @@ EXPORTS = [
     "dj_mlp_create", "dj_mlp_num_params", "dj_mlp_get_params", "dj_mlp_set_params",
     "dj_mlp_get_grads", "dj_mlp_forward", "dj_mlp_loss_grad", "dj_mlp_adam_step",
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
+    "dj_set_step", "dj_batch_set_step",
 ]
 
 
@@ -135,6 +136,8 @@ def lib():
         "dj_pod_fit": (C.c_int, [_P, C.c_longlong, C.c_int, C.c_int, _P, _P, _D, _P]),
         "dj_pod_project": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
+        "dj_set_step": (C.c_int, [_P, C.c_longlong]),
+        "dj_batch_set_step": (C.c_int, [_P, C.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -399,6 +402,14 @@ def dj_batch_destroy(b):
 
 def dj_set_displacements_device(h, d_ptr, stream=None):
     _check(lib().dj_set_displacements_device(h, d_ptr, _stream(stream)), "dj_set_displacements_device", h)
+
+
+def dj_set_step(h, step):
+    _check(lib().dj_set_step(h, int(step)), "dj_set_step", h)
+
+
+def dj_batch_set_step(b, step):
+    _bcheck(lib().dj_batch_set_step(b, int(step)), "dj_batch_set_step", b)
 
 
 def dj_evaluate_field(h, d_ptr, stream=None):

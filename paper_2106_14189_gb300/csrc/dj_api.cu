@@ -1228,6 +1228,15 @@ dj_status dj_get_displacements_device(dj_mesh* m, float* d_U_out, void* stream) 
   return DJ_OK;
 }
 
+dj_status dj_set_step(dj_mesh* m, long long step) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (step < 0) return fail(m, DJ_ERR_INVALID_ARG, "step < 0");
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&m->d_state->step, &step, sizeof(long long), cudaMemcpyHostToDevice));
+  return DJ_OK;
+}
+
 dj_status dj_set_displacements_device(dj_mesh* m, const float* d_U0, void* stream) {
   dj_status s = need_ready(m);
   if (s) return s;
@@ -1743,6 +1752,16 @@ dj_status dj_batch_get_displacements(dj_batch* b, int i, double* U_out) {
     U_out[3 * q + 1] = (double)U[v].y + (double)L[v].y;
     U_out[3 * q + 2] = (double)U[v].z + (double)L[v].z;
   }
+  return DJ_OK;
+}
+
+dj_status dj_batch_set_step(dj_batch* b, long long step) {
+  if (!b) return DJ_ERR_INVALID_ARG;
+  for (int pt = 0; pt < 2; ++pt)
+    if (b->part[pt]) {
+      dj_status s = dj_set_step(b->part[pt], step);
+      if (s) return bfail(b, s, b->part[pt]->last_error.c_str());
+    }
   return DJ_OK;
 }
 

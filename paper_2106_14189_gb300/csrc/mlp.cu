@@ -195,43 +195,96 @@ cudaError_t gemm(int M, int N, int K, float alpha, const float* A, long long sar
 
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// cyclic Jacobi eigen-decomposition of a symmetric n x n matrix (FP64, host);
-// on return a holds garbage, w the eigenvalues, V the eigenvectors (columns)
-void jacobi_eigen(std::vector<double>& a, int n, std::vector<double>& w, std::vector<double>& V) {
+// Symmetric eigen-decomposition (FP64, host): Householder reduction to
+// tridiagonal form T = Q^T A Q, then the QL iteration with implicit Wilkinson
+// shifts on T, accumulating the plane rotations into Q.  On return w holds the
+// eigenvalues and V (row-major n x n) the eigenvectors as columns.
+void symmetric_eigen(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& V) {
+  auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
   V.assign((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, diag = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) (i == j ? diag : off) += a[(size_t)i * n + j] * a[(size_t)i * n + j];
-    if (off <= 1e-30 * diag) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = a[(size_t)p * n + q];
-        if (std::fabs(apq) < 1e-300) continue;
-        const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
-        // rotation angle that zeroes a_pq: tan(2 theta) = 2 a_pq / (a_qq - a_pp)
-        const double theta = 0.5 * std::atan2(2.0 * apq, aqq - app);
-        const double c = std::cos(theta), s = std::sin(theta);
-        for (int k = 0; k < n; ++k) {  // columns p, q
-          const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
-          a[(size_t)k * n + p] = c * akp - s * akq;
-          a[(size_t)k * n + q] = s * akp + c * akq;
+  std::vector<double> v(n), p(n), wv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    // Householder vector of column k below the diagonal
+    double nx = 0.0;
+    for (int i = k + 1; i < n; ++i) nx += a(i, k) * a(i, k);
+    nx = std::sqrt(nx);
+    if (nx == 0.0) continue;
+    const double alpha = a(k + 1, k) > 0 ? -nx : nx;
+    for (int i = 0; i < n; ++i) v[i] = 0.0;
+    for (int i = k + 1; i < n; ++i) v[i] = a(i, k);
+    v[k + 1] -= alpha;
+    double nv = 0.0;
+    for (int i = k + 1; i < n; ++i) nv += v[i] * v[i];
+    nv = std::sqrt(nv);
+    if (nv == 0.0) continue;
+    for (int i = k + 1; i < n; ++i) v[i] /= nv;
+    // A <- H A H with H = I - 2 v v^T:  p = 2 A v, K = v^T p, w = p - K v, A -= v w^T + w v^T
+    for (int i = k; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += a(i, j) * v[j];
+      p[i] = 2.0 * s;
+    }
+    double K = 0.0;
+    for (int i = k + 1; i < n; ++i) K += v[i] * p[i];
+    for (int i = k; i < n; ++i) wv[i] = p[i] - K * v[i];
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j) a(i, j) -= v[i] * wv[j] + wv[i] * v[j];
+    // Q <- Q H
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += V[(size_t)i * n + j] * v[j];
+      for (int j = k + 1; j < n; ++j) V[(size_t)i * n + j] -= 2.0 * s * v[j];
+    }
+  }
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = a(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+  // QL with implicit shifts: deflate from the top, e[i] couples d[i] and d[i+1]
+  for (int l = 0; l < n; ++l) {
+    for (int iter = 0; iter < 60; ++iter) {
+      int m = l;
+      for (; m + 1 < n; ++m) {
+        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
+        if (std::fabs(e[m]) <= 1e-15 * dd) break;
+      }
+      if (m == l) break;
+      // Wilkinson shift from the leading 2 x 2 block
+      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+      double r = std::hypot(g, 1.0);
+      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
+      double s = 1.0, c = 1.0, pp = 0.0;
+      int i = m - 1;
+      for (; i >= l; --i) {
+        double f = s * e[i];
+        const double b = c * e[i];
+        r = std::hypot(f, g);
+        e[i + 1] = r;
+        if (r == 0.0) {
+          d[i + 1] -= pp;
+          e[m] = 0.0;
+          break;
         }
-        for (int k = 0; k < n; ++k) {  // rows p, q
-          const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
-          a[(size_t)p * n + k] = c * apk - s * aqk;
-          a[(size_t)q * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = c * vkp - s * vkq;
-          V[(size_t)k * n + q] = s * vkp + c * vkq;
+        s = f / r;
+        c = g / r;
+        g = d[i + 1] - pp;
+        r = (d[i] - g) * s + 2.0 * c * b;
+        pp = s * r;
+        d[i + 1] = g + pp;
+        g = c * r - b;
+        for (int k = 0; k < n; ++k) {  // rotate eigenvector columns i, i+1
+          f = V[(size_t)k * n + i + 1];
+          V[(size_t)k * n + i + 1] = s * V[(size_t)k * n + i] + c * f;
+          V[(size_t)k * n + i] = c * V[(size_t)k * n + i] - s * f;
         }
       }
+      if (r == 0.0 && i >= l) continue;
+      d[l] -= pp;
+      e[l] = g;
+      e[m] = 0.0;
+    }
   }
-  w.resize(n);
-  for (int i = 0; i < n; ++i) w[i] = a[(size_t)i * n + i];
+  w = d;
 }
 
 }  // namespace
@@ -478,7 +531,7 @@ dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d
   std::vector<double> a(hG.begin(), hG.end()), w, V;
   for (int i = 0; i < cols; ++i)
     for (int j = 0; j < i; ++j) a[(size_t)i * cols + j] = a[(size_t)j * cols + i] = 0.5 * (a[(size_t)i * cols + j] + a[(size_t)j * cols + i]);
-  jacobi_eigen(a, cols, w, V);
+  symmetric_eigen(a, cols, w, V);
   std::vector<int> order(cols);
   for (int i = 0; i < cols; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });

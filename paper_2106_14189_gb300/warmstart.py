@@ -1,0 +1,203 @@
+"""Learned warm start for dynamic relaxation.
+
+A small MLP maps the prescribed surface displacements of a load case to an
+initial nodal field for dynamic relaxation (the paper names learning methods
+only as future work, Sec. 8).  Everything numerical runs in the CUDA library:
+
+* training data: the method's own relaxed solutions, computed in batches of
+  load cases on copies of the mesh (dj_batch_relax_to_tol);
+* inputs: the leading POD coefficients of the prescribed-displacement vector,
+  outputs: the leading POD coefficients of the relaxed field (dj_pod_fit /
+  dj_pod_project / dj_pod_expand);
+* MLP training and inference: dj_mlp_loss_grad / dj_mlp_adam_step /
+  dj_mlp_forward.
+
+A relaxation from the predicted field uses plain DJ-TLED relaxation both as
+fallback and as judge: if the predicted field inverts an element or has a
+larger residual than the prescribed-values-only field, the solve restarts from
+rest; the result is always a relaxation of the method to the same tolerance.
+Torch provides device buffers and a few one-time tensor operations of the
+set-up (scaling of the POD bases by the coefficient spread).
+"""
+from __future__ import annotations
+
+import copy
+import time
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+from . import binding as B
+from . import workloads as W
+
+
+@dataclass
+class RelaxResult:
+    steps: int
+    residual: float
+    seconds: float
+    warm: bool
+    fallback: bool
+    status: int
+
+
+class WarmStart:
+    def __init__(self, problem: W.Problem, n_in: int = 64, n_out: int = 128,
+                 hidden=(256, 256, 256), seed: int = 0, alpha: float = 130.0,
+                 ramp_steps: int = 400, check_every: int = 50, tol: float = 1e-5,
+                 max_steps: int = 400000, precision: int = 1):
+        import torch
+        self.torch = torch
+        self.p = problem
+        self.n_in, self.n_out = n_in, n_out
+        self.widths = [n_in, *hidden, n_out]
+        self.seed = seed
+        self.alpha, self.ramp_steps, self.check_every = alpha, ramp_steps, check_every
+        self.tol, self.max_steps, self.precision = tol, max_steps, precision
+        self.n_bc = problem.bc_dof.size
+        self.n_dof = 3 * problem.n_nodes
+        self.mlp = None
+        self.dev = torch.device("cuda")
+
+    # ------------------------------------------------------------ problems --
+    def problem_for(self, targets) -> W.Problem:
+        q = copy.copy(self.p)
+        q.bc_target = np.asarray(targets, dtype=np.float64)
+        q.alpha, q.ramp_steps = self.alpha, self.ramp_steps
+        return q
+
+    def mesh_params(self):
+        return dict(alpha=self.alpha, ramp_steps=self.ramp_steps,
+                    relax_check_every=self.check_every, precision=self.precision)
+
+    # --------------------------------------------------------------- data ---
+    def solve_batch(self, targets: List[np.ndarray], batch_size: int = 64):
+        """Relax every load case from rest; returns (S x n_dof) device tensor of
+        fields (each row one snapshot) and the step counts."""
+        torch = self.torch
+        S = len(targets)
+        Y = torch.empty((S, self.n_dof), dtype=torch.float32, device=self.dev)
+        steps = []
+        for s0 in range(0, S, batch_size):
+            chunk = targets[s0:s0 + batch_size]
+            with B.Batch([self.problem_for(t) for t in chunk], **self.mesh_params()) as bt:
+                st, n, r = bt.relax(self.tol, self.max_steps)
+                for i in range(len(chunk)):
+                    B.dj_batch_get_displacements_device(bt.b, i, Y[s0 + i].data_ptr())
+                bt.sync()
+                steps.append(n)
+        return Y, steps
+
+    # ---------------------------------------------------------------- fit ---
+    def fit(self, T_host: np.ndarray, Y: "torch.Tensor", epochs: int = 400, batch: int = 256,
+            lr: float = 1e-3, lr_final: float = 1e-5):
+        """T_host: (S x n_bc) load targets, Y: (S x n_dof) device relaxed fields."""
+        torch = self.torch
+        S = T_host.shape[0]
+        dT = torch.tensor(np.asarray(T_host, dtype=np.float32), device=self.dev)  # rows = snapshots
+        self.mean_in = torch.empty(self.n_bc, device=self.dev)
+        self.modes_in = torch.empty((self.n_bc, self.n_in), device=self.dev)
+        self.mean_out = torch.empty(self.n_dof, device=self.dev)
+        self.modes_out = torch.empty((self.n_dof, self.n_out), device=self.dev)
+        self.sig_in = B.dj_pod_fit(dT.data_ptr(), self.n_bc, S, self.n_in, self.mean_in.data_ptr(),
+                                   self.modes_in.data_ptr())
+        self.sig_out = B.dj_pod_fit(Y.data_ptr(), self.n_dof, S, self.n_out, self.mean_out.data_ptr(),
+                                    self.modes_out.data_ptr())
+        # scale the bases so that coefficients have unit spread over the training set
+        s_in = torch.tensor(np.maximum(self.sig_in, 1e-30) / np.sqrt(S), dtype=torch.float32,
+                            device=self.dev)
+        s_out = torch.tensor(np.maximum(self.sig_out, 1e-30) / np.sqrt(S), dtype=torch.float32,
+                             device=self.dev)
+        self.modes_in /= s_in
+        self.modes_out *= s_out
+        Xc = torch.empty((S, self.n_in), device=self.dev)
+        Qc = torch.empty((S, self.n_out), device=self.dev)
+        B.dj_pod_project(self.modes_in.data_ptr(), self.mean_in.data_ptr(), self.n_bc, self.n_in,
+                         dT.data_ptr(), S, Xc.data_ptr())
+        # outputs: coefficients in the scaled output basis (modes_out has spread s_out^2)
+        proj = self.modes_out / (s_out * s_out)
+        B.dj_pod_project(proj.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
+                         Y.data_ptr(), S, Qc.data_ptr())
+        # loss weights: output variance shares, so the loss tracks the field error
+        var = self.sig_out ** 2
+        self.w = torch.tensor(var / var.mean(), dtype=torch.float32, device=self.dev)
+        if self.mlp is not None:
+            B.dj_mlp_destroy(self.mlp)
+        self.mlp = B.dj_mlp_create(self.widths, seed=self.seed)
+        rng = np.random.default_rng(self.seed)
+        n_iter = epochs * max(1, S // batch)
+        losses = []
+        bsz = min(batch, S)
+        for it in range(n_iter):
+            idx = torch.tensor(rng.choice(S, size=bsz, replace=False), device=self.dev)
+            xb = Xc.index_select(0, idx).contiguous()
+            tb = Qc.index_select(0, idx).contiguous()
+            want = (it % 200 == 0) or it == n_iter - 1
+            loss = B.dj_mlp_loss_grad(self.mlp, xb.data_ptr(), tb.data_ptr(), self.w.data_ptr(), bsz,
+                                      want_loss=want)
+            if want:
+                losses.append((it, loss))
+            frac = it / max(1, n_iter - 1)
+            B.dj_mlp_adam_step(self.mlp, lr * (lr_final / lr) ** frac)
+        torch.cuda.synchronize()
+        self.losses = losses
+        return losses
+
+    # ------------------------------------------------------------ predict ---
+    def predict(self, targets: np.ndarray) -> "torch.Tensor":
+        """Predicted nodal field (n_dof floats on the device) for one load case."""
+        torch = self.torch
+        t = torch.tensor(np.asarray(targets, dtype=np.float32), device=self.dev)
+        c = torch.empty((1, self.n_in), device=self.dev)
+        q = torch.empty((1, self.n_out), device=self.dev)
+        out = torch.empty(self.n_dof, device=self.dev)
+        B.dj_pod_project(self.modes_in.data_ptr(), self.mean_in.data_ptr(), self.n_bc, self.n_in,
+                         t.data_ptr(), 1, c.data_ptr())
+        B.dj_mlp_forward(self.mlp, c.data_ptr(), 1, q.data_ptr())
+        B.dj_pod_expand(self.modes_out.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
+                        q.data_ptr(), 1, out.data_ptr())
+        return out
+
+    # -------------------------------------------------------------- solve ---
+    def relax(self, targets: np.ndarray, warm: bool, mesh: Optional[B.Mesh] = None) -> RelaxResult:
+        """Relax one load case from rest (warm=False) or from the prediction."""
+        torch = self.torch
+        own = mesh is None
+        if own:
+            mesh = B.Mesh(self.problem_for(targets), **self.mesh_params())
+        else:
+            B.dj_mesh_update_bc_targets(mesh.h, targets)
+            mesh.set_displacements(np.zeros((self.p.n_nodes, 3)))
+            B.dj_set_step(mesh.h, 0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fallback = False
+        if warm:
+            field = self.predict(targets)
+            r_warm, inverted = B.dj_evaluate_field(mesh.h, field.data_ptr())
+            bc_only = torch.zeros(self.n_dof, device=self.dev)
+            bc_only[torch.as_tensor(self.p.bc_dof, device=self.dev)] = torch.as_tensor(
+                np.asarray(targets, dtype=np.float32), device=self.dev)
+            r_rest, _ = B.dj_evaluate_field(mesh.h, bc_only.data_ptr())
+            if inverted or not (r_warm < r_rest):
+                fallback = True
+            else:
+                B.dj_set_displacements_device(mesh.h, field.data_ptr())
+                B.dj_set_step(mesh.h, self.ramp_steps)
+        st, n, r = mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        if own:
+            mesh.close()
+        return RelaxResult(steps=n, residual=r, seconds=sec, warm=warm and not fallback,
+                           fallback=fallback, status=st)
+
+    def close(self):
+        if self.mlp is not None:
+            B.dj_mlp_destroy(self.mlp)
+            self.mlp = None
+
+
+def load_cases(problem: W.Problem, seeds) -> np.ndarray:
+    return np.stack([W.ellipsoid_load_case(problem, int(s)) for s in seeds])

@@ -335,10 +335,12 @@ def ellipsoid_tet4(h: float = 1.76e-3, axes=(0.070, 0.055, 0.045), seed: int = 0
     taken = np.zeros(X.shape[0], dtype=bool)
     taken[fixed] = True
     dofs, tgts = [3 * fixed, 3 * fixed + 1, 3 * fixed + 2], [np.zeros(fixed.size)] * 3
+    patch_nodes = []
     for p in range(n_patches):
         d = np.linalg.norm(X[surf] - centres[p], axis=1)
         nodes = surf[(d < patch_radius) & ~taken[surf]]
         taken[nodes] = True
+        patch_nodes.append(nodes)
         for comp in range(3):
             dofs.append(3 * nodes + comp)
             tgts.append(np.full(nodes.size, mags[p] * dirs[p, comp]))
@@ -348,8 +350,31 @@ def ellipsoid_tet4(h: float = 1.76e-3, axes=(0.070, 0.055, 0.045), seed: int = 0
                    b_dir=np.tile([0.0, 1.0, 0.0], (E_count, 1)),
                    bc_dof=np.concatenate(dofs).astype(np.int64),
                    bc_target=np.concatenate(tgts), ramp_kind=RAMP_SMOOTH,
-                   meta=dict(h=h, axes=axes, seed=seed, surface_nodes=surf,
-                             patch_centres=centres, patch_dirs=dirs, patch_mags=mags))
+                   meta=dict(h=h, axes=axes, seed=seed, surface_nodes=surf, fixed_nodes=fixed,
+                             patch_nodes=patch_nodes, patch_centres=centres, patch_radius=patch_radius,
+                             patch_dirs=dirs, patch_mags=mags, disp_range=disp_range))
+
+
+def ellipsoid_load_case(problem: Problem, seed: int) -> np.ndarray:
+    """Prescribed targets (ordered as problem.bc_dof) of one seeded load case.
+
+    The fixed base stays fixed; every surface patch gets a displacement of
+    seeded direction and magnitude U(disp_range) with a smooth bump profile
+    1 - (r / R)^2 over the patch (r distance to the patch centre).
+    """
+    m = problem.meta
+    rng = np.random.default_rng(seed)
+    X = problem.X
+    target_of = {}
+    for p, nodes in enumerate(m["patch_nodes"]):
+        d = rng.normal(size=3)
+        d *= rng.uniform(*m["disp_range"]) / np.linalg.norm(d)
+        r = np.linalg.norm(X[nodes] - m["patch_centres"][p], axis=1) / m["patch_radius"]
+        w = np.clip(1.0 - r * r, 0.0, 1.0)
+        for comp in range(3):
+            for n, v in zip(nodes, w * d[comp]):
+                target_of[3 * int(n) + comp] = v
+    return np.array([target_of.get(int(dof), 0.0) for dof in problem.bc_dof])
 
 
 def random_tet_mesh_problem(n_elems_target: int, seed: int, model: int = NH,

@@ -1,0 +1,134 @@
+"""Learned warm start: GPU kernels against the FP64 reference, and the gain of
+the trained network over plain relaxation from rest."""
+import numpy as np
+import pytest
+
+from oracle import mlp as ref
+from paper_2106_14189_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_14189_gb300 import binding
+    return torch, binding
+
+
+def test_mlp_loss_and_gradients_match_reference(env):
+    torch, B = env
+    rng = np.random.default_rng(0)
+    widths = [64, 256, 256, 256, 128]
+    m = B.dj_mlp_create(widths, seed=3)
+    try:
+        n = B.dj_mlp_num_params(m)
+        _, n_ref = ref.layout(widths)
+        assert n == n_ref
+        p = B.dj_mlp_get_params(m).astype(np.float64)
+        X = rng.normal(size=(200, 64))
+        T = rng.normal(size=(200, 128))
+        w = rng.uniform(0.1, 3.0, size=128)
+        dX = torch.tensor(X, dtype=torch.float32, device="cuda")
+        dT = torch.tensor(T, dtype=torch.float32, device="cuda")
+        dw = torch.tensor(w, dtype=torch.float32, device="cuda")
+        loss = B.dj_mlp_loss_grad(m, dX.data_ptr(), dT.data_ptr(), dw.data_ptr(), 200)
+        g = B.dj_mlp_get_grads(m).astype(np.float64)
+        L_ref, g_ref = ref.loss_grad(p, widths, X, T, w)
+        assert abs(loss - L_ref) < 1e-5 * L_ref
+        assert np.abs(g - g_ref).max() < 1e-4 * np.abs(g_ref).max()
+        dY = torch.empty((200, 128), device="cuda")
+        B.dj_mlp_forward(m, dX.data_ptr(), 200, dY.data_ptr())
+        Y_ref = ref.forward(p, widths, X)[-1]
+        assert np.abs(dY.cpu().numpy() - Y_ref).max() < 1e-5 * np.abs(Y_ref).max()
+        # one Adam step
+        B.dj_mlp_adam_step(m, 1e-3)
+        p1 = B.dj_mlp_get_params(m).astype(np.float64)
+        p_ref, _, _ = ref.adam_step(p, g, np.zeros(n), np.zeros(n), 1, 1e-3)
+        assert np.abs(p1 - p_ref).max() < 1e-6 + 1e-5 * np.abs(p_ref).max()
+    finally:
+        B.dj_mlp_destroy(m)
+
+
+def test_training_reduces_loss(env):
+    torch, B = env
+    rng = np.random.default_rng(1)
+    widths = [8, 32, 32, 4]
+    X = rng.normal(size=(256, 8))
+    T = np.tanh(X @ rng.normal(size=(8, 4)))
+    m = B.dj_mlp_create(widths, seed=0)
+    dX = torch.tensor(X, dtype=torch.float32, device="cuda")
+    dT = torch.tensor(T, dtype=torch.float32, device="cuda")
+    first = B.dj_mlp_loss_grad(m, dX.data_ptr(), dT.data_ptr(), 0, 256)
+    for _ in range(500):
+        B.dj_mlp_loss_grad(m, dX.data_ptr(), dT.data_ptr(), 0, 256, want_loss=False)
+        B.dj_mlp_adam_step(m, 3e-3)
+    last = B.dj_mlp_loss_grad(m, dX.data_ptr(), dT.data_ptr(), 0, 256)
+    B.dj_mlp_destroy(m)
+    assert last < 0.05 * first
+
+
+def test_pod_matches_svd(env):
+    torch, B = env
+    rng = np.random.default_rng(2)
+    rows, cols, r = 3000, 96, 12
+    basis = np.linalg.qr(rng.normal(size=(rows, 20)))[0]
+    Y = basis @ (rng.normal(size=(20, cols)) * np.geomspace(10, 0.01, 20)[:, None]) \
+        + rng.normal(size=rows)[:, None]
+    dY = torch.tensor(Y.T.copy(), dtype=torch.float32, device="cuda")  # snapshot-major
+    mean = torch.empty(rows, device="cuda")
+    modes = torch.empty((rows, r), device="cuda")
+    sig = B.dj_pod_fit(dY.data_ptr(), rows, cols, r, mean.data_ptr(), modes.data_ptr())
+    mean_ref, U_ref, s_ref = ref.pod(Y, r)
+    assert np.abs(mean.cpu().numpy() - mean_ref).max() < 1e-5 * np.abs(mean_ref).max()
+    assert np.allclose(sig, s_ref, rtol=1e-4)
+    M = modes.cpu().numpy().astype(np.float64)
+    assert np.abs(M.T @ M - np.eye(r)).max() < 1e-4
+    # same subspace: projection of the reference modes onto the GPU modes
+    assert np.abs(np.abs(np.diag(U_ref.T @ M)) - 1).max() < 1e-3
+    # project / expand round trip of a snapshot in the span
+    Q = torch.empty((cols, r), device="cuda")
+    B.dj_pod_project(modes.data_ptr(), mean.data_ptr(), rows, r, dY.data_ptr(), cols, Q.data_ptr())
+    R = torch.empty((cols, rows), device="cuda")
+    B.dj_pod_expand(modes.data_ptr(), mean.data_ptr(), rows, r, Q.data_ptr(), cols, R.data_ptr())
+    Yr = mean_ref[:, None] + U_ref @ (U_ref.T @ (Y - mean_ref[:, None]))
+    assert np.abs(R.cpu().numpy().T - Yr).max() < 1e-4 * np.abs(Y).max()
+
+
+def test_warm_start_relaxes_faster_than_rest(env):
+    """Train on the method's own relaxed solutions of seeded loads on a coarse
+    brain-sized ellipsoid; on held-out loads the warm-started relaxation reaches
+    the same residual in fewer steps than relaxation from rest, and lands on the
+    same equilibrium."""
+    torch, B = env
+    from paper_2106_14189_gb300.warmstart import WarmStart, load_cases
+    p = W.ellipsoid_tet4(h=6e-3, seed=0)
+    ws = WarmStart(p, n_in=64, n_out=128, alpha=140.0, ramp_steps=300, tol=1e-5)
+    T_train = load_cases(p, range(1000, 1256))
+    Y, steps = ws.solve_batch(list(T_train), batch_size=64)
+    losses = ws.fit(T_train, Y, epochs=300, batch=128)
+    assert losses[-1][1] < 0.1 * losses[0][1]
+    T_test = load_cases(p, range(5000, 5012))
+    cold, warm = [], []
+    for t in T_test:
+        with B.Mesh(ws.problem_for(t), **ws.mesh_params()) as m:
+            rc = ws.relax(t, warm=False, mesh=m)
+            Uc = m.displacements()
+            rw = ws.relax(t, warm=True, mesh=m)
+            Uw = m.displacements()
+        assert rc.status == 0 and rw.status == 0 and rw.residual <= 1e-5
+        assert np.abs(Uw - Uc).max() <= 2e-3 * np.abs(Uc).max()
+        cold.append(rc)
+        warm.append(rw)
+    ws.close()
+    n_fallback = sum(r.fallback for r in warm)
+    assert n_fallback <= len(warm) // 4
+    mean_cold = np.mean([r.steps for r in cold])
+    mean_warm = np.mean([r.steps for r in warm])
+    print(f"warm start: {mean_warm:.0f} vs {mean_cold:.0f} steps, "
+          f"{np.mean([r.seconds for r in warm]) * 1e3:.1f} vs {np.mean([r.seconds for r in cold]) * 1e3:.1f} ms")
+    assert mean_warm < 0.8 * mean_cold
