@@ -306,6 +306,28 @@ dj_status dj_batch_get_info(const dj_batch* batch, int* n_instances, long long* 
 const char* dj_batch_last_error(const dj_batch* batch);
 void dj_batch_destroy(dj_batch* batch);
 
+/* Allocation-free residual norms (no counterpart in the paper).  For callers
+ * that cannot allocate device memory when they need the residual -- code that
+ * runs inside another framework's memory pool, real-time loops that must not
+ * enter the allocator, plugins that only receive buffers from their host
+ * application.  It computes the two FP64 sums of the dj_relax_to_tol residual,
+ * d_out[0] = sum of F^2 over free DOFs and d_out[1] = sum of F^2 over
+ * prescribed DOFs, from caller buffers:
+ *   d_F           device, n_nodes * 3 floats (F - R per DOF)
+ *   d_prescribed  device, n_nodes * 3 bytes, nonzero = prescribed DOF
+ *   d_out         device, 2 doubles
+ * Its block partial sums live in a fixed 1 MiB device array inside the library
+ * (held on every GPU that loads the library until the process exits), so it
+ * calls no allocator.  n_nodes must be <= 16,777,216 (65536 blocks of 256
+ * nodes); larger inputs return DJ_ERR_UNSUPPORTED, null pointers or
+ * n_nodes <= 0 DJ_ERR_INVALID_ARG.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) for the current device: make
+ * that first call outside stream capture.  Enqueued on `stream`.  All calls
+ * share the array and each overwrites the slots it uses, so calls that overlap
+ * on the GPU (other streams, other threads) race and must be serialized. */
+dj_status dj_residual_norms_static(const float* d_F, const unsigned char* d_prescribed, long long n_nodes,
+                                   double* d_out, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned warm start for dynamic relaxation (no counterpart in the paper, which
  * names learning only as future work, Sec. 8): proper orthogonal decomposition

@@ -38,7 +38,7 @@ EXPORTS = [
     "dj_mlp_create", "dj_mlp_num_params", "dj_mlp_get_params", "dj_mlp_set_params",
     "dj_mlp_get_grads", "dj_mlp_forward", "dj_mlp_loss_grad", "dj_mlp_adam_step",
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
-    "dj_set_step", "dj_batch_set_step",
+    "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step",
 ]
 
 
@@ -136,6 +136,7 @@ def lib():
         "dj_pod_fit": (C.c_int, [_P, C.c_longlong, C.c_int, C.c_int, _P, _P, _D, _P]),
         "dj_pod_project": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
+        "dj_residual_norms_static": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
         "dj_set_step": (C.c_int, [_P, C.c_longlong]),
         "dj_batch_set_step": (C.c_int, [_P, C.c_longlong]),
     }
@@ -478,6 +479,11 @@ def dj_mlp_adam_step(m, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
 
 def dj_mlp_destroy(m):
     lib().dj_mlp_destroy(m)
+
+
+def dj_residual_norms_static(d_F, d_prescribed, n_nodes, d_out, stream=None):
+    """Allocation-free residual sums (see include/dj_tled.h); returns the status."""
+    return int(lib().dj_residual_norms_static(d_F, d_prescribed, int(n_nodes), d_out, _stream(stream)))
 
 
 def dj_pod_fit(d_Y, rows, cols, r, d_mean, d_modes, stream=None):
