@@ -106,8 +106,9 @@ def test_warm_start_relaxes_faster_than_rest(env):
     same equilibrium."""
     torch, B = env
     from paper_2106_14189_gb300.warmstart import WarmStart, load_cases
-    p = W.ellipsoid_tet4(h=6e-3, seed=0)
-    ws = WarmStart(p, n_in=64, n_out=128, alpha=140.0, ramp_steps=300, tol=1e-5)
+    # coarse (6 mm) ellipsoid: patches span ~2.5 elements, so loads of 1-4 mm
+    p = W.ellipsoid_tet4(h=6e-3, seed=0, disp_range=(1e-3, 4e-3))
+    ws = WarmStart(p, n_in=64, n_out=128, alpha=140.0, ramp_steps=400, tol=1e-5)
     T_train = load_cases(p, range(1000, 1256))
     Y, steps = ws.solve_batch(list(T_train), batch_size=64)
     losses = ws.fit(T_train, Y, epochs=300, batch=128)
