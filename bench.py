@@ -228,14 +228,14 @@ def run_warmstart(args):
     from paper_2106_14189_gb300 import binding as B
     from paper_2106_14189_gb300.warmstart import WarmStart, load_cases
     torch.cuda.set_device(0)
-    p = W.ellipsoid_tet4(h=args.ws_h, seed=0)
-    ws = WarmStart(p, n_in=64, n_out=128, alpha=130.0, ramp_steps=600, tol=1e-5)
+    p = W.ellipsoid_tet4(h=args.ws_h, seed=0, patch_radius=0.025)
+    ws = WarmStart(p, n_in=64, n_out=128, alpha=130.0, ramp_steps=1500, tol=1e-5)
     t0 = time.perf_counter()
     T_train = load_cases(p, range(100000, 100000 + args.ws_train))
-    Y, steps = ws.solve_batch(list(T_train), batch_size=64)
+    Y, kept, steps = ws.solve_batch(list(T_train), batch_size=64)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    losses = ws.fit(T_train, Y, epochs=400, batch=128)
+    losses = ws.fit(T_train[kept], Y, epochs=400, batch=128)
     t_fit = time.perf_counter() - t0
     T_test = load_cases(p, range(900000, 900000 + args.ws_test))
     cold, warm = [], []
@@ -253,11 +253,12 @@ def run_warmstart(args):
             "steps_warm": float(np.mean([r.steps for r in warm])),
             "steps_plain": float(np.mean([r.steps for r in cold])),
             "fallbacks": int(sum(r.fallback for r in warm)), "all_converged": ok,
-            "train_loads": args.ws_train, "test_loads": args.ws_test,
+            "train_loads": args.ws_train, "train_loads_kept": len(kept), "test_loads": args.ws_test,
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4 TI, {p.n_nodes} nodes), 6 surface patches "
-                                   f"2-10 mm, compensated precision, alpha = 130 1/s, "
+                                   f"(r = 25 mm, bump profile) 2-10 mm, ramp 1500 steps, "
+                                   f"compensated precision, alpha = 130 1/s, "
                                    f"MLP 64-256-256-256-128 tanh on POD coefficients"},
             "dtype": "f32", "data": "synthetic"}
     print(json.dumps(line), flush=True)
@@ -281,7 +282,8 @@ def main():
     ap.add_argument("--ws-h", type=float, default=3e-3)
     ap.add_argument("--ws-train", type=int, default=512)
     ap.add_argument("--ws-test", type=int, default=32)
-    ap.add_argument("--assembly", type=int, default=1, help="1 tiles (default), 0 element slots")
+    ap.add_argument("--assembly", type=int, default=1,
+                    help="1 tiles (default), 2 tiles with the bulk-copy pipeline, 0 element slots")
     ap.add_argument("--tile-size", type=int, default=0)
     args = ap.parse_args()
     world, rank, local = dist_setup()

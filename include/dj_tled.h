@@ -367,7 +367,7 @@ void dj_mlp_destroy(dj_mlp* mlp);
 dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d_mean, float* d_modes,
                      double* sigma_out, void* stream);
 /* d_Q (cols x r) = (X - mean)^T modes for column-major d_X (rows x cols);
- * d_mean may be NULL.  Synchronous. */
+ * d_mean may be NULL.  Enqueued on `stream`; allocates nothing. */
 dj_status dj_pod_project(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_X,
                          int cols, float* d_Q, void* stream);
 /* d_X (column-major rows x cols) = mean + modes Q^T for d_Q (cols x r). */

@@ -58,6 +58,7 @@ struct dj_mesh {
   float4* d_fout = nullptr;
   float4* d_Ulo = nullptr;  // compensated mode: low part of U
   int cmp = 0;
+  float4* d_save = nullptr;  // dj_evaluate_field: saved U, V, low part (3 N), allocated on first use
   // groups: per-group time step, damping factor and residual
   std::vector<double> group_dt, group_dt_crit, group_r;
   std::vector<int> group_node_ptr;  // internal node range of each group
@@ -83,7 +84,7 @@ struct dj_mesh {
   long long device_bytes = 0;
   long long sell_entries = 0;
   // tiled assembly
-  int assembly = ASSEMBLY_TILES, T = 0, n_tiles = 0, smem_nodes = 0;
+  int assembly = ASSEMBLY_TILES, T = 0, n_tiles = 0, cap = 0, tma_grid = 0;
   long long n_parts = 0;
   int* d_tile_ptr = nullptr;
   int* d_tile_nodes = nullptr;
@@ -146,7 +147,7 @@ void release_device(dj_mesh* m) {
   m->run_chunk = m->relax_k = 0;
   void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
-                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx,
+                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_save,
                   m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
                   m->d_group_node_ptr};
   for (void* p : ptrs)
@@ -155,6 +156,7 @@ void release_device(dj_mesh* m) {
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
   m->d_parts = nullptr;
   m->d_Ulo = nullptr;
+  m->d_save = nullptr;
   m->d_bm1 = nullptr;
   m->d_node_resid = m->d_group_resid = nullptr;
   m->d_group_node_ptr = nullptr;
@@ -283,17 +285,21 @@ ForceArgs force_args(dj_mesh* m, int advance) {
 TileArgs tile_args(dj_mesh* m) {
   TileArgs t;
   t.tile_ptr = m->d_tile_ptr;
-  t.tile_nodes = m->d_tile_nodes;
+  t.tnodes = m->d_tile_nodes;
   t.lconn = m->d_lconn;
   t.lptr = m->d_lptr;
   t.lidx = m->d_lidx;
   t.partials = m->d_parts;
   t.T = m->T;
-  t.smem_nodes = m->smem_nodes;
+  t.cap = m->cap;
+  t.n_consts = m->n_consts;
+  t.n_tiles = m->n_tiles;
   return t;
 }
 
 cudaError_t launch_force_any(dj_mesh* m, int advance, cudaStream_t s) {
+  if (m->assembly == ASSEMBLY_TILES_TMA)
+    return launch_force_tma(m->elem_type, m->variant, m->cmp, force_args(m, advance), tile_args(m), m->tma_grid, s);
   if (m->assembly == ASSEMBLY_TILES)
     return launch_force_tiled(m->elem_type, m->variant, m->cmp, force_args(m, advance), tile_args(m),
                               m->n_tiles, s);
@@ -304,7 +310,7 @@ NodeArgs node_args(dj_mesh* m) {
   NodeArgs a;
   a.sell = m->d_sell;
   a.chunk_ptr = m->d_chunk_ptr;
-  a.slots = m->assembly == ASSEMBLY_TILES ? m->d_parts : m->d_slots;
+  a.slots = m->assembly != ASSEMBLY_SLOTS ? m->d_parts : m->d_slots;
   a.U = m->d_U;
   a.Ulo = m->d_Ulo;
   a.V = m->d_V;
@@ -539,11 +545,11 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     dj_params_default(&prm);
   if (!(prm.dt_scale > 0) || !(prm.alpha >= 0) || !(prm.hg_coeff >= 0) || prm.relax_check_every <= 0 ||
       (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt) ||
-      (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES) ||
+      (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES && prm.assembly != ASSEMBLY_TILES_TMA) ||
       (prm.precision != 0 && prm.precision != 1))
     return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
   {
-    const int tmax = m->ne == 4 ? 512 : 256;
+    const int tmax = prm.assembly == ASSEMBLY_TILES_TMA ? 256 : (m->ne == 4 ? 512 : 256);
     if (prm.tile_size < 0 || prm.tile_size % 32 != 0 || prm.tile_size > tmax)
       return fail(m, DJ_ERR_INVALID_ARG, "tile_size must be a multiple of 32 and <= %d", tmax);
   }
@@ -639,15 +645,17 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   std::vector<int> chunk_ptr, sell;
   build_sell(cnt, csr, N, chunk_ptr, sell);  // node -> element slots (lumped mass, slot assembly)
   m->assembly = prm.assembly;
-  std::vector<int> tile_ptr, tile_nodes, part_chunk_ptr, part_sell;
+  std::vector<int> tile_ptr, tile_nodes, tnodes_pad, part_chunk_ptr, part_sell;
   std::vector<unsigned short> lconn, lptr, lidx;
-  if (m->assembly == ASSEMBLY_TILES) {
+  if (m->assembly != ASSEMBLY_SLOTS) {
     const int T = prm.tile_size > 0 ? prm.tile_size : (ne == 4 ? 256 : 128);
     m->T = T;
     m->n_tiles = (int)((E + T - 1) / T);
     tile_ptr.assign(m->n_tiles + 1, 0);
-    lconn.assign((size_t)E_pad * ne, 0);
+    lconn.assign((size_t)m->n_tiles * T * ne, 0);
     lidx.assign((size_t)m->n_tiles * T * ne, 0);
+    std::vector<std::vector<int>> tile_loc(m->n_tiles);
+    std::vector<std::vector<unsigned short>> tile_lptr(m->n_tiles);
     int smax = 0;
     std::vector<int> loc;
     for (int t = 0; t < m->n_tiles; ++t) {
@@ -668,16 +676,24 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
           kcnt[k + 1]++;
         }
       for (int k = 0; k < n_t; ++k) kcnt[k + 1] += kcnt[k];
-      for (int k = 0; k <= n_t; ++k) lptr.push_back((unsigned short)kcnt[k]);
+      for (int k = 0; k <= n_t; ++k) tile_lptr[t].push_back((unsigned short)kcnt[k]);
       std::vector<int> fillk(kcnt.begin(), kcnt.end() - 1);
       for (long long e = e0; e < e1; ++e)
         for (int b = 0; b < ne; ++b) {
           const int k = lconn[e * ne + b];
           lidx[(size_t)t * T * ne + fillk[k]++] = (unsigned short)(b * T + (int)(e - e0));
         }
+      tile_loc[t] = loc;
     }
-    m->smem_nodes = smax;
+    m->cap = (smax + 7) / 8 * 8;
     m->n_parts = tile_ptr[m->n_tiles];
+    // fixed-size per-tile segments
+    tnodes_pad.assign((size_t)m->n_tiles * m->cap, 0);
+    lptr.assign((size_t)m->n_tiles * (m->cap + 8), 0);
+    for (int t = 0; t < m->n_tiles; ++t) {
+      std::copy(tile_loc[t].begin(), tile_loc[t].end(), tnodes_pad.begin() + (size_t)t * m->cap);
+      std::copy(tile_lptr[t].begin(), tile_lptr[t].end(), lptr.begin() + (size_t)t * (m->cap + 8));
+    }
     // node -> partial ids, ascending tile
     std::vector<int> pc(N + 1, 0);
     for (int v : tile_nodes) pc[v + 1]++;
@@ -714,8 +730,9 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   const size_t conn4_count = (size_t)E_pad * (ne / 4);
   CK(dalloc(m, &m->d_conn, conn4_count));
   CK(cudaMemset(m->d_conn, 0, conn4_count * sizeof(int4)));
-  CK(dalloc(m, &m->d_consts, (size_t)nc * E_pad));
-  CK(cudaMemset(m->d_consts, 0, (size_t)nc * E_pad * sizeof(float)));
+  const size_t table_floats = m->assembly != ASSEMBLY_SLOTS ? (size_t)m->n_tiles * nc * m->T : (size_t)nc * E_pad;
+  CK(dalloc(m, &m->d_consts, table_floats));
+  CK(cudaMemset(m->d_consts, 0, table_floats * sizeof(float)));
   int* d_mass_sell = nullptr;  // node -> element slots, for the lumped mass (tiled mode)
   int* d_mass_chunk = nullptr;
   if (m->assembly == ASSEMBLY_SLOTS) {
@@ -730,8 +747,8 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   } else {
     CK(dalloc(m, &m->d_tile_ptr, tile_ptr.size()));
     CK(cudaMemcpy(m->d_tile_ptr, tile_ptr.data(), tile_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
-    CK(dalloc(m, &m->d_tile_nodes, tile_nodes.size()));
-    CK(cudaMemcpy(m->d_tile_nodes, tile_nodes.data(), tile_nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_tile_nodes, tnodes_pad.size()));
+    CK(cudaMemcpy(m->d_tile_nodes, tnodes_pad.data(), tnodes_pad.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(dalloc(m, &m->d_lconn, lconn.size()));
     CK(cudaMemcpy(m->d_lconn, lconn.data(), lconn.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
     CK(dalloc(m, &m->d_lptr, lptr.size()));
@@ -773,6 +790,13 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     CK(dalloc(m, &m->d_R, N));
     CK(cudaMemcpy(m->d_R, Rn.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   }
+  if (m->assembly == ASSEMBLY_TILES_TMA) {
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int per_sm = tma_blocks_per_sm(m->elem_type, m->variant, m->cmp, tile_args(m));
+    if (per_sm <= 0) return fail(m, DJ_ERR_UNSUPPORTED, "tile too large for shared memory (tile_size %d)", m->T);
+    m->tma_grid = std::min(m->n_tiles, per_sm * sms);
+  }
   m->n_node_blocks = (int)((N + NODE_THREADS - 1) / NODE_THREADS);
   CK(dalloc(m, &m->d_partials, m->n_node_blocks));
   CK(dalloc(m, &m->d_state, 1));
@@ -805,7 +829,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
       void* ps[] = {dX, dmu, dka, drh, dea, deb, dc1, dad, dbd, dem, ddt, dmass, dred, dmo, dcn, dbad, dbc};
       for (void* q : ps)
         if (q) cudaFree(q);
-      if (m->assembly == ASSEMBLY_TILES) {
+      if (m->assembly != ASSEMBLY_SLOTS) {
         if (d_mass_sell) cudaFree(d_mass_sell);
         if (d_mass_chunk) cudaFree(d_mass_chunk);
         d_mass_sell = d_mass_chunk = nullptr;
@@ -877,6 +901,8 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     pa.off_mr = m->off_mr;
     pa.off_hg = m->off_hg;
     pa.hg_coeff = prm.hg_coeff;
+    pa.tile_T = m->assembly != ASSEMBLY_SLOTS ? m->T : 0;
+    pa.n_consts = nc;
     CKP(launch_precompute_elements(pa, 0));
     int bad = 0;
     CKP(cudaMemcpy(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1250,50 +1276,52 @@ dj_status dj_evaluate_field(dj_mesh* m, const float* d_U, double* residual_out, 
   if (s) return s;
   if (!d_U) return fail(m, DJ_ERR_INVALID_ARG, "null field");
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t nb = m->N * sizeof(float4);
-  float4 *sU = nullptr, *sV = nullptr, *sL = nullptr;
-  cudaError_t e = cudaMalloc(&sU, nb);
-  if (e == cudaSuccess) e = cudaMalloc(&sV, nb);
-  if (e == cudaSuccess && m->cmp) e = cudaMalloc(&sL, nb);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sU, m->d_U, nb, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(sV, m->d_V, nb, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess && sL) e = cudaMemcpyAsync(sL, m->d_Ulo, nb, cudaMemcpyDeviceToDevice, st);
-  DevState before{};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&before, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  DevState clean = before;  // evaluate with cleared error flags
+  const size_t N = m->N, nb = N * sizeof(float4);
+  if (!m->d_save) CK(dalloc(m, &m->d_save, 3 * N));
+  float4 *sU = m->d_save, *sV = m->d_save + N, *sL = m->d_save + 2 * N;
+  // save the stepping state; clear the error flags for the evaluation
+  CK(cudaMemcpyAsync(sU, m->d_U, nb, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(sV, m->d_V, nb, cudaMemcpyDeviceToDevice, st));
+  if (m->cmp) CK(cudaMemcpyAsync(sL, m->d_Ulo, nb, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const DevState before = *m->h_state;
+  DevState clean = before;
   clean.err_flags = 0;
   clean.bad_elem = INT_MAX;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_state, &clean, sizeof(DevState), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = launch_from_caller_order(d_U, m->d_perm, (int)m->N, m->d_U, m->d_V, m->d_Ulo, st);
+  *m->h_state = clean;
+  CK(cudaMemcpyAsync(m->d_state, m->h_state, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  cudaError_t e = launch_from_caller_order(d_U, m->d_perm, (int)m->N, m->d_U, m->d_V, m->d_Ulo, st);
   if (e == cudaSuccess) e = launch_force_any(m, 0, st);
   if (e == cudaSuccess) e = launch_node(NODE_RESID_ONLY, m->cmp, node_args(m), st);
   if (e == cudaSuccess) {
-    if (m->n_groups > 0)
+    if (m->n_groups > 0) {
       e = launch_group_resid(m->d_node_resid, m->d_group_node_ptr, m->n_groups, m->d_group_resid, st);
-    else
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(m->h_group_resid, m->d_group_resid, m->n_groups * sizeof(double2),
+                            cudaMemcpyDeviceToHost, st);
+    } else {
       e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, st);
+    }
   }
-  std::vector<double2> gr(std::max(1, m->n_groups));
-  if (e == cudaSuccess && m->n_groups > 0)
-    e = cudaMemcpyAsync(gr.data(), m->d_group_resid, m->n_groups * sizeof(double2), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // h_state is not yet reused
   DevState after{};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&after, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) after = *m->h_state;
   // restore the stepping state and its error flags
-  if (sU) cudaMemcpyAsync(m->d_U, sU, nb, cudaMemcpyDeviceToDevice, st);
-  if (sV) cudaMemcpyAsync(m->d_V, sV, nb, cudaMemcpyDeviceToDevice, st);
-  if (sL) cudaMemcpyAsync(m->d_Ulo, sL, nb, cudaMemcpyDeviceToDevice, st);
-  cudaMemcpyAsync(m->d_state, &before, sizeof(DevState), cudaMemcpyHostToDevice, st);
-  cudaStreamSynchronize(st);
-  if (sU) cudaFree(sU);
-  if (sV) cudaFree(sV);
-  if (sL) cudaFree(sL);
+  *m->h_state = before;
+  cudaMemcpyAsync(m->d_U, sU, nb, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(m->d_V, sV, nb, cudaMemcpyDeviceToDevice, st);
+  if (m->cmp) cudaMemcpyAsync(m->d_Ulo, sL, nb, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(m->d_state, m->h_state, sizeof(DevState), cudaMemcpyHostToDevice, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (e == cudaSuccess) e = e2;
   if (e != cudaSuccess) return fail(m, DJ_ERR_CUDA, "evaluate field: %s", cudaGetErrorString(e));
   double r = 0;
   if (m->n_groups > 0) {
     for (int g = 0; g < m->n_groups; ++g) {
-      const double num = std::sqrt(gr[g].x), den = std::sqrt(gr[g].y);
+      const double num = std::sqrt(m->h_group_resid[g].x), den = std::sqrt(m->h_group_resid[g].y);
       r = std::max(r, den > 0 ? num / den : num);
     }
   } else {
@@ -1418,7 +1446,7 @@ dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
   info->dt_crit = m->dt_crit;
   info->total_mass = m->total_mass;
   info->device_bytes = m->device_bytes;
-  if (m->assembly == ASSEMBLY_TILES) {
+  if (m->assembly != ASSEMBLY_SLOTS) {
     info->elem_table_bytes_per_elem = (long long)m->n_consts * 4 + 2 * m->ne;
     info->slot_bytes_per_elem = 16 * m->n_parts / std::max(1LL, m->E);
   } else {

@@ -38,7 +38,7 @@ struct DevState {
   double resid_den2;  // sum of squared reaction over prescribed DOFs
 };
 
-enum { ERR_INVERTED = 1, ERR_NONFINITE = 2 };
+enum { ERR_INVERTED = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
 
 struct ForceArgs {
   const int4* conn;      // tet: E_pad int4; hex: 2 E_pad int4 (nodes 0-3, 4-7)
@@ -76,19 +76,29 @@ struct NodeArgs {
 // block.  Its unique nodes are staged in shared memory, the element forces are
 // summed per unique node inside the tile in a fixed order, and one partial force
 // per (tile, node) is written; the node kernel gathers those partials.
+// Per-tile data is stored in fixed-size segments (multiples of 16 bytes) so a
+// tile can be staged with bulk asynchronous copies:
+//   element table   n_consts x T floats, tile-major: row r of element (t, i) at
+//                   (t n_consts + r) T + i
+//   lconn           T x n_e local node indices (element-major)
+//   lidx            T x n_e local slots a T + e_local, grouped by node
+//   tnodes          cap internal node ids (n_t used)
+//   lptr            cap + 8 offsets into lidx (n_t + 1 used)
 struct TileArgs {
   const int* tile_ptr;          // n_tiles + 1: first partial of each tile
-  const int* tile_nodes;        // per partial: internal node id
-  const unsigned short* lconn;  // per element n_e local node indices (element-major)
-  const unsigned short* lptr;   // per tile n_t + 1 offsets (tile t starts at tile_ptr[t] + t)
-  const unsigned short* lidx;   // per tile T n_e local slots a * T + e_local, grouped by node
+  const int* tnodes;            // n_tiles x cap
+  const unsigned short* lconn;  // n_tiles x T x n_e
+  const unsigned short* lptr;   // n_tiles x (cap + 8)
+  const unsigned short* lidx;   // n_tiles x T x n_e
   float4* partials;             // per (tile, node) force
   int T;
-  int smem_nodes;               // capacity of the staged-node array
+  int cap;                      // node capacity of a tile segment (multiple of 8, >= max n_t)
+  int n_consts;
+  int n_tiles;
 };
 
 enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_ONLY = 3 };
-enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1 };
+enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1, ASSEMBLY_TILES_TMA = 2 };
 
 constexpr int NODE_THREADS = 256;
 constexpr int SELL_C = 32;
@@ -99,6 +109,11 @@ cudaError_t launch_force(int elem_type, int variant, int cmp, const ForceArgs& a
                          cudaStream_t s);
 cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceArgs& a,
                                const TileArgs& t, int n_tiles, cudaStream_t s);
+// kernels_tma.cu: persistent, double-buffered tiles staged with bulk async copies
+cudaError_t launch_force_tma(int elem_type, int variant, int cmp, const ForceArgs& a,
+                             const TileArgs& t, int grid, cudaStream_t s);
+size_t tma_smem_bytes(int elem_type, int cmp, const TileArgs& t);
+int tma_blocks_per_sm(int elem_type, int variant, int cmp, const TileArgs& t);
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
 // per-group residual sums over contiguous node ranges (one block per group)
@@ -129,6 +144,8 @@ struct PreArgs {
   int E, E_pad, ne;
   int off_fa, off_fb, off_mr, off_hg;
   double hg_coeff;
+  int tile_T;    // > 0: tile-major table with tiles of tile_T elements
+  int n_consts;
 };
 cudaError_t launch_precompute_elements(const PreArgs& a, cudaStream_t s);
 // dt_node: per-node time step (grouped meshes) or nullptr to use dt

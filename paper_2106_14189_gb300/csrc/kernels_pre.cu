@@ -26,8 +26,13 @@ __device__ constexpr double H8D[4][8] = {{1, -1, 1, -1, 1, -1, 1, -1},
                                          {1, -1, -1, 1, -1, 1, 1, -1},
                                          {-1, 1, -1, 1, 1, -1, 1, -1}};
 
-__device__ void put(float* t, int k, int E_pad, int e, double v) {
-  t[(size_t)k * E_pad + e] = (float)v;
+// table row k of element e: structure of arrays (stride E_pad) or tile-major
+__device__ void put(const PreArgs& a, float* t, int k, int e, double v) {
+  const int T = a.tile_T;
+  if (T > 0)
+    t[((size_t)(e / T) * a.n_consts + k) * T + (e % T)] = (float)v;
+  else
+    t[(size_t)k * a.E_pad + e] = (float)v;
 }
 
 // S = 2 V Jinv^T d d^T Jinv  (d unit) -> sym6
@@ -107,7 +112,7 @@ __global__ void precompute_elements_kernel(PreArgs a) {
   // 0J, P = (mu/2) I1m, kappa 0V, 1/det (common block)
   float* t = a.consts;
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) put(t, K_J0 + 3 * i + j, a.E_pad, e, J0[i][j]);
+    for (int j = 0; j < 3; ++j) put(a, t, K_J0 + 3 * i + j, e, J0[i][j]);
   double K[6];  // 0J^-T 0J^-1
   const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
   for (int k = 0; k < 6; ++k) {
@@ -115,9 +120,9 @@ __global__ void precompute_elements_kernel(PreArgs a) {
     for (int m = 0; m < 3; ++m) s += Ji[m][ii[k]] * Ji[m][jj[k]];
     K[k] = s;
   }
-  for (int k = 0; k < 6; ++k) put(t, K_P + k, a.E_pad, e, 0.5 * mu * 2.0 * V0 * K[k]);
-  put(t, K_KV, a.E_pad, e, kappa * V0);
-  put(t, K_R0, a.E_pad, e, id);
+  for (int k = 0; k < 6; ++k) put(a, t, K_P + k, e, 0.5 * mu * 2.0 * V0 * K[k]);
+  put(a, t, K_KV, e, kappa * V0);
+  put(a, t, K_R0, e, id);
   if (a.off_fa >= 0) {
     double S[6] = {0, 0, 0, 0, 0, 0};
     if (eta_a > 0.0) {
@@ -126,8 +131,8 @@ __global__ void precompute_elements_kernel(PreArgs a) {
       for (int j = 0; j < 3; ++j) d[j] /= n;
       fibre_tensor(Ji, d, 2.0 * V0, S);
     }
-    for (int k = 0; k < 6; ++k) put(t, a.off_fa + k, a.E_pad, e, eta_a * S[k]);
-    put(t, a.off_fa + 6, a.E_pad, e, eta_a > 0.0 ? 1.0 / (2.0 * eta_a * V0) : 0.0);
+    for (int k = 0; k < 6; ++k) put(a, t, a.off_fa + k, e, eta_a * S[k]);
+    put(a, t, a.off_fa + 6, e, eta_a > 0.0 ? 1.0 / (2.0 * eta_a * V0) : 0.0);
   }
   if (a.off_fb >= 0) {
     double S[6] = {0, 0, 0, 0, 0, 0};
@@ -137,12 +142,12 @@ __global__ void precompute_elements_kernel(PreArgs a) {
       for (int j = 0; j < 3; ++j) d[j] /= n;
       fibre_tensor(Ji, d, 2.0 * V0, S);
     }
-    for (int k = 0; k < 6; ++k) put(t, a.off_fb + k, a.E_pad, e, eta_b * S[k]);
-    put(t, a.off_fb + 6, a.E_pad, e, eta_b > 0.0 ? 1.0 / (2.0 * eta_b * V0) : 0.0);
+    for (int k = 0; k < 6; ++k) put(a, t, a.off_fb + k, e, eta_b * S[k]);
+    put(a, t, a.off_fb + 6, e, eta_b > 0.0 ? 1.0 / (2.0 * eta_b * V0) : 0.0);
   }
   if (a.off_mr >= 0) {
     const double c10 = 0.5 * mu;
-    put(t, a.off_mr, a.E_pad, e, c01 / (2.0 * c10 * c10 * V0));
+    put(a, t, a.off_mr, e, c01 / (2.0 * c10 * c10 * V0));
   }
   // 0B = 0J^-1 H_xi and sum of squares
   double B0[3][8];
@@ -162,10 +167,10 @@ __global__ void precompute_elements_kernel(PreArgs a) {
         double s = 0.0;
         for (int b = 0; b < 8; ++b) s += H8D[q][b] * Xe[b][j];
         cq[q][j] = s;
-        put(t, a.off_hg + 3 * q + j, a.E_pad, e, s);
+        put(a, t, a.off_hg + 3 * q + j, e, s);
       }
     const double khg = a.hg_coeff * (kappa + 4.0 / 3.0 * mu) * V0 * sumB2 / 8.0;
-    put(t, a.off_hg + 12, a.E_pad, e, khg);
+    put(a, t, a.off_hg + 12, e, khg);
     double gam[4][8];
     for (int q = 0; q < 4; ++q)
       for (int b = 0; b < 8; ++b)

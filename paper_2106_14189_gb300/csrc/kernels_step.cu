@@ -21,507 +21,14 @@
 //        J tJ^-1 / det tJ ... = r0 adj  (Eq. 12).
 #include <cuda_runtime.h>
 
+#include "dj_elem.cuh"
 #include "dj_internal.h"
 
 namespace dj {
 
 namespace {
 
-__device__ __forceinline__ float ldg_stream(const float* p) { return __ldcs(p); }
-
-struct M3 {
-  float m[3][3];
-};
-
-__device__ __forceinline__ float det3(const M3& a) {
-  return a.m[0][0] * (a.m[1][1] * a.m[2][2] - a.m[1][2] * a.m[2][1]) -
-         a.m[0][1] * (a.m[1][0] * a.m[2][2] - a.m[1][2] * a.m[2][0]) +
-         a.m[0][2] * (a.m[1][0] * a.m[2][1] - a.m[1][1] * a.m[2][0]);
-}
-
-// adjugate: adj(a) = det(a) a^-1
-__device__ __forceinline__ M3 adj3(const M3& a) {
-  M3 r;
-  r.m[0][0] = a.m[1][1] * a.m[2][2] - a.m[1][2] * a.m[2][1];
-  r.m[0][1] = a.m[0][2] * a.m[2][1] - a.m[0][1] * a.m[2][2];
-  r.m[0][2] = a.m[0][1] * a.m[1][2] - a.m[0][2] * a.m[1][1];
-  r.m[1][0] = a.m[1][2] * a.m[2][0] - a.m[1][0] * a.m[2][2];
-  r.m[1][1] = a.m[0][0] * a.m[2][2] - a.m[0][2] * a.m[2][0];
-  r.m[1][2] = a.m[0][2] * a.m[1][0] - a.m[0][0] * a.m[1][2];
-  r.m[2][0] = a.m[1][0] * a.m[2][1] - a.m[1][1] * a.m[2][0];
-  r.m[2][1] = a.m[0][1] * a.m[2][0] - a.m[0][0] * a.m[2][1];
-  r.m[2][2] = a.m[0][0] * a.m[1][1] - a.m[0][1] * a.m[1][0];
-  return r;
-}
-
-// symmetric 3x3 stored as s[6] = {00, 11, 22, 01, 02, 12}
-__device__ __forceinline__ float sym_at(const float* s, int i, int j) {
-  if (i == j) return s[i];
-  int k = i + j;  // (0,1)->1, (0,2)->2, (1,2)->3
-  return s[2 + k];
-}
-
-__device__ __forceinline__ void load_sym(const float* c, int off, int E_pad, int e, float* s) {
-#pragma unroll
-  for (int k = 0; k < 6; ++k) s[k] = ldg_stream(c + (size_t)(off + k) * E_pad + e);
-}
-
-// g : S  (Frobenius product of symmetric g with symmetric S)
-__device__ __forceinline__ float frob_sym(const float* g, const float* s) {
-  return g[0] * s[0] + g[1] * s[1] + g[2] * s[2] + 2.f * (g[3] * s[3] + g[4] * s[4] + g[5] * s[5]);
-}
-
-// acc += w * tJ^T S  (S symmetric)
-__device__ __forceinline__ void add_tJT_sym(M3& acc, const M3& tJ, const float* s, float w) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float v = tJ.m[0][i] * sym_at(s, 0, j) + tJ.m[1][i] * sym_at(s, 1, j) +
-                tJ.m[2][i] * sym_at(s, 2, j);
-      acc.m[i][j] = fmaf(w, v, acc.m[i][j]);
-    }
-}
-
-// Per-element constants of the table, loaded once into registers.
-template <bool FA, bool FB, bool MR>
-struct ElemConsts {
-  float J0[3][3];
-  float P[6];
-  float kV, r0;
-  float Qa[FA ? 6 : 1], sa;
-  float Qb[FB ? 6 : 1], sb;
-  float gm;
-
-  __device__ __forceinline__ void load(const float* __restrict__ c, int E_pad, int e,
-                                       const ForceArgs& a) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) J0[i][j] = ldg_stream(c + (size_t)(K_J0 + 3 * i + j) * E_pad + e);
-    load_sym(c, K_P, E_pad, e, P);
-    kV = ldg_stream(c + (size_t)K_KV * E_pad + e);
-    r0 = ldg_stream(c + (size_t)K_R0 * E_pad + e);
-    if (FA) {
-      load_sym(c, a.off_fa, E_pad, e, Qa);
-      sa = ldg_stream(c + (size_t)(a.off_fa + 6) * E_pad + e);
-    }
-    if (FB) {
-      load_sym(c, a.off_fb, E_pad, e, Qb);
-      sb = ldg_stream(c + (size_t)(a.off_fb + 6) * E_pad + e);
-    }
-    if (MR) gm = ldg_stream(c + (size_t)a.off_mr * E_pad + e);
-  }
-};
-
-// Hourglass constants of a brick: c_{alpha j} = h_alpha . X_j and k.
-struct HgConsts {
-  float cc[4][3];
-  float k;
-  __device__ __forceinline__ void load(const float* __restrict__ c, int E_pad, int e, int off) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) cc[q][j] = ldg_stream(c + (size_t)(off + 3 * q + j) * E_pad + e);
-    k = ldg_stream(c + (size_t)(off + 12) * E_pad + e);
-  }
-};
-
-// F = J^-2/3 tJ^T (P + psi_a Q_a + psi_b Q_b + MR) + coefficient * adj(tJ)   (Table 3)
-template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA, FB, MR>& k,
-                                              bool& bad) {
-  const float D = det3(tJ);
-  const float J = D * k.r0;  // Eq. 12
-  bad = !(D > 0.f);
-  const float rc = rcbrtf(J);
-  const float Jm23 = rc * rc;  // J^-2/3
-  // g = tJ tJ^T (Eq. 17), symmetric
-  float g[6];
-  g[0] = tJ.m[0][0] * tJ.m[0][0] + tJ.m[0][1] * tJ.m[0][1] + tJ.m[0][2] * tJ.m[0][2];
-  g[1] = tJ.m[1][0] * tJ.m[1][0] + tJ.m[1][1] * tJ.m[1][1] + tJ.m[1][2] * tJ.m[1][2];
-  g[2] = tJ.m[2][0] * tJ.m[2][0] + tJ.m[2][1] * tJ.m[2][1] + tJ.m[2][2] * tJ.m[2][2];
-  g[3] = tJ.m[0][0] * tJ.m[1][0] + tJ.m[0][1] * tJ.m[1][1] + tJ.m[0][2] * tJ.m[1][2];
-  g[4] = tJ.m[0][0] * tJ.m[2][0] + tJ.m[0][1] * tJ.m[2][1] + tJ.m[0][2] * tJ.m[2][2];
-  g[5] = tJ.m[1][0] * tJ.m[2][0] + tJ.m[1][1] * tJ.m[2][1] + tJ.m[1][2] * tJ.m[2][2];
-
-  const float gP = frob_sym(g, k.P);  // = mu 0V I1
-  M3 T;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
-  float vol_over_D = -gP / 3.f;  // multiplies Jm23 adj / D
-  if (FA) {
-    const float gQ = frob_sym(g, k.Qa);
-    const float psi = Jm23 * gQ * k.sa - 1.f;  // I4bar - 1 (Eq. 31, Table 1)
-    add_tJT_sym(T, tJ, k.Qa, psi);
-    vol_over_D -= psi * gQ / 3.f;
-  }
-  if (FB) {
-    const float gQ = frob_sym(g, k.Qb);
-    const float psi = Jm23 * gQ * k.sb - 1.f;  // I6bar - 1 (Eq. 32)
-    add_tJT_sym(T, tJ, k.Qb, psi);
-    vol_over_D -= psi * gQ / 3.f;
-  }
-  add_tJT_sym(T, tJ, k.P, 1.f);
-  float mr_vol = 0.f;
-  if (MR) {
-    // C01 g_hat^T I2m = gm (g:P P - P g P), gm = C01 / (2 C10^2 0V)   (Eq. 39-42)
-    float Pg[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Pg[i][j] = sym_at(k.P, i, 0) * sym_at(g, 0, j) + sym_at(k.P, i, 1) * sym_at(g, 1, j) +
-                   sym_at(k.P, i, 2) * sym_at(g, 2, j);
-    float S2[6];
-    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int i = ii[q], j = jj[q];
-      const float PgP = Pg[i][0] * sym_at(k.P, 0, j) + Pg[i][1] * sym_at(k.P, 1, j) +
-                        Pg[i][2] * sym_at(k.P, 2, j);
-      S2[q] = k.gm * (gP * sym_at(k.P, i, j) - PgP);
-    }
-    float trPgPg = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
-    add_tJT_sym(T, tJ, S2, Jm23);                               // extra J^-2/3 of Eq. 39
-    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
-  }
-  const M3 A = adj3(tJ);
-  const float invD = 1.f / D;
-  const float ca = (Jm23 * vol_over_D + mr_vol) * invD + k.kV * (J - 1.f) * k.r0;
-  M3 F;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) F.m[i][j] = fmaf(Jm23, T.m[i][j], ca * A.m[i][j]);
-  return F;
-}
-
-__device__ __forceinline__ void flag_error(DevState* st, int e, bool inverted, bool nonfinite) {
-  int f = (inverted ? ERR_INVERTED : 0) | (nonfinite ? ERR_NONFINITE : 0);
-  if (f) {
-    atomicOr(&st->err_flags, f);
-    atomicMin(&st->bad_elem, e);
-  }
-}
-
-__device__ __forceinline__ void advance_clock(const ForceArgs& a) {
-  if (a.advance && blockIdx.x == 0 && threadIdx.x == 0) {
-    const long long n1 = a.st->step + 1;
-    double s = 1.0;
-    if (a.ramp_steps > 0) {
-      double tau = (double)n1 / (double)a.ramp_steps;
-      tau = tau > 1.0 ? 1.0 : tau;
-      s = a.ramp_kind == DJ_RAMP_LINEAR ? tau : tau * tau * tau * (10.0 - 15.0 * tau + 6.0 * tau * tau);
-    }
-    a.st->ramp_s = (float)s;
-    a.st->step = n1;
-  }
-}
-
-__device__ __forceinline__ bool finite3(float x, float y, float z) {
-  return isfinite(x) && isfinite(y) && isfinite(z);
-}
-
-// natural coordinates of the brick nodes (bottom face CCW, then top face)
-__device__ constexpr float XI8[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
-                                        {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
-// hourglass base vectors h1 = xi eta, h2 = eta zeta, h3 = zeta xi, h4 = xi eta zeta
-__device__ constexpr float H8[4][8] = {{1, -1, 1, -1, 1, -1, 1, -1},
-                                       {1, 1, -1, -1, -1, -1, 1, 1},
-                                       {1, -1, -1, 1, -1, 1, 1, -1},
-                                       {-1, 1, -1, 1, 1, -1, 1, -1}};
-
-template <int NE>
-struct ElemExtra;
-template <>
-struct ElemExtra<4> {
-  __device__ __forceinline__ void load(const float*, int, int, int) {}
-};
-template <>
-struct ElemExtra<8> : HgConsts {};
-
-// adj(A + B) - adj(A), expanded so that no O(1) terms cancel
-__device__ __forceinline__ M3 adj_delta(const M3& A, const M3& B) {
-#define DJ_ADJD(p0, p1, q0, q1, r0, r1, s0, s1)                                                  \
-  (A.m[p0][p1] * B.m[q0][q1] + B.m[p0][p1] * A.m[q0][q1] + B.m[p0][p1] * B.m[q0][q1] -           \
-   (A.m[r0][r1] * B.m[s0][s1] + B.m[r0][r1] * A.m[s0][s1] + B.m[r0][r1] * B.m[s0][s1]))
-  M3 r;
-  r.m[0][0] = DJ_ADJD(1, 1, 2, 2, 1, 2, 2, 1);
-  r.m[0][1] = DJ_ADJD(0, 2, 2, 1, 0, 1, 2, 2);
-  r.m[0][2] = DJ_ADJD(0, 1, 1, 2, 0, 2, 1, 1);
-  r.m[1][0] = DJ_ADJD(1, 2, 2, 0, 1, 0, 2, 2);
-  r.m[1][1] = DJ_ADJD(0, 0, 2, 2, 0, 2, 2, 0);
-  r.m[1][2] = DJ_ADJD(0, 2, 1, 0, 0, 0, 1, 2);
-  r.m[2][0] = DJ_ADJD(1, 0, 2, 1, 1, 1, 2, 0);
-  r.m[2][1] = DJ_ADJD(0, 1, 2, 0, 0, 0, 2, 1);
-  r.m[2][2] = DJ_ADJD(0, 0, 1, 1, 0, 1, 1, 0);
-#undef DJ_ADJD
-  return r;
-}
-
-// Compensated form of the same force: with A = 0J and B = tJ - 0J (Eq. 11),
-//   J - 1        = (tr(adj(A) B) + tr(A adj(B)) + det B) / det A          (Eq. 12)
-//   g:P - 3 mu0V = P : (A B^T + B A^T + B B^T),  mu 0V = P : A A^T / 3
-//   tJ^T P - (g:P)/3 tJ^-1
-//                = mu0V (J-1) adj(A) / D + B^T P - mu0V (adj(tJ) - adj(A)) / D
-//                  - (g:P - 3 mu0V) / 3 adj(tJ) / D
-//   I4bar - 1    = (J^-2/3 - 1) + J^-2/3 (P_a : (A B^T + B A^T + B B^T)) s_a
-// Every term is of the order of the increment, so FP32 keeps its relative
-// accuracy at small strain instead of losing it to cancellation.
-template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, const ElemConsts<FA, FB, MR>& k,
-                                                  bool& bad) {
-  M3 tJ;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) tJ.m[i][j] = A.m[i][j] + B.m[i][j];
-  const M3 adjA = adj3(A);
-  const M3 adjB = adj3(B);
-  float dD = det3(B);
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) dD += adjA.m[i][j] * B.m[j][i] + A.m[i][j] * adjB.m[j][i];
-  const float jm1 = dD * k.r0;  // J - 1
-  const float J = 1.f + jm1;
-  bad = !(J > 0.f);
-  const float D = 1.f / k.r0 + dD;
-  const float invD = 1.f / D;
-  const float lJ = log1pf(jm1);
-  const float Jm23 = expf(-2.f / 3.f * lJ);
-  const float Jm23m1 = expm1f(-2.f / 3.f * lJ);
-  // g0 = A A^T and dg = A B^T + B A^T + B B^T (symmetric, {00,11,22,01,02,12})
-  const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
-  float g0[6], dg[6], g[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const int i = ii[q], j = jj[q];
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      s0 += A.m[i][m] * A.m[j][m];
-      s1 += A.m[i][m] * B.m[j][m] + B.m[i][m] * A.m[j][m] + B.m[i][m] * B.m[j][m];
-    }
-    g0[q] = s0;
-    dg[q] = s1;
-    g[q] = s0 + s1;
-  }
-  const float mV = frob_sym(g0, k.P) / 3.f;  // mu 0V
-  const float dgP = frob_sym(dg, k.P);       // g:P - 3 mu 0V
-  const M3 adjD = adj_delta(A, B);
-  M3 adjT;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) adjT.m[i][j] = adjA.m[i][j] + adjD.m[i][j];
-  M3 T;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
-  add_tJT_sym(T, B, k.P, 1.f);  // B^T P
-  float cT = -dgP / 3.f * invD;  // coefficient of adj(tJ) inside the J^-2/3 bracket
-  if (FA) {
-    const float d4 = frob_sym(dg, k.Qa);
-    const float psi = Jm23m1 + Jm23 * d4 * k.sa;  // I4bar - 1
-    add_tJT_sym(T, tJ, k.Qa, psi);
-    cT -= psi * frob_sym(g, k.Qa) / 3.f * invD;
-  }
-  if (FB) {
-    const float d6 = frob_sym(dg, k.Qb);
-    const float psi = Jm23m1 + Jm23 * d6 * k.sb;  // I6bar - 1
-    add_tJT_sym(T, tJ, k.Qb, psi);
-    cT -= psi * frob_sym(g, k.Qb) / 3.f * invD;
-  }
-  float mr_vol = 0.f;
-  if (MR) {
-    const float gP = 3.f * mV + dgP;
-    float Pg[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        Pg[i][j] = sym_at(k.P, i, 0) * sym_at(g, 0, j) + sym_at(k.P, i, 1) * sym_at(g, 1, j) +
-                   sym_at(k.P, i, 2) * sym_at(g, 2, j);
-    float S2[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int i = ii[q], j = jj[q];
-      const float PgP = Pg[i][0] * sym_at(k.P, 0, j) + Pg[i][1] * sym_at(k.P, 1, j) +
-                        Pg[i][2] * sym_at(k.P, 2, j);
-      S2[q] = k.gm * (gP * sym_at(k.P, i, j) - PgP);
-    }
-    float trPgPg = 0.f;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
-    add_tJT_sym(T, tJ, S2, Jm23);
-    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;
-  }
-  const float cA = mV * jm1 * invD, cD = -mV * invD;
-  const float cadj = mr_vol * invD + k.kV * jm1 * k.r0;  // volumetric: kappa 0V (J-1) r0 adj(tJ)
-  M3 F;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const float br = T.m[i][j] + cA * adjA.m[i][j] + cD * adjD.m[i][j] + cT * adjT.m[i][j];
-      F.m[i][j] = fmaf(Jm23, br, cadj * adjT.m[i][j]);
-    }
-  return F;
-}
-
-template <bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ M3 force_matrix(const M3& A, const M3& B, const ElemConsts<FA, FB, MR>& k,
-                                           bool& bad) {
-  if constexpr (CMP) {
-    return dj_force_matrix_cmp<FA, FB, MR>(A, B, k, bad);
-  } else {
-    M3 tJ;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) tJ.m[i][j] = A.m[i][j] + B.m[i][j];
-    return dj_force_matrix<FA, FB, MR>(tJ, k, bad);
-  }
-}
-
-// u_b - u_0 of one component; compensated mode: from the (hi, lo) pairs with an
-// error-free difference of the high parts
-template <bool CMP>
-__device__ __forceinline__ float node_diff(float hb, float h0, float lb, float l0) {
-  if constexpr (!CMP) {
-    return hb - h0;
-  } else {
-    const float s = hb - h0;
-    const float bb = s - hb;
-    const float err = (hb - (s - bb)) + (-h0 - bb);
-    return s + (err + (lb - l0));
-  }
-}
-
-// Nodal forces of one T4 element from d_b = u_b - u_0 (b = 1..3):
-// tJ = 0J + H_xi u has rows d_1, d_2, d_3 (Eq. 11); F H_xi gives node b = 1..3
-// column b-1 and node 0 minus their sum (Sec. 7).
-template <bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ void tet4_forces(const float (&d)[4][3], const ElemConsts<FA, FB, MR>& k,
-                                            const ElemExtra<4>&, float (&f)[4][3], bool& inv) {
-  M3 A, B;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      A.m[i][j] = k.J0[i][j];
-      B.m[i][j] = d[i + 1][j];
-    }
-  const M3 F = force_matrix<FA, FB, MR, CMP>(A, B, k, inv);
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    f[1][j] = F.m[j][0];
-    f[2][j] = F.m[j][1];
-    f[3][j] = F.m[j][2];
-    f[0][j] = -(F.m[j][0] + F.m[j][1] + F.m[j][2]);
-  }
-}
-
-// Nodal forces of one 1-point H8 element with hourglass control, from
-// d_b = u_b - u_0 (H_xi and the hourglass vectors annihilate constants, so
-// sums over d_b equal sums over u_b).
-template <bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ void hex8_forces(const float (&d)[8][3], const ElemConsts<FA, FB, MR>& k,
-                                            const ElemExtra<8>& hg, float (&f)[8][3], bool& inv) {
-  // s_i = (H_xi u)_i = sum_b xi_{b,i} d_b / 8
-  float s[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float acc = 0.f;
-#pragma unroll
-      for (int b = 1; b < 8; ++b) acc += XI8[b][i] * d[b][j];
-      s[i][j] = 0.125f * acc;
-    }
-  M3 A, B;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      A.m[i][j] = k.J0[i][j];
-      B.m[i][j] = s[i][j];  // Eq. 11
-    }
-  const M3 F = force_matrix<FA, FB, MR, CMP>(A, B, k, inv);
-  // hourglass: q_alpha = gamma_alpha . u, gamma_alpha = h_alpha - sum_j c_aj 0B_j,
-  // 0B = 0J^-1 H_xi with 0J^-1 = adj(0J) / det 0J
-  const M3 J0a = adj3(A);
-  float eq[4][3];  // e_{alpha,i} = sum_j c_{alpha j} (0J^-1)_{j i}
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-      eq[q][i] = k.r0 * (hg.cc[q][0] * J0a.m[0][i] + hg.cc[q][1] * J0a.m[1][i] + hg.cc[q][2] * J0a.m[2][i]);
-  float H[4][3];  // k q_alpha
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float hu = 0.f;
-#pragma unroll
-      for (int b = 1; b < 8; ++b) hu += H8[q][b] * d[b][j];
-      H[q][j] = hg.k * (hu - (eq[q][0] * s[0][j] + eq[q][1] * s[1][j] + eq[q][2] * s[2][j]));
-    }
-  // G_i = F[:, i] / 8 - (1/8) sum_alpha e_{alpha,i} H_alpha;  f_b = sum_i xi_{b,i} G_i + sum_alpha h_{alpha,b} H_alpha
-  float G[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      G[i][j] = 0.125f * (F.m[j][i] - (eq[0][i] * H[0][j] + eq[1][i] * H[1][j] + eq[2][i] * H[2][j] +
-                                       eq[3][i] * H[3][j]));
-#pragma unroll
-  for (int b = 0; b < 8; ++b)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-      f[b][j] = XI8[b][0] * G[0][j] + XI8[b][1] * G[1][j] + XI8[b][2] * G[2][j] + H8[0][b] * H[0][j] +
-                H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
-}
-
-template <int NE, bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemConsts<FA, FB, MR>& k,
-                                            const ElemExtra<NE>& x, float (&f)[NE][3], bool& inv) {
-  if constexpr (NE == 4)
-    tet4_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
-  else
-    hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
-}
-
-template <int NE>
-__device__ __forceinline__ bool all_finite(const float (&f)[NE][3]) {
-  bool ok = true;
-#pragma unroll
-  for (int b = 0; b < NE; ++b) ok &= finite3(f[b][0], f[b][1], f[b][2]);
-  return ok;
-}
-
-// d_b = u_b - u_0 from the nodal records (hi, lo)
-template <int NE, bool CMP>
-__device__ __forceinline__ void node_deltas(const float4 (&h)[NE], const float4 (&l)[NE], float (&d)[NE][3]) {
-  d[0][0] = d[0][1] = d[0][2] = 0.f;
-#pragma unroll
-  for (int b = 1; b < NE; ++b) {
-    d[b][0] = node_diff<CMP>(h[b].x, h[0].x, l[b].x, l[0].x);
-    d[b][1] = node_diff<CMP>(h[b].y, h[0].y, l[b].y, l[0].y);
-    d[b][2] = node_diff<CMP>(h[b].z, h[0].z, l[b].z, l[0].z);
-  }
-}
+using namespace elem;
 
 // Element-slot assembly: one thread per element, forces to slot a * E_pad + e.
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
@@ -531,10 +38,11 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
   if (e >= a.E) return;
   const int E_pad = a.E_pad;
   const float* __restrict__ c = a.consts;
+  const auto ld = [&](int r) { return __ldcs(c + (size_t)r * E_pad + e); };
   ElemConsts<FA, FB, MR> k;
-  k.load(c, E_pad, e, a);
+  k.load(ld, a);
   ElemExtra<NE> x;
-  if constexpr (NE == 8) x.load(c, E_pad, e, a.off_hg);
+  if constexpr (NE == 8) x.load(ld, a.off_hg);
   int nid[NE];
   {
     const int4 n0 = __ldcs(a.conn + (NE / 4) * (size_t)e);
@@ -569,8 +77,8 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
   advance_clock(a);
   const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
   float4* su = smem4;                                          // staged U (high part)
-  float4* sl = smem4 + t.smem_nodes;                           // staged low part (compensated)
-  float* sf = reinterpret_cast<float*>(smem4 + (CMP ? 2 : 1) * t.smem_nodes);  // 3 x (NE T) forces
+  float4* sl = smem4 + t.cap;                                  // staged low part (compensated)
+  float* sf = reinterpret_cast<float*>(smem4 + (CMP ? 2 : 1) * t.cap);  // 3 x (NE T) forces
   const int base = __ldg(t.tile_ptr + tile);
   const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
   const int e = tile * T + tid;
@@ -580,8 +88,11 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
   ElemExtra<NE> x;
   unsigned short lc[NE];
   if (valid) {
-    k.load(c, a.E_pad, e, a);
-    if constexpr (NE == 8) x.load(c, a.E_pad, e, a.off_hg);
+    // tile-major table: row r of element (tile, tid) at ((tile n_consts) + r) T + tid
+    const float* ct = c + (size_t)tile * t.n_consts * T + tid;
+    const auto ld = [&](int r) { return __ldcs(ct + (size_t)r * T); };
+    k.load(ld, a);
+    if constexpr (NE == 8) x.load(ld, a.off_hg);
     if constexpr (NE == 4) {
       const ushort4 v = __ldcs(reinterpret_cast<const ushort4*>(t.lconn) + e);
       lc[0] = v.x; lc[1] = v.y; lc[2] = v.z; lc[3] = v.w;
@@ -593,7 +104,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
     }
   }
   for (int q = tid; q < n_t; q += T) {
-    const int gid = __ldg(t.tile_nodes + base + q);
+    const int gid = __ldg(t.tnodes + (size_t)tile * t.cap + q);
     su[q] = __ldg(a.U + gid);
     if (CMP) sl[q] = __ldg(a.Ulo + gid);
   }
@@ -621,7 +132,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
   }
   __syncthreads();
   const int S = NE * T;
-  const unsigned short* lp = t.lptr + base + tile;
+  const unsigned short* lp = t.lptr + (size_t)tile * (t.cap + 8);
   const unsigned short* li = t.lidx + (size_t)tile * S;
   for (int q = tid; q < n_t; q += T) {
     const int p0 = lp[q], p1 = lp[q + 1];
@@ -813,7 +324,7 @@ cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t smem = (size_t)(CMP ? 2 : 1) * t.smem_nodes * sizeof(float4) +
+  const size_t smem = (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) +
                       (size_t)3 * NE * t.T * sizeof(float);
   static bool attr_set = false;
   if (!attr_set) {

@@ -1,0 +1,252 @@
+// Persistent element-force kernel with bulk asynchronous copies (TMA) for sm_103a.
+//
+// Each block walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The
+// per-tile segments (tile-major element table, local connectivity, local slot
+// index, node list, node offsets; see TileArgs) of the next tile are copied into
+// one of two shared-memory stages with cp.async.bulk while the current tile is
+// computed; an mbarrier per stage counts the arriving bytes.  Table reads are
+// then shared-memory loads at constant offsets.  Every wait is bounded: on
+// timeout the kernel records ERR_TIMEOUT, waits (bounded) for the copies it
+// still has in flight, and returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dj_elem.cuh"
+#include "dj_internal.h"
+
+namespace dj {
+namespace {
+
+using namespace elem;
+
+constexpr long long kWaitLimit = 1LL << 22;  // polls of an mbarrier before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// bounded wait for the completion of phase `parity`; true if it completed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <int NE>
+struct StageLayout {
+  uint32_t tab, lconn, lidx, tnodes, lptr, bytes;  // byte offsets inside a stage
+  __device__ __host__ StageLayout(const TileArgs& t) {
+    tab = 0;
+    lconn = tab + (uint32_t)t.n_consts * t.T * 4;
+    lidx = lconn + (uint32_t)t.T * NE * 2;
+    tnodes = lidx + (uint32_t)t.T * NE * 2;
+    lptr = tnodes + (uint32_t)t.cap * 4;
+    bytes = lptr + (uint32_t)(t.cap + 8) * 2;
+  }
+};
+
+// issue the bulk copies of tile `tile` into `stage` (one thread)
+template <int NE>
+__device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t, const StageLayout<NE>& L,
+                                           char* stage, uint64_t* bar, int tile) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_arrive_expect_tx(bar, L.bytes);
+  bulk_copy(stage + L.tab, a.consts + (size_t)tile * t.n_consts * t.T, L.lconn - L.tab, bar);
+  bulk_copy(stage + L.lconn, t.lconn + (size_t)tile * t.T * NE, L.lidx - L.lconn, bar);
+  bulk_copy(stage + L.lidx, t.lidx + (size_t)tile * t.T * NE, L.tnodes - L.lidx, bar);
+  bulk_copy(stage + L.tnodes, t.tnodes + (size_t)tile * t.cap, L.lptr - L.tnodes, bar);
+  bulk_copy(stage + L.lptr, t.lptr + (size_t)tile * (t.cap + 8), L.bytes - L.lptr, bar);
+}
+
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
+__global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t) {
+  extern __shared__ __align__(128) char smem[];
+  const StageLayout<NE> L(t);
+  const int T = t.T, tid = threadIdx.x;
+  const uint32_t stage_bytes = (L.bytes + 127) & ~127u;
+  float4* su = reinterpret_cast<float4*>(smem + 2 * stage_bytes);
+  float4* sl = su + t.cap;
+  float* sf = reinterpret_cast<float*>(su + (CMP ? 2 : 1) * t.cap);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sf + 3 * NE * T);  // 8-byte aligned: sizes are multiples of 16
+  advance_clock(a);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const int first = blockIdx.x;
+  if (first >= t.n_tiles) return;
+  if (tid == 0) issue_tile<NE>(a, t, L, smem, &bars[0], first);
+  int i = 0;
+  for (int tile = first; tile < t.n_tiles; tile += gridDim.x, ++i) {
+    const int s = i & 1;
+    const int next = tile + gridDim.x;
+    const bool has_next = next < t.n_tiles;
+    if (tid == 0 && has_next) issue_tile<NE>(a, t, L, smem + (s ^ 1) * stage_bytes, &bars[s ^ 1], next);
+    const bool ok = mbar_wait(&bars[s], (uint32_t)((i >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicOr(&a.st->err_flags, ERR_TIMEOUT);
+        if (has_next) mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+      }
+      return;
+    }
+    const char* st = smem + s * stage_bytes;
+    const float* tab = reinterpret_cast<const float*>(st + L.tab);
+    const unsigned short* lconn = reinterpret_cast<const unsigned short*>(st + L.lconn);
+    const unsigned short* lidx = reinterpret_cast<const unsigned short*>(st + L.lidx);
+    const int* tnodes = reinterpret_cast<const int*>(st + L.tnodes);
+    const unsigned short* lptr = reinterpret_cast<const unsigned short*>(st + L.lptr);
+    const int base = __ldg(t.tile_ptr + tile);
+    const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
+    for (int q = tid; q < n_t; q += T) {
+      const int gid = tnodes[q];
+      su[q] = __ldg(a.U + gid);
+      if (CMP) sl[q] = __ldg(a.Ulo + gid);
+    }
+    __syncthreads();
+    const int e = tile * T + tid;
+    if (e < a.E) {
+      const auto ld = [&](int r) { return tab[r * T + tid]; };
+      ElemConsts<FA, FB, MR> k;
+      k.load(ld, a);
+      ElemExtra<NE> x;
+      if constexpr (NE == 8) x.load(ld, a.off_hg);
+      float4 h[NE], l[NE];
+#pragma unroll
+      for (int b = 0; b < NE; ++b) {
+        const int lcb = lconn[tid * NE + b];
+        h[b] = su[lcb];
+        l[b] = CMP ? sl[lcb] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float d[NE][3];
+      node_deltas<NE, CMP>(h, l, d);
+      float f[NE][3];
+      bool inv;
+      elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
+      flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
+      const int S = NE * T;
+#pragma unroll
+      for (int b = 0; b < NE; ++b) {
+        sf[b * T + tid] = f[b][0];
+        sf[S + b * T + tid] = f[b][1];
+        sf[2 * S + b * T + tid] = f[b][2];
+      }
+    }
+    __syncthreads();
+    const int S = NE * T;
+    for (int q = tid; q < n_t; q += T) {
+      const int p0 = lptr[q], p1 = lptr[q + 1];
+      float fx = 0.f, fy = 0.f, fz = 0.f;
+      for (int p = p0; p < p1; ++p) {
+        const int l = lidx[p];
+        fx += sf[l];
+        fy += sf[S + l];
+        fz += sf[2 * S + l];
+      }
+      t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
+    }
+    __syncthreads();  // stage s and the shared forces are reused by later tiles
+  }
+}
+
+template <int NE, bool CMP>
+size_t smem_bytes_t(const TileArgs& t) {
+  const StageLayout<NE> L(t);
+  const size_t stage = (L.bytes + 127) & ~size_t(127);
+  return 2 * stage + (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)3 * NE * t.T * sizeof(float) + 16;
+}
+
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
+cudaError_t launch_t(const ForceArgs& a, const TileArgs& t, int grid, cudaStream_t s) {
+  const size_t smem = smem_bytes_t<NE, CMP>(t);
+  force_tma_kernel<NE, FA, FB, MR, CMP><<<grid, t.T, smem, s>>>(a, t);
+  return cudaGetLastError();
+}
+
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
+int occupancy_t(const TileArgs& t) {
+  const size_t smem = smem_bytes_t<NE, CMP>(t);
+  // allow the largest dynamic shared memory once, outside any stream capture
+  if (cudaFuncSetAttribute(force_tma_kernel<NE, FA, FB, MR, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           227 * 1024) != cudaSuccess)
+    return 0;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, force_tma_kernel<NE, FA, FB, MR, CMP>, t.T, smem) !=
+      cudaSuccess)
+    return 0;
+  return n;
+}
+
+template <int NE, bool CMP>
+cudaError_t launch_v(int variant, const ForceArgs& a, const TileArgs& t, int grid, cudaStream_t s) {
+  switch (variant) {
+    case VAR_NH: return launch_t<NE, false, false, false, CMP>(a, t, grid, s);
+    case VAR_TI: return launch_t<NE, true, false, false, CMP>(a, t, grid, s);
+    case VAR_OT: return launch_t<NE, true, true, false, CMP>(a, t, grid, s);
+    case VAR_MR: return launch_t<NE, false, false, true, CMP>(a, t, grid, s);
+    default: return launch_t<NE, true, true, true, CMP>(a, t, grid, s);
+  }
+}
+
+template <int NE, bool CMP>
+int occupancy_v(int variant, const TileArgs& t) {
+  switch (variant) {
+    case VAR_NH: return occupancy_t<NE, false, false, false, CMP>(t);
+    case VAR_TI: return occupancy_t<NE, true, false, false, CMP>(t);
+    case VAR_OT: return occupancy_t<NE, true, true, false, CMP>(t);
+    case VAR_MR: return occupancy_t<NE, false, false, true, CMP>(t);
+    default: return occupancy_t<NE, true, true, true, CMP>(t);
+  }
+}
+
+}  // namespace
+
+size_t tma_smem_bytes(int elem_type, int cmp, const TileArgs& t) {
+  if (elem_type == DJ_TET4) return cmp ? smem_bytes_t<4, true>(t) : smem_bytes_t<4, false>(t);
+  return cmp ? smem_bytes_t<8, true>(t) : smem_bytes_t<8, false>(t);
+}
+
+int tma_blocks_per_sm(int elem_type, int variant, int cmp, const TileArgs& t) {
+  if (elem_type == DJ_TET4) return cmp ? occupancy_v<4, true>(variant, t) : occupancy_v<4, false>(variant, t);
+  return cmp ? occupancy_v<8, true>(variant, t) : occupancy_v<8, false>(variant, t);
+}
+
+cudaError_t launch_force_tma(int elem_type, int variant, int cmp, const ForceArgs& a, const TileArgs& t,
+                             int grid, cudaStream_t s) {
+  if (elem_type == DJ_TET4)
+    return cmp ? launch_v<4, true>(variant, a, t, grid, s) : launch_v<4, false>(variant, a, t, grid, s);
+  return cmp ? launch_v<8, true>(variant, a, t, grid, s) : launch_v<8, false>(variant, a, t, grid, s);
+}
+
+}  // namespace dj

@@ -33,11 +33,12 @@ constexpr int TM = 64, TN = 64, TK = 16;
 
 // C[i, j] = alpha sum_k A(i, k) B(k, j) + beta C[i, j], with A(i, k) = A[i * sar + k * sac]
 // and B(k, j) = B[k * sbr + j * sbc]; C row-major with leading dimension ldc.
+// subA (optional): A(i, k) - subA[k], which centres snapshots inside the product
 template <typename ACC>
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
                                                    long long sar, long long sac, const float* __restrict__ B,
                                                    long long sbr, long long sbc, float beta, float* __restrict__ C,
-                                                   long long ldc) {
+                                                   long long ldc, const float* __restrict__ subA) {
   __shared__ float As[TK][TM + 4];
   __shared__ float Bs[TK][TN + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, float al
     for (int q = threadIdx.x; q < TM * TK; q += 256) {
       const int ii = q / TK, kk = q % TK;
       const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < M && k < K) ? A[i * sar + k * sac] : 0.f;
+      As[kk][ii] = (i < M && k < K) ? A[i * sar + k * sac] - (subA ? subA[k] : 0.f) : 0.f;
     }
     for (int q = threadIdx.x; q < TN * TK; q += 256) {
       const int jj = q % TN, kk = q / TN;
@@ -186,10 +187,11 @@ __global__ void add_mean_kernel(float* X, const float* __restrict__ mean, long l
 
 template <typename ACC>
 cudaError_t gemm(int M, int N, int K, float alpha, const float* A, long long sar, long long sac, const float* B,
-                 long long sbr, long long sbc, float beta, float* C, long long ldc, cudaStream_t s) {
+                 long long sbr, long long sbc, float beta, float* C, long long ldc, cudaStream_t s,
+                 const float* subA = nullptr) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_kernel<ACC><<<grid, 256, 0, s>>>(M, N, K, alpha, A, sar, sac, B, sbr, sbc, beta, C, ldc);
+  gemm_kernel<ACC><<<grid, 256, 0, s>>>(M, N, K, alpha, A, sar, sac, B, sbr, sbc, beta, C, ldc, subA);
   return cudaGetLastError();
 }
 
@@ -553,21 +555,11 @@ dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d
 
 dj_status dj_pod_project(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_X,
                          int cols, float* d_Q, void* stream) {
-  // Q (cols x r, row-major) = (X - mean)^T modes, X column-major rows x cols
+  // Q (cols x r, row-major) = (X - mean)^T modes, X column-major rows x cols; the
+  // centring happens inside the product, so no temporary is allocated
   if (!d_modes || !d_X || !d_Q || rows <= 0 || r <= 0 || cols <= 0) return DJ_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  float* Xc = nullptr;
-  if (cudaMalloc(&Xc, (size_t)rows * cols * sizeof(float)) != cudaSuccess) return DJ_ERR_OOM;
-  cudaError_t e = cudaSuccess;
-  if (d_mean) {
-    center_kernel<<<blocks(rows * (long long)cols, 256), 256, 0, s>>>(d_X, d_mean, rows, cols, Xc);
-    e = cudaGetLastError();
-  } else {
-    e = cudaMemcpyAsync(Xc, d_X, (size_t)rows * cols * sizeof(float), cudaMemcpyDeviceToDevice, s);
-  }
-  if (e == cudaSuccess) e = gemm<double>(cols, r, (int)rows, 1.f, Xc, rows, 1, d_modes, r, 1, 0.f, d_Q, r, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(Xc);
+  cudaError_t e = gemm<double>(cols, r, (int)rows, 1.f, d_X, rows, 1, d_modes, r, 1, 0.f, d_Q, r, s, d_mean);
   return e == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
 }
 

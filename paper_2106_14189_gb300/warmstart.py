@@ -59,6 +59,11 @@ class WarmStart:
         self.n_dof = 3 * problem.n_nodes
         self.mlp = None
         self.dev = torch.device("cuda")
+        self.bc_index = torch.as_tensor(problem.bc_dof, device=self.dev)
+        self.buf_c = torch.empty((1, n_in), device=self.dev)
+        self.buf_q = torch.empty((1, n_out), device=self.dev)
+        self.buf_field = torch.empty(self.n_dof, device=self.dev)
+        self.buf_rest = torch.zeros(self.n_dof, device=self.dev)
 
     # ------------------------------------------------------------ problems --
     def problem_for(self, targets) -> W.Problem:
@@ -73,21 +78,36 @@ class WarmStart:
 
     # --------------------------------------------------------------- data ---
     def solve_batch(self, targets: List[np.ndarray], batch_size: int = 64):
-        """Relax every load case from rest; returns (S x n_dof) device tensor of
-        fields (each row one snapshot) and the step counts."""
+        """Relax every load case from rest.  Returns (S' x n_dof) device tensor of
+        relaxed fields (one row per snapshot), the indices of the load cases that
+        were kept, and the step counts.  A batch whose relaxation fails (an
+        element inverts) is redone case by case and the failing cases are
+        dropped."""
         torch = self.torch
         S = len(targets)
         Y = torch.empty((S, self.n_dof), dtype=torch.float32, device=self.dev)
-        steps = []
+        steps, kept = [], []
         for s0 in range(0, S, batch_size):
             chunk = targets[s0:s0 + batch_size]
-            with B.Batch([self.problem_for(t) for t in chunk], **self.mesh_params()) as bt:
-                st, n, r = bt.relax(self.tol, self.max_steps)
-                for i in range(len(chunk)):
-                    B.dj_batch_get_displacements_device(bt.b, i, Y[s0 + i].data_ptr())
-                bt.sync()
-                steps.append(n)
-        return Y, steps
+            try:
+                with B.Batch([self.problem_for(t) for t in chunk], **self.mesh_params()) as bt:
+                    st, n, r = bt.relax(self.tol, self.max_steps)
+                    for i in range(len(chunk)):
+                        B.dj_batch_get_displacements_device(bt.b, i, Y[len(kept)].data_ptr())
+                        kept.append(s0 + i)
+                    bt.sync()
+                    steps.append(n)
+            except B.DJError:
+                for i, t in enumerate(chunk):
+                    with B.Mesh(self.problem_for(t), **self.mesh_params()) as m:
+                        st, n, r = m.relax(self.tol, self.max_steps, raise_on_fail=False)
+                        if st != 0:
+                            continue
+                        B.dj_get_displacements_device(m.h, Y[len(kept)].data_ptr())
+                        m.sync()
+                        kept.append(s0 + i)
+                        steps.append(n)
+        return Y[:len(kept)], kept, steps
 
     # ---------------------------------------------------------------- fit ---
     def fit(self, T_host: np.ndarray, Y: "torch.Tensor", epochs: int = 400, batch: int = 256,
@@ -148,10 +168,8 @@ class WarmStart:
     def predict(self, targets: np.ndarray) -> "torch.Tensor":
         """Predicted nodal field (n_dof floats on the device) for one load case."""
         torch = self.torch
-        t = torch.tensor(np.asarray(targets, dtype=np.float32), device=self.dev)
-        c = torch.empty((1, self.n_in), device=self.dev)
-        q = torch.empty((1, self.n_out), device=self.dev)
-        out = torch.empty(self.n_dof, device=self.dev)
+        t = torch.as_tensor(np.asarray(targets, dtype=np.float32)).to(self.dev, non_blocking=True)
+        c, q, out = self.buf_c, self.buf_q, self.buf_field
         B.dj_pod_project(self.modes_in.data_ptr(), self.mean_in.data_ptr(), self.n_bc, self.n_in,
                          t.data_ptr(), 1, c.data_ptr())
         B.dj_mlp_forward(self.mlp, c.data_ptr(), 1, q.data_ptr())
@@ -176,9 +194,8 @@ class WarmStart:
         if warm:
             field = self.predict(targets)
             r_warm, inverted = B.dj_evaluate_field(mesh.h, field.data_ptr())
-            bc_only = torch.zeros(self.n_dof, device=self.dev)
-            bc_only[torch.as_tensor(self.p.bc_dof, device=self.dev)] = torch.as_tensor(
-                np.asarray(targets, dtype=np.float32), device=self.dev)
+            bc_only = self.buf_rest
+            bc_only[self.bc_index] = torch.as_tensor(np.asarray(targets, dtype=np.float32)).to(self.dev)
             r_rest, _ = B.dj_evaluate_field(mesh.h, bc_only.data_ptr())
             if inverted or not (r_warm < r_rest):
                 fallback = True

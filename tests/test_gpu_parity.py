@@ -39,7 +39,8 @@ MODELS = [W.NH, W.TI, W.OT, W.MR]
 @pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("renumber,assembly,tile,prec", [(1, 1, 0, 0), (0, 1, 96, 0), (1, 0, 0, 0),
                                                          (0, 0, 0, 0), (1, 1, 512, 0), (1, 1, 32, 0),
-                                                         (1, 1, 0, 1), (1, 0, 0, 1)])
+                                                         (1, 1, 0, 1), (1, 0, 0, 1), (1, 2, 0, 0),
+                                                         (1, 2, 64, 1), (0, 2, 160, 0)])
 def test_tet4_forces_match_oracle(B, model, renumber, assembly, tile, prec):
     # 6 * 7^3 = 2058 elements: several tiles plus a ragged tail
     p = W.random_tet_mesh_problem(2058, seed=11 + model, model=model)
@@ -54,7 +55,7 @@ def test_tet4_forces_match_oracle(B, model, renumber, assembly, tile, prec):
 
 @pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("assembly,tile,prec", [(1, 0, 0), (0, 0, 0), (1, 256, 0), (1, 64, 0),
-                                                (1, 0, 1), (0, 0, 1)])
+                                                (1, 0, 1), (0, 0, 1), (2, 0, 0), (2, 256, 1)])
 def test_hex8_forces_match_oracle(B, model, assembly, tile, prec):
     p = W.random_hex_mesh_problem(9, seed=21 + model, model=model)  # 729 bricks, ragged
     p.hg_coeff = 0.15
@@ -229,6 +230,18 @@ def test_slot_and_tile_assembly_trajectories_agree(B):
         b.run(400)
         Ua, Ub = a.displacements(), b.displacements()
     assert rel_linf(Ub, Ua) < 1e-5
+
+
+@pytest.mark.parametrize("et", [4, 8])
+def test_tma_pipeline_equals_per_tile_blocks(B, et):
+    """Same tiles, same fixed summation order: the persistent bulk-copy pipeline
+    and the one-block-per-tile kernel give bit-identical trajectories."""
+    p = W.cube_shear(et, 9 if et == 4 else 10, n_steps=300)
+    with B.Mesh(p, assembly=1) as a, B.Mesh(p, assembly=2) as b:
+        a.run(300)
+        b.run(300)
+        assert np.array_equal(a.displacements(), b.displacements())
+        b.sync()
 
 
 def test_relaxation_matches_oracle(B):

@@ -110,8 +110,9 @@ def test_warm_start_relaxes_faster_than_rest(env):
     p = W.ellipsoid_tet4(h=6e-3, seed=0, disp_range=(1e-3, 4e-3))
     ws = WarmStart(p, n_in=64, n_out=128, alpha=140.0, ramp_steps=400, tol=1e-5)
     T_train = load_cases(p, range(1000, 1256))
-    Y, steps = ws.solve_batch(list(T_train), batch_size=64)
-    losses = ws.fit(T_train, Y, epochs=300, batch=128)
+    Y, kept, steps = ws.solve_batch(list(T_train), batch_size=64)
+    assert len(kept) == len(T_train)
+    losses = ws.fit(T_train[kept], Y, epochs=300, batch=128)
     assert losses[-1][1] < 0.1 * losses[0][1]
     T_test = load_cases(p, range(5000, 5012))
     cold, warm = [], []
