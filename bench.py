@@ -57,7 +57,7 @@ def algorithmic_bytes(info, n_nodes):
     E = float(info.n_elems)
     ne = info.elem_type
     nE = n_nodes / E
-    if info.assembly == 1:
+    if info.assembly != 0:
         pE = info.n_parts / E
         force = 2 * ne + 4 * info.n_consts + 2 * ne + (4 + 2 + 12) * pE + 16 * nE
         update = (4 + 12) * pE + 64 * nE
@@ -362,7 +362,7 @@ def main():
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": ("element force (" + ("tiles" if minfo.assembly == 1 else "slots") + ")")
+                "kernel": ("element force (" + {0: "slots", 1: "tiles", 2: "tiles, bulk-copy pipeline"}[minfo.assembly] + ")")
                 if dominant == "force" else "node gather-update",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_dom,
@@ -419,6 +419,11 @@ def main():
         t_setup = time.perf_counter() - t_setup
         bt.run(20, stream)
         bt.sync(stream)
+        t_tune = time.perf_counter()
+        B.dj_batch_autotune(bt.b, steps=20, stream=stream)
+        t_tune = time.perf_counter() - t_tune
+        bt.run(20, stream)
+        bt.sync(stream)
         kb = args.batch_steps
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -433,8 +438,9 @@ def main():
                              f"[5k, 150k]: {n_el_b} elements ({n_tet_b} T4, {n_hex_b} H8), "
                              f"{n_nodes_b} nodes, each its own dt = 0.9 dt_crit",
                  "value": n_el_b * kb / (msb * 1e-3), "unit": "element-updates/s",
-                 "ms_per_step": msb / kb, "steps": kb, "setup_s": t_setup,
-                 "schedule": "two kernel chains (T4 part, H8 part) in one CUDA graph"}
+                 "ms_per_step": msb / kb, "steps": kb, "setup_s": t_setup, "autotune_s": t_tune,
+                 "schedule": "two kernel chains (T4 part, H8 part) in one CUDA graph, "
+                             "schedules chosen by dj_batch_autotune"}
         bt.close()
 
     cpu = None
@@ -452,7 +458,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": desc, "elements": E, "nodes": N,
                            "parallelism": f"replicas x{world}",
-                           "assembly": "tiles" if minfo.assembly == 1 else "slots",
+                           "assembly": {0: "slots", 1: "tiles", 2: "tiles, bulk-copy pipeline"}[minfo.assembly],
                            "tile_size": minfo.tile_size,
                            "l2": "working set ~215 MB > 129 MB L2 (no flush needed)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

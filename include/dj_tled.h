@@ -202,14 +202,24 @@ dj_status dj_run_n(dj_mesh* mesh, long long n, void* stream);
 dj_status dj_run_n_profiled(dj_mesh* mesh, long long n, void* stream, double* ms_force,
                             double* ms_update);
 
+/* Autotuner: time `steps` steps of each schedule -- assembly (slots, tiles,
+ * tiles with the bulk-copy pipeline) x tile size (64 ... 512) -- on this mesh
+ * from its current state, keep the fastest, and restore the state (so the
+ * trajectory continues unchanged).  chosen (optional) receives the parameters
+ * in use afterwards, ms_per_step (optional) their time per step.
+ * Synchronous; re-runs dj_precompute for every candidate. */
+dj_status dj_autotune(dj_mesh* mesh, int steps, void* stream, dj_params* chosen, double* ms_per_step);
+
 /* Wait for `stream` and report device-side errors of earlier steps
  * (DJ_ERR_INVERTED_ELEMENT / DJ_ERR_NONFINITE). */
 dj_status dj_sync(dj_mesh* mesh, void* stream);
 
 /* Dynamic relaxation (Sec. 6): step with the current damping until the
  * residual r = ||F - R||_free / ||F - R||_prescribed (FP64, every
- * relax_check_every steps) is <= tol, or max_steps steps were taken.  On
- * success the state is one step past the checked one.  Synchronous.
+ * relax_check_every steps) is <= tol, or max_steps steps were taken.  A checked
+ * state counts only once its step index is >= ramp_steps (prescribed values at
+ * their targets).  On success the state is one step past the checked one.
+ * Synchronous.
  *   steps_out, residual_out  optional
  * Errors: DJ_ERR_NOT_CONVERGED, DJ_ERR_INVERTED_ELEMENT, DJ_ERR_NONFINITE. */
 dj_status dj_relax_to_tol(dj_mesh* mesh, double tol, long long max_steps, long long* steps_out,
@@ -303,6 +313,8 @@ dj_status dj_batch_get_displacements_device(dj_batch* batch, int i, float* d_U_o
 dj_status dj_batch_set_displacements(dj_batch* batch, int i, const double* U0);
 dj_status dj_batch_get_info(const dj_batch* batch, int* n_instances, long long* n_nodes,
                             long long* n_elems, long long* n_tet_elems, long long* n_hex_elems);
+/* dj_autotune of each part (T4 instances, H8 instances) of the batch. */
+dj_status dj_batch_autotune(dj_batch* batch, int steps, void* stream);
 const char* dj_batch_last_error(const dj_batch* batch);
 void dj_batch_destroy(dj_batch* batch);
 

@@ -35,9 +35,11 @@ Readings (the paper is silent on these):
   ||F - R|| over prescribed DOFs (the reaction), or the numerator alone when
   the reaction is zero.
 * relaxation (Sec. 6 names dynamic relaxation only): the same damped step,
-  checked every k steps on the force of the current state; on success the
-  update of that step is kept, so the returned state is one step past the
-  checked one.
+  checked every k steps on the force of the current state; a checked state
+  counts only once its prescribed values have reached their targets (step
+  index >= ramp_steps), since a slow ramp is quasi-static and has small
+  residuals on the way; on success the update of that step is kept, so the
+  returned state is one step past the checked one.
 """
 import numpy as np
 
@@ -192,10 +194,12 @@ class ExplicitSolver:
     def relax(self, tol, max_steps, check_every=100):
         r = np.inf
         for i in range(int(max_steps)):
+            n = self.n  # index of the state whose force is evaluated in this step
             check = (i + 1) % check_every == 0
             F = self.step(return_force=True)
             if check:
                 r = self.residual(F)
-                if r <= tol:
+                # a state counts only once its prescribed values are at the targets
+                if r <= tol and n >= self.ramp_steps:
                     return i + 1, r, True
         return int(max_steps), r, False

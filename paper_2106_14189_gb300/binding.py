@@ -38,7 +38,8 @@ EXPORTS = [
     "dj_mlp_create", "dj_mlp_num_params", "dj_mlp_get_params", "dj_mlp_set_params",
     "dj_mlp_get_grads", "dj_mlp_forward", "dj_mlp_loss_grad", "dj_mlp_adam_step",
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
-    "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step",
+    "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
+    "dj_batch_autotune",
 ]
 
 
@@ -139,6 +140,8 @@ def lib():
         "dj_residual_norms_static": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
         "dj_set_step": (C.c_int, [_P, C.c_longlong]),
         "dj_batch_set_step": (C.c_int, [_P, C.c_longlong]),
+        "dj_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(dj_params), _D]),
+        "dj_batch_autotune": (C.c_int, [_P, C.c_int, _P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -403,6 +406,17 @@ def dj_batch_destroy(b):
 
 def dj_set_displacements_device(h, d_ptr, stream=None):
     _check(lib().dj_set_displacements_device(h, d_ptr, _stream(stream)), "dj_set_displacements_device", h)
+
+
+def dj_autotune(h, steps=200, stream=None):
+    p = dj_params()
+    ms = C.c_double(0)
+    _check(lib().dj_autotune(h, int(steps), _stream(stream), C.byref(p), C.byref(ms)), "dj_autotune", h)
+    return p, ms.value
+
+
+def dj_batch_autotune(b, steps=100, stream=None):
+    _bcheck(lib().dj_batch_autotune(b, int(steps), _stream(stream)), "dj_batch_autotune", b)
 
 
 def dj_set_step(h, step):

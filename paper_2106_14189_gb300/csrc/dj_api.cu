@@ -1188,7 +1188,10 @@ dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long
       const double num = std::sqrt(m->h_state->resid_num2), den = std::sqrt(m->h_state->resid_den2);
       r = den > 0 ? num / den : num;
     }
-    if (r <= tol) {
+    // the checked state is the one before the last step; it counts only once its
+    // prescribed values are at their targets
+    const long long checked = m->h_state->step - 1;
+    if (r <= tol && (m->params.ramp_steps <= 0 || checked >= m->params.ramp_steps)) {
       if (steps_out) *steps_out = done;
       if (residual_out) *residual_out = r;
       return DJ_OK;
@@ -1463,6 +1466,62 @@ dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
   return DJ_OK;
 }
 
+dj_status dj_autotune(dj_mesh* m, int steps, void* stream, dj_params* chosen, double* ms_per_step) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (steps <= 0) return fail(m, DJ_ERR_INVALID_ARG, "steps <= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t bytes = 0;
+  dj_state_size(m, &bytes);
+  std::vector<char> blob(bytes);
+  s = dj_get_state(m, blob.data(), bytes);
+  if (s) return s;
+  const dj_params base = m->params;
+  struct Cand {
+    int assembly, tile;
+  };
+  std::vector<Cand> cands = {{ASSEMBLY_SLOTS, 0}};
+  const int tiles4[] = {64, 128, 256, 512}, tiles8[] = {64, 128, 256};
+  if (m->ne == 4)
+    for (int T : tiles4) cands.push_back({ASSEMBLY_TILES, T});
+  else
+    for (int T : tiles8) cands.push_back({ASSEMBLY_TILES, T});
+  for (int T : {64, 128, 256}) cands.push_back({ASSEMBLY_TILES_TMA, T});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = INFINITY;
+  dj_params best_p = base;
+  for (const Cand& c : cands) {
+    dj_params p = base;
+    p.assembly = c.assembly;
+    p.tile_size = c.tile;
+    if (dj_precompute(m, &p, nullptr) != DJ_OK) continue;  // e.g. a tile too large for shared memory
+    if (dj_set_state(m, blob.data(), bytes) != DJ_OK) continue;
+    if (dj_run_n(m, 8, stream) != DJ_OK) continue;  // graph capture and warm-up
+    if (cudaEventRecord(e0, st) != cudaSuccess) break;
+    if (dj_run_n(m, steps, stream) != DJ_OK) continue;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
+    if (read_state(m, st) != DJ_OK || check_flags(m) != DJ_OK) continue;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_p = p;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s = dj_precompute(m, &best_p, nullptr);
+  if (s) return s;
+  s = dj_set_state(m, blob.data(), bytes);
+  if (s) return s;
+  if (!std::isfinite(best)) return fail(m, DJ_ERR_CUDA, "no schedule could be timed");
+  if (chosen) *chosen = best_p;
+  if (ms_per_step) *ms_per_step = best / steps;
+  return DJ_OK;
+}
+
 dj_status dj_get_group_info(const dj_mesh* mc, int* n_groups, double* dt, double* dt_crit,
                             double* residual) {
   dj_mesh* m = const_cast<dj_mesh*>(mc);
@@ -1734,7 +1793,8 @@ dj_status dj_batch_relax_to_tol(dj_batch* b, double tol, long long max_steps, lo
         r = std::max(r, m->group_r[g]);
       }
     }
-    if (r <= tol) {
+    const long long checked = any->h_state->step - 1;
+    if (r <= tol && (any->params.ramp_steps <= 0 || checked >= any->params.ramp_steps)) {
       if (steps_out) *steps_out = done;
       if (residual_out) *residual_out = r;
       return DJ_OK;
@@ -1844,6 +1904,18 @@ dj_status dj_batch_get_info(const dj_batch* b, int* n_instances, long long* n_no
   if (n_elems) *n_elems = ne;
   if (n_tet_elems) *n_tet_elems = nt;
   if (n_hex_elems) *n_hex_elems = nh;
+  return DJ_OK;
+}
+
+dj_status dj_batch_autotune(dj_batch* b, int steps, void* stream) {
+  if (!b) return DJ_ERR_INVALID_ARG;
+  if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
+  batch_release_graphs(b);
+  for (int pt = 0; pt < 2; ++pt)
+    if (b->part[pt]) {
+      dj_status s = dj_autotune(b->part[pt], steps, stream, nullptr, nullptr);
+      if (s) return bfail(b, s, b->part[pt]->last_error.c_str());
+    }
   return DJ_OK;
 }
 

@@ -121,8 +121,7 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
   const float D = det3(tJ);
   const float J = D * k.r0;  // Eq. 12
   bad = !(D > 0.f);
-  const float rc = rcbrtf(J);
-  const float Jm23 = rc * rc;  // J^-2/3
+  const float Jm23 = __powf(J, -2.f / 3.f);  // J^-2/3 (fast exp2/log2 intrinsics, ~1e-7 relative)
   // g = tJ tJ^T (Eq. 17), symmetric
   float g[6];
   g[0] = tJ.m[0][0] * tJ.m[0][0] + tJ.m[0][1] * tJ.m[0][1] + tJ.m[0][2] * tJ.m[0][2];
@@ -180,7 +179,7 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
     mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
   }
   const M3 A = adj3(tJ);
-  const float invD = 1.f / D;
+  const float invD = __fdividef(1.f, D);
   const float ca = (Jm23 * vol_over_D + mr_vol) * invD + k.kV * (J - 1.f) * k.r0;
   M3 F;
 #pragma unroll
@@ -281,8 +280,8 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
   const float jm1 = dD * k.r0;  // J - 1
   const float J = 1.f + jm1;
   bad = !(J > 0.f);
-  const float D = 1.f / k.r0 + dD;
-  const float invD = 1.f / D;
+  const float D = __fdividef(1.f, k.r0) + dD;
+  const float invD = __fdividef(1.f, D);
   const float lJ = log1pf(jm1);
   const float Jm23 = expf(-2.f / 3.f * lJ);
   const float Jm23m1 = expm1f(-2.f / 3.f * lJ);
@@ -491,12 +490,13 @@ __device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemC
     hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
 }
 
+// a NaN or Inf in any force propagates into the sum (Inf - Inf = NaN)
 template <int NE>
 __device__ __forceinline__ bool all_finite(const float (&f)[NE][3]) {
-  bool ok = true;
+  float s = 0.f;
 #pragma unroll
-  for (int b = 0; b < NE; ++b) ok &= finite3(f[b][0], f[b][1], f[b][2]);
-  return ok;
+  for (int b = 0; b < NE; ++b) s += f[b][0] + f[b][1] + f[b][2];
+  return isfinite(s);
 }
 
 // d_b = u_b - u_0 from the nodal records (hi, lo)

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
   const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
   float4* su = smem4;                                          // staged U (high part)
   float4* sl = smem4 + t.cap;                                  // staged low part (compensated)
-  float* sf = reinterpret_cast<float*>(smem4 + (CMP ? 2 : 1) * t.cap);  // 3 x (NE T) forces
+  float4* sf4 = smem4 + (CMP ? 2 : 1) * t.cap;  // NE T force records (slot a T + e)
   const int base = __ldg(t.tile_ptr + tile);
   const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
   const int e = tile * T + tid;
@@ -122,26 +122,21 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
     bool inv;
     elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
     flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
-    const int S = NE * T;
 #pragma unroll
-    for (int b = 0; b < NE; ++b) {
-      sf[b * T + tid] = f[b][0];
-      sf[S + b * T + tid] = f[b][1];
-      sf[2 * S + b * T + tid] = f[b][2];
-    }
+    for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
   }
   __syncthreads();
-  const int S = NE * T;
+  const int S = NE * T;  // slots per tile
   const unsigned short* lp = t.lptr + (size_t)tile * (t.cap + 8);
   const unsigned short* li = t.lidx + (size_t)tile * S;
   for (int q = tid; q < n_t; q += T) {
     const int p0 = lp[q], p1 = lp[q + 1];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     for (int p = p0; p < p1; ++p) {
-      const int l = li[p];
-      fx += sf[l];
-      fy += sf[S + l];
-      fz += sf[2 * S + l];
+      const float4 v = sf4[li[p]];
+      fx += v.x;
+      fy += v.y;
+      fz += v.z;
     }
     t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
   }
@@ -324,8 +319,7 @@ cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t smem = (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) +
-                      (size_t)3 * NE * t.T * sizeof(float);
+  const size_t smem = (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4);
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR, CMP>,

@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   const uint32_t stage_bytes = (L.bytes + 127) & ~127u;
   float4* su = reinterpret_cast<float4*>(smem + 2 * stage_bytes);
   float4* sl = su + t.cap;
-  float* sf = reinterpret_cast<float*>(su + (CMP ? 2 : 1) * t.cap);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sf + 3 * NE * T);  // 8-byte aligned: sizes are multiples of 16
+  float4* sf4 = su + (CMP ? 2 : 1) * t.cap;  // NE T force records (slot a T + e)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sf4 + NE * T);
   advance_clock(a);
   if (tid == 0) {
     mbar_init(&bars[0], 1);
@@ -155,24 +155,18 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       bool inv;
       elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
       flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
-      const int S = NE * T;
 #pragma unroll
-      for (int b = 0; b < NE; ++b) {
-        sf[b * T + tid] = f[b][0];
-        sf[S + b * T + tid] = f[b][1];
-        sf[2 * S + b * T + tid] = f[b][2];
-      }
+      for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
     }
     __syncthreads();
-    const int S = NE * T;
     for (int q = tid; q < n_t; q += T) {
       const int p0 = lptr[q], p1 = lptr[q + 1];
       float fx = 0.f, fy = 0.f, fz = 0.f;
       for (int p = p0; p < p1; ++p) {
-        const int l = lidx[p];
-        fx += sf[l];
-        fy += sf[S + l];
-        fz += sf[2 * S + l];
+        const float4 v = sf4[lidx[p]];
+        fx += v.x;
+        fy += v.y;
+        fz += v.z;
       }
       t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
     }
@@ -184,7 +178,7 @@ template <int NE, bool CMP>
 size_t smem_bytes_t(const TileArgs& t) {
   const StageLayout<NE> L(t);
   const size_t stage = (L.bytes + 127) & ~size_t(127);
-  return 2 * stage + (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)3 * NE * t.T * sizeof(float) + 16;
+  return 2 * stage + (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) + 16;
 }
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>

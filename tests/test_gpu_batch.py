@@ -116,3 +116,32 @@ def test_grouped_mesh_has_per_group_steps(B):
         assert np.allclose(dt, 0.9 * dtc)
     finally:
         B.dj_mesh_destroy(h)
+
+
+def test_autotune_keeps_the_trajectory(B):
+    """The autotuner times every schedule from the current state, keeps the
+    fastest and restores the state: stepping on afterwards matches a mesh built
+    with the chosen schedule from the start."""
+    p = W.cube_shear(W.TET4, 12, n_steps=400)
+    with B.Mesh(p) as m:
+        m.run(200)
+        chosen, ms = B.dj_autotune(m.h, steps=50)
+        assert ms > 0 and chosen.assembly in (0, 1, 2)
+        assert B.dj_get_info(m.h).step == 200
+        m.run(200)
+        U = m.displacements()
+    with B.Mesh(p, assembly=chosen.assembly, tile_size=chosen.tile_size) as r:
+        r.run(400)
+        assert rel_linf(U, r.displacements()) < 1e-5
+
+
+def test_batch_autotune(B):
+    probs = small_batch(4, seed=7, steps=200)
+    with B.Batch(probs) as bt:
+        bt.run(100)
+        B.dj_batch_autotune(bt.b, steps=20)
+        bt.run(100)
+        bt.sync()
+        for i, p in enumerate(probs):
+            ref = dynamics.ExplicitSolver.from_problem(p).run(200)
+            assert rel_linf(bt.displacements(i), ref) < DISP_TOL
