@@ -71,14 +71,37 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
 // Tiled assembly: block = tile of T elements.  The tile's unique nodes are
 // staged in shared memory, element forces go to shared memory (slot a * T + e),
 // and each unique node sums its slots in the fixed order of the local index.
+// T4 neo-Hookean / transversely isotropic FP32 variants are held to 40
+// registers (3 blocks of 512 or 6 of 256 per SM): the kernel is latency-bound
+// and the extra resident warps outweigh a few spilled words.
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
-__global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceArgs a, TileArgs t) {
+constexpr int tiles_min_blocks() { return (NE == 4 && !CMP && !FB && !MR) ? 3 : 1; }
+
+template <int NE, bool FA, bool FB, bool MR, bool CMP>
+__global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA, FB, MR, CMP>()))
+    force_tiles_kernel(ForceArgs a, TileArgs t) {
   extern __shared__ float4 smem4[];
   advance_clock(a);
   const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
-  float4* su = smem4;                                          // staged U (high part)
-  float4* sl = smem4 + t.cap;                                  // staged low part (compensated)
-  float4* sf4 = smem4 + (CMP ? 2 : 1) * t.cap;  // NE T force records (slot a T + e)
+  const int S = NE * T;  // slots per tile
+  float4* su = smem4;                            // staged U (high part)
+  float4* sl = smem4 + t.cap;                    // staged low part (compensated)
+  float4* sf4 = smem4 + (CMP ? 2 : 1) * t.cap;   // S force records (slot a T + e)
+  // the tile's reduction lists, staged with the inputs so that their latency
+  // overlaps the node gather instead of following the element math
+  unsigned short* sidx = reinterpret_cast<unsigned short*>(sf4 + S);  // S local slot ids
+  unsigned short* sptr = sidx + S;                                     // cap + 8 list offsets
+  {
+    const uint4* gi = reinterpret_cast<const uint4*>(t.lidx + (size_t)tile * S);
+    const uint4* gp = reinterpret_cast<const uint4*>(t.lptr + (size_t)tile * (t.cap + 8));
+    uint4* di = reinterpret_cast<uint4*>(sidx);
+    uint4* dp = reinterpret_cast<uint4*>(sptr);
+    const int ni = S / 8, np = (t.cap + 8) / 8;
+    for (int q = tid; q < ni + np; q += T) {
+      if (q < ni) di[q] = __ldcs(gi + q);
+      else dp[q - ni] = __ldcs(gp + (q - ni));
+    }
+  }
   const int base = __ldg(t.tile_ptr + tile);
   const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
   const int e = tile * T + tid;
@@ -126,9 +149,8 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256) force_tiles_kernel(ForceA
     for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
   }
   __syncthreads();
-  const int S = NE * T;  // slots per tile
-  const unsigned short* lp = t.lptr + (size_t)tile * (t.cap + 8);
-  const unsigned short* li = t.lidx + (size_t)tile * S;
+  const unsigned short* lp = sptr;
+  const unsigned short* li = sidx;
   for (int q = tid; q < n_t; q += T) {
     const int p0 = lp[q], p1 = lp[q + 1];
     float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -319,7 +341,8 @@ cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t smem = (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4);
+  const size_t smem = (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) +
+                      (size_t)NE * t.T * 2 + (size_t)(t.cap + 8) * 2;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR, CMP>,

@@ -13,7 +13,7 @@ only as future work, Sec. 8).  Everything numerical runs in the CUDA library:
   dj_mlp_forward.
 
 A relaxation from the predicted field uses plain DJ-TLED relaxation both as
-fallback and as judge: if the predicted field inverts an element or has a
+fallback and as arbiter: if the predicted field inverts an element or has a
 larger residual than the prescribed-values-only field, the solve restarts from
 rest; the result is always a relaxation of the method to the same tolerance.
 Torch provides device buffers and a few one-time tensor operations of the
@@ -40,6 +40,7 @@ class RelaxResult:
     warm: bool
     fallback: bool
     status: int
+    predict_seconds: float = 0.0
 
 
 class WarmStart:
@@ -202,13 +203,17 @@ class WarmStart:
             else:
                 B.dj_set_displacements_device(mesh.h, field.data_ptr())
                 B.dj_set_step(mesh.h, self.ramp_steps)
+        t_pred = 0.0
+        if warm:
+            torch.cuda.synchronize()
+            t_pred = time.perf_counter() - t0
         st, n, r = mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         if own:
             mesh.close()
         return RelaxResult(steps=n, residual=r, seconds=sec, warm=warm and not fallback,
-                           fallback=fallback, status=st)
+                           fallback=fallback, status=st, predict_seconds=t_pred)
 
     def close(self):
         if self.mlp is not None:
