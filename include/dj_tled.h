@@ -225,8 +225,9 @@ dj_status dj_sync(dj_mesh* mesh, void* stream);
 dj_status dj_relax_to_tol(dj_mesh* mesh, double tol, long long max_steps, long long* steps_out,
                           double* residual_out, void* stream);
 
-/* Warm start: U^0 = U^-1 = U0 (host, n_nodes * 3 doubles); step counter kept.
- * Synchronous. */
+/* Warm start: U^0 = U^-1 = U0 (host, n_nodes * 3 doubles); step counter kept;
+ * the error record (inverted / non-finite flags) is cleared, since the field
+ * starts a new trajectory.  Synchronous. */
 dj_status dj_set_displacements(dj_mesh* mesh, const double* U0);
 
 /* Current displacements U^n, host n_nodes * 3 doubles.  Synchronizes the
@@ -243,7 +244,8 @@ dj_status dj_get_displacements_device(dj_mesh* mesh, float* d_U_out, void* strea
 dj_status dj_set_step(dj_mesh* mesh, long long step);
 
 /* Warm start from device memory: U^0 = U^-1 = d_U0 (n_nodes * 3 floats, caller
- * order); enqueued on `stream`; compensated low parts are reset to 0. */
+ * order); enqueued on `stream`; compensated low parts are reset to 0 and the
+ * error record is cleared as in dj_set_displacements. */
 dj_status dj_set_displacements_device(dj_mesh* mesh, const float* d_U0, void* stream);
 
 /* Evaluate a candidate field d_U (device, n_nodes * 3 floats, caller order)

@@ -91,6 +91,8 @@ struct dj_mesh {
   unsigned short* d_lconn = nullptr;
   unsigned short* d_lptr = nullptr;
   unsigned short* d_lidx = nullptr;
+  float4* d_xloc = nullptr;  // geometric T4 table: tile-local reference coordinates
+  int geometric = 0;
   float4* d_parts = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t run_exec = nullptr;
@@ -147,13 +149,14 @@ void release_device(dj_mesh* m) {
   m->run_chunk = m->relax_k = 0;
   void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
-                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_save,
+                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_save,
                   m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
                   m->d_group_node_ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_tile_ptr = m->d_tile_nodes = nullptr;
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
+  m->d_xloc = nullptr;
   m->d_parts = nullptr;
   m->d_Ulo = nullptr;
   m->d_save = nullptr;
@@ -245,6 +248,14 @@ dj_status check_flags(dj_mesh* m) {
   return DJ_OK;
 }
 
+// A new displacement field starts a new trajectory: its error record starts
+// empty (err_flags = 0, bad_elem above every element id).
+cudaError_t clear_error_flags(dj_mesh* m, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&m->d_state->err_flags, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&m->d_state->bad_elem, 0x7f, sizeof(int), s);
+  return e;
+}
+
 // Sliced ELL (chunks of SELL_C rows, column-major, -1 padding) of CSR lists.
 void build_sell(const std::vector<int>& ptr, const std::vector<int>& idx, long long N,
                 std::vector<int>& chunk_ptr, std::vector<int>& sell) {
@@ -289,6 +300,7 @@ TileArgs tile_args(dj_mesh* m) {
   t.lconn = m->d_lconn;
   t.lptr = m->d_lptr;
   t.lidx = m->d_lidx;
+  t.xloc = m->d_xloc;
   t.partials = m->d_parts;
   t.T = m->T;
   t.cap = m->cap;
@@ -627,7 +639,9 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   } else {
     m->variant = VAR_NH;
   }
-  int nc = K_COMMON;
+  // tiled T4 meshes rebuild 0J, det 0J and P from staged reference coordinates
+  m->geometric = ne == 4 && prm.assembly != ASSEMBLY_SLOTS;
+  int nc = m->geometric ? KG_COMMON : K_COMMON;
   m->off_fa = m->off_fb = m->off_mr = m->off_hg = -1;
   if (fa) { m->off_fa = nc; nc += 7; }
   if (fb) { m->off_fb = nc; nc += 7; }
@@ -646,6 +660,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   build_sell(cnt, csr, N, chunk_ptr, sell);  // node -> element slots (lumped mass, slot assembly)
   m->assembly = prm.assembly;
   std::vector<int> tile_ptr, tile_nodes, tnodes_pad, part_chunk_ptr, part_sell;
+  std::vector<float4> xloc_pad;
   std::vector<unsigned short> lconn, lptr, lidx;
   if (m->assembly != ASSEMBLY_SLOTS) {
     const int T = prm.tile_size > 0 ? prm.tile_size : (ne == 4 ? 256 : 128);
@@ -693,6 +708,19 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     for (int t = 0; t < m->n_tiles; ++t) {
       std::copy(tile_loc[t].begin(), tile_loc[t].end(), tnodes_pad.begin() + (size_t)t * m->cap);
       std::copy(tile_lptr[t].begin(), tile_lptr[t].end(), lptr.begin() + (size_t)t * (m->cap + 8));
+    }
+    if (m->geometric) {
+      // reference coordinates relative to the tile's first node, formed in FP64
+      // and rounded once, so that FP32 differences keep the element's scale
+      xloc_pad.assign((size_t)m->n_tiles * m->cap, make_float4(0.f, 0.f, 0.f, 0.f));
+      for (int t = 0; t < m->n_tiles; ++t) {
+        const double* x0 = &Xn[3 * (size_t)tile_loc[t][0]];
+        for (size_t q = 0; q < tile_loc[t].size(); ++q) {
+          const double* x = &Xn[3 * (size_t)tile_loc[t][q]];
+          xloc_pad[(size_t)t * m->cap + q] =
+              make_float4((float)(x[0] - x0[0]), (float)(x[1] - x0[1]), (float)(x[2] - x0[2]), 0.f);
+        }
+      }
     }
     // node -> partial ids, ascending tile
     std::vector<int> pc(N + 1, 0);
@@ -755,6 +783,10 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     CK(cudaMemcpy(m->d_lptr, lptr.data(), lptr.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
     CK(dalloc(m, &m->d_lidx, lidx.size()));
     CK(cudaMemcpy(m->d_lidx, lidx.data(), lidx.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
+    if (m->geometric) {
+      CK(dalloc(m, &m->d_xloc, xloc_pad.size()));
+      CK(cudaMemcpy(m->d_xloc, xloc_pad.data(), xloc_pad.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
     CK(dalloc(m, &m->d_parts, (size_t)m->n_parts));
     CK(cudaMemset(m->d_parts, 0, (size_t)m->n_parts * sizeof(float4)));
     CK(dalloc(m, &m->d_sell, part_sell.size() + 1));
@@ -903,6 +935,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     pa.hg_coeff = prm.hg_coeff;
     pa.tile_T = m->assembly != ASSEMBLY_SLOTS ? m->T : 0;
     pa.n_consts = nc;
+    pa.geometric = m->geometric;
     CKP(launch_precompute_elements(pa, 0));
     int bad = 0;
     CKP(cudaMemcpy(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1226,6 +1259,8 @@ dj_status dj_set_displacements(dj_mesh* m, const double* U0) {
   CK(cudaMemcpy(m->d_U, U.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   if (m->cmp) CK(cudaMemcpy(m->d_Ulo, L.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(m->d_V, V.data(), N * sizeof(float4), cudaMemcpyHostToDevice));
+  CK(clear_error_flags(m, 0));
+  CK(cudaDeviceSynchronize());
   return DJ_OK;
 }
 
@@ -1271,6 +1306,7 @@ dj_status dj_set_displacements_device(dj_mesh* m, const float* d_U0, void* strea
   if (s) return s;
   if (!d_U0) return fail(m, DJ_ERR_INVALID_ARG, "null field");
   CK(launch_from_caller_order(d_U0, m->d_perm, (int)m->N, m->d_U, m->d_V, m->d_Ulo, (cudaStream_t)stream));
+  CK(clear_error_flags(m, (cudaStream_t)stream));
   return DJ_OK;
 }
 

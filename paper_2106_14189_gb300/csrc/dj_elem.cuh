@@ -98,6 +98,50 @@ struct ElemConsts {
     }
     if (MR) gm = ld(a.off_mr);
   }
+
+  // geometric T4 table (KG_*): the stored scalars first, then geometry()
+  float cP;
+  template <class Ld>
+  __device__ __forceinline__ void load_geometric(Ld ld, const ForceArgs& a) {
+    cP = ld(KG_CP);
+    kV = ld(KG_KV);
+    if (FA) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Qa[q] = ld(a.off_fa + q);
+      sa = ld(a.off_fa + 6);
+    }
+    if (FB) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) Qb[q] = ld(a.off_fb + q);
+      sb = ld(a.off_fb + 6);
+    }
+    if (MR) gm = ld(a.off_mr);
+  }
+
+  // xd[i] = X_{i+1} - X_0 (tile-local reference coordinates) is 0J (Eq. 3);
+  // det 0J, r0 and P = c_P adj(0J)^T adj(0J) (Eq. 37) follow
+  __device__ __forceinline__ void geometry(const float (&xd)[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) J0[i][j] = xd[i][j];
+    float ad[3][3];  // adj(0J): 0J adj(0J) = det I
+    ad[0][0] = J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1];
+    ad[0][1] = J0[0][2] * J0[2][1] - J0[0][1] * J0[2][2];
+    ad[0][2] = J0[0][1] * J0[1][2] - J0[0][2] * J0[1][1];
+    ad[1][0] = J0[1][2] * J0[2][0] - J0[1][0] * J0[2][2];
+    ad[1][1] = J0[0][0] * J0[2][2] - J0[0][2] * J0[2][0];
+    ad[1][2] = J0[0][2] * J0[1][0] - J0[0][0] * J0[1][2];
+    ad[2][0] = J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0];
+    ad[2][1] = J0[0][1] * J0[2][0] - J0[0][0] * J0[2][1];
+    ad[2][2] = J0[0][0] * J0[1][1] - J0[0][1] * J0[1][0];
+    const float det = J0[0][0] * ad[0][0] + J0[0][1] * ad[1][0] + J0[0][2] * ad[2][0];
+    r0 = __frcp_rn(det);
+    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      P[q] = cP * (ad[0][ii[q]] * ad[0][jj[q]] + ad[1][ii[q]] * ad[1][jj[q]] + ad[2][ii[q]] * ad[2][jj[q]]);
+  }
 };
 
 // Hourglass constants of a brick: c_{alpha j} = h_alpha . X_j and k.

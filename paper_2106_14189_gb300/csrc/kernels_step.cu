@@ -84,9 +84,12 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   advance_clock(a);
   const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
   const int S = NE * T;  // slots per tile
+  constexpr bool GEO = NE == 4;                  // geometric T4 table, 0J from staged coordinates
+  constexpr int NSTAGE = 1 + (CMP ? 1 : 0) + (GEO ? 1 : 0);
   float4* su = smem4;                            // staged U (high part)
   float4* sl = smem4 + t.cap;                    // staged low part (compensated)
-  float4* sf4 = smem4 + (CMP ? 2 : 1) * t.cap;   // S force records (slot a T + e)
+  float4* sx = smem4 + (NSTAGE - 1) * t.cap;     // staged tile-local reference coordinates (T4)
+  float4* sf4 = smem4 + NSTAGE * t.cap;          // S force records (slot a T + e)
   // the tile's reduction lists, staged with the inputs so that their latency
   // overlaps the node gather instead of following the element math
   unsigned short* sidx = reinterpret_cast<unsigned short*>(sf4 + S);  // S local slot ids
@@ -114,7 +117,8 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
     // tile-major table: row r of element (tile, tid) at ((tile n_consts) + r) T + tid
     const float* ct = c + (size_t)tile * t.n_consts * T + tid;
     const auto ld = [&](int r) { return __ldcs(ct + (size_t)r * T); };
-    k.load(ld, a);
+    if constexpr (GEO) k.load_geometric(ld, a);
+    else k.load(ld, a);
     if constexpr (NE == 8) x.load(ld, a.off_hg);
     if constexpr (NE == 4) {
       const ushort4 v = __ldcs(reinterpret_cast<const ushort4*>(t.lconn) + e);
@@ -128,11 +132,24 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   }
   for (int q = tid; q < n_t; q += T) {
     const int gid = __ldg(t.tnodes + (size_t)tile * t.cap + q);
+    if (GEO) sx[q] = __ldcs(t.xloc + (size_t)tile * t.cap + q);
     su[q] = __ldg(a.U + gid);
     if (CMP) sl[q] = __ldg(a.Ulo + gid);
   }
   __syncthreads();
   if (valid) {
+    if constexpr (GEO) {
+      const float4 x0 = sx[lc[0]];
+      float xd[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float4 xi = sx[lc[i + 1]];
+        xd[i][0] = xi.x - x0.x;
+        xd[i][1] = xi.y - x0.y;
+        xd[i][2] = xi.z - x0.z;
+      }
+      k.geometry(xd);
+    }
     float4 h[NE], l[NE];
 #pragma unroll
     for (int b = 0; b < NE; ++b) {
@@ -341,7 +358,8 @@ cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t smem = (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) +
+  const size_t nstage = 1 + (CMP ? 1 : 0) + (NE == 4 ? 1 : 0);
+  const size_t smem = nstage * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) +
                       (size_t)NE * t.T * 2 + (size_t)(t.cap + 8) * 2;
   static bool attr_set = false;
   if (!attr_set) {

@@ -63,9 +63,10 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 
 template <int NE>
 struct StageLayout {
-  uint32_t tab, lconn, lidx, tnodes, lptr, bytes;  // byte offsets inside a stage
+  uint32_t xloc, tab, lconn, lidx, tnodes, lptr, bytes;  // byte offsets inside a stage
   __device__ __host__ StageLayout(const TileArgs& t) {
-    tab = 0;
+    xloc = 0;  // T4 only: tile-local reference coordinates (geometric table)
+    tab = xloc + (NE == 4 ? (uint32_t)t.cap * 16 : 0u);
     lconn = tab + (uint32_t)t.n_consts * t.T * 4;
     lidx = lconn + (uint32_t)t.T * NE * 2;
     tnodes = lidx + (uint32_t)t.T * NE * 2;
@@ -80,6 +81,7 @@ __device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t
                                            char* stage, uint64_t* bar, int tile) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_arrive_expect_tx(bar, L.bytes);
+  if (NE == 4) bulk_copy(stage + L.xloc, t.xloc + (size_t)tile * t.cap, L.tab - L.xloc, bar);
   bulk_copy(stage + L.tab, a.consts + (size_t)tile * t.n_consts * t.T, L.lconn - L.tab, bar);
   bulk_copy(stage + L.lconn, t.lconn + (size_t)tile * t.T * NE, L.lidx - L.lconn, bar);
   bulk_copy(stage + L.lidx, t.lidx + (size_t)tile * t.T * NE, L.tnodes - L.lidx, bar);
@@ -122,6 +124,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       return;
     }
     const char* st = smem + s * stage_bytes;
+    const float4* sx = reinterpret_cast<const float4*>(st + L.xloc);
     const float* tab = reinterpret_cast<const float*>(st + L.tab);
     const unsigned short* lconn = reinterpret_cast<const unsigned short*>(st + L.lconn);
     const unsigned short* lidx = reinterpret_cast<const unsigned short*>(st + L.lidx);
@@ -139,15 +142,31 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     if (e < a.E) {
       const auto ld = [&](int r) { return tab[r * T + tid]; };
       ElemConsts<FA, FB, MR> k;
-      k.load(ld, a);
       ElemExtra<NE> x;
-      if constexpr (NE == 8) x.load(ld, a.off_hg);
+      int lc[NE];
+#pragma unroll
+      for (int b = 0; b < NE; ++b) lc[b] = lconn[tid * NE + b];
+      if constexpr (NE == 4) {
+        k.load_geometric(ld, a);
+        const float4 x0 = sx[lc[0]];
+        float xd[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const float4 xi = sx[lc[i + 1]];
+          xd[i][0] = xi.x - x0.x;
+          xd[i][1] = xi.y - x0.y;
+          xd[i][2] = xi.z - x0.z;
+        }
+        k.geometry(xd);
+      } else {
+        k.load(ld, a);
+        x.load(ld, a.off_hg);
+      }
       float4 h[NE], l[NE];
 #pragma unroll
       for (int b = 0; b < NE; ++b) {
-        const int lcb = lconn[tid * NE + b];
-        h[b] = su[lcb];
-        l[b] = CMP ? sl[lcb] : make_float4(0.f, 0.f, 0.f, 0.f);
+        h[b] = su[lc[b]];
+        l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       float d[NE][3];
       node_deltas<NE, CMP>(h, l, d);

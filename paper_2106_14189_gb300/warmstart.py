@@ -208,6 +208,14 @@ class WarmStart:
             torch.cuda.synchronize()
             t_pred = time.perf_counter() - t0
         st, n, r = mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
+        if warm and not fallback and st != 0:
+            # the relaxation from the prediction failed (an element inverted on
+            # the way): the same solve from rest decides
+            fallback = True
+            mesh.set_displacements(np.zeros((self.p.n_nodes, 3)))
+            B.dj_set_step(mesh.h, 0)
+            st, n2, r = mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
+            n += n2
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         if own:

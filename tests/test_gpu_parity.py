@@ -210,6 +210,12 @@ def test_inversion_while_stepping_is_reported(B):
         with pytest.raises(B.DJError) as e:
             m.sync()
         assert e.value.status in (3, 5)
+        # a new field starts a new trajectory with an empty error record
+        m.set_displacements(np.zeros((p.n_nodes, 3)))
+        B.dj_set_step(m.h, 0)
+        m.run(5)
+        m.sync()
+        assert np.isfinite(m.displacements()).all()
 
 
 def test_dt_above_critical_rejected(B):
