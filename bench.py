@@ -176,6 +176,20 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_throughput(units_local, ms_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed divided by the slowest rank's time (units per second), and that
+    time in ms.  `dist` is torch.distributed (initialised) or None."""
+    import torch
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return float(u.item()) / (ms_max * 1e-3), ms_max
+
+
 def oracle_rate(p_small, n_steps, dt=None):
     """Oracle element-updates/s on a problem, timed over n_steps (after set-up)."""
     from oracle import dynamics
@@ -350,12 +364,8 @@ def main():
     # per-kernel device time over the same number of steps (events between kernels)
     ms_force, ms_update = B.dj_run_n_profiled(mesh.h, args.steps, stream)
     mesh.sync(stream)
-    t_max = torch.tensor([ms], device="cuda")
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
     E, N = p.n_elems, p.n_nodes
-    value = world * E * args.steps / (ms_max * 1e-3)
+    value, ms_max = replica_throughput(E * args.steps, ms, dist, device="cuda")
 
     # roofline of the dominant kernel
     peak, peak_kind = measured_peak()
@@ -404,9 +414,9 @@ def main():
             B.dj_step(mesh.h, stream)
             U_host = B.dj_get_displacements(mesh.h, N)
         t1 = time.perf_counter()
-        info = mesh.info()
         n_bc_nodes = len(np.unique(p.bc_dof // 3))
-        e2e = {"value": E * n_e2e / (t1 - t0), "unit": "element-updates/s",
+        e2e_value, _ = replica_throughput(E * n_e2e, (t1 - t0) * 1e3, dist, device="cuda")
+        e2e = {"value": e2e_value, "unit": "element-updates/s",
                "h2d_bytes_per_step": int(n_bc_nodes * 16), "d2h_bytes_per_step": int(N * 16),
                "steps": n_e2e}
 
