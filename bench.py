@@ -257,7 +257,7 @@ def run_warmstart(args):
     Y, kept, steps = ws.solve_batch(list(T_train), batch_size=64)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    losses = ws.fit(T_train[kept], Y, epochs=400, batch=128)
+    losses = ws.fit(T_train[kept], Y, epochs=1500, batch=128)
     t_fit = time.perf_counter() - t0
     T_test = load_cases(p, range(900000, 900000 + args.ws_test))
     cold, warm = [], []
@@ -265,8 +265,13 @@ def run_warmstart(args):
         # warm-up of both paths (graph capture, first-use module loads)
         ws.relax(T_test[0], warm=False, mesh=m)
         ws.relax(T_test[0], warm=True, mesh=m)
+        pred_err = []
         for t in T_test:
             cold.append(ws.relax(t, warm=False, mesh=m))
+            if cold[-1].status == 0:
+                Uc = m.displacements().reshape(-1)
+                Up = ws.predict(t).double().cpu().numpy()
+                pred_err.append(float(np.abs(Up - Uc).max() / max(np.abs(Uc).max(), 1e-30)))
             warm.append(ws.relax(t, warm=True, mesh=m))
     ws.close()
     ok = all(r.status == 0 for r in cold + warm)
@@ -280,6 +285,8 @@ def run_warmstart(args):
             "steps_warm": float(np.mean([r.steps for r in warm])),
             "steps_plain": float(np.mean([r.steps for r in cold])),
             "fallbacks": int(sum(r.fallback for r in warm)), "all_converged": ok,
+            "prediction_rel_linf": float(np.median(pred_err)) if pred_err else None,
+            "input_modes_kept": int(ws.keep_in.sum()),
             "train_loads": args.ws_train, "train_loads_kept": len(kept), "test_loads": args.ws_test,
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "
@@ -309,8 +316,9 @@ def main():
     ap.add_argument("--ws-h", type=float, default=3e-3)
     ap.add_argument("--ws-train", type=int, default=512)
     ap.add_argument("--ws-test", type=int, default=32)
-    ap.add_argument("--assembly", type=int, default=1,
-                    help="1 tiles (default), 2 tiles with the bulk-copy pipeline, 0 element slots")
+    ap.add_argument("--assembly", type=int, default=-1,
+                    help="-1 autotune (default), 0 element slots, 1 tiles, 2 tiles with the "
+                         "bulk-copy pipeline")
     ap.add_argument("--tile-size", type=int, default=0)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -338,9 +346,20 @@ def main():
     from paper_2106_14189_gb300 import binding as B
 
     p, desc = workload(args.workload)
-    mesh = B.Mesh(p, assembly=args.assembly, tile_size=args.tile_size)
-    minfo = mesh.info()
     stream = torch.cuda.current_stream()
+    tune = None
+    if args.assembly < 0:
+        # the schedule a user gets from dj_autotune on this mesh (slots, tiles
+        # 64-512, bulk-copy pipeline 64-256), chosen before the warm-up
+        mesh = B.Mesh(p)
+        t_tune = time.perf_counter()
+        chosen, ms_tuned = B.dj_autotune(mesh.h, steps=100, stream=stream)
+        tune = {"seconds": time.perf_counter() - t_tune, "ms_per_step": ms_tuned}
+        B.dj_set_step(mesh.h, 0)
+        mesh.set_displacements(np.zeros((p.n_nodes, 3)))
+    else:
+        mesh = B.Mesh(p, assembly=args.assembly, tile_size=args.tile_size)
+    minfo = mesh.info()
     # warm-up
     mesh.run(args.warmup, stream)
     mesh.sync(stream)
@@ -424,7 +443,9 @@ def main():
     also = None
     if args.workload == "tet4_cube59" and world == 1 and not args.no_also:
         ph, desch = workload("hex8_cube64")
-        mh = B.Mesh(ph, assembly=args.assembly)
+        mh = B.Mesh(ph, assembly=max(args.assembly, 1))
+        if args.assembly < 0:
+            B.dj_autotune(mh.h, steps=100, stream=stream)
         mh.run(args.warmup, stream)
         mh.sync(stream)
         kh = max(1000, args.steps // 2)
@@ -436,8 +457,11 @@ def main():
         torch.cuda.synchronize()
         mh.sync(stream)
         msh = e0.elapsed_time(e1)
+        hi = mh.info()
         also = {"workload": desch, "value": ph.n_elems * kh / (msh * 1e-3),
-                "unit": "element-updates/s", "ms_per_step": msh / kh, "steps": kh}
+                "unit": "element-updates/s", "ms_per_step": msh / kh, "steps": kh,
+                "assembly": {0: "slots", 1: "tiles", 2: "tiles, bulk-copy pipeline"}[hi.assembly],
+                "tile_size": hi.tile_size}
         mh.close()
 
     # batched solves: 256 seeded instances, T4 / H8 50/50, 5k-150k elements each
@@ -490,6 +514,7 @@ def main():
                            "parallelism": f"replicas x{world}",
                            "assembly": {0: "slots", 1: "tiles", 2: "tiles, bulk-copy pipeline"}[minfo.assembly],
                            "tile_size": minfo.tile_size,
+                           "schedule": "dj_autotune" if tune else "fixed",
                            "l2": "working set ~215 MB > 129 MB L2 (no flush needed)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": 2 * args.steps, "also": also, "batch": batch,

@@ -125,23 +125,30 @@ class WarmStart:
                                    self.modes_in.data_ptr())
         self.sig_out = B.dj_pod_fit(Y.data_ptr(), self.n_dof, S, self.n_out, self.mean_out.data_ptr(),
                                     self.modes_out.data_ptr())
-        # scale the bases so that coefficients have unit spread over the training set
-        s_in = torch.tensor(np.maximum(self.sig_in, 1e-30) / np.sqrt(S), dtype=torch.float32,
-                            device=self.dev)
-        s_out = torch.tensor(np.maximum(self.sig_out, 1e-30) / np.sqrt(S), dtype=torch.float32,
-                             device=self.dev)
-        self.modes_in /= s_in
+        # scale the bases so that coefficients have unit spread over the training set;
+        # modes beyond the numerical rank of the snapshots (a load family of low
+        # dimension has few input modes) are switched off instead of being
+        # scaled up to unit-variance noise
+        def spreads(sig, rel):
+            keep = sig > rel * max(sig[0], 1e-300)
+            return np.where(keep, sig / np.sqrt(S), 0.0), keep
+        s_in_np, self.keep_in = spreads(self.sig_in, 1e-4)
+        s_out_np, self.keep_out = spreads(self.sig_out, 1e-6)
+        inv_in = np.where(self.keep_in, 1.0 / np.where(self.keep_in, s_in_np, 1.0), 0.0)
+        self.modes_in *= torch.tensor(inv_in, dtype=torch.float32, device=self.dev)
+        s_out = torch.tensor(s_out_np, dtype=torch.float32, device=self.dev)
         self.modes_out *= s_out
         Xc = torch.empty((S, self.n_in), device=self.dev)
         Qc = torch.empty((S, self.n_out), device=self.dev)
         B.dj_pod_project(self.modes_in.data_ptr(), self.mean_in.data_ptr(), self.n_bc, self.n_in,
                          dT.data_ptr(), S, Xc.data_ptr())
         # outputs: coefficients in the scaled output basis (modes_out has spread s_out^2)
-        proj = self.modes_out / (s_out * s_out)
+        inv_out2 = np.where(self.keep_out, 1.0 / np.where(self.keep_out, s_out_np, 1.0) ** 2, 0.0)
+        proj = self.modes_out * torch.tensor(inv_out2, dtype=torch.float32, device=self.dev)
         B.dj_pod_project(proj.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
                          Y.data_ptr(), S, Qc.data_ptr())
         # loss weights: output variance shares, so the loss tracks the field error
-        var = self.sig_out ** 2
+        var = np.where(self.keep_out, self.sig_out ** 2, 0.0)
         self.w = torch.tensor(var / var.mean(), dtype=torch.float32, device=self.dev)
         if self.mlp is not None:
             B.dj_mlp_destroy(self.mlp)
