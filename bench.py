@@ -265,13 +265,16 @@ def run_warmstart(args):
         # warm-up of both paths (graph capture, first-use module loads)
         ws.relax(T_test[0], warm=False, mesh=m)
         ws.relax(T_test[0], warm=True, mesh=m)
-        pred_err = []
+        pred_err, recon_err = [], []
         for t in T_test:
             cold.append(ws.relax(t, warm=False, mesh=m))
             if cold[-1].status == 0:
                 Uc = m.displacements().reshape(-1)
                 Up = ws.predict(t).double().cpu().numpy()
-                pred_err.append(float(np.abs(Up - Uc).max() / max(np.abs(Uc).max(), 1e-30)))
+                sc = max(np.abs(Uc).max(), 1e-30)
+                pred_err.append(float(np.abs(Up - Uc).max() / sc))
+                Ur = ws.reconstruct(torch.tensor(Uc, dtype=torch.float32, device="cuda"))
+                recon_err.append(float(np.abs(Ur.double().cpu().numpy() - Uc).max() / sc))
             warm.append(ws.relax(t, warm=True, mesh=m))
     ws.close()
     ok = all(r.status == 0 for r in cold + warm)
@@ -286,6 +289,7 @@ def run_warmstart(args):
             "steps_plain": float(np.mean([r.steps for r in cold])),
             "fallbacks": int(sum(r.fallback for r in warm)), "all_converged": ok,
             "prediction_rel_linf": float(np.median(pred_err)) if pred_err else None,
+            "pod_reconstruction_rel_linf": float(np.median(recon_err)) if recon_err else None,
             "input_modes_kept": int(ws.keep_in.sum()),
             "train_loads": args.ws_train, "train_loads_kept": len(kept), "test_loads": args.ws_test,
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
@@ -294,6 +298,62 @@ def run_warmstart(args):
                                    f"(r = 25 mm, bump profile) 1-5 mm, ramp 1500 steps, "
                                    f"compensated precision, alpha = 130 1/s, "
                                    f"MLP 64-256-256-256-128 tanh on POD coefficients"},
+            "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+
+
+CUTOUT_SIZES = (10, 14, 18, 22, 28, 34)   # 0.37e4 ... 1.0e5 DOFs (Sec. 5.1: 0.4-10.1e4)
+
+
+def run_cutout(args):
+    """Sec. 5.1 verification model at six sizes, T4 / H8, NH / TI / OT / MR:
+    GPU solution time of the full simulation (20000 steps of 5e-5 s, t = 1 s)
+    and each model's overhead over NH (the quantities of Table 7), one mesh at
+    a time, every step a graph-replayed DJ-TLED step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_14189_gb300 import binding as B
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    names = {W.NH: "NH", W.TI: "TI", W.OT: "OT", W.MR: "MR"}
+    rows = []
+    for et in (W.TET4, W.HEX8):
+        for n in CUTOUT_SIZES:
+            for model in (W.NH, W.TI, W.OT, W.MR):
+                p = W.cutout_cube(et, n, model)
+                with B.Mesh(p) as m:
+                    m.run(200, stream)
+                    m.sync(stream)
+                    B.dj_set_step(m.h, 0)
+                    m.set_displacements(np.zeros((p.n_nodes, 3)))
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    m.run(p.n_steps, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    m.sync(stream)
+                    ms = e0.elapsed_time(e1)
+                    uz = float(np.abs(m.displacements()[:, 2]).max())
+                rows.append({"elem": "T4" if et == W.TET4 else "H8", "n": n, "dofs": 3 * p.n_nodes,
+                             "elements": p.n_elems, "model": names[model], "steps": p.n_steps,
+                             "solve_ms": ms, "us_per_step": 1e3 * ms / p.n_steps,
+                             "max_uz": uz})
+    over = {}
+    for el in ("T4", "H8"):
+        for mo in ("TI", "OT", "MR"):
+            r = [x["solve_ms"] / y["solve_ms"] - 1.0 for x in rows for y in rows
+                 if x["elem"] == el and y["elem"] == el and x["n"] == y["n"]
+                 and x["model"] == mo and y["model"] == "NH"]
+            over[f"{el}_{mo}"] = float(np.mean(r))
+    line = {"metric": "cut-out cube simulation time (20000 steps, t = 1 s)", "unit": "ms",
+            "rows": rows, "mean_overhead_vs_NH": over,
+            "paper_gpu_overhead_vs_NH": {"T4_TI": 0.077, "T4_OT": 0.147, "T4_MR": 0.399,
+                                         "H8_TI": 0.019, "H8_OT": 0.037, "H8_MR": 0.139},
+            "config": {"workload": "cube 0.1 m with four cylindrical recesses (r = 25 mm, depth 30 mm), "
+                                   "back face fixed, front face u_z -> 0.05 m linear ramp, "
+                                   "dt = 5e-5 s, Sec. 5.1 materials"},
             "dtype": "f32", "data": "synthetic"}
     print(json.dumps(line), flush=True)
 
@@ -313,6 +373,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=400)
     ap.add_argument("--warmstart", action="store_true",
                     help="learned warm start evaluation instead of the step benchmark")
+    ap.add_argument("--cutout", action="store_true",
+                    help="Sec. 5.1 cut-out cube: six sizes x T4/H8 x four models, full 1 s simulations")
     ap.add_argument("--ws-h", type=float, default=3e-3)
     ap.add_argument("--ws-train", type=int, default=512)
     ap.add_argument("--ws-test", type=int, default=32)
@@ -327,6 +389,9 @@ def main():
         return
     if args.warmstart:
         run_warmstart(args)
+        return
+    if args.cutout:
+        run_cutout(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -47,7 +47,7 @@ typedef enum {
   DJ_ERR_BAD_MESH = 2,          /* empty mesh or connectivity out of range */
   DJ_ERR_INVERTED_ELEMENT = 3,  /* det 0J <= 0 at set-up, or det tJ <= 0 while stepping */
   DJ_ERR_NOT_PRECOMPUTED = 4,   /* stepping before dj_precompute */
-  DJ_ERR_NONFINITE = 5,         /* NaN/Inf produced by an element force */
+  DJ_ERR_NONFINITE = 5,         /* NaN/Inf in a nodal force or displacement */
   DJ_ERR_NOT_CONVERGED = 6,     /* dj_relax_to_tol hit max_steps */
   DJ_ERR_CUDA = 7,              /* a CUDA runtime call failed */
   DJ_ERR_OOM = 8,               /* device or host allocation failed */
@@ -173,7 +173,8 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* mesh, const double* target);
 dj_status dj_mesh_set_groups(dj_mesh* mesh, const int* elem_group, int n_groups);
 
 /* External nodal forces R (Eq. 13), host n_nodes * 3 doubles, constant in
- * time; NULL clears them.  Must be called before dj_precompute. */
+ * time; NULL clears them.  Must be called before dj_precompute.
+ * Errors: DJ_ERR_INVALID_ARG for a value that is not finite in single precision. */
 dj_status dj_mesh_set_loads(dj_mesh* mesh, const double* R);
 
 /* One-time set-up on the current CUDA device (Algorithm 1, pre-computation):
@@ -376,7 +377,7 @@ void dj_mlp_destroy(dj_mlp* mlp);
  * d_Y + c * rows; cols <= 4096): d_mean (rows) the snapshot mean, d_modes
  * (rows x r, row-major) the r leading orthonormal modes of the centred
  * snapshots (method of snapshots: Gram matrix on the GPU with FP64 slab
- * accumulation, FP64 Jacobi eigen-decomposition on the host), sigma_out (host,
+ * accumulation, FP64 Householder + QL eigen-decomposition on the host), sigma_out (host,
  * optional, r) the singular values.  Synchronous. */
 dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d_mean, float* d_modes,
                      double* sigma_out, void* stream);
@@ -387,6 +388,20 @@ dj_status dj_pod_project(const float* d_modes, const float* d_mean, long long ro
 /* d_X (column-major rows x cols) = mean + modes Q^T for d_Q (cols x r). */
 dj_status dj_pod_expand(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_Q,
                         int cols, float* d_X, void* stream);
+
+/* Ridge least squares (the linear part of the warm-start map; no counterpart in
+ * the paper): d_W (n_out x n_in, row-major) minimises
+ * |X W^T - Y|^2 + ridge * tr(X^T X) / n_in * |W|^2 for d_X (S x n_in) and d_Y
+ * (S x n_out), both row-major device arrays.  Products on the device, FP64
+ * Cholesky solve on the host; n_in <= 1024.  Synchronous.
+ * Errors: DJ_ERR_INVALID_ARG (sizes, ridge < 0, or singular normal equations
+ * with ridge = 0), DJ_ERR_CUDA. */
+dj_status dj_linear_fit(const float* d_X, const float* d_Y, int S, int n_in, int n_out, double ridge,
+                        float* d_W, void* stream);
+/* d_Y (S x n_out) = alpha X W^T + beta Y for d_X (S x n_in) and d_W (n_out x n_in),
+ * row-major device arrays; enqueued on `stream`; allocates nothing. */
+dj_status dj_linear_apply(const float* d_W, int n_out, int n_in, const float* d_X, int S, float alpha, float beta,
+                          float* d_Y, void* stream);
 
 #ifdef __cplusplus
 }

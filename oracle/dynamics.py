@@ -155,6 +155,8 @@ class ExplicitSolver:
 
     @classmethod
     def from_problem(cls, p, dt=None, alpha=None, R=None):
+        if dt is None and getattr(p, "dt", 0.0) > 0.0:
+            dt = p.dt
         return cls(Model.from_problem(p, R), p.bc_dof, p.bc_target, dt=dt,
                    dt_scale=p.dt_scale, alpha=p.alpha if alpha is None else alpha,
                    ramp_kind=p.ramp_kind, ramp_steps=p.ramp_steps)

@@ -11,6 +11,8 @@ textbook definitions used to check the GPU kernels:
 * POD of snapshots Y (rows x cols, one snapshot per column): mean over
   columns, then the left singular vectors of the centred matrix and its
   singular values (library SVD).
+* ridge least squares W = argmin |X W^T - Y|^2 + lam tr(X^T X) / n_in |W|^2
+  (the linear part of the warm-start map), by the normal equations.
 
 Parameters are packed as [W_1 (row-major), b_1, W_2, b_2, ...] in float64.
 """
@@ -83,3 +85,12 @@ def pod(Y, r):
     mean = Y.mean(axis=1)
     U, s, _ = np.linalg.svd(Y - mean[:, None], full_matrices=False)
     return mean, U[:, :r], s[:r]
+
+
+def linear_fit(X, Y, ridge):
+    """W (n_out x n_in) of ridge least squares, normal equations in FP64."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    G = X.T @ X
+    n = G.shape[0]
+    return np.linalg.solve(G + ridge * np.trace(G) / n * np.eye(n), X.T @ Y).T

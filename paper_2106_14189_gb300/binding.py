@@ -39,7 +39,7 @@ EXPORTS = [
     "dj_mlp_get_grads", "dj_mlp_forward", "dj_mlp_loss_grad", "dj_mlp_adam_step",
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
     "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
-    "dj_batch_autotune",
+    "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply",
 ]
 
 
@@ -136,6 +136,8 @@ def lib():
         "dj_mlp_destroy": (None, [_P]),
         "dj_pod_fit": (C.c_int, [_P, C.c_longlong, C.c_int, C.c_int, _P, _P, _D, _P]),
         "dj_pod_project": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
+        "dj_linear_fit": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
+        "dj_linear_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_float, C.c_float, _P, _P]),
         "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_residual_norms_static": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
         "dj_set_step": (C.c_int, [_P, C.c_longlong]),
@@ -517,6 +519,16 @@ def dj_pod_expand(d_modes, d_mean, rows, r, d_Q, cols, d_X, stream=None):
            "dj_pod_expand")
 
 
+def dj_linear_fit(d_X, d_Y, S, n_in, n_out, ridge, d_W, stream=None):
+    _check(lib().dj_linear_fit(d_X, d_Y, int(S), int(n_in), int(n_out), float(ridge), d_W, _stream(stream)),
+           "dj_linear_fit")
+
+
+def dj_linear_apply(d_W, n_out, n_in, d_X, S, alpha, beta, d_Y, stream=None):
+    _check(lib().dj_linear_apply(d_W, int(n_out), int(n_in), d_X, int(S), float(alpha), float(beta), d_Y,
+                                 _stream(stream)), "dj_linear_apply")
+
+
 # ------------------------------------------------------------- convenience --
 class Mesh:
     """Owning wrapper of a dj_mesh handle built from a workloads.Problem."""
@@ -532,7 +544,7 @@ class Mesh:
                                   p.a_dir, p.b_dir)
             dj_mesh_set_bcs(self.h, p.bc_dof, p.bc_target)
             if params is None:
-                kw = dict(dt_scale=p.dt_scale, alpha=p.alpha, hg_coeff=p.hg_coeff,
+                kw = dict(dt=p.dt, dt_scale=p.dt_scale, alpha=p.alpha, hg_coeff=p.hg_coeff,
                           ramp_steps=p.ramp_steps, ramp_kind=p.ramp_kind)
                 kw.update(param_kw)
                 params = default_params(**kw)
@@ -603,7 +615,7 @@ class Batch:
             for h in handles:
                 dj_mesh_destroy(h)
         p0 = self.problems[0]
-        kw = dict(dt_scale=p0.dt_scale, alpha=p0.alpha, hg_coeff=p0.hg_coeff,
+        kw = dict(dt=p0.dt, dt_scale=p0.dt_scale, alpha=p0.alpha, hg_coeff=p0.hg_coeff,
                   ramp_steps=p0.ramp_steps, ramp_kind=p0.ramp_kind)
         kw.update(param_kw)
         self.params = default_params(**kw)

@@ -242,8 +242,13 @@ dj_status check_flags(dj_mesh* m) {
     if (st.err_flags & ERR_INVERTED)
       return fail(m, DJ_ERR_INVERTED_ELEMENT, "element %d inverted (det tJ <= 0) by step %lld",
                   caller, st.step);
-    return fail(m, DJ_ERR_NONFINITE, "non-finite force in element %d by step %lld", caller,
-                st.step);
+    if (st.err_flags & ERR_NONFINITE) {
+      const int bn = st.bad_node;
+      const int node = (bn >= 0 && bn < (int)m->N) ? m->node_old_of_new[bn] : -1;
+      return fail(m, DJ_ERR_NONFINITE, "non-finite force or displacement at node %d by step %lld", node,
+                  st.step);
+    }
+    return fail(m, DJ_ERR_CUDA, "a bounded device wait timed out by step %lld", st.step);
   }
   return DJ_OK;
 }
@@ -252,7 +257,7 @@ dj_status check_flags(dj_mesh* m) {
 // empty (err_flags = 0, bad_elem above every element id).
 cudaError_t clear_error_flags(dj_mesh* m, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(&m->d_state->err_flags, 0, sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(&m->d_state->bad_elem, 0x7f, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&m->d_state->bad_elem, 0x7f, 2 * sizeof(int), s);  // and bad_node
   return e;
 }
 
@@ -540,7 +545,8 @@ dj_status dj_mesh_set_loads(dj_mesh* m, const double* R) {
     m->R.clear();
   } else {
     for (long long i = 0; i < 3 * m->N; ++i)
-      if (!std::isfinite(R[i])) return fail(m, DJ_ERR_INVALID_ARG, "non-finite load");
+      if (!std::isfinite(R[i]) || std::fabs(R[i]) > 3.0e38)
+        return fail(m, DJ_ERR_INVALID_ARG, "load not finite in single precision");
     m->R.assign(R, R + 3 * m->N);
   }
   m->precomputed = false;
@@ -1026,6 +1032,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   st0.ramp_s = 0.f;
   st0.err_flags = 0;
   st0.bad_elem = INT_MAX;
+  st0.bad_node = INT_MAX;
   CK(cudaMemcpy(m->d_state, &st0, sizeof(DevState), cudaMemcpyHostToDevice));
   CK(cudaDeviceSynchronize());
   m->precomputed = true;
@@ -1328,6 +1335,7 @@ dj_status dj_evaluate_field(dj_mesh* m, const float* d_U, double* residual_out, 
   DevState clean = before;
   clean.err_flags = 0;
   clean.bad_elem = INT_MAX;
+  clean.bad_node = INT_MAX;
   *m->h_state = clean;
   CK(cudaMemcpyAsync(m->d_state, m->h_state, sizeof(DevState), cudaMemcpyHostToDevice, st));
   cudaError_t e = launch_from_caller_order(d_U, m->d_perm, (int)m->N, m->d_U, m->d_V, m->d_Ulo, st);
@@ -1462,6 +1470,7 @@ dj_status dj_set_state(dj_mesh* m, const void* buf, size_t bytes) {
   DevState st{};
   st.step = h.step;
   st.bad_elem = INT_MAX;
+  st.bad_node = INT_MAX;
   CK(cudaMemcpy(m->d_state, &st, sizeof(st), cudaMemcpyHostToDevice));
   return DJ_OK;
 }

@@ -233,10 +233,16 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
   return F;
 }
 
-__device__ __forceinline__ void flag_error(DevState* st, int e, bool inverted, bool nonfinite) {
-  int f = (inverted ? ERR_INVERTED : 0) | (nonfinite ? ERR_NONFINITE : 0);
-  if (f) {
-    atomicOr(&st->err_flags, f);
+__device__ __forceinline__ void flag_nonfinite(DevState* st, int node) {
+  atomicOr(&st->err_flags, ERR_NONFINITE);
+  atomicMin(&st->bad_node, node);
+}
+
+// det tJ <= 0 (or not a number) in element e.  Non-finite values are detected
+// per node in the update kernel, where U^{n+1} is formed.
+__device__ __forceinline__ void flag_inverted(DevState* st, int e, bool inverted) {
+  if (inverted) {
+    atomicOr(&st->err_flags, ERR_INVERTED);
     atomicMin(&st->bad_elem, e);
   }
 }
@@ -532,15 +538,6 @@ __device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemC
     tet4_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
   else
     hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
-}
-
-// a NaN or Inf in any force propagates into the sum (Inf - Inf = NaN)
-template <int NE>
-__device__ __forceinline__ bool all_finite(const float (&f)[NE][3]) {
-  float s = 0.f;
-#pragma unroll
-  for (int b = 0; b < NE; ++b) s += f[b][0] + f[b][1] + f[b][2];
-  return isfinite(s);
 }
 
 // d_b = u_b - u_0 from the nodal records (hi, lo)

@@ -37,9 +37,9 @@ enum { KG_CP = 0, KG_KV = 1, KG_COMMON = 2 };
 struct DevState {
   long long step;     // n of the current displacement U^n
   float ramp_s;       // s(tau) for the step being computed (U^{n+1})
-  int err_flags;      // bit 0: det tJ <= 0, bit 1: non-finite force
-  int bad_elem;       // smallest internal element id with an error
-  int pad0;
+  int err_flags;      // bit 0: det tJ <= 0, bit 1: non-finite value, bit 2: wait timeout
+  int bad_elem;       // smallest internal element id with det tJ <= 0
+  int bad_node;       // smallest internal node id with a non-finite force or displacement
   double resid_num2;  // sum of squared residual over free DOFs
   double resid_den2;  // sum of squared reaction over prescribed DOFs
 };
@@ -73,7 +73,7 @@ struct NodeArgs {
   double2* partials;      // residual partial sums per block
   double2* node_resid;    // grouped meshes: per-node residual sums (else nullptr)
   const float* bm1_node;  // grouped meshes with damping: per-node b - 1 (else nullptr)
-  const DevState* st;
+  DevState* st;           // ramp value (read), error flags (written)
   int N;
   float bm1;              // b - 1 = (2 - alpha dt) / (2 + alpha dt)
 };

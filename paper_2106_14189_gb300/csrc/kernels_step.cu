@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
   float f[NE][3];
   bool inv;
   elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
-  flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
+  flag_inverted(a.st, e, inv);
 #pragma unroll
   for (int b = 0; b < NE; ++b) a.slots[(size_t)b * E_pad + e] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
 }
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
     float f[NE][3];
     bool inv;
     elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
-    flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
+    flag_inverted(a.st, e, inv);
 #pragma unroll
     for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
   }
@@ -207,6 +207,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
     // now f = F_int - R
     const float4 V = a.V[i];
     const int bc = __float_as_int(V.w);
+    if (MODE == NODE_FORCE_ONLY || MODE == NODE_RESID_ONLY) {
+      if (!isfinite(fx + fy + fz)) flag_nonfinite(a.st, i);
+    }
     if (MODE == NODE_FORCE_ONLY) {
       a.fout[i] = make_float4(fx, fy, fz, 0.f);
     } else if (MODE == NODE_RESID_ONLY) {
@@ -260,6 +263,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
             dd[q] = (nh[q] - uh[q]) - ul[q];
           }
       }
+      // a non-finite element force reaches U^{n+1} of its nodes (NaN and Inf
+      // propagate through the update), or the reaction of prescribed ones
+      if (!isfinite(nh[0] + nh[1] + nh[2] + fx + fy + fz)) flag_nonfinite(a.st, i);
       a.U[i] = make_float4(nh[0], nh[1], nh[2], ai);
       if (CMP) a.Ulo[i] = make_float4(nl[0], nl[1], nl[2], 0.f);
       a.V[i] = make_float4(dd[0], dd[1], dd[2], V.w);

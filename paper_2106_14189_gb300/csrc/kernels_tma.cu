@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       float f[NE][3];
       bool inv;
       elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
-      flag_error(a.st, e, inv, !inv && !all_finite<NE>(f));
+      flag_inverted(a.st, e, inv);
 #pragma unroll
       for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
     }

@@ -577,4 +577,74 @@ dj_status dj_pod_expand(const float* d_modes, const float* d_mean, long long row
   return e == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
 }
 
+dj_status dj_linear_fit(const float* d_X, const float* d_Y, int S, int n_in, int n_out, double ridge,
+                        float* d_W, void* stream) {
+  // W (n_out x n_in) minimises |X W^T - Y|^2 + ridge tr(G) / n_in |W|^2, G = X^T X:
+  // the normal equations (G + ridge tr(G) / n_in I) W^T = X^T Y, products on the
+  // device (FP64 accumulation over K-slabs), Cholesky solve on the host in FP64
+  if (!d_X || !d_Y || !d_W || S <= 0 || n_in <= 0 || n_out <= 0 || n_in > 1024 || !(ridge >= 0.0))
+    return DJ_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  float *G = nullptr, *R = nullptr;
+  cudaError_t e = cudaMalloc(&G, (size_t)n_in * n_in * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&R, (size_t)n_in * n_out * sizeof(float));
+  // G(i, j) = sum_k X[k n_in + i] X[k n_in + j];  R(i, o) = sum_k X[k n_in + i] Y[k n_out + o]
+  if (e == cudaSuccess) e = gemm<double>(n_in, n_in, S, 1.f, d_X, 1, n_in, d_X, n_in, 1, 0.f, G, n_in, s);
+  if (e == cudaSuccess) e = gemm<double>(n_in, n_out, S, 1.f, d_X, 1, n_in, d_Y, n_out, 1, 0.f, R, n_out, s);
+  std::vector<float> hG((size_t)n_in * n_in), hR((size_t)n_in * n_out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hR.data(), R, hR.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (G) cudaFree(G);
+  if (R) cudaFree(R);
+  if (e != cudaSuccess) return DJ_ERR_CUDA;
+  const int n = n_in;
+  std::vector<double> L((size_t)n * n, 0.0);
+  double tr = 0.0;
+  for (int i = 0; i < n; ++i) tr += hG[(size_t)i * n + i];
+  const double shift = ridge * tr / n + 1e-300;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) L[(size_t)i * n + j] = 0.5 * ((double)hG[(size_t)i * n + j] + hG[(size_t)j * n + i]);
+  for (int i = 0; i < n; ++i) L[(size_t)i * n + i] += shift;
+  for (int j = 0; j < n; ++j) {  // Cholesky, lower triangle in place
+    double d = L[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > 0.0)) return DJ_ERR_INVALID_ARG;  // singular normal equations (ridge = 0, rank-deficient X)
+    d = std::sqrt(d);
+    L[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double v = L[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = v / d;
+    }
+  }
+  std::vector<float> hW((size_t)n_out * n);
+  std::vector<double> z(n);
+  for (int o = 0; o < n_out; ++o) {
+    for (int i = 0; i < n; ++i) {  // L z = r
+      double v = hR[(size_t)i * n_out + o];
+      for (int k = 0; k < i; ++k) v -= L[(size_t)i * n + k] * z[k];
+      z[i] = v / L[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T w = z
+      double v = z[i];
+      for (int k = i + 1; k < n; ++k) v -= L[(size_t)k * n + i] * z[k];
+      z[i] = v / L[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) hW[(size_t)o * n + i] = (float)z[i];
+  }
+  e = cudaMemcpyAsync(d_W, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
+}
+
+dj_status dj_linear_apply(const float* d_W, int n_out, int n_in, const float* d_X, int S, float alpha, float beta,
+                          float* d_Y, void* stream) {
+  // Y (S x n_out) = alpha X W^T + beta Y, X row-major S x n_in, W row-major n_out x n_in
+  if (!d_W || !d_X || !d_Y || n_out <= 0 || n_in <= 0 || S <= 0) return DJ_ERR_INVALID_ARG;
+  cudaError_t e = gemm<float>(S, n_out, n_in, alpha, d_X, n_in, 1, d_W, 1, n_in, beta, d_Y, n_out,
+                              (cudaStream_t)stream);
+  return e == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
+}
+
 }  // extern "C"

@@ -9,8 +9,9 @@ only as future work, Sec. 8).  Everything numerical runs in the CUDA library:
 * inputs: the leading POD coefficients of the prescribed-displacement vector,
   outputs: the leading POD coefficients of the relaxed field (dj_pod_fit /
   dj_pod_project / dj_pod_expand);
-* MLP training and inference: dj_mlp_loss_grad / dj_mlp_adam_step /
-  dj_mlp_forward.
+* the map from input to output coefficients: a ridge least-squares linear part
+  (dj_linear_fit / dj_linear_apply) plus an MLP trained on what the linear
+  part leaves (dj_mlp_loss_grad / dj_mlp_adam_step / dj_mlp_forward).
 
 A relaxation from the predicted field uses plain DJ-TLED relaxation both as
 fallback and as arbiter: if the predicted field inverts an element or has a
@@ -47,7 +48,7 @@ class WarmStart:
     def __init__(self, problem: W.Problem, n_in: int = 64, n_out: int = 128,
                  hidden=(256, 256, 256), seed: int = 0, alpha: float = 130.0,
                  ramp_steps: int = 400, check_every: int = 50, tol: float = 1e-5,
-                 max_steps: int = 400000, precision: int = 1):
+                 max_steps: int = 400000, precision: int = 1, linear: bool = True):
         import torch
         self.torch = torch
         self.p = problem
@@ -56,6 +57,7 @@ class WarmStart:
         self.seed = seed
         self.alpha, self.ramp_steps, self.check_every = alpha, ramp_steps, check_every
         self.tol, self.max_steps, self.precision = tol, max_steps, precision
+        self.linear = linear
         self.n_bc = problem.bc_dof.size
         self.n_dof = 3 * problem.n_nodes
         self.mlp = None
@@ -145,8 +147,16 @@ class WarmStart:
         # outputs: coefficients in the scaled output basis (modes_out has spread s_out^2)
         inv_out2 = np.where(self.keep_out, 1.0 / np.where(self.keep_out, s_out_np, 1.0) ** 2, 0.0)
         proj = self.modes_out * torch.tensor(inv_out2, dtype=torch.float32, device=self.dev)
+        self.proj_out = proj
         B.dj_pod_project(proj.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
                          Y.data_ptr(), S, Qc.data_ptr())
+        # linear part of the map by ridge least squares; the MLP learns the rest
+        self.W_lin = torch.zeros((self.n_out, self.n_in), device=self.dev)
+        if self.linear:
+            B.dj_linear_fit(Xc.data_ptr(), Qc.data_ptr(), S, self.n_in, self.n_out, 1e-6,
+                            self.W_lin.data_ptr())
+            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, Xc.data_ptr(), S, -1.0, 1.0,
+                              Qc.data_ptr())
         # loss weights: output variance shares, so the loss tracks the field error
         var = np.where(self.keep_out, self.sig_out ** 2, 0.0)
         self.w = torch.tensor(var / var.mean(), dtype=torch.float32, device=self.dev)
@@ -181,6 +191,20 @@ class WarmStart:
         B.dj_pod_project(self.modes_in.data_ptr(), self.mean_in.data_ptr(), self.n_bc, self.n_in,
                          t.data_ptr(), 1, c.data_ptr())
         B.dj_mlp_forward(self.mlp, c.data_ptr(), 1, q.data_ptr())
+        B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, c.data_ptr(), 1, 1.0, 1.0,
+                          q.data_ptr())
+        B.dj_pod_expand(self.modes_out.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
+                        q.data_ptr(), 1, out.data_ptr())
+        return out
+
+    def reconstruct(self, field: "torch.Tensor") -> "torch.Tensor":
+        """Projection of a nodal field (n_dof floats on the device) onto the
+        output basis and back: the best the output representation can do."""
+        torch = self.torch
+        q = torch.empty((1, self.n_out), device=self.dev)
+        out = torch.empty(self.n_dof, device=self.dev)
+        B.dj_pod_project(self.proj_out.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
+                         field.data_ptr(), 1, q.data_ptr())
         B.dj_pod_expand(self.modes_out.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
                         q.data_ptr(), 1, out.data_ptr())
         return out

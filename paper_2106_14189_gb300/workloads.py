@@ -83,6 +83,7 @@ class Problem:
     bc_dof: np.ndarray
     bc_target: np.ndarray
     n_steps: int = 0
+    dt: float = 0.0          # > 0: fixed time step [s]; else dt_scale * dt_crit
     dt_scale: float = 0.9
     alpha: float = 0.0
     hg_coeff: float = 0.1
@@ -266,6 +267,62 @@ def cube_shear(elem_type: int, n: int, n_steps: int = 5000, shear: float = 0.1,
                    bc_dof=np.concatenate([d0, d1]), bc_target=np.concatenate([t0, t1]),
                    n_steps=n_steps, ramp_steps=n_steps, ramp_kind=RAMP_SMOOTH,
                    hg_coeff=hg_coeff, **mat)
+
+
+def voxel_hex8(voxels: np.ndarray, nx: int, ny: int) -> np.ndarray:
+    """Bricks of the listed voxels (V, 3) [i, j, k] -> (V, 8) corner ids
+    (bottom face CCW, then top face)."""
+    i, j, k = voxels[:, 0], voxels[:, 1], voxels[:, 2]
+    c = lambda di, dj, dk: _corner_ids(nx, ny, i + di, j + dj, k + dk)
+    return np.stack([c(0, 0, 0), c(1, 0, 0), c(1, 1, 0), c(0, 1, 0),
+                     c(0, 0, 1), c(1, 0, 1), c(1, 1, 1), c(0, 1, 1)], axis=1).astype(np.int64)
+
+
+# materials of the cut-out cube experiment (Sec. 5.1)
+CUTOUT_MU, CUTOUT_KAPPA, CUTOUT_RHO, CUTOUT_C01 = 6567.0, 326210.0, 1060.0, 3000.0
+
+
+def cutout_cube(elem_type: int, n: int, model: int = NH, n_steps: int = 20000,
+                extension: float = 0.05, L: float = 0.1, radius: float = 0.025,
+                depth: float = 0.03, dt: float = 5e-5) -> Problem:
+    """The verification model of Sec. 5.1: a cube of side L with a cylindrical
+    recess of the given radius and depth centred on each of the four faces
+    normal to x and y, voxelised with n cells per side (Kuhn tets or bricks).
+    The back face z = 0 is fixed, the front face z = L is pulled by u_z on a
+    linear ramp to `extension` over n_steps steps of dt = 5e-5 s (t = 1 s).
+    Materials (Sec. 5.1): NH mu = 6567 Pa, kappa = 326210 Pa; TI eta_a = 2 mu,
+    a = x; OT eta_a = eta_b = 2 mu, a = x, b = y; MR C10 = mu / 2,
+    C01 = 3000 Pa; rho = 1060 kg/m^3.  The printed recess radius (0.05 m, the
+    face's half width) is read as its diameter: radius 0.025 m."""
+    h = L / n
+    k, j, i = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vox = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1)
+    cen = (vox + 0.5) * h
+    c = 0.5 * L
+    in_x = ((cen[:, 1] - c) ** 2 + (cen[:, 2] - c) ** 2 < radius ** 2) & \
+        ((cen[:, 0] < depth) | (cen[:, 0] > L - depth))
+    in_y = ((cen[:, 0] - c) ** 2 + (cen[:, 2] - c) ** 2 < radius ** 2) & \
+        ((cen[:, 1] < depth) | (cen[:, 1] > L - depth))
+    vox = vox[~(in_x | in_y)]
+    Xg = _grid_nodes(n, n, n, L, L, L)
+    conn = voxel_tets(vox, n, n) if elem_type == TET4 else voxel_hex8(vox, n, n)
+    X, conn, _ = _compact(Xg, conn)
+    E = conn.shape[0]
+    mat = _uniform_material(E, CUTOUT_MU, CUTOUT_KAPPA, CUTOUT_RHO, model)
+    if model in (TI, OT):
+        mat["eta_a"][:] = 2.0 * CUTOUT_MU
+    if model == OT:
+        mat["eta_b"][:] = 2.0 * CUTOUT_MU
+    if model == MR:
+        mat["c01"][:] = CUTOUT_C01
+    tol = 1e-9 * L
+    d0, t0 = _face_bcs(X, 2, 0.0, tol, [(0, 0.0), (1, 0.0), (2, 0.0)])
+    d1, t1 = _face_bcs(X, 2, L, tol, [(2, extension)])
+    kind = "hex8" if elem_type == HEX8 else "tet4"
+    names = {NH: "nh", TI: "ti", OT: "ot", MR: "mr"}
+    return Problem(name=f"{kind}_cutout_{n}_{names[model]}", elem_type=elem_type, X=X, conn=conn,
+                   bc_dof=np.concatenate([d0, d1]), bc_target=np.concatenate([t0, t1]),
+                   n_steps=n_steps, ramp_steps=n_steps, ramp_kind=RAMP_LINEAR, dt=dt, **mat)
 
 
 def _smooth_field(rng, pts, n_modes, scale):

@@ -99,6 +99,26 @@ def test_pod_matches_svd(env):
     assert np.abs(R.cpu().numpy().T - Yr).max() < 1e-4 * np.abs(Y).max()
 
 
+def test_linear_fit_and_apply_match_reference(env):
+    torch, B = env
+    rng = np.random.default_rng(4)
+    S, n_in, n_out = 300, 24, 40
+    X = rng.normal(size=(S, n_in))
+    X[:, -3:] = 0.0                      # switched-off inputs: ridge keeps the system solvable
+    Y = X @ rng.normal(size=(n_in, n_out)) + 0.01 * rng.normal(size=(S, n_out))
+    dX = torch.tensor(X, dtype=torch.float32, device="cuda")
+    dY = torch.tensor(Y, dtype=torch.float32, device="cuda")
+    dW = torch.empty((n_out, n_in), device="cuda")
+    B.dj_linear_fit(dX.data_ptr(), dY.data_ptr(), S, n_in, n_out, 1e-6, dW.data_ptr())
+    W_ref = ref.linear_fit(X, Y, 1e-6)
+    W = dW.cpu().numpy().astype(np.float64)
+    assert np.abs(W - W_ref).max() < 1e-4 * np.abs(W_ref).max()
+    dZ = torch.ones((S, n_out), device="cuda")
+    B.dj_linear_apply(dW.data_ptr(), n_out, n_in, dX.data_ptr(), S, -1.0, 2.0, dZ.data_ptr())
+    Z_ref = 2.0 - X @ W.T
+    assert np.abs(dZ.cpu().numpy() - Z_ref).max() < 1e-5 * np.abs(Z_ref).max()
+
+
 def test_warm_start_relaxes_faster_than_rest(env):
     """Train on the method's own relaxed solutions of seeded loads on a coarse
     brain-sized ellipsoid; on held-out loads the warm-started relaxation reaches

@@ -55,3 +55,20 @@ def test_pod_reconstructs_low_rank_snapshots():
     assert np.abs(R - Y).max() < 1e-9
     assert np.allclose(U.T @ U, np.eye(5), atol=1e-12)
     assert np.all(np.diff(s) <= 0)
+
+
+def test_linear_fit_recovers_exact_maps_and_matches_lstsq():
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(80, 6))
+    Wt = rng.normal(size=(4, 6))
+    assert np.abs(mlp.linear_fit(X, X @ Wt.T, 0.0) - Wt).max() < 1e-12
+    Y = rng.normal(size=(80, 4))
+    ref = np.linalg.lstsq(X, Y, rcond=None)[0].T
+    assert np.abs(mlp.linear_fit(X, Y, 0.0) - ref).max() < 1e-12
+    # ridge: the solution of the augmented least-squares problem [X; sqrt(c) I]
+    lam = 0.1
+    c = lam * np.trace(X.T @ X) / 6
+    Xa = np.vstack([X, np.sqrt(c) * np.eye(6)])
+    Ya = np.vstack([Y, np.zeros((6, 4))])
+    ref = np.linalg.lstsq(Xa, Ya, rcond=None)[0].T
+    assert np.abs(mlp.linear_fit(X, Y, lam) - ref).max() < 1e-12

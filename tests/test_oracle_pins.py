@@ -463,3 +463,22 @@ def test_ramp_shapes():
     assert s[0] == 0 and abs(s[-1] - 1) < 1e-15 and np.all(np.diff(s) >= 0)
     assert abs(dynamics.ramp(0.5, 1) - 0.5) < 1e-15
     assert dynamics.ramp(2.0, 1) == 1.0
+
+
+def test_cutout_cube_geometry():
+    """Sec. 5.1 model: volume = cube - four cylindrical recesses (within the
+    voxelisation error), every element positively oriented, the back face fully
+    fixed and only u_z prescribed on the front face."""
+    for et in (W.TET4, W.HEX8):
+        p = W.cutout_cube(et, 24)
+        m = dynamics.Model.from_problem(p)
+        V = float(m.pre["V0"].sum())
+        exact = 0.1 ** 3 - 4 * np.pi * 0.025 ** 2 * 0.03
+        assert abs(V - exact) < 0.03 * exact
+        assert (m.pre["V0"] > 0).all()
+        comps = p.bc_dof % 3
+        front = np.abs(p.X[p.bc_dof // 3, 2] - 0.1) < 1e-12
+        assert (comps[front] == 2).all() and np.allclose(p.bc_target[front], 0.05)
+        assert np.allclose(p.bc_target[~front], 0.0)
+        back_nodes = np.nonzero(np.abs(p.X[:, 2]) < 1e-12)[0]
+        assert (p.bc_dof[~front] // 3).size == 3 * back_nodes.size
