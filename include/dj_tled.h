@@ -194,6 +194,18 @@ dj_status dj_step(dj_mesh* mesh, void* stream);
 /* Advance n >= 0 steps on `stream` (replays of a captured CUDA graph). Async. */
 dj_status dj_run_n(dj_mesh* mesh, long long n, void* stream);
 
+/* Device time of one launch of each kernel of the step, each launch timed
+ * alone with CUDA events on `stream`: `launches` launches of the element-force
+ * kernel (no clock advance), then `launches` of the node update kernel (on a
+ * saved copy of U and V, restored afterwards).  With d_flush non-NULL
+ * (caller-owned device buffer of flush_bytes, at least twice the L2 size) every
+ * launch is preceded by an L2 eviction (the first half of the buffer written,
+ * the second half read), so each launch starts with a cold cache.
+ * ms_force / ms_update (optional) receive the mean per launch.  Synchronous;
+ * allocates two state copies.  Not a counterpart of anything in the paper. */
+dj_status dj_profile_kernels(dj_mesh* mesh, int launches, void* d_flush, size_t flush_bytes, void* stream,
+                             double* ms_force, double* ms_update);
+
 /* Advance n steps (as dj_run_n), then measure the device time of each kernel
  * of the step: the element-force kernel and the node update kernel are each
  * replayed back to back in a CUDA graph (the update on a saved copy of the

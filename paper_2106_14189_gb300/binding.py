@@ -39,7 +39,7 @@ EXPORTS = [
     "dj_mlp_get_grads", "dj_mlp_forward", "dj_mlp_loss_grad", "dj_mlp_adam_step",
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
     "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
-    "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply",
+    "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply", "dj_profile_kernels",
 ]
 
 
@@ -137,6 +137,7 @@ def lib():
         "dj_pod_fit": (C.c_int, [_P, C.c_longlong, C.c_int, C.c_int, _P, _P, _D, _P]),
         "dj_pod_project": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_linear_fit": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
+        "dj_profile_kernels": (C.c_int, [_P, C.c_int, _P, C.c_size_t, _P, _D, _D]),
         "dj_linear_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_float, C.c_float, _P, _P]),
         "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_residual_norms_static": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
@@ -517,6 +518,15 @@ def dj_pod_project(d_modes, d_mean, rows, r, d_X, cols, d_Q, stream=None):
 def dj_pod_expand(d_modes, d_mean, rows, r, d_Q, cols, d_X, stream=None):
     _check(lib().dj_pod_expand(d_modes, d_mean, int(rows), int(r), d_Q, int(cols), d_X, _stream(stream)),
            "dj_pod_expand")
+
+
+def dj_profile_kernels(h, launches, d_flush=None, flush_bytes=0, stream=None):
+    """(ms per force launch, ms per update launch), each launch timed alone
+    after an L2 eviction when a flush buffer is given."""
+    f, u = C.c_double(0), C.c_double(0)
+    _check(lib().dj_profile_kernels(h, int(launches), d_flush, int(flush_bytes), _stream(stream),
+                                    C.byref(f), C.byref(u)), "dj_profile_kernels", h)
+    return f.value, u.value
 
 
 def dj_linear_fit(d_X, d_Y, S, n_in, n_out, ridge, d_W, stream=None):

@@ -1170,6 +1170,53 @@ dj_status dj_run_n_profiled(dj_mesh* m, long long n, void* stream, double* ms_fo
   return DJ_OK;
 }
 
+dj_status dj_profile_kernels(dj_mesh* m, int launches, void* d_flush, size_t flush_bytes, void* stream,
+                             double* ms_force, double* ms_update) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (launches <= 0 || (d_flush && flush_bytes < 32)) return fail(m, DJ_ERR_INVALID_ARG, "bad launches or flush size");
+  cudaStream_t st = (cudaStream_t)stream;
+  float4 *sU = nullptr, *sV = nullptr, *sL = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t err = cudaMalloc(&sU, m->N * sizeof(float4));
+  if (err == cudaSuccess) err = cudaMalloc(&sV, m->N * sizeof(float4));
+  if (err == cudaSuccess && m->cmp) err = cudaMalloc(&sL, m->N * sizeof(float4));
+  if (err == cudaSuccess) err = cudaMemcpyAsync(sU, m->d_U, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(sV, m->d_V, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess && m->cmp)
+    err = cudaMemcpyAsync(sL, m->d_Ulo, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (err == cudaSuccess) err = cudaEventCreate(&e0);
+  if (err == cudaSuccess) err = cudaEventCreate(&e1);
+  double tf = 0.0, tu = 0.0;
+  for (int pass = 0; pass < 2 && err == cudaSuccess; ++pass) {
+    for (int i = 0; i < launches && err == cudaSuccess; ++i) {
+      if (d_flush) err = launch_l2_flush(d_flush, flush_bytes, st);
+      if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+      if (err == cudaSuccess)
+        err = pass == 0 ? launch_force_any(m, 0, st) : launch_node(NODE_UPDATE, m->cmp, node_args(m), st);
+      if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+      (pass == 0 ? tf : tu) += ms;
+    }
+  }
+  // restore the state (the update launches advanced U and V without new forces)
+  if (sU) cudaMemcpyAsync(m->d_U, sU, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (sV) cudaMemcpyAsync(m->d_V, sV, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  if (sL) cudaMemcpyAsync(m->d_Ulo, sL, m->N * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (err == cudaSuccess) err = e2;
+  for (void* p : {(void*)sU, (void*)sV, (void*)sL})
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : {e0, e1})
+    if (e) cudaEventDestroy(e);
+  if (err != cudaSuccess) return fail(m, DJ_ERR_CUDA, "kernel profile: %s", cudaGetErrorString(err));
+  if (ms_force) *ms_force = tf / launches;
+  if (ms_update) *ms_update = tu / launches;
+  return DJ_OK;
+}
+
 dj_status dj_sync(dj_mesh* m, void* stream) {
   dj_status s = need_ready(m);
   if (s) return s;

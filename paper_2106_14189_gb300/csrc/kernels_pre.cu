@@ -219,6 +219,17 @@ __global__ void node_mass_kernel(const int* __restrict__ sell, const int* __rest
   V[i] = make_float4(0.f, 0.f, 0.f, __int_as_float(bc_index[i]));
 }
 
+// reads every 16-byte word of a buffer (evicting what the L2 cache held); the
+// store never happens for a buffer that was zero-filled, it keeps the loads live
+__global__ void read_sweep_kernel(const uint4* __restrict__ p, long long n, unsigned int* sink) {
+  unsigned int acc = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint4 v = __ldcg(p + i);
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x9e3779b9u) *sink = acc;
+}
+
 __global__ void min_reduce_kernel(const double* __restrict__ v, int n, double* out) {
   __shared__ double sm[256];
   double m = DBL_MAX;
@@ -281,6 +292,18 @@ cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double
 }
 
 // out must hold 256 doubles; the host takes the min of those
+cudaError_t launch_l2_flush(void* buf, size_t bytes, cudaStream_t s) {
+  // write the first half, then read the second: the cache ends up holding clean
+  // lines of a buffer no kernel of the step touches
+  const size_t half = bytes / 2 / 16 * 16;
+  cudaError_t e = cudaMemsetAsync(buf, 0, half, s);
+  if (e != cudaSuccess) return e;
+  char* r = static_cast<char*>(buf) + half;
+  read_sweep_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const uint4*>(r), (long long)(half / 16),
+                                        reinterpret_cast<unsigned int*>(buf));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_min_reduce(const double* v, int n, double* out, cudaStream_t s) {
   min_reduce_kernel<<<256, 256, 0, s>>>(v, n, out);
   return cudaGetLastError();

@@ -1,13 +1,14 @@
 // Persistent element-force kernel with bulk asynchronous copies (TMA) for sm_103a.
 //
 // Each block walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The
-// per-tile segments (tile-major element table, local connectivity, local slot
-// index, node list, node offsets; see TileArgs) of the next tile are copied into
-// one of two shared-memory stages with cp.async.bulk while the current tile is
-// computed; an mbarrier per stage counts the arriving bytes.  Table reads are
-// then shared-memory loads at constant offsets.  Every wait is bounded: on
-// timeout the kernel records ERR_TIMEOUT, waits (bounded) for the copies it
-// still has in flight, and returns.
+// per-tile segments (tile-major element table, tile-local coordinates, local
+// connectivity, local slot index, node list, node offsets; see TileArgs) are
+// copied with cp.async.bulk into one of two shared-memory stages, two tiles
+// ahead; an mbarrier per stage counts the arriving bytes.  The nodal values of
+// the next tile are gathered with cp.async while the current tile's element
+// forces are reduced.  Every wait is bounded: on timeout the kernel records
+// ERR_TIMEOUT, waits once more (bounded) for the copy that timed out, the only
+// one in flight, and returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,15 +90,37 @@ __device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t
   bulk_copy(stage + L.lptr, t.lptr + (size_t)tile * (t.cap + 8), L.bytes - L.lptr, bar);
 }
 
+// cp.async of one 16-byte record global -> shared (completion per thread)
+__device__ __forceinline__ void async_copy16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// stage the tile's nodal U (and low parts) into su / sl with cp.async
+template <bool CMP>
+__device__ __forceinline__ void gather_nodes(const ForceArgs& a, const int* tnodes, int n_t, float4* su,
+                                             float4* sl, int tid, int T) {
+  for (int q = tid; q < n_t; q += T) {
+    const int gid = tnodes[q];
+    async_copy16(su + q, a.U + gid);
+    if (CMP) async_copy16(sl + q, a.Ulo + gid);
+  }
+}
+
+// Software pipeline per block, tiles blockIdx.x + k gridDim.x:
+//   bulk copies of a tile's segments are issued two tiles ahead (stages 0/1),
+//   the nodal gather of tile k+1 (cp.async) is in flight while tile k's
+//   element forces are reduced, and a tile costs two block barriers.
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t) {
   extern __shared__ __align__(128) char smem[];
   const StageLayout<NE> L(t);
-  const int T = t.T, tid = threadIdx.x;
+  const int T = t.T, tid = threadIdx.x, cap = t.cap;
   const uint32_t stage_bytes = (L.bytes + 127) & ~127u;
-  float4* su = reinterpret_cast<float4*>(smem + 2 * stage_bytes);
-  float4* sl = su + t.cap;
-  float4* sf4 = su + (CMP ? 2 : 1) * t.cap;  // NE T force records (slot a T + e)
+  float4* sbase = reinterpret_cast<float4*>(smem + 2 * stage_bytes);
+  float4* su2 = sbase;                              // [2][cap] staged U, by tile parity
+  float4* sl2 = sbase + 2 * cap;                    // [2][cap] staged low parts (compensated)
+  float4* sf4 = sbase + (CMP ? 4 : 2) * cap;        // NE T force records (slot a T + e)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sf4 + NE * T);
   advance_clock(a);
   if (tid == 0) {
@@ -106,38 +129,43 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int first = blockIdx.x;
+  const int first = blockIdx.x, stride = gridDim.x;
   if (first >= t.n_tiles) return;
-  if (tid == 0) issue_tile<NE>(a, t, L, smem, &bars[0], first);
-  int i = 0;
-  for (int tile = first; tile < t.n_tiles; tile += gridDim.x, ++i) {
-    const int s = i & 1;
-    const int next = tile + gridDim.x;
-    const bool has_next = next < t.n_tiles;
-    if (tid == 0 && has_next) issue_tile<NE>(a, t, L, smem + (s ^ 1) * stage_bytes, &bars[s ^ 1], next);
-    const bool ok = mbar_wait(&bars[s], (uint32_t)((i >> 1) & 1));
+  const bool second = first + stride < t.n_tiles;
+  if (tid == 0) {
+    issue_tile<NE>(a, t, L, smem, &bars[0], first);
+    if (second) issue_tile<NE>(a, t, L, smem + stage_bytes, &bars[1], first + stride);
+  }
+  // prologue: the first tile's nodes
+  {
+    const bool ok = mbar_wait(&bars[0], 0u);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         atomicOr(&a.st->err_flags, ERR_TIMEOUT);
-        if (has_next) mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+        if (second) mbar_wait(&bars[1], 0u);
       }
       return;
     }
+    const int* tn = reinterpret_cast<const int*>(smem + L.tnodes);
+    const int n0 = __ldg(t.tile_ptr + first + 1) - __ldg(t.tile_ptr + first);
+    gather_nodes<CMP>(a, tn, n0, su2, sl2, tid, T);
+    async_wait_all();
+    __syncthreads();
+  }
+  int i = 0;
+  for (int tile = first; tile < t.n_tiles; tile += stride, ++i) {
+    const int s = i & 1;
     const char* st = smem + s * stage_bytes;
     const float4* sx = reinterpret_cast<const float4*>(st + L.xloc);
     const float* tab = reinterpret_cast<const float*>(st + L.tab);
     const unsigned short* lconn = reinterpret_cast<const unsigned short*>(st + L.lconn);
     const unsigned short* lidx = reinterpret_cast<const unsigned short*>(st + L.lidx);
-    const int* tnodes = reinterpret_cast<const int*>(st + L.tnodes);
     const unsigned short* lptr = reinterpret_cast<const unsigned short*>(st + L.lptr);
+    const float4* su = su2 + s * cap;
+    const float4* sl = sl2 + s * cap;
     const int base = __ldg(t.tile_ptr + tile);
     const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
-    for (int q = tid; q < n_t; q += T) {
-      const int gid = tnodes[q];
-      su[q] = __ldg(a.U + gid);
-      if (CMP) sl[q] = __ldg(a.Ulo + gid);
-    }
-    __syncthreads();
+    // 1. element forces of this tile into shared memory
     const int e = tile * T + tid;
     if (e < a.E) {
       const auto ld = [&](int r) { return tab[r * T + tid]; };
@@ -151,11 +179,11 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
         const float4 x0 = sx[lc[0]];
         float xd[3][3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float4 xi = sx[lc[i + 1]];
-          xd[i][0] = xi.x - x0.x;
-          xd[i][1] = xi.y - x0.y;
-          xd[i][2] = xi.z - x0.z;
+        for (int r = 0; r < 3; ++r) {
+          const float4 xr = sx[lc[r + 1]];
+          xd[r][0] = xr.x - x0.x;
+          xd[r][1] = xr.y - x0.y;
+          xd[r][2] = xr.z - x0.z;
         }
         k.geometry(xd);
       } else {
@@ -177,7 +205,25 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
 #pragma unroll
       for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
     }
-    __syncthreads();
+    // 2. the next tile's segments must have landed; barrier: records complete
+    const int next = tile + stride;
+    const bool has_next = next < t.n_tiles;
+    const bool ok = has_next ? mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1)) : true;
+    if (__syncthreads_or(!ok)) {
+      // the only copy in flight is the one that timed out: give it one more
+      // bounded wait before the block's shared memory is released
+      if (tid == 0) {
+        atomicOr(&a.st->err_flags, ERR_TIMEOUT);
+        mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+      }
+      return;
+    }
+    // 3. gather the next tile's nodes (async) while this tile is reduced
+    if (has_next) {
+      const int* tn = reinterpret_cast<const int*>(smem + (s ^ 1) * stage_bytes + L.tnodes);
+      const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
+      gather_nodes<CMP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, tid, T);
+    }
     for (int q = tid; q < n_t; q += T) {
       const int p0 = lptr[q], p1 = lptr[q + 1];
       float fx = 0.f, fy = 0.f, fz = 0.f;
@@ -189,7 +235,10 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       }
       t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
     }
-    __syncthreads();  // stage s and the shared forces are reused by later tiles
+    async_wait_all();
+    // 4. barrier: stage s and the records are free, the next tile's nodes staged
+    __syncthreads();
+    if (tid == 0 && next + stride < t.n_tiles) issue_tile<NE>(a, t, L, smem + s * stage_bytes, &bars[s], next + stride);
   }
 }
 
@@ -197,7 +246,7 @@ template <int NE, bool CMP>
 size_t smem_bytes_t(const TileArgs& t) {
   const StageLayout<NE> L(t);
   const size_t stage = (L.bytes + 127) & ~size_t(127);
-  return 2 * stage + (size_t)(CMP ? 2 : 1) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) + 16;
+  return 2 * stage + (size_t)(CMP ? 4 : 2) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) + 16;
 }
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
