@@ -50,10 +50,10 @@ FALLBACK_HBM_GBS = 6800.0
 #   tiled assembly (default)
 #     force kernel : local connectivity 2 n_e + element table 4 n_consts
 #                    + local slot index 2 n_e
-#                    + per partial (P / E): node id 4 + local offsets 2 + force 12
-#                      (+ tile-local reference coordinates 16 for T4)
+#                    + per partial (P / E): node id 4 + destination 4 + local offsets 2
+#                      + force 12 (+ tile-local reference coordinates 16 for T4)
 #                    + u^n read once per node 16 N / E
-#     update kernel: per partial: gather index 4 + force 12; node state 64 N / E
+#     update kernel: per partial: force 12; per node: offsets 4 + node state 64
 #   slot assembly
 #     force kernel : connectivity 4 n_e + table 4 n_consts + forces 12 n_e + u^n 16 N / E
 #     update kernel: forces 12 n_e + gather index 4 n_e + node state 64 N / E
@@ -64,8 +64,8 @@ def algorithmic_bytes(info, n_nodes):
     if info.assembly != 0:
         pE = info.n_parts / E
         xloc = 16 if ne == 4 else 0
-        force = 2 * ne + 4 * info.n_consts + 2 * ne + (4 + 2 + 12 + xloc) * pE + 16 * nE
-        update = (4 + 12) * pE + 64 * nE
+        force = 2 * ne + 4 * info.n_consts + 2 * ne + (4 + 4 + 2 + 12 + xloc) * pE + 16 * nE
+        update = 12 * pE + (4 + 64) * nE
     else:
         force = 4 * ne + 4 * info.n_consts + 12 * ne + 16 * nE
         update = 12 * ne + 4 * ne + 64 * nE

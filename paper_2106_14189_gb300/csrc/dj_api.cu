@@ -92,6 +92,8 @@ struct dj_mesh {
   unsigned short* d_lptr = nullptr;
   unsigned short* d_lidx = nullptr;
   float4* d_xloc = nullptr;  // geometric T4 table: tile-local reference coordinates
+  int* d_pdst = nullptr;     // tiles: node-major position of each (tile, node) partial
+  int* d_node_ptr = nullptr; // tiles: N + 1 offsets of each node's partials
   int geometric = 0;
   float4* d_parts = nullptr;
   cudaStream_t cap_stream = nullptr;
@@ -149,7 +151,7 @@ void release_device(dj_mesh* m) {
   m->run_chunk = m->relax_k = 0;
   void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
-                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_save,
+                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_pdst, m->d_node_ptr, m->d_save,
                   m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
                   m->d_group_node_ptr};
   for (void* p : ptrs)
@@ -157,6 +159,7 @@ void release_device(dj_mesh* m) {
   m->d_tile_ptr = m->d_tile_nodes = nullptr;
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
   m->d_xloc = nullptr;
+  m->d_pdst = m->d_node_ptr = nullptr;
   m->d_parts = nullptr;
   m->d_Ulo = nullptr;
   m->d_save = nullptr;
@@ -306,6 +309,7 @@ TileArgs tile_args(dj_mesh* m) {
   t.lptr = m->d_lptr;
   t.lidx = m->d_lidx;
   t.xloc = m->d_xloc;
+  t.pdst = m->d_pdst;
   t.partials = m->d_parts;
   t.T = m->T;
   t.cap = m->cap;
@@ -327,6 +331,7 @@ NodeArgs node_args(dj_mesh* m) {
   NodeArgs a;
   a.sell = m->d_sell;
   a.chunk_ptr = m->d_chunk_ptr;
+  a.node_ptr = m->assembly != ASSEMBLY_SLOTS ? m->d_node_ptr : nullptr;
   a.slots = m->assembly != ASSEMBLY_SLOTS ? m->d_parts : m->d_slots;
   a.U = m->d_U;
   a.Ulo = m->d_Ulo;
@@ -665,8 +670,9 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   std::vector<int> chunk_ptr, sell;
   build_sell(cnt, csr, N, chunk_ptr, sell);  // node -> element slots (lumped mass, slot assembly)
   m->assembly = prm.assembly;
-  std::vector<int> tile_ptr, tile_nodes, tnodes_pad, part_chunk_ptr, part_sell;
+  std::vector<int> tile_ptr, tile_nodes, tnodes_pad;
   std::vector<float4> xloc_pad;
+  std::vector<int> node_ptr, pdst_pad;
   std::vector<unsigned short> lconn, lptr, lidx;
   if (m->assembly != ASSEMBLY_SLOTS) {
     const int T = prm.tile_size > 0 ? prm.tile_size : (ne == 4 ? 256 : 128);
@@ -728,13 +734,16 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
         }
       }
     }
-    // node -> partial ids, ascending tile
-    std::vector<int> pc(N + 1, 0);
-    for (int v : tile_nodes) pc[v + 1]++;
-    for (long long i = 0; i < N; ++i) pc[i + 1] += pc[i];
-    std::vector<int> plist(tile_nodes.size()), pf(pc.begin(), pc.end() - 1);
-    for (size_t q = 0; q < tile_nodes.size(); ++q) plist[pf[tile_nodes[q]]++] = (int)q;
-    build_sell(pc, plist, N, part_chunk_ptr, part_sell);
+    // node-major order of the partials: node i owns [node_ptr[i], node_ptr[i+1]),
+    // ascending tile; every (tile, local node) gets its destination there
+    node_ptr.assign(N + 1, 0);
+    for (int v : tile_nodes) node_ptr[v + 1]++;
+    for (long long i = 0; i < N; ++i) node_ptr[i + 1] += node_ptr[i];
+    std::vector<int> fillp(node_ptr.begin(), node_ptr.end() - 1);
+    pdst_pad.assign((size_t)m->n_tiles * m->cap, 0);
+    for (int t = 0; t < m->n_tiles; ++t)
+      for (int q = 0; q < tile_ptr[t + 1] - tile_ptr[t]; ++q)
+        pdst_pad[(size_t)t * m->cap + q] = fillp[tile_nodes[tile_ptr[t] + q]]++;
   }
   m->sell_entries = (long long)sell.size();
   // ---- prescribed nodes ----------------------------------------------------
@@ -795,12 +804,11 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     }
     CK(dalloc(m, &m->d_parts, (size_t)m->n_parts));
     CK(cudaMemset(m->d_parts, 0, (size_t)m->n_parts * sizeof(float4)));
-    CK(dalloc(m, &m->d_sell, part_sell.size() + 1));
-    CK(cudaMemcpy(m->d_sell, part_sell.data(), part_sell.size() * sizeof(int), cudaMemcpyHostToDevice));
-    CK(dalloc(m, &m->d_chunk_ptr, part_chunk_ptr.size()));
-    CK(cudaMemcpy(m->d_chunk_ptr, part_chunk_ptr.data(), part_chunk_ptr.size() * sizeof(int),
-                  cudaMemcpyHostToDevice));
-    m->sell_entries = (long long)part_sell.size();
+    CK(dalloc(m, &m->d_pdst, pdst_pad.size()));
+    CK(cudaMemcpy(m->d_pdst, pdst_pad.data(), pdst_pad.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(dalloc(m, &m->d_node_ptr, node_ptr.size()));
+    CK(cudaMemcpy(m->d_node_ptr, node_ptr.data(), node_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    m->sell_entries = (long long)node_ptr.size();
     CK(cudaMalloc(&d_mass_sell, (sell.size() + 1) * sizeof(int)));
     CK(cudaMemcpy(d_mass_sell, sell.data(), sell.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d_mass_chunk, chunk_ptr.size() * sizeof(int)));

@@ -63,6 +63,8 @@ struct ForceArgs {
 struct NodeArgs {
   const int* sell;        // sliced-ELL slot ids, chunks of 32 nodes, column-major
   const int* chunk_ptr;   // n_chunks + 1 offsets into sell
+  const int* node_ptr;    // tiled assembly: N + 1 offsets of each node's partials in `slots`
+                          // (node-major, ascending tile); nullptr: sliced-ELL gather
   const float4* slots;
   float4* U;              // in/out: U^n -> U^{n+1}; w = a_i
   float4* Ulo;            // compensated mode: low part of U
@@ -98,6 +100,7 @@ struct TileArgs {
   const unsigned short* lidx;   // n_tiles x T x n_e
   float4* partials;             // per (tile, node) force
   const float4* xloc;           // T4: n_tiles x cap reference coordinates minus the tile's first node
+  const int* pdst;              // n_tiles x cap: node-major position of each (tile, node) partial
   int T;
   int cap;                      // node capacity of a tile segment (multiple of 8, >= max n_t)
   int n_consts;

@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   const unsigned short* lp = sptr;
   const unsigned short* li = sidx;
   for (int q = tid; q < n_t; q += T) {
+    const int dst = __ldcs(t.pdst + (size_t)tile * t.cap + q);
     const int p0 = lp[q], p1 = lp[q + 1];
     float fx = 0.f, fy = 0.f, fz = 0.f;
     for (int p = p0; p < p1; ++p) {
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
       fy += v.y;
       fz += v.z;
     }
-    t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
+    t.partials[dst] = make_float4(fx, fy, fz, 0.f);
   }
 }
 
@@ -187,15 +188,26 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   const int chunk = i / SELL_C, lane = i % SELL_C;
   double num2 = 0.0, den2 = 0.0;
   if (i < a.N) {
-    const int beg = __ldg(a.chunk_ptr + chunk), end = __ldg(a.chunk_ptr + chunk + 1);
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int p = beg + lane; p < end; p += SELL_C) {
-      const int sid = __ldcs(a.sell + p);
-      if (sid >= 0) {
-        const float4 f = __ldcs(a.slots + sid);
+    if (a.node_ptr) {
+      // node-major partials: one contiguous run per node, ascending tile
+      const int beg = __ldg(a.node_ptr + i), end = __ldg(a.node_ptr + i + 1);
+      for (int p = beg; p < end; ++p) {
+        const float4 f = __ldcs(a.slots + p);
         fx += f.x;
         fy += f.y;
         fz += f.z;
+      }
+    } else {
+      const int beg = __ldg(a.chunk_ptr + chunk), end = __ldg(a.chunk_ptr + chunk + 1);
+      for (int p = beg + lane; p < end; p += SELL_C) {
+        const int sid = __ldcs(a.sell + p);
+        if (sid >= 0) {
+          const float4 f = __ldcs(a.slots + sid);
+          fx += f.x;
+          fy += f.y;
+          fz += f.z;
+        }
       }
     }
     if (a.R) {

@@ -2,7 +2,8 @@
 //
 // Each block walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The
 // per-tile segments (tile-major element table, tile-local coordinates, local
-// connectivity, local slot index, node list, node offsets; see TileArgs) are
+// connectivity, local slot index, node list, partial destinations, node
+// offsets; see TileArgs) are
 // copied with cp.async.bulk into one of two shared-memory stages, two tiles
 // ahead; an mbarrier per stage counts the arriving bytes.  The nodal values of
 // the next tile are gathered with cp.async while the current tile's element
@@ -64,14 +65,15 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 
 template <int NE>
 struct StageLayout {
-  uint32_t xloc, tab, lconn, lidx, tnodes, lptr, bytes;  // byte offsets inside a stage
+  uint32_t xloc, tab, lconn, lidx, tnodes, pdst, lptr, bytes;  // byte offsets inside a stage
   __device__ __host__ StageLayout(const TileArgs& t) {
     xloc = 0;  // T4 only: tile-local reference coordinates (geometric table)
     tab = xloc + (NE == 4 ? (uint32_t)t.cap * 16 : 0u);
     lconn = tab + (uint32_t)t.n_consts * t.T * 4;
     lidx = lconn + (uint32_t)t.T * NE * 2;
     tnodes = lidx + (uint32_t)t.T * NE * 2;
-    lptr = tnodes + (uint32_t)t.cap * 4;
+    pdst = tnodes + (uint32_t)t.cap * 4;
+    lptr = pdst + (uint32_t)t.cap * 4;
     bytes = lptr + (uint32_t)(t.cap + 8) * 2;
   }
 };
@@ -86,7 +88,8 @@ __device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t
   bulk_copy(stage + L.tab, a.consts + (size_t)tile * t.n_consts * t.T, L.lconn - L.tab, bar);
   bulk_copy(stage + L.lconn, t.lconn + (size_t)tile * t.T * NE, L.lidx - L.lconn, bar);
   bulk_copy(stage + L.lidx, t.lidx + (size_t)tile * t.T * NE, L.tnodes - L.lidx, bar);
-  bulk_copy(stage + L.tnodes, t.tnodes + (size_t)tile * t.cap, L.lptr - L.tnodes, bar);
+  bulk_copy(stage + L.tnodes, t.tnodes + (size_t)tile * t.cap, L.pdst - L.tnodes, bar);
+  bulk_copy(stage + L.pdst, t.pdst + (size_t)tile * t.cap, L.lptr - L.pdst, bar);
   bulk_copy(stage + L.lptr, t.lptr + (size_t)tile * (t.cap + 8), L.bytes - L.lptr, bar);
 }
 
@@ -161,6 +164,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     const unsigned short* lconn = reinterpret_cast<const unsigned short*>(st + L.lconn);
     const unsigned short* lidx = reinterpret_cast<const unsigned short*>(st + L.lidx);
     const unsigned short* lptr = reinterpret_cast<const unsigned short*>(st + L.lptr);
+    const int* pdst = reinterpret_cast<const int*>(st + L.pdst);
     const float4* su = su2 + s * cap;
     const float4* sl = sl2 + s * cap;
     const int base = __ldg(t.tile_ptr + tile);
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
         fy += v.y;
         fz += v.z;
       }
-      t.partials[base + q] = make_float4(fx, fy, fz, 0.f);
+      t.partials[pdst[q]] = make_float4(fx, fy, fz, 0.f);
     }
     async_wait_all();
     // 4. barrier: stage s and the records are free, the next tile's nodes staged
