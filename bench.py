@@ -433,7 +433,7 @@ def main():
     # cache: 256 MB written, then another 256 MB read (clean lines of a buffer
     # no step touches)
     flush_w = torch.empty(L2_FLUSH_BYTES // 2, dtype=torch.uint8, device="cuda")
-    flush_r = torch.zeros(L2_FLUSH_BYTES // 2, dtype=torch.uint8, device="cuda")
+    flush_r = torch.zeros(L2_FLUSH_BYTES // 8, dtype=torch.float32, device="cuda")
     flush_buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def l2_flush():

@@ -136,7 +136,7 @@ struct ElemConsts {
     ad[2][1] = J0[0][1] * J0[2][0] - J0[0][0] * J0[2][1];
     ad[2][2] = J0[0][0] * J0[1][1] - J0[0][1] * J0[1][0];
     const float det = J0[0][0] * ad[0][0] + J0[0][1] * ad[1][0] + J0[0][2] * ad[2][0];
-    r0 = __frcp_rn(det);
+    r0 = __fdividef(1.f, det);  // fast reciprocal, ~1 ulp: J carries FP32 rounding anyway
     const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
     for (int q = 0; q < 6; ++q)
@@ -162,26 +162,34 @@ struct HgConsts {
 template <bool FA, bool FB, bool MR>
 __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA, FB, MR>& k,
                                               bool& bad) {
-  const float D = det3(tJ);
+  const M3 A = adj3(tJ);  // det(tJ) tJ^-1
+  const float D = tJ.m[0][0] * A.m[0][0] + tJ.m[0][1] * A.m[1][0] + tJ.m[0][2] * A.m[2][0];
   const float J = D * k.r0;  // Eq. 12
   bad = !(D > 0.f);
   const float Jm23 = __powf(J, -2.f / 3.f);  // J^-2/3 (fast exp2/log2 intrinsics, ~1e-7 relative)
-  // g = tJ tJ^T (Eq. 17), symmetric
-  float g[6];
-  g[0] = tJ.m[0][0] * tJ.m[0][0] + tJ.m[0][1] * tJ.m[0][1] + tJ.m[0][2] * tJ.m[0][2];
-  g[1] = tJ.m[1][0] * tJ.m[1][0] + tJ.m[1][1] * tJ.m[1][1] + tJ.m[1][2] * tJ.m[1][2];
-  g[2] = tJ.m[2][0] * tJ.m[2][0] + tJ.m[2][1] * tJ.m[2][1] + tJ.m[2][2] * tJ.m[2][2];
-  g[3] = tJ.m[0][0] * tJ.m[1][0] + tJ.m[0][1] * tJ.m[1][1] + tJ.m[0][2] * tJ.m[1][2];
-  g[4] = tJ.m[0][0] * tJ.m[2][0] + tJ.m[0][1] * tJ.m[2][1] + tJ.m[0][2] * tJ.m[2][2];
-  g[5] = tJ.m[1][0] * tJ.m[2][0] + tJ.m[1][1] * tJ.m[2][1] + tJ.m[1][2] * tJ.m[2][2];
-
-  const float gP = frob_sym(g, k.P);  // = mu 0V I1
+  // T = tJ^T P, and P : g = tr(tJ^T P tJ) = T : tJ^T  (g = tJ tJ^T, Eq. 17)
   M3 T;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
+    for (int j = 0; j < 3; ++j)
+      T.m[i][j] = tJ.m[0][i] * sym_at(k.P, 0, j) + tJ.m[1][i] * sym_at(k.P, 1, j) +
+                  tJ.m[2][i] * sym_at(k.P, 2, j);
+  float gP = 0.f;  // = mu 0V I1
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) gP = fmaf(T.m[i][j], tJ.m[j][i], gP);
   float vol_over_D = -gP / 3.f;  // multiplies Jm23 adj / D
+  float g[6];
+  if (FA || FB || MR) {
+    g[0] = tJ.m[0][0] * tJ.m[0][0] + tJ.m[0][1] * tJ.m[0][1] + tJ.m[0][2] * tJ.m[0][2];
+    g[1] = tJ.m[1][0] * tJ.m[1][0] + tJ.m[1][1] * tJ.m[1][1] + tJ.m[1][2] * tJ.m[1][2];
+    g[2] = tJ.m[2][0] * tJ.m[2][0] + tJ.m[2][1] * tJ.m[2][1] + tJ.m[2][2] * tJ.m[2][2];
+    g[3] = tJ.m[0][0] * tJ.m[1][0] + tJ.m[0][1] * tJ.m[1][1] + tJ.m[0][2] * tJ.m[1][2];
+    g[4] = tJ.m[0][0] * tJ.m[2][0] + tJ.m[0][1] * tJ.m[2][1] + tJ.m[0][2] * tJ.m[2][2];
+    g[5] = tJ.m[1][0] * tJ.m[2][0] + tJ.m[1][1] * tJ.m[2][1] + tJ.m[1][2] * tJ.m[2][2];
+  }
   if (FA) {
     const float gQ = frob_sym(g, k.Qa);
     const float psi = Jm23 * gQ * k.sa - 1.f;  // I4bar - 1 (Eq. 31, Table 1)
@@ -194,7 +202,6 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
     add_tJT_sym(T, tJ, k.Qb, psi);
     vol_over_D -= psi * gQ / 3.f;
   }
-  add_tJT_sym(T, tJ, k.P, 1.f);
   float mr_vol = 0.f;
   if (MR) {
     // C01 g_hat^T I2m = gm (g:P P - P g P), gm = C01 / (2 C10^2 0V)   (Eq. 39-42)
@@ -222,7 +229,6 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
     add_tJT_sym(T, tJ, S2, Jm23);                               // extra J^-2/3 of Eq. 39
     mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
   }
-  const M3 A = adj3(tJ);
   const float invD = __fdividef(1.f, D);
   const float ca = (Jm23 * vol_over_D + mr_vol) * invD + k.kV * (J - 1.f) * k.r0;
   M3 F;
@@ -538,6 +544,28 @@ __device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemC
     tet4_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
   else
     hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
+}
+
+// Sum of the force records sf4[li[p]], p = p0 .. p1-1, in that order.  Four
+// slot ids and four records are loaded before they are added, so a node's
+// list costs about a quarter of the dependent shared-memory round trips; the
+// additions keep the sequential order (bit-identical to the plain loop).
+__device__ __forceinline__ float4 sum_records(const float4* sf4, const unsigned short* li, int p0, int p1) {
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  int p = p0;
+  for (; p + 4 <= p1; p += 4) {
+    const int i0 = li[p], i1 = li[p + 1], i2 = li[p + 2], i3 = li[p + 3];
+    const float4 v0 = sf4[i0], v1 = sf4[i1], v2 = sf4[i2], v3 = sf4[i3];
+    fx += v0.x; fy += v0.y; fz += v0.z;
+    fx += v1.x; fy += v1.y; fz += v1.z;
+    fx += v2.x; fy += v2.y; fz += v2.z;
+    fx += v3.x; fy += v3.y; fz += v3.z;
+  }
+  for (; p < p1; ++p) {
+    const float4 v = sf4[li[p]];
+    fx += v.x; fy += v.y; fz += v.z;
+  }
+  return make_float4(fx, fy, fz, 0.f);
 }
 
 // d_b = u_b - u_0 from the nodal records (hi, lo)

@@ -170,15 +170,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   const unsigned short* li = sidx;
   for (int q = tid; q < n_t; q += T) {
     const int dst = __ldcs(t.pdst + (size_t)tile * t.cap + q);
-    const int p0 = lp[q], p1 = lp[q + 1];
-    float fx = 0.f, fy = 0.f, fz = 0.f;
-    for (int p = p0; p < p1; ++p) {
-      const float4 v = sf4[li[p]];
-      fx += v.x;
-      fy += v.y;
-      fz += v.z;
-    }
-    t.partials[dst] = make_float4(fx, fy, fz, 0.f);
+    t.partials[dst] = sum_records(sf4, li, lp[q], lp[q + 1]);
   }
 }
 
@@ -188,6 +180,12 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   const int chunk = i / SELL_C, lane = i % SELL_C;
   double num2 = 0.0, den2 = 0.0;
   if (i < a.N) {
+    // node state first: independent of the force gather, so these loads are in
+    // flight while the partials arrive
+    const float4 V = a.V[i];
+    const float4 U = (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID) ? a.U[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 L = (CMP && (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID)) ? a.Ulo[i]
+                                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (a.node_ptr) {
       // node-major partials: one contiguous run per node, ascending tile
@@ -217,7 +215,6 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       fz -= r.z;
     }
     // now f = F_int - R
-    const float4 V = a.V[i];
     const int bc = __float_as_int(V.w);
     if (MODE == NODE_FORCE_ONLY || MODE == NODE_RESID_ONLY) {
       if (!isfinite(fx + fy + fz)) flag_nonfinite(a.st, i);
@@ -234,7 +231,6 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
         else num2 += f3[q] * f3[q];
       }
     } else {
-      const float4 U = a.U[i];
       const float ai = U.w;
       // velocity form of the central difference: D^{n+1} = a (R - F) + (b - 1) D^n
       const float bm1 = a.bm1_node ? __ldg(a.bm1_node + i) : a.bm1;
@@ -242,7 +238,6 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       const float uh[3] = {U.x, U.y, U.z};
       float nh[3], nl[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
       if (CMP) {
-        const float4 L = a.Ulo[i];
         ul[0] = L.x;
         ul[1] = L.y;
         ul[2] = L.z;

@@ -228,17 +228,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
       gather_nodes<CMP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, tid, T);
     }
-    for (int q = tid; q < n_t; q += T) {
-      const int p0 = lptr[q], p1 = lptr[q + 1];
-      float fx = 0.f, fy = 0.f, fz = 0.f;
-      for (int p = p0; p < p1; ++p) {
-        const float4 v = sf4[lidx[p]];
-        fx += v.x;
-        fy += v.y;
-        fz += v.z;
-      }
-      t.partials[pdst[q]] = make_float4(fx, fy, fz, 0.f);
-    }
+    for (int q = tid; q < n_t; q += T) t.partials[pdst[q]] = sum_records(sf4, lidx, lptr[q], lptr[q + 1]);
     async_wait_all();
     // 4. barrier: stage s and the records are free, the next tile's nodes staged
     __syncthreads();
