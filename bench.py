@@ -51,7 +51,7 @@ FALLBACK_HBM_GBS = 6800.0
 #     force kernel : local connectivity 2 n_e + element table 4 n_consts
 #                    + local slot index 2 n_e
 #                    + per partial (P / E): node id 4 + destination 4 + local offsets 2
-#                      + force 12 (+ tile-local reference coordinates 16 for T4)
+#                      + force 12 + tile-local reference coordinates 16
 #                    + u^n read once per node 16 N / E
 #     update kernel: per partial: force 12; per node: offsets 4 + node state 64
 #   slot assembly
@@ -63,8 +63,7 @@ def algorithmic_bytes(info, n_nodes):
     nE = n_nodes / E
     if info.assembly != 0:
         pE = info.n_parts / E
-        xloc = 16 if ne == 4 else 0
-        force = 2 * ne + 4 * info.n_consts + 2 * ne + (4 + 4 + 2 + 12 + xloc) * pE + 16 * nE
+        force = 2 * ne + 4 * info.n_consts + 2 * ne + (4 + 4 + 2 + 12 + 16) * pE + 16 * nE
         update = 12 * pE + (4 + 64) * nE
     else:
         force = 4 * ne + 4 * info.n_consts + 12 * ne + 16 * nE

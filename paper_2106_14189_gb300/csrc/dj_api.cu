@@ -91,7 +91,7 @@ struct dj_mesh {
   unsigned short* d_lconn = nullptr;
   unsigned short* d_lptr = nullptr;
   unsigned short* d_lidx = nullptr;
-  float4* d_xloc = nullptr;  // geometric T4 table: tile-local reference coordinates
+  float4* d_xloc = nullptr;  // geometric table: tile-local reference coordinates
   int* d_pdst = nullptr;     // tiles: node-major position of each (tile, node) partial
   int* d_node_ptr = nullptr; // tiles: N + 1 offsets of each node's partials
   int geometric = 0;
@@ -650,14 +650,15 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   } else {
     m->variant = VAR_NH;
   }
-  // tiled T4 meshes rebuild 0J, det 0J and P from staged reference coordinates
-  m->geometric = ne == 4 && prm.assembly != ASSEMBLY_SLOTS;
+  // tiled meshes rebuild 0J, det 0J, P (and the H8 hourglass c) from staged
+  // reference coordinates
+  m->geometric = prm.assembly != ASSEMBLY_SLOTS;
   int nc = m->geometric ? KG_COMMON : K_COMMON;
   m->off_fa = m->off_fb = m->off_mr = m->off_hg = -1;
   if (fa) { m->off_fa = nc; nc += 7; }
   if (fb) { m->off_fb = nc; nc += 7; }
   if (mr) { m->off_mr = nc; nc += 1; }
-  if (ne == 8) { m->off_hg = nc; nc += 13; }
+  if (ne == 8) { m->off_hg = nc; nc += m->geometric ? 1 : 13; }
   m->n_consts = nc;
   m->threads_force = ne == 4 ? 256 : 128;
   // ---- gather index: node -> slots (ascending element, local node) ---------

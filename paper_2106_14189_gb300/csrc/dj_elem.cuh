@@ -156,6 +156,11 @@ struct HgConsts {
       for (int j = 0; j < 3; ++j) cc[q][j] = ld(off + 3 * q + j);
     k = ld(off + 12);
   }
+  // geometric table: only k is stored; c is formed from reference coordinates
+  template <class Ld>
+  __device__ __forceinline__ void load_k(Ld ld, int off) {
+    k = ld(off);
+  }
 };
 
 // F = J^-2/3 tJ^T (P + psi_a Q_a + psi_b Q_b + MR) + coefficient * adj(tJ)   (Table 3)
@@ -537,6 +542,111 @@ __device__ __forceinline__ void hex8_forces(const float (&d)[8][3], const ElemCo
                 H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
 }
 
+// The same H8 forces, consuming the element's nodes one at a time and emitting
+// each node's force as soon as it is known, so that neither the 24 nodal
+// differences nor the 24 forces are live at once (register pressure sets the
+// occupancy of the H8 kernels):
+//   ld(b, hi, lo)  nodal displacement of local node b (low part: compensated)
+//   ldx(b)         reference coordinates (GEO: 0J = H_xi X, Eq. 3, and the
+//                  hourglass c_{alpha j} = h_alpha . X_j are formed from them)
+//   out(b, f)      force on local node b
+// Summation orders equal those of hex8_forces.
+template <bool FA, bool FB, bool MR, bool CMP, bool GEO, class Ld, class LdX, class Out>
+__device__ __forceinline__ void hex8_forces_stream(Ld ld, LdX ldx, ElemConsts<FA, FB, MR>& k, HgConsts& hg,
+                                                   Out out, bool& inv) {
+  float s[3][3], hu[4][3], jx[3][3], cx[4][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) s[i][j] = jx[i][j] = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) hu[q][j] = cx[q][j] = 0.f;
+  }
+  float4 h0, l0;
+  ld(0, h0, l0);
+  float4 x0 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (GEO) x0 = ldx(0);
+#pragma unroll
+  for (int b = 1; b < 8; ++b) {
+    float4 hb, lb;
+    ld(b, hb, lb);
+    const float db[3] = {node_diff<CMP>(hb.x, h0.x, lb.x, l0.x), node_diff<CMP>(hb.y, h0.y, lb.y, l0.y),
+                         node_diff<CMP>(hb.z, h0.z, lb.z, l0.z)};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s[i][j] += XI8[b][i] * db[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) hu[q][j] += H8[q][b] * db[j];
+    }
+    if (GEO) {
+      const float4 xb = ldx(b);
+      const float dx[3] = {xb.x - x0.x, xb.y - x0.y, xb.z - x0.z};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) jx[i][j] += XI8[b][i] * dx[j];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cx[q][j] += H8[q][b] * dx[j];
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) s[i][j] *= 0.125f;
+  if (GEO) {
+    float xd[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) xd[i][j] = 0.125f * jx[i][j];
+    k.geometry(xd);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) hg.cc[q][j] = cx[q][j];
+  }
+  M3 A, B;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      A.m[i][j] = k.J0[i][j];
+      B.m[i][j] = s[i][j];  // Eq. 11
+    }
+  const M3 F = force_matrix<FA, FB, MR, CMP>(A, B, k, inv);
+  const M3 J0a = adj3(A);
+  float eq[4][3];  // e_{alpha,i} = sum_j c_{alpha j} (0J^-1)_{j i}
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      eq[q][i] = k.r0 * (hg.cc[q][0] * J0a.m[0][i] + hg.cc[q][1] * J0a.m[1][i] + hg.cc[q][2] * J0a.m[2][i]);
+  float H[4][3];  // k q_alpha
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      H[q][j] = hg.k * (hu[q][j] - (eq[q][0] * s[0][j] + eq[q][1] * s[1][j] + eq[q][2] * s[2][j]));
+  float G[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      G[i][j] = 0.125f * (F.m[j][i] - (eq[0][i] * H[0][j] + eq[1][i] * H[1][j] + eq[2][i] * H[2][j] +
+                                       eq[3][i] * H[3][j]));
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    float fb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      fb[j] = XI8[b][0] * G[0][j] + XI8[b][1] * G[1][j] + XI8[b][2] * G[2][j] + H8[0][b] * H[0][j] +
+              H8[1][b] * H[1][j] + H8[2][b] * H[2][j] + H8[3][b] * H[3][j];
+    out(b, make_float4(fb[0], fb[1], fb[2], 0.f));
+  }
+}
+
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 __device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemConsts<FA, FB, MR>& k,
                                             const ElemExtra<NE>& x, float (&f)[NE][3], bool& inv) {
@@ -546,26 +656,46 @@ __device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemC
     hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
 }
 
-// Sum of the force records sf4[li[p]], p = p0 .. p1-1, in that order.  Four
-// slot ids and four records are loaded before they are added, so a node's
-// list costs about a quarter of the dependent shared-memory round trips; the
-// additions keep the sequential order (bit-identical to the plain loop).
-__device__ __forceinline__ float4 sum_records(const float4* sf4, const unsigned short* li, int p0, int p1) {
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  int p = p0;
-  for (; p + 4 <= p1; p += 4) {
-    const int i0 = li[p], i1 = li[p + 1], i2 = li[p + 2], i3 = li[p + 3];
-    const float4 v0 = sf4[i0], v1 = sf4[i1], v2 = sf4[i2], v3 = sf4[i3];
-    fx += v0.x; fy += v0.y; fz += v0.z;
-    fx += v1.x; fy += v1.y; fz += v1.z;
-    fx += v2.x; fy += v2.y; fz += v2.z;
-    fx += v3.x; fy += v3.y; fz += v3.z;
+// Per-tile reduction of the force records into one partial per local node,
+// spread over the whole block: G consecutive lanes share a node (G = the
+// largest of 1, 2, 4, 8 with G n_t <= T), lane r adds the node's records
+// r, r + G, r + 2G, ... in order, and the G lane sums are combined by an xor
+// butterfly (fixed order).  All lanes of a warp take part in every butterfly.
+// store(q, f) receives node q's partial.  The choice of G depends only on n_t
+// and T, so every kernel that uses this gives bit-identical partials.
+template <int G, class Store>
+__device__ __forceinline__ void reduce_tile_g(const float4* sf4, const unsigned short* li,
+                                              const unsigned short* lp, int n_t, int tid, int T, Store store) {
+  const int sub = tid % G, per_pass = T / G;
+  for (int q0 = 0; q0 < n_t; q0 += per_pass) {
+    const int q = q0 + tid / G;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
+    if (q < n_t) {
+      const int p1 = lp[q + 1];
+      for (int p = lp[q] + sub; p < p1; p += G) {
+        const float4 v = sf4[li[p]];
+        fx += v.x;
+        fy += v.y;
+        fz += v.z;
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, o);
+      fy += __shfl_xor_sync(0xffffffffu, fy, o);
+      fz += __shfl_xor_sync(0xffffffffu, fz, o);
+    }
+    if (q < n_t && sub == 0) store(q, make_float4(fx, fy, fz, 0.f));
   }
-  for (; p < p1; ++p) {
-    const float4 v = sf4[li[p]];
-    fx += v.x; fy += v.y; fz += v.z;
-  }
-  return make_float4(fx, fy, fz, 0.f);
+}
+
+template <class Store>
+__device__ __forceinline__ void reduce_tile(const float4* sf4, const unsigned short* li, const unsigned short* lp,
+                                            int n_t, int tid, int T, Store store) {
+  if (8 * n_t <= T) reduce_tile_g<8>(sf4, li, lp, n_t, tid, T, store);
+  else if (4 * n_t <= T) reduce_tile_g<4>(sf4, li, lp, n_t, tid, T, store);
+  else if (2 * n_t <= T) reduce_tile_g<2>(sf4, li, lp, n_t, tid, T, store);
+  else reduce_tile_g<1>(sf4, li, lp, n_t, tid, T, store);
 }
 
 // d_b = u_b - u_0 from the nodal records (hi, lo)

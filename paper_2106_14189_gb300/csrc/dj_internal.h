@@ -26,11 +26,13 @@ namespace dj {
 //   H8 hourglass: c_{alpha j} = h_alpha . X_{:,j} (12 floats, alpha-major), k
 // ---------------------------------------------------------------------------
 enum { K_J0 = 0, K_P = 9, K_KV = 15, K_R0 = 16, K_COMMON = 17 };
-// Geometric T4 table (tiled assembly of T4 meshes): the common part is only
+// Geometric table (tiled assembly): the common part is only
 //   0      c_P = mu 0V / det(0J)^2, so that P = c_P adj(0J)^T adj(0J)  (Eq. 37)
 //   1      kappa 0V
 // and 0J, det 0J and P are rebuilt per step from tile-local reference
-// coordinates (TileArgs::xloc); the optional blocks follow as above.
+// coordinates (TileArgs::xloc); the optional blocks follow as above, except
+// that the H8 hourglass block holds k alone (c_{alpha j} = h_alpha . X_j is
+// rebuilt from the coordinates too).
 enum { KG_CP = 0, KG_KV = 1, KG_COMMON = 2 };
 
 // Device-resident stepping state, one per mesh.
@@ -99,7 +101,7 @@ struct TileArgs {
   const unsigned short* lptr;   // n_tiles x (cap + 8)
   const unsigned short* lidx;   // n_tiles x T x n_e
   float4* partials;             // per (tile, node) force
-  const float4* xloc;           // T4: n_tiles x cap reference coordinates minus the tile's first node
+  const float4* xloc;           // n_tiles x cap reference coordinates minus the tile's first node
   const int* pdst;              // n_tiles x cap: node-major position of each (tile, node) partial
   int T;
   int cap;                      // node capacity of a tile segment (multiple of 8, >= max n_t)
@@ -156,7 +158,7 @@ struct PreArgs {
   double hg_coeff;
   int tile_T;    // > 0: tile-major table with tiles of tile_T elements
   int n_consts;
-  int geometric; // 1: geometric T4 table (KG_*), else the full table (K_*)
+  int geometric; // 1: geometric table (KG_*, tiled assembly), else the full table (K_*)
 };
 cudaError_t launch_precompute_elements(const PreArgs& a, cudaStream_t s);
 // dt_node: per-node time step (grouped meshes) or nullptr to use dt

@@ -173,10 +173,10 @@ __global__ void precompute_elements_kernel(PreArgs a) {
         double s = 0.0;
         for (int b = 0; b < 8; ++b) s += H8D[q][b] * Xe[b][j];
         cq[q][j] = s;
-        put(a, t, a.off_hg + 3 * q + j, e, s);
+        if (!a.geometric) put(a, t, a.off_hg + 3 * q + j, e, s);
       }
     const double khg = a.hg_coeff * (kappa + 4.0 / 3.0 * mu) * V0 * sumB2 / 8.0;
-    put(a, t, a.off_hg + 12, e, khg);
+    put(a, t, a.off_hg + (a.geometric ? 0 : 12), e, khg);
     double gam[4][8];
     for (int q = 0; q < 4; ++q)
       for (int b = 0; b < 8; ++b)

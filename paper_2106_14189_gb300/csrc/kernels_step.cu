@@ -41,8 +41,6 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
   const auto ld = [&](int r) { return __ldcs(c + (size_t)r * E_pad + e); };
   ElemConsts<FA, FB, MR> k;
   k.load(ld, a);
-  ElemExtra<NE> x;
-  if constexpr (NE == 8) x.load(ld, a.off_hg);
   int nid[NE];
   {
     const int4 n0 = __ldcs(a.conn + (NE / 4) * (size_t)e);
@@ -52,20 +50,33 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
       nid[4] = n1.x; nid[5] = n1.y; nid[6] = n1.z; nid[7] = n1.w;
     }
   }
-  float4 h[NE], l[NE];
-#pragma unroll
-  for (int b = 0; b < NE; ++b) {
-    h[b] = __ldg(a.U + nid[b]);
-    l[b] = CMP ? __ldg(a.Ulo + nid[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-  float d[NE][3];
-  node_deltas<NE, CMP>(h, l, d);
-  float f[NE][3];
   bool inv;
-  elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
-  flag_inverted(a.st, e, inv);
+  if constexpr (NE == 8) {
+    HgConsts hg;
+    hg.load(ld, a.off_hg);
+    const auto ldn = [&](int b, float4& h, float4& l) {
+      h = __ldg(a.U + nid[b]);
+      l = CMP ? __ldg(a.Ulo + nid[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    const auto ldx = [&](int) { return make_float4(0.f, 0.f, 0.f, 0.f); };
+    const auto out = [&](int b, float4 f) { a.slots[(size_t)b * E_pad + e] = f; };
+    hex8_forces_stream<FA, FB, MR, CMP, false>(ldn, ldx, k, hg, out, inv);
+  } else {
+    float4 h[NE], l[NE];
 #pragma unroll
-  for (int b = 0; b < NE; ++b) a.slots[(size_t)b * E_pad + e] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
+    for (int b = 0; b < NE; ++b) {
+      h[b] = __ldg(a.U + nid[b]);
+      l[b] = CMP ? __ldg(a.Ulo + nid[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float d[NE][3];
+    node_deltas<NE, CMP>(h, l, d);
+    float f[NE][3];
+    ElemExtra<NE> x;
+    elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
+#pragma unroll
+    for (int b = 0; b < NE; ++b) a.slots[(size_t)b * E_pad + e] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
+  }
+  flag_inverted(a.st, e, inv);
 }
 
 // Tiled assembly: block = tile of T elements.  The tile's unique nodes are
@@ -84,11 +95,10 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   advance_clock(a);
   const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
   const int S = NE * T;  // slots per tile
-  constexpr bool GEO = NE == 4;                  // geometric T4 table, 0J from staged coordinates
-  constexpr int NSTAGE = 1 + (CMP ? 1 : 0) + (GEO ? 1 : 0);
+  constexpr int NSTAGE = 2 + (CMP ? 1 : 0);  // U, (low parts), reference coordinates
   float4* su = smem4;                            // staged U (high part)
   float4* sl = smem4 + t.cap;                    // staged low part (compensated)
-  float4* sx = smem4 + (NSTAGE - 1) * t.cap;     // staged tile-local reference coordinates (T4)
+  float4* sx = smem4 + (NSTAGE - 1) * t.cap;     // staged tile-local reference coordinates
   float4* sf4 = smem4 + NSTAGE * t.cap;          // S force records (slot a T + e)
   // the tile's reduction lists, staged with the inputs so that their latency
   // overlaps the node gather instead of following the element math
@@ -111,15 +121,14 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   const bool valid = e < a.E;
   const float* __restrict__ c = a.consts;
   ElemConsts<FA, FB, MR> k;
-  ElemExtra<NE> x;
+  HgConsts hg;
   unsigned short lc[NE];
   if (valid) {
     // tile-major table: row r of element (tile, tid) at ((tile n_consts) + r) T + tid
     const float* ct = c + (size_t)tile * t.n_consts * T + tid;
     const auto ld = [&](int r) { return __ldcs(ct + (size_t)r * T); };
-    if constexpr (GEO) k.load_geometric(ld, a);
-    else k.load(ld, a);
-    if constexpr (NE == 8) x.load(ld, a.off_hg);
+    k.load_geometric(ld, a);
+    if constexpr (NE == 8) hg.load_k(ld, a.off_hg);
     if constexpr (NE == 4) {
       const ushort4 v = __ldcs(reinterpret_cast<const ushort4*>(t.lconn) + e);
       lc[0] = v.x; lc[1] = v.y; lc[2] = v.z; lc[3] = v.w;
@@ -132,13 +141,22 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   }
   for (int q = tid; q < n_t; q += T) {
     const int gid = __ldg(t.tnodes + (size_t)tile * t.cap + q);
-    if (GEO) sx[q] = __ldcs(t.xloc + (size_t)tile * t.cap + q);
+    sx[q] = __ldcs(t.xloc + (size_t)tile * t.cap + q);
     su[q] = __ldg(a.U + gid);
     if (CMP) sl[q] = __ldg(a.Ulo + gid);
   }
   __syncthreads();
   if (valid) {
-    if constexpr (GEO) {
+    bool inv;
+    if constexpr (NE == 8) {
+      const auto ldn = [&](int b, float4& h, float4& l) {
+        h = su[lc[b]];
+        l = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      };
+      const auto ldx = [&](int b) { return sx[lc[b]]; };
+      const auto out = [&](int b, float4 f) { sf4[b * T + tid] = f; };
+      hex8_forces_stream<FA, FB, MR, CMP, true>(ldn, ldx, k, hg, out, inv);
+    } else {
       const float4 x0 = sx[lc[0]];
       float xd[3][3];
 #pragma unroll
@@ -149,29 +167,27 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
         xd[i][2] = xi.z - x0.z;
       }
       k.geometry(xd);
-    }
-    float4 h[NE], l[NE];
+      float4 h[NE], l[NE];
 #pragma unroll
-    for (int b = 0; b < NE; ++b) {
-      h[b] = su[lc[b]];
-      l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int b = 0; b < NE; ++b) {
+        h[b] = su[lc[b]];
+        l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      float d[NE][3];
+      node_deltas<NE, CMP>(h, l, d);
+      float f[NE][3];
+      ElemExtra<NE> x;
+      elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
+#pragma unroll
+      for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
     }
-    float d[NE][3];
-    node_deltas<NE, CMP>(h, l, d);
-    float f[NE][3];
-    bool inv;
-    elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
     flag_inverted(a.st, e, inv);
-#pragma unroll
-    for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
   }
   __syncthreads();
   const unsigned short* lp = sptr;
   const unsigned short* li = sidx;
-  for (int q = tid; q < n_t; q += T) {
-    const int dst = __ldcs(t.pdst + (size_t)tile * t.cap + q);
-    t.partials[dst] = sum_records(sf4, li, lp[q], lp[q + 1]);
-  }
+  const int* pd = t.pdst + (size_t)tile * t.cap;
+  reduce_tile(sf4, li, lp, n_t, tid, T, [&](int q, float4 f) { t.partials[__ldcs(pd + q)] = f; });
 }
 
 template <int MODE, bool CMP>
@@ -371,7 +387,7 @@ cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t nstage = 1 + (CMP ? 1 : 0) + (NE == 4 ? 1 : 0);
+  const size_t nstage = 2 + (CMP ? 1 : 0);
   const size_t smem = nstage * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) +
                       (size_t)NE * t.T * 2 + (size_t)(t.cap + 8) * 2;
   static bool attr_set = false;

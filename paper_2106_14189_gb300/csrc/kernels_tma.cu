@@ -67,8 +67,8 @@ template <int NE>
 struct StageLayout {
   uint32_t xloc, tab, lconn, lidx, tnodes, pdst, lptr, bytes;  // byte offsets inside a stage
   __device__ __host__ StageLayout(const TileArgs& t) {
-    xloc = 0;  // T4 only: tile-local reference coordinates (geometric table)
-    tab = xloc + (NE == 4 ? (uint32_t)t.cap * 16 : 0u);
+    xloc = 0;  // tile-local reference coordinates (geometric table)
+    tab = xloc + (uint32_t)t.cap * 16;
     lconn = tab + (uint32_t)t.n_consts * t.T * 4;
     lidx = lconn + (uint32_t)t.T * NE * 2;
     tnodes = lidx + (uint32_t)t.T * NE * 2;
@@ -84,7 +84,7 @@ __device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t
                                            char* stage, uint64_t* bar, int tile) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_arrive_expect_tx(bar, L.bytes);
-  if (NE == 4) bulk_copy(stage + L.xloc, t.xloc + (size_t)tile * t.cap, L.tab - L.xloc, bar);
+  bulk_copy(stage + L.xloc, t.xloc + (size_t)tile * t.cap, L.tab - L.xloc, bar);
   bulk_copy(stage + L.tab, a.consts + (size_t)tile * t.n_consts * t.T, L.lconn - L.tab, bar);
   bulk_copy(stage + L.lconn, t.lconn + (size_t)tile * t.T * NE, L.lidx - L.lconn, bar);
   bulk_copy(stage + L.lidx, t.lidx + (size_t)tile * t.T * NE, L.tnodes - L.lidx, bar);
@@ -174,12 +174,22 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     if (e < a.E) {
       const auto ld = [&](int r) { return tab[r * T + tid]; };
       ElemConsts<FA, FB, MR> k;
-      ElemExtra<NE> x;
       int lc[NE];
 #pragma unroll
       for (int b = 0; b < NE; ++b) lc[b] = lconn[tid * NE + b];
-      if constexpr (NE == 4) {
-        k.load_geometric(ld, a);
+      k.load_geometric(ld, a);
+      bool inv;
+      if constexpr (NE == 8) {
+        HgConsts hg;
+        hg.load_k(ld, a.off_hg);
+        const auto ldn = [&](int b, float4& h, float4& l) {
+          h = su[lc[b]];
+          l = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        const auto ldx = [&](int b) { return sx[lc[b]]; };
+        const auto out = [&](int b, float4 f) { sf4[b * T + tid] = f; };
+        hex8_forces_stream<FA, FB, MR, CMP, true>(ldn, ldx, k, hg, out, inv);
+      } else {
         const float4 x0 = sx[lc[0]];
         float xd[3][3];
 #pragma unroll
@@ -190,24 +200,21 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
           xd[r][2] = xr.z - x0.z;
         }
         k.geometry(xd);
-      } else {
-        k.load(ld, a);
-        x.load(ld, a.off_hg);
-      }
-      float4 h[NE], l[NE];
+        float4 h[NE], l[NE];
 #pragma unroll
-      for (int b = 0; b < NE; ++b) {
-        h[b] = su[lc[b]];
-        l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int b = 0; b < NE; ++b) {
+          h[b] = su[lc[b]];
+          l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        float d[NE][3];
+        node_deltas<NE, CMP>(h, l, d);
+        float f[NE][3];
+        ElemExtra<NE> x;
+        elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
+#pragma unroll
+        for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
       }
-      float d[NE][3];
-      node_deltas<NE, CMP>(h, l, d);
-      float f[NE][3];
-      bool inv;
-      elem_forces<NE, FA, FB, MR, CMP>(d, k, x, f, inv);
       flag_inverted(a.st, e, inv);
-#pragma unroll
-      for (int b = 0; b < NE; ++b) sf4[b * T + tid] = make_float4(f[b][0], f[b][1], f[b][2], 0.f);
     }
     // 2. the next tile's segments must have landed; barrier: records complete
     const int next = tile + stride;
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
       gather_nodes<CMP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, tid, T);
     }
-    for (int q = tid; q < n_t; q += T) t.partials[pdst[q]] = sum_records(sf4, lidx, lptr[q], lptr[q + 1]);
+    reduce_tile(sf4, lidx, lptr, n_t, tid, T, [&](int q, float4 f) { t.partials[pdst[q]] = f; });
     async_wait_all();
     // 4. barrier: stage s and the records are free, the next tile's nodes staged
     __syncthreads();

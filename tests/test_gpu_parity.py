@@ -192,6 +192,23 @@ def test_graph_and_direct_launch_agree(B, assembly):
         assert fa > 0 and fu > 0
 
 
+@pytest.mark.parametrize("assembly", [2, 0])
+def test_profile_kernels_leaves_the_trajectory_unchanged(B, assembly):
+    import torch
+    p = W.cube_shear(W.TET4, 6, n_steps=60)
+    flush = torch.empty(8 << 20, dtype=torch.uint8, device="cuda")
+    with B.Mesh(p, assembly=assembly) as a, B.Mesh(p, assembly=assembly) as b:
+        a.run(30)
+        b.run(30)
+        tf, tu = B.dj_profile_kernels(b.h, 5, flush.data_ptr(), flush.numel())
+        assert tf > 0 and tu > 0
+        tf, tu = B.dj_profile_kernels(b.h, 3)
+        assert tf > 0 and tu > 0
+        a.run(30)
+        b.run(30)
+        assert np.array_equal(a.displacements(), b.displacements())
+
+
 def test_inverted_reference_element_is_reported(B):
     X, conn = W.cube_tet4(3)
     conn = conn.copy()
