@@ -223,6 +223,14 @@ dj_status dj_run_n_profiled(dj_mesh* mesh, long long n, void* stream, double* ms
  * Synchronous; re-runs dj_precompute for every candidate. */
 dj_status dj_autotune(dj_mesh* mesh, int steps, void* stream, dj_params* chosen, double* ms_per_step);
 
+/* dj_autotune for a cold L2 cache: with d_flush non-NULL (caller-owned device
+ * buffer of flush_bytes, at least twice the L2 size) every timed step runs
+ * alone after an L2 eviction (the first half of the buffer written, the second
+ * read), so the choice fits meshes stepped between other work; with d_flush
+ * NULL it is dj_autotune.  Synchronous. */
+dj_status dj_autotune_cold(dj_mesh* mesh, int steps, void* d_flush, size_t flush_bytes, void* stream,
+                           dj_params* chosen, double* ms_per_step);
+
 /* Wait for `stream` and report device-side errors of earlier steps
  * (DJ_ERR_INVERTED_ELEMENT / DJ_ERR_NONFINITE). */
 dj_status dj_sync(dj_mesh* mesh, void* stream);

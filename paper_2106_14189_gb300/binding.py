@@ -40,6 +40,7 @@ EXPORTS = [
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
     "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
     "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply", "dj_profile_kernels",
+    "dj_autotune_cold",
 ]
 
 
@@ -138,6 +139,7 @@ def lib():
         "dj_pod_project": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_linear_fit": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
         "dj_profile_kernels": (C.c_int, [_P, C.c_int, _P, C.c_size_t, _P, _D, _D]),
+        "dj_autotune_cold": (C.c_int, [_P, C.c_int, _P, C.c_size_t, _P, C.POINTER(dj_params), _D]),
         "dj_linear_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_float, C.c_float, _P, _P]),
         "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_residual_norms_static": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
@@ -415,6 +417,14 @@ def dj_autotune(h, steps=200, stream=None):
     p = dj_params()
     ms = C.c_double(0)
     _check(lib().dj_autotune(h, int(steps), _stream(stream), C.byref(p), C.byref(ms)), "dj_autotune", h)
+    return p, ms.value
+
+
+def dj_autotune_cold(h, steps=50, d_flush=None, flush_bytes=0, stream=None):
+    p = dj_params()
+    ms = C.c_double(0)
+    _check(lib().dj_autotune_cold(h, int(steps), d_flush, int(flush_bytes), _stream(stream), C.byref(p),
+                                  C.byref(ms)), "dj_autotune_cold", h)
     return p, ms.value
 
 

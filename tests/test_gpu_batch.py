@@ -135,6 +135,22 @@ def test_autotune_keeps_the_trajectory(B):
         assert rel_linf(U, r.displacements()) < 1e-5
 
 
+def test_cold_autotune_keeps_the_trajectory(B):
+    import torch
+    p = W.cube_shear(W.HEX8, 8, n_steps=300)
+    flush = torch.empty(8 << 20, dtype=torch.uint8, device="cuda")
+    with B.Mesh(p) as m:
+        m.run(100)
+        chosen, ms = B.dj_autotune_cold(m.h, 10, flush.data_ptr(), flush.numel())
+        assert ms > 0 and chosen.assembly in (0, 1, 2)
+        assert B.dj_get_info(m.h).step == 100
+        m.run(200)
+        U = m.displacements()
+    with B.Mesh(p, assembly=chosen.assembly, tile_size=chosen.tile_size) as r:
+        r.run(300)
+        assert rel_linf(U, r.displacements()) < 1e-5
+
+
 def test_batch_autotune(B):
     probs = small_batch(4, seed=7, steps=200)
     with B.Batch(probs) as bt:
