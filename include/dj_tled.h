@@ -77,10 +77,12 @@ typedef struct dj_mesh dj_mesh;
  *                     deterministic: 1 (default) tiles -- each block of
  *                     tile_size consecutive elements sums its forces per node in
  *                     shared memory and the node update gathers one partial per
- *                     (tile, node); 0 slots -- every element writes one force per
- *                     node and the node update gathers all of them.
+ *                     (tile, node); 2 tiles with a persistent bulk-copy
+ *                     (TMA) pipeline; 0 slots -- every element writes one force
+ *                     per node and the node update gathers all of them.
  *   tile_size         elements per tile, a multiple of 32 (T4 <= 512, H8 <= 256);
- *                     0 selects 256 (T4) / 128 (H8).
+ *                     0 selects 256 (T4) / 128 (H8); 32 (assembly 1) runs one
+ *                     tile per warp.
  *   precision         0 (default): FP32 nodal state and forces.  1: compensated
  *                     FP32 -- the displacement is kept as an unevaluated sum of
  *                     two floats and the element force is evaluated from the

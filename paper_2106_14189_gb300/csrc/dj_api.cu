@@ -1588,7 +1588,7 @@ dj_status dj_autotune_cold(dj_mesh* m, int steps, void* d_flush, size_t flush_by
     int assembly, tile;
   };
   std::vector<Cand> cands = {{ASSEMBLY_SLOTS, 0}};
-  const int tiles4[] = {64, 128, 256, 512}, tiles8[] = {64, 128, 256};
+  const int tiles4[] = {32, 64, 128, 256, 512}, tiles8[] = {32, 64, 128, 256};  // 32: one warp per tile
   if (m->ne == 4)
     for (int T : tiles4) cands.push_back({ASSEMBLY_TILES, T});
   else

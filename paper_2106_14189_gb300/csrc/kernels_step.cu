@@ -88,12 +88,30 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 constexpr int tiles_min_blocks() { return (NE == 4 && !CMP && !FB && !MR) ? 3 : 1; }
 
-template <int NE, bool FA, bool FB, bool MR, bool CMP>
+// Shared memory of one tile (float4 units): staged U, (low parts), coordinates,
+// the NE T records, then the uint16 slot ids and list offsets.
+__host__ __device__ inline int tile_smem_f4(int NE, bool CMP, int T, int cap) {
+  const int nstage = 2 + (CMP ? 1 : 0);
+  return nstage * cap + NE * T + (2 * (NE * T + cap + 8) + 15) / 16;
+}
+
+// WARP: T = 32 and one warp per tile (a block holds blockDim / 32 tiles, each
+// with its own shared-memory region); the tile's phases are separated by warp
+// barriers instead of block barriers, so warps never wait for one another.
+template <int NE, bool FA, bool FB, bool MR, bool CMP, bool WARP>
 __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA, FB, MR, CMP>()))
     force_tiles_kernel(ForceArgs a, TileArgs t) {
-  extern __shared__ float4 smem4[];
+  extern __shared__ float4 smem_all[];
   advance_clock(a);
-  const int tile = blockIdx.x, tid = threadIdx.x, T = t.T;
+  const int T = t.T;
+  const int tile = WARP ? blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : blockIdx.x;
+  const int tid = WARP ? threadIdx.x % 32 : threadIdx.x;
+  if (WARP && tile >= t.n_tiles) return;
+  float4* smem4 = WARP ? smem_all + (threadIdx.x / 32) * tile_smem_f4(NE, CMP, T, t.cap) : smem_all;
+  const auto tile_sync = [] {
+    if (WARP) __syncwarp();
+    else __syncthreads();
+  };
   const int S = NE * T;  // slots per tile
   constexpr int NSTAGE = 2 + (CMP ? 1 : 0);  // U, (low parts), reference coordinates
   float4* su = smem4;                            // staged U (high part)
@@ -145,7 +163,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
     su[q] = __ldg(a.U + gid);
     if (CMP) sl[q] = __ldg(a.Ulo + gid);
   }
-  __syncthreads();
+  tile_sync();
   if (valid) {
     bool inv;
     if constexpr (NE == 8) {
@@ -183,7 +201,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
     }
     flag_inverted(a.st, e, inv);
   }
-  __syncthreads();
+  tile_sync();
   const unsigned short* lp = sptr;
   const unsigned short* li = sidx;
   const int* pd = t.pdst + (size_t)tile * t.cap;
@@ -387,16 +405,21 @@ cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, cudaStream_t s) {
-  const size_t nstage = 2 + (CMP ? 1 : 0);
-  const size_t smem = nstage * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) +
-                      (size_t)NE * t.T * 2 + (size_t)(t.cap + 8) * 2;
+  const size_t per_tile = (size_t)tile_smem_f4(NE, CMP, t.T, t.cap) * sizeof(float4);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR, CMP>,
+    cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR, CMP, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    cudaFuncSetAttribute(force_tiles_kernel<NE, FA, FB, MR, CMP, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     attr_set = true;
   }
-  force_tiles_kernel<NE, FA, FB, MR, CMP><<<n_tiles, t.T, smem, s>>>(a, t);
+  if (t.T == 32) {
+    constexpr int W = 8;  // tiles (warps) per block
+    force_tiles_kernel<NE, FA, FB, MR, CMP, true><<<(n_tiles + W - 1) / W, 32 * W, W * per_tile, s>>>(a, t);
+  } else {
+    force_tiles_kernel<NE, FA, FB, MR, CMP, false><<<n_tiles, t.T, per_tile, s>>>(a, t);
+  }
   return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ MODELS = [W.NH, W.TI, W.OT, W.MR]
 @pytest.mark.parametrize("renumber,assembly,tile,prec", [(1, 1, 0, 0), (0, 1, 96, 0), (1, 0, 0, 0),
                                                          (0, 0, 0, 0), (1, 1, 512, 0), (1, 1, 32, 0),
                                                          (1, 1, 0, 1), (1, 0, 0, 1), (1, 2, 0, 0),
-                                                         (1, 2, 64, 1), (0, 2, 160, 0)])
+                                                         (1, 2, 64, 1), (0, 2, 160, 0), (1, 1, 32, 1)])
 def test_tet4_forces_match_oracle(B, model, renumber, assembly, tile, prec):
     # 6 * 7^3 = 2058 elements: several tiles plus a ragged tail
     p = W.random_tet_mesh_problem(2058, seed=11 + model, model=model)
@@ -55,7 +55,8 @@ def test_tet4_forces_match_oracle(B, model, renumber, assembly, tile, prec):
 
 @pytest.mark.parametrize("model", MODELS)
 @pytest.mark.parametrize("assembly,tile,prec", [(1, 0, 0), (0, 0, 0), (1, 256, 0), (1, 64, 0),
-                                                (1, 0, 1), (0, 0, 1), (2, 0, 0), (2, 256, 1)])
+                                                (1, 0, 1), (0, 0, 1), (2, 0, 0), (2, 256, 1),
+                                                (1, 32, 0), (1, 32, 1)])
 def test_hex8_forces_match_oracle(B, model, assembly, tile, prec):
     p = W.random_hex_mesh_problem(9, seed=21 + model, model=model)  # 729 bricks, ragged
     p.hg_coeff = 0.15
@@ -257,11 +258,13 @@ def test_slot_and_tile_assembly_trajectories_agree(B):
 
 
 @pytest.mark.parametrize("et", [4, 8])
-def test_tma_pipeline_equals_per_tile_blocks(B, et):
+@pytest.mark.parametrize("tile", [0, 32])
+def test_tma_pipeline_equals_per_tile_blocks(B, et, tile):
     """Same tiles, same fixed summation order: the persistent bulk-copy pipeline
-    and the one-block-per-tile kernel give bit-identical trajectories."""
+    and the one-block-per-tile kernel (one warp per tile at 32) give
+    bit-identical trajectories."""
     p = W.cube_shear(et, 9 if et == 4 else 10, n_steps=300)
-    with B.Mesh(p, assembly=1) as a, B.Mesh(p, assembly=2) as b:
+    with B.Mesh(p, assembly=1, tile_size=tile) as a, B.Mesh(p, assembly=2, tile_size=tile) as b:
         a.run(300)
         b.run(300)
         assert np.array_equal(a.displacements(), b.displacements())
