@@ -258,6 +258,12 @@ __device__ __forceinline__ void flag_inverted(DevState* st, int e, bool inverted
   }
 }
 
+// griddepcontrol (programmatic dependent launch, see launch_pdl)
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Writes the step state that the update kernel of the previous step reads:
+// only after pdl_wait.
 __device__ __forceinline__ void advance_clock(const ForceArgs& a) {
   if (a.advance && blockIdx.x == 0 && threadIdx.x == 0) {
     const long long n1 = a.st->step + 1;

@@ -110,6 +110,27 @@ struct TileArgs {
 };
 
 enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_ONLY = 3 };
+
+// Programmatic dependent launch: the kernels of a step may start while the
+// kernel before them in the stream finishes; each of them reads or writes what
+// the previous one produces or consumes only after griddepcontrol.wait, which
+// returns once that kernel has completed and its writes are visible (and at
+// once when there is no programmatic dependency).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1, ASSEMBLY_TILES_TMA = 2 };
 
 constexpr int NODE_THREADS = 256;

@@ -33,16 +33,15 @@ using namespace elem;
 // Element-slot assembly: one thread per element, forces to slot a * E_pad + e.
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceArgs a) {
-  advance_clock(a);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.E) return;
+  const bool valid = e < a.E;
   const int E_pad = a.E_pad;
   const float* __restrict__ c = a.consts;
   const auto ld = [&](int r) { return __ldcs(c + (size_t)r * E_pad + e); };
   ElemConsts<FA, FB, MR> k;
-  k.load(ld, a);
   int nid[NE];
-  {
+  if (valid) {  // the table and the connectivity do not depend on the previous kernel
+    k.load(ld, a);
     const int4 n0 = __ldcs(a.conn + (NE / 4) * (size_t)e);
     nid[0] = n0.x; nid[1] = n0.y; nid[2] = n0.z; nid[3] = n0.w;
     if constexpr (NE == 8) {
@@ -50,6 +49,12 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
       nid[4] = n1.x; nid[5] = n1.y; nid[6] = n1.z; nid[7] = n1.w;
     }
   }
+  pdl_wait();  // U of the previous update; the slots are read by it
+  // the next update kernel may start now: what it reads before its own wait
+  // (U, V) is final once the previous update has completed
+  pdl_launch_dependents();
+  advance_clock(a);
+  if (!valid) return;
   bool inv;
   if constexpr (NE == 8) {
     HgConsts hg;
@@ -102,7 +107,6 @@ template <int NE, bool FA, bool FB, bool MR, bool CMP, bool WARP>
 __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA, FB, MR, CMP>()))
     force_tiles_kernel(ForceArgs a, TileArgs t) {
   extern __shared__ float4 smem_all[];
-  advance_clock(a);
   const int T = t.T;
   const int tile = WARP ? blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : blockIdx.x;
   const int tid = WARP ? threadIdx.x % 32 : threadIdx.x;
@@ -157,6 +161,9 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
       lc[4] = v1.x; lc[5] = v1.y; lc[6] = v1.z; lc[7] = v1.w;
     }
   }
+  pdl_wait();  // U of the previous update; the partials are read by it
+  pdl_launch_dependents();  // see force_slots_kernel
+  if (!WARP || threadIdx.x < 32) advance_clock(a);
   for (int q = tid; q < n_t; q += T) {
     const int gid = __ldg(t.tnodes + (size_t)tile * t.cap + q);
     sx[q] = __ldcs(t.xloc + (size_t)tile * t.cap + q);
@@ -213,17 +220,28 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = i / SELL_C, lane = i % SELL_C;
   double num2 = 0.0, den2 = 0.0;
+  // the next force kernel may start now: before its own wait it reads only the
+  // mesh's constant tables
+  pdl_launch_dependents();
+  // node state and offsets first: the force kernel before this one does not
+  // write them (and launched this kernel only after the previous update had
+  // completed), so they are loaded while it finishes
+  float4 V = make_float4(0.f, 0.f, 0.f, 0.f), U = V, L = V;
+  int beg = 0, end = 0;
   if (i < a.N) {
-    // node state first: independent of the force gather, so these loads are in
-    // flight while the partials arrive
-    const float4 V = a.V[i];
-    const float4 U = (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID) ? a.U[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 L = (CMP && (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID)) ? a.Ulo[i]
-                                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    V = a.V[i];
+    if (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID) U = a.U[i];
+    if (CMP && (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID)) L = a.Ulo[i];
+    if (a.node_ptr) {
+      beg = __ldg(a.node_ptr + i);
+      end = __ldg(a.node_ptr + i + 1);
+    }
+  }
+  pdl_wait();  // the forces of this step; U and V are read by the previous force kernel
+  if (i < a.N) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (a.node_ptr) {
       // node-major partials: one contiguous run per node, ascending tile
-      const int beg = __ldg(a.node_ptr + i), end = __ldg(a.node_ptr + i + 1);
       for (int p = beg; p < end; ++p) {
         const float4 f = __ldcs(a.slots + p);
         fx += f.x;
@@ -399,7 +417,8 @@ __global__ void group_resid_kernel(const double2* __restrict__ nr, const int* __
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_force_t(const ForceArgs& a, int threads, cudaStream_t s) {
   const int grid = (a.E + threads - 1) / threads;
-  force_slots_kernel<NE, FA, FB, MR, CMP><<<grid, threads, 0, s>>>(a);
+  cudaError_t e = launch_pdl(force_slots_kernel<NE, FA, FB, MR, CMP>, dim3(grid), dim3(threads), 0, s, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -416,11 +435,10 @@ cudaError_t launch_tiles_t(const ForceArgs& a, const TileArgs& t, int n_tiles, c
   }
   if (t.T == 32) {
     constexpr int W = 8;  // tiles (warps) per block
-    force_tiles_kernel<NE, FA, FB, MR, CMP, true><<<(n_tiles + W - 1) / W, 32 * W, W * per_tile, s>>>(a, t);
-  } else {
-    force_tiles_kernel<NE, FA, FB, MR, CMP, false><<<n_tiles, t.T, per_tile, s>>>(a, t);
+    return launch_pdl(force_tiles_kernel<NE, FA, FB, MR, CMP, true>, dim3((n_tiles + W - 1) / W), dim3(32 * W),
+                      W * per_tile, s, a, t);
   }
-  return cudaGetLastError();
+  return launch_pdl(force_tiles_kernel<NE, FA, FB, MR, CMP, false>, dim3(n_tiles), dim3(t.T), per_tile, s, a, t);
 }
 
 template <int NE, bool CMP>
@@ -467,10 +485,9 @@ cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceA
 template <int MODE>
 cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
   const int grid = (a.N + NODE_THREADS - 1) / NODE_THREADS;
-  if (cmp)
-    node_kernel<MODE, true><<<grid, NODE_THREADS, 0, s>>>(a);
-  else
-    node_kernel<MODE, false><<<grid, NODE_THREADS, 0, s>>>(a);
+  cudaError_t e = cmp ? launch_pdl(node_kernel<MODE, true>, dim3(grid), dim3(NODE_THREADS), 0, s, a)
+                      : launch_pdl(node_kernel<MODE, false>, dim3(grid), dim3(NODE_THREADS), 0, s, a);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -125,7 +125,6 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   float4* sl2 = sbase + 2 * cap;                    // [2][cap] staged low parts (compensated)
   float4* sf4 = sbase + (CMP ? 4 : 2) * cap;        // NE T force records (slot a T + e)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sf4 + NE * T);
-  advance_clock(a);
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -133,12 +132,15 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   }
   __syncthreads();
   const int first = blockIdx.x, stride = gridDim.x;
-  if (first >= t.n_tiles) return;
   const bool second = first + stride < t.n_tiles;
-  if (tid == 0) {
+  if (tid == 0 && first < t.n_tiles) {  // constant tables: before the wait
     issue_tile<NE>(a, t, L, smem, &bars[0], first);
     if (second) issue_tile<NE>(a, t, L, smem + stage_bytes, &bars[1], first + stride);
   }
+  pdl_wait();  // U of the previous update; the partials are read by it
+  pdl_launch_dependents();
+  advance_clock(a);
+  if (first >= t.n_tiles) return;
   // prologue: the first tile's nodes
   {
     const bool ok = mbar_wait(&bars[0], 0u);
@@ -253,8 +255,7 @@ size_t smem_bytes_t(const TileArgs& t) {
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
 cudaError_t launch_t(const ForceArgs& a, const TileArgs& t, int grid, cudaStream_t s) {
   const size_t smem = smem_bytes_t<NE, CMP>(t);
-  force_tma_kernel<NE, FA, FB, MR, CMP><<<grid, t.T, smem, s>>>(a, t);
-  return cudaGetLastError();
+  return launch_pdl(force_tma_kernel<NE, FA, FB, MR, CMP>, dim3(grid), dim3(t.T), smem, s, a, t);
 }
 
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
