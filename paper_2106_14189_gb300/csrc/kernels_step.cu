@@ -220,9 +220,6 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = i / SELL_C, lane = i % SELL_C;
   double num2 = 0.0, den2 = 0.0;
-  // the next force kernel may start now: before its own wait it reads only the
-  // mesh's constant tables
-  pdl_launch_dependents();
   // node state and offsets first: the force kernel before this one does not
   // write them (and launched this kernel only after the previous update had
   // completed), so they are loaded while it finishes
@@ -238,6 +235,10 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
     }
   }
   pdl_wait();  // the forces of this step; U and V are read by the previous force kernel
+  // the next force kernel may start as these blocks retire: before its own wait
+  // it reads only the mesh's constant tables (launching it earlier, while this
+  // kernel's blocks are still arriving, lets it take their resources)
+  pdl_launch_dependents();
   if (i < a.N) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (a.node_ptr) {
