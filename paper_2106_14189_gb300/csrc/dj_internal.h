@@ -115,10 +115,15 @@ enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_O
 // kernel before them in the stream finishes; each of them reads or writes what
 // the previous one produces or consumes only after griddepcontrol.wait, which
 // returns once that kernel has completed and its writes are visible (and at
-// once when there is no programmatic dependency).
+// once when there is no programmatic dependency).  Used for launches made
+// directly on a stream; kernels captured into a CUDA graph keep ordinary
+// edges (graph replays of back-to-back steps were measured faster that way).
 template <class... KArgs, class... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -128,7 +133,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1, ASSEMBLY_TILES_TMA = 2 };
