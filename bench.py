@@ -297,7 +297,7 @@ def run_warmstart(args):
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4 TI, {p.n_nodes} nodes), 6 surface patches "
-                                   f"(r = 25 mm, bump profile) 1-5 mm, ramp 1500 steps, "
+                                   f"(r = 25 mm, bump (1 - (r/R)^2)^2) 1-5 mm, ramp 1500 steps, "
                                    f"compensated precision, alpha = 130 1/s, "
                                    f"MLP 64-256-256-256-128 tanh on POD coefficients"},
             "dtype": "f32", "data": "synthetic"}
@@ -307,16 +307,17 @@ def run_warmstart(args):
 def run_relax(args):
     """Brain-sized anisotropic ellipsoid (h = 1.76 mm, ~0.8M T4, two materials,
     TI fibres) relaxed from rest to r <= 1e-5 in compensated precision, for
-    seeded loads of six surface patches (bump profile, 2-10 mm)."""
+    seeded loads of six surface patches (C1 bump profile, 2-10 mm by default)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2106_14189_gb300 import binding as B
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    p = W.ellipsoid_tet4(h=args.relax_h, seed=0)
+    p = W.ellipsoid_tet4(h=args.relax_h, seed=0, patch_radius=args.relax_r,
+                         disp_range=(args.relax_dmin, args.relax_dmax))
     p.alpha = 130.0
-    p.ramp_steps = int(round(1500 * 3e-3 / args.relax_h))
+    p.ramp_steps = int(round(1500 * args.relax_ramp_scale * 3e-3 / args.relax_h))
     rows = []
     with B.Mesh(p, relax_check_every=50, precision=1) as m:
         info = m.info()
@@ -339,8 +340,9 @@ def run_relax(args):
             "converged": len(ok), "loads": len(rows), "rows": rows,
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.relax_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4, {p.n_nodes} nodes), inner mu 3 kPa / outer 1 kPa, "
-                                   f"nu 0.49, TI fibres eta_a/mu 2-5, 6 surface patches (r = 15 mm, bump "
-                                   f"profile) 2-10 mm, base fixed, ramp {p.ramp_steps} steps, alpha 130 1/s, "
+                                   f"nu 0.49, TI fibres eta_a/mu 2-5, 6 surface patches (r = {args.relax_r * 1e3:.0f} mm, "
+                                   f"bump (1 - (r/R)^2)^2) {args.relax_dmin * 1e3:.0f}-{args.relax_dmax * 1e3:.0f} mm, "
+                                   f"base fixed, ramp {p.ramp_steps} steps, alpha 130 1/s, "
                                    f"compensated precision, check every 50 steps",
                        "dt": info.dt, "assembly": info.assembly, "tile_size": info.tile_size},
             "dtype": "f32 (compensated)", "data": "synthetic"}
@@ -422,6 +424,10 @@ def main():
                     help="brain-sized ellipsoid relaxed to 1e-5 from rest (config of the relax workload)")
     ap.add_argument("--relax-h", type=float, default=1.76e-3)
     ap.add_argument("--relax-loads", type=int, default=4)
+    ap.add_argument("--relax-r", type=float, default=0.015)
+    ap.add_argument("--relax-dmin", type=float, default=0.002)
+    ap.add_argument("--relax-dmax", type=float, default=0.010)
+    ap.add_argument("--relax-ramp-scale", type=float, default=1.0)
     ap.add_argument("--cutout", action="store_true",
                     help="Sec. 5.1 cut-out cube: six sizes x T4/H8 x four models, full 1 s simulations")
     ap.add_argument("--ws-h", type=float, default=3e-3)
@@ -573,9 +579,12 @@ def main():
     # the prescribed-displacement targets of that step and reads U back
     e2e = None
     if args.e2e_steps > 0:
-        targets = np.array(p.bc_target, dtype=np.float64)
+        # the step's inputs and result live in pinned host memory
+        targets_t = torch.tensor(p.bc_target, dtype=torch.float64).pin_memory()
+        targets = targets_t.numpy()
+        U_host_t = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        U_host = U_host_t.numpy()
         n_e2e = args.e2e_steps
-        U_host = np.empty((N, 3))
         t_e2e = 0.0
         for k in range(n_e2e):
             l2_flush()
@@ -583,12 +592,12 @@ def main():
             t0 = time.perf_counter()
             B.dj_mesh_update_bc_targets(mesh.h, targets)
             B.dj_step(mesh.h, stream)
-            U_host = B.dj_get_displacements(mesh.h, N)
+            B.dj_get_displacements(mesh.h, N, out=U_host)
             t_e2e += time.perf_counter() - t0
         n_bc_nodes = len(np.unique(p.bc_dof // 3))
         e2e_value, _ = replica_throughput(E * n_e2e, t_e2e * 1e3, dist, device="cuda")
         e2e = {"value": e2e_value, "unit": "element-updates/s",
-               "h2d_bytes_per_step": int(n_bc_nodes * 16), "d2h_bytes_per_step": int(N * 16),
+               "h2d_bytes_per_step": int(n_bc_nodes * 16), "d2h_bytes_per_step": int(N * 24 + 48),
                "steps": n_e2e}
 
     # secondary workload: the hex8 cube (same metric)

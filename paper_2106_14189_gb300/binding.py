@@ -275,8 +275,13 @@ def dj_set_displacements(h, U0):
     _check(lib().dj_set_displacements(h, _dptr(U0)), "dj_set_displacements", h)
 
 
-def dj_get_displacements(h, n_nodes: int) -> np.ndarray:
-    out = np.empty((n_nodes, 3), dtype=np.float64)
+def dj_get_displacements(h, n_nodes: int, out=None) -> np.ndarray:
+    """U in caller order (n_nodes x 3 doubles); `out` may be a caller-owned
+    C-contiguous float64 array (e.g. a view of pinned host memory)."""
+    if out is None:
+        out = np.empty((n_nodes, 3), dtype=np.float64)
+    elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size != 3 * n_nodes:
+        raise ValueError("out must be a C-contiguous float64 array of n_nodes x 3")
     _check(lib().dj_get_displacements(h, _dptr(out)), "dj_get_displacements", h)
     return out
 

@@ -59,6 +59,7 @@ struct dj_mesh {
   float4* d_Ulo = nullptr;  // compensated mode: low part of U
   int cmp = 0;
   float4* d_save = nullptr;  // dj_evaluate_field: saved U, V, low part (3 N), allocated on first use
+  double* d_out64 = nullptr;  // dj_get_displacements: caller-order FP64 output (3 N), allocated on first use
   // groups: per-group time step, damping factor and residual
   std::vector<double> group_dt, group_dt_crit, group_r;
   std::vector<int> group_node_ptr;  // internal node range of each group
@@ -76,6 +77,7 @@ struct dj_mesh {
   std::vector<int> bc_node_of_entry;  // per bc entry: prescribed-node row
   std::vector<int> bc_comp_of_entry;
   std::vector<float4> h_bct;
+  float4* h_bct_pinned = nullptr;  // pinned staging of h_bct for target updates
   std::vector<float> h_ai;
   std::vector<int> h_bcidx;
   double dt = 0, dt_crit = 0, total_mass = 0;
@@ -151,7 +153,7 @@ void release_device(dj_mesh* m) {
   m->run_chunk = m->relax_k = 0;
   void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
-                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_pdst, m->d_node_ptr, m->d_save,
+                  m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_pdst, m->d_node_ptr, m->d_save, m->d_out64,
                   m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
                   m->d_group_node_ptr};
   for (void* p : ptrs)
@@ -163,12 +165,15 @@ void release_device(dj_mesh* m) {
   m->d_parts = nullptr;
   m->d_Ulo = nullptr;
   m->d_save = nullptr;
+  m->d_out64 = nullptr;
   m->d_bm1 = nullptr;
   m->d_node_resid = m->d_group_resid = nullptr;
   m->d_group_node_ptr = nullptr;
   if (m->h_group_resid) cudaFreeHost(m->h_group_resid);
   m->h_group_resid = nullptr;
   if (m->h_state) cudaFreeHost(m->h_state);
+  if (m->h_bct_pinned) cudaFreeHost(m->h_bct_pinned);
+  m->h_bct_pinned = nullptr;
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
   m->d_conn = nullptr;
   m->d_consts = nullptr;
@@ -1064,8 +1069,12 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
     if (m->bc_comp_of_entry[k] == 1) t.y = v;
     if (m->bc_comp_of_entry[k] == 2) t.z = v;
   }
-  if (m->n_bc_nodes)
-    CK(cudaMemcpy(m->d_bct, m->h_bct.data(), m->h_bct.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  if (m->n_bc_nodes) {
+    // staged through pinned memory (allocated once per mesh)
+    if (!m->h_bct_pinned) CK(cudaMallocHost((void**)&m->h_bct_pinned, m->h_bct.size() * sizeof(float4)));
+    std::memcpy(m->h_bct_pinned, m->h_bct.data(), m->h_bct.size() * sizeof(float4));
+    CK(cudaMemcpy(m->d_bct, m->h_bct_pinned, m->h_bct.size() * sizeof(float4), cudaMemcpyHostToDevice));
+  }
   return DJ_OK;
 }
 
@@ -1333,15 +1342,10 @@ dj_status dj_get_displacements(dj_mesh* m, double* U_out) {
   if (!U_out) return fail(m, DJ_ERR_INVALID_ARG, "null U_out");
   CK(cudaDeviceSynchronize());
   const long long N = m->N;
-  std::vector<float4> U(N), L(N, make_float4(0.f, 0.f, 0.f, 0.f));
-  CK(cudaMemcpy(U.data(), m->d_U, N * sizeof(float4), cudaMemcpyDeviceToHost));
-  if (m->cmp) CK(cudaMemcpy(L.data(), m->d_Ulo, N * sizeof(float4), cudaMemcpyDeviceToHost));
-  for (long long i = 0; i < N; ++i) {
-    const size_t o = 3 * (size_t)m->node_old_of_new[i];
-    U_out[o] = (double)U[i].x + (double)L[i].x;
-    U_out[o + 1] = (double)U[i].y + (double)L[i].y;
-    U_out[o + 2] = (double)U[i].z + (double)L[i].z;
-  }
+  // caller order and FP64 on the device, then one copy into the caller's buffer
+  if (!m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
+  CK(launch_to_caller_order_f64(m->d_U, m->cmp ? m->d_Ulo : nullptr, m->d_perm, (int)N, m->d_out64, 0));
+  CK(cudaMemcpy(U_out, m->d_out64, 3 * N * sizeof(double), cudaMemcpyDeviceToHost));
   s = read_state(m, 0);
   if (s) return s;
   return check_flags(m);

@@ -195,6 +195,8 @@ cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double
 cudaError_t launch_min_reduce(const double* v, int n, double* out, cudaStream_t s);
 // evict the L2 cache: write the first half of buf, read the second (bytes >= 2 x L2)
 cudaError_t launch_l2_flush(void* buf, size_t bytes, cudaStream_t s);
+cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
+                                       double* out, cudaStream_t s);
 cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, int N, float* out,
                                    cudaStream_t s);
 // U (internal) = caller-order field (N x 3 floats); w of U and of V kept,

@@ -254,6 +254,26 @@ __global__ void to_caller_order_kernel(const float4* __restrict__ U, const int* 
   out[3 * (size_t)i + 2] = u.z;
 }
 
+// U (+ compensated low part) in caller order as doubles, the layout of the
+// host call's output
+__global__ void to_caller_order_f64_kernel(const float4* __restrict__ U, const float4* __restrict__ Ulo,
+                                           const int* __restrict__ perm, int N, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // caller node id
+  if (i >= N) return;
+  const int v = perm[i];
+  const float4 u = U[v];
+  double x = u.x, y = u.y, z = u.z;
+  if (Ulo) {
+    const float4 l = Ulo[v];
+    x += l.x;
+    y += l.y;
+    z += l.z;
+  }
+  out[3 * (size_t)i] = x;
+  out[3 * (size_t)i + 1] = y;
+  out[3 * (size_t)i + 2] = z;
+}
+
 __global__ void from_caller_order_kernel(const float* __restrict__ src, const int* __restrict__ perm, int N,
                                          float4* U, float4* V, float4* Ulo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // caller node id
@@ -313,6 +333,13 @@ cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, 
                                    cudaStream_t s) {
   const int t = 256;
   to_caller_order_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, node_new_of_old, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
+                                       double* out, cudaStream_t s) {
+  const int t = 256;
+  to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
   return cudaGetLastError();
 }
 

@@ -416,8 +416,9 @@ def ellipsoid_load_case(problem: Problem, seed: int) -> np.ndarray:
     """Prescribed targets (ordered as problem.bc_dof) of one seeded load case.
 
     The fixed base stays fixed; every surface patch gets a displacement of
-    seeded direction and magnitude U(disp_range) with a smooth bump profile
-    1 - (r / R)^2 over the patch (r distance to the patch centre).
+    seeded direction and magnitude U(disp_range) with the smooth bump profile
+    (1 - (r / R)^2)^2 over the patch (r distance to the patch centre), which
+    meets the free surface with zero slope at r = R.
     """
     m = problem.meta
     rng = np.random.default_rng(seed)
@@ -427,7 +428,7 @@ def ellipsoid_load_case(problem: Problem, seed: int) -> np.ndarray:
         d = rng.normal(size=3)
         d *= rng.uniform(*m["disp_range"]) / np.linalg.norm(d)
         r = np.linalg.norm(X[nodes] - m["patch_centres"][p], axis=1) / m["patch_radius"]
-        w = np.clip(1.0 - r * r, 0.0, 1.0)
+        w = np.clip(1.0 - r * r, 0.0, 1.0) ** 2
         for comp in range(3):
             for n, v in zip(nodes, w * d[comp]):
                 target_of[3 * int(n) + comp] = v
