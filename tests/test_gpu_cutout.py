@@ -40,4 +40,5 @@ def test_cutout_cube_trajectory(B, et, model):
     assert err.max() <= DISP_TOL * np.abs(ref).max()
     # root-mean-square difference (Eq. 52 form), as reported for DJ-TLED vs TLED (Fig. 4)
     rmse = float(np.sqrt(np.mean(err ** 2)))
+    print(f"cut-out cube {p.name}: rel-Linf {err.max() / np.abs(ref).max():.3e}, RMSE {rmse:.3e} m")
     assert rmse <= DISP_TOL * np.abs(ref).max()

@@ -123,7 +123,9 @@ def test_hex8_trajectory_shear(B):
     s = dynamics.ExplicitSolver.from_problem(p)
     assert abs(s.dt - dt) < 1e-12 * dt
     ref = s.run(1500)
-    assert rel_linf(U, ref) < DISP_TOL
+    e = rel_linf(U, ref)
+    print(f"hex8 cube 8 shear 1500 steps rel-Linf {e:.3e}")
+    assert e < DISP_TOL
 
 
 def test_anisotropic_ellipsoid_damped(B):
@@ -136,7 +138,9 @@ def test_anisotropic_ellipsoid_damped(B):
         m.run(700)
         U = m.displacements()
     ref = dynamics.ExplicitSolver.from_problem(p).run(700)
-    assert rel_linf(U, ref) < DISP_TOL
+    e = rel_linf(U, ref)
+    print(f"ellipsoid (7 mm, TI) 700 steps rel-Linf {e:.3e}")
+    assert e < DISP_TOL
 
 
 def test_orthotropic_and_mooney_rivlin_trajectories(B):
