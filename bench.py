@@ -307,7 +307,8 @@ def run_warmstart(args):
 def run_relax(args):
     """Brain-sized anisotropic ellipsoid (h = 1.76 mm, ~0.8M T4, two materials,
     TI fibres) relaxed from rest to r <= 1e-5 in compensated precision, for
-    seeded loads of six surface patches (C1 bump profile, 2-10 mm by default)."""
+    seeded loads of six surface patches (C1 bump profile, 0.5-2.5 mm on 25 mm
+    discs by default: larger loads invert surface elements at this resolution)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -424,9 +425,9 @@ def main():
                     help="brain-sized ellipsoid relaxed to 1e-5 from rest (config of the relax workload)")
     ap.add_argument("--relax-h", type=float, default=1.76e-3)
     ap.add_argument("--relax-loads", type=int, default=4)
-    ap.add_argument("--relax-r", type=float, default=0.015)
-    ap.add_argument("--relax-dmin", type=float, default=0.002)
-    ap.add_argument("--relax-dmax", type=float, default=0.010)
+    ap.add_argument("--relax-r", type=float, default=0.025)
+    ap.add_argument("--relax-dmin", type=float, default=0.0005)
+    ap.add_argument("--relax-dmax", type=float, default=0.0025)
     ap.add_argument("--relax-ramp-scale", type=float, default=1.0)
     ap.add_argument("--cutout", action="store_true",
                     help="Sec. 5.1 cut-out cube: six sizes x T4/H8 x four models, full 1 s simulations")

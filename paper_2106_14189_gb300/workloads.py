@@ -345,8 +345,9 @@ def ellipsoid_tet4(h: float = 1.76e-3, axes=(0.070, 0.055, 0.045), seed: int = 0
     (0.6 scale) mu = 3 kPa, outer mu = 1 kPa, nu = 0.49, rho = 1000.  Fibre
     direction: normalised sum of 8 random Fourier modes, fibre stiffness
     eta_a / mu in [2, 5] from a smooth field.  n_patches surface discs of radius
-    patch_radius get a displacement of seeded direction and magnitude in
-    disp_range; nodes with z < -0.8 c are fixed.  The brain-shift example of
+    patch_radius, centred on the upper surface with |x| <= a / 2, get a
+    displacement of seeded direction and magnitude in disp_range; nodes with
+    z < -0.8 c are fixed.  The brain-shift example of
     Sec. 6 prescribes 10-20 mm surface displacements and a fixed base.
     """
     rng = np.random.default_rng(seed)
@@ -384,7 +385,9 @@ def ellipsoid_tet4(h: float = 1.76e-3, axes=(0.070, 0.055, 0.045), seed: int = 0
     # boundary conditions: fixed base, displaced surface patches
     surf = np.nonzero(bmask)[0]
     fixed = surf[X[surf, 2] < -0.8 * c]
-    cand = surf[X[surf, 2] > -0.3 * c]
+    # patch centres on the upper part of the surface and away from the pointed
+    # ends of the long axis (|x| <= a / 2), where the voxelised surface is steepest
+    cand = surf[(X[surf, 2] > -0.3 * c) & (np.abs(X[surf, 0]) <= 0.5 * a)]
     centres = X[rng.choice(cand, size=n_patches, replace=False)]
     dirs = rng.normal(size=(n_patches, 3))
     dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
