@@ -99,11 +99,11 @@ struct ElemConsts {
     if (MR) gm = ld(a.off_mr);
   }
 
-  // geometric table (KG_*): the stored constants first, then geometry()
+  // geometric T4 table (KG_*): the stored scalars first, then geometry()
+  float cP;
   template <class Ld>
   __device__ __forceinline__ void load_geometric(Ld ld, const ForceArgs& a) {
-#pragma unroll
-    for (int q = 0; q < 6; ++q) P[q] = ld(KG_P + q);
+    cP = ld(KG_CP);
     kV = ld(KG_KV);
     if (FA) {
 #pragma unroll
@@ -118,17 +118,29 @@ struct ElemConsts {
     if (MR) gm = ld(a.off_mr);
   }
 
-  // 0J (Eq. 3) from tile-local reference coordinates (T4 xd[i] = X_{i+1} - X_0,
-  // H8 xd = H_xi X) and r0 = 1 / det 0J of that same FP32 0J
+  // xd[i] = X_{i+1} - X_0 (tile-local reference coordinates) is 0J (Eq. 3);
+  // det 0J, r0 and P = c_P adj(0J)^T adj(0J) (Eq. 37) follow
   __device__ __forceinline__ void geometry(const float (&xd)[3][3]) {
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) J0[i][j] = xd[i][j];
-    const float det = xd[0][0] * (xd[1][1] * xd[2][2] - xd[1][2] * xd[2][1]) -
-                      xd[0][1] * (xd[1][0] * xd[2][2] - xd[1][2] * xd[2][0]) +
-                      xd[0][2] * (xd[1][0] * xd[2][1] - xd[1][1] * xd[2][0]);
+    float ad[3][3];  // adj(0J): 0J adj(0J) = det I
+    ad[0][0] = J0[1][1] * J0[2][2] - J0[1][2] * J0[2][1];
+    ad[0][1] = J0[0][2] * J0[2][1] - J0[0][1] * J0[2][2];
+    ad[0][2] = J0[0][1] * J0[1][2] - J0[0][2] * J0[1][1];
+    ad[1][0] = J0[1][2] * J0[2][0] - J0[1][0] * J0[2][2];
+    ad[1][1] = J0[0][0] * J0[2][2] - J0[0][2] * J0[2][0];
+    ad[1][2] = J0[0][2] * J0[1][0] - J0[0][0] * J0[1][2];
+    ad[2][0] = J0[1][0] * J0[2][1] - J0[1][1] * J0[2][0];
+    ad[2][1] = J0[0][1] * J0[2][0] - J0[0][0] * J0[2][1];
+    ad[2][2] = J0[0][0] * J0[1][1] - J0[0][1] * J0[1][0];
+    const float det = J0[0][0] * ad[0][0] + J0[0][1] * ad[1][0] + J0[0][2] * ad[2][0];
     r0 = __fdividef(1.f, det);  // fast reciprocal, ~1 ulp: J carries FP32 rounding anyway
+    const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      P[q] = cP * (ad[0][ii[q]] * ad[0][jj[q]] + ad[1][ii[q]] * ad[1][jj[q]] + ad[2][ii[q]] * ad[2][jj[q]]);
   }
 };
 

@@ -26,15 +26,14 @@ namespace dj {
 //   H8 hourglass: c_{alpha j} = h_alpha . X_{:,j} (12 floats, alpha-major), k
 // ---------------------------------------------------------------------------
 enum { K_J0 = 0, K_P = 9, K_KV = 15, K_R0 = 16, K_COMMON = 17 };
-// Geometric table (tiled assembly): the common part is
-//   0..5   P = (mu / 2) I1m as above
-//   6      kappa 0V
-// and 0J and 1/det 0J are rebuilt per step from tile-local reference
-// coordinates (TileArgs::xloc), so that J = det tJ / det 0J is 1 at rest to
-// FP32 rounding; the optional blocks follow as above, except that the H8
-// hourglass block holds k alone (c_{alpha j} = h_alpha . X_j is rebuilt from
-// the coordinates too).
-enum { KG_P = 0, KG_KV = 6, KG_COMMON = 7 };
+// Geometric table (tiled assembly): the common part is only
+//   0      c_P = mu 0V / det(0J)^2, so that P = c_P adj(0J)^T adj(0J)  (Eq. 37)
+//   1      kappa 0V
+// and 0J, det 0J and P are rebuilt per step from tile-local reference
+// coordinates (TileArgs::xloc); the optional blocks follow as above, except
+// that the H8 hourglass block holds k alone (c_{alpha j} = h_alpha . X_j is
+// rebuilt from the coordinates too).
+enum { KG_CP = 0, KG_KV = 1, KG_COMMON = 2 };
 
 // Device-resident stepping state, one per mesh.
 struct DevState {

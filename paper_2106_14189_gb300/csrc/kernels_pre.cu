@@ -111,21 +111,20 @@ __global__ void precompute_elements_kernel(PreArgs a) {
   const double c01 = (model == DJ_MR) && a.c01 ? a.c01[e] : 0.0;
   // 0J, P = (mu/2) I1m, kappa 0V, 1/det (common block)
   float* t = a.consts;
-  double K[6];  // 0J^-T 0J^-1
-  {
+  if (a.geometric) {
+    // P = mu 0V 0J^-T 0J^-1 = (mu 0V / det^2) adj(0J)^T adj(0J): one scalar
+    put(a, t, KG_CP, e, mu * V0 * id * id);
+    put(a, t, KG_KV, e, kappa * V0);
+  } else {
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) put(a, t, K_J0 + 3 * i + j, e, J0[i][j]);
+    double K[6];  // 0J^-T 0J^-1
     const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
     for (int k = 0; k < 6; ++k) {
       double s = 0.0;
       for (int m = 0; m < 3; ++m) s += Ji[m][ii[k]] * Ji[m][jj[k]];
       K[k] = s;
     }
-  }
-  if (a.geometric) {  // 0J is rebuilt from tile-local coordinates
-    for (int k = 0; k < 6; ++k) put(a, t, KG_P + k, e, 0.5 * mu * 2.0 * V0 * K[k]);
-    put(a, t, KG_KV, e, kappa * V0);
-  } else {
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) put(a, t, K_J0 + 3 * i + j, e, J0[i][j]);
     for (int k = 0; k < 6; ++k) put(a, t, K_P + k, e, 0.5 * mu * 2.0 * V0 * K[k]);
     put(a, t, K_KV, e, kappa * V0);
     put(a, t, K_R0, e, id);
