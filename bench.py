@@ -252,7 +252,7 @@ def run_warmstart(args):
     from paper_2106_14189_gb300 import binding as B
     from paper_2106_14189_gb300.warmstart import WarmStart, load_cases
     torch.cuda.set_device(0)
-    p = W.ellipsoid_tet4(h=args.ws_h, seed=0, patch_radius=0.025, disp_range=(1e-3, 5e-3))
+    p = W.ellipsoid_tet4(h=args.ws_h, seed=0, patch_radius=0.025, disp_range=(0.5e-3, 2.5e-3))
     ws = WarmStart(p, n_in=64, n_out=128, alpha=130.0, ramp_steps=1500, tol=1e-5)
     t0 = time.perf_counter()
     T_train = load_cases(p, range(100000, 100000 + args.ws_train))
@@ -297,7 +297,7 @@ def run_warmstart(args):
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4 TI, {p.n_nodes} nodes), 6 surface patches "
-                                   f"(r = 25 mm, bump (1 - (r/R)^2)^2) 1-5 mm, ramp 1500 steps, "
+                                   f"(r = 25 mm, bump (1 - (r/R)^2)^2) 0.5-2.5 mm, ramp 1500 steps, "
                                    f"compensated precision, alpha = 130 1/s, "
                                    f"MLP 64-256-256-256-128 tanh on POD coefficients"},
             "dtype": "f32", "data": "synthetic"}
@@ -555,7 +555,8 @@ def main():
     traffic = None
     try:
         tr = json.load(open(TRAFFIC_FILE))
-        if tr.get("source_hash") == kernel_source_hash() and tr.get("workload") == args.workload:
+        if (tr.get("source_hash") == kernel_source_hash() and tr.get("workload") == args.workload
+                and tr.get("assembly") == minfo.assembly and tr.get("tile_size") == minfo.tile_size):
             traffic = tr.get(f"{dominant}_bytes_per_launch")
     except Exception:
         pass
