@@ -293,6 +293,8 @@ def run_warmstart(args):
             "prediction_rel_linf": float(np.median(pred_err)) if pred_err else None,
             "pod_reconstruction_rel_linf": float(np.median(recon_err)) if recon_err else None,
             "input_modes_kept": int(ws.keep_in.sum()),
+            "validation_loss": {"linear": ws.val_loss_linear, "linear_plus_mlp": ws.val_loss,
+                                "mlp_used": bool(ws.use_mlp)},
             "train_loads": args.ws_train, "train_loads_kept": len(kept), "test_loads": args.ws_test,
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "

@@ -61,6 +61,7 @@ class WarmStart:
         self.n_bc = problem.bc_dof.size
         self.n_dof = 3 * problem.n_nodes
         self.mlp = None
+        self.use_mlp = True
         self.dev = torch.device("cuda")
         self.bc_index = torch.as_tensor(problem.bc_dof, device=self.dev)
         self.buf_c = torch.empty((1, n_in), device=self.dev)
@@ -150,6 +151,16 @@ class WarmStart:
         self.proj_out = proj
         B.dj_pod_project(proj.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
                          Y.data_ptr(), S, Qc.data_ptr())
+        # a seeded tenth of the snapshots is held out to decide whether the MLP
+        # improves on the linear part alone
+        rng = np.random.default_rng(self.seed)
+        perm = rng.permutation(S)
+        n_val = max(1, S // 10) if S >= 20 else 0
+        val_idx = torch.tensor(perm[:n_val], device=self.dev)
+        tr_idx = torch.tensor(perm[n_val:], device=self.dev)
+        Xv, Qv = Xc.index_select(0, val_idx).contiguous(), Qc.index_select(0, val_idx).contiguous()
+        Xc, Qc = Xc.index_select(0, tr_idx).contiguous(), Qc.index_select(0, tr_idx).contiguous()
+        S = S - n_val
         # linear part of the map by ridge least squares; the MLP learns the rest
         self.W_lin = torch.zeros((self.n_out, self.n_in), device=self.dev)
         if self.linear:
@@ -163,7 +174,6 @@ class WarmStart:
         if self.mlp is not None:
             B.dj_mlp_destroy(self.mlp)
         self.mlp = B.dj_mlp_create(self.widths, seed=self.seed)
-        rng = np.random.default_rng(self.seed)
         n_iter = epochs * max(1, S // batch)
         losses = []
         bsz = min(batch, S)
@@ -180,6 +190,20 @@ class WarmStart:
             B.dj_mlp_adam_step(self.mlp, lr * (lr_final / lr) ** frac)
         torch.cuda.synchronize()
         self.losses = losses
+        # validation: weighted error of the output coefficients, linear part
+        # alone against linear part + MLP; the MLP is kept only if it helps
+        self.use_mlp = True
+        self.val_loss_linear = self.val_loss = None
+        if n_val > 0:
+            lin = torch.zeros((n_val, self.n_out), device=self.dev)
+            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, Xv.data_ptr(), n_val, 1.0, 0.0,
+                              lin.data_ptr())
+            full = torch.empty((n_val, self.n_out), device=self.dev)
+            B.dj_mlp_forward(self.mlp, Xv.data_ptr(), n_val, full.data_ptr())
+            full += lin
+            self.val_loss_linear = float(((lin - Qv) ** 2 * self.w).mean())
+            self.val_loss = float(((full - Qv) ** 2 * self.w).mean())
+            self.use_mlp = self.val_loss < self.val_loss_linear
         return losses
 
     # ------------------------------------------------------------ predict ---
@@ -190,9 +214,10 @@ class WarmStart:
         c, q, out = self.buf_c, self.buf_q, self.buf_field
         B.dj_pod_project(self.modes_in.data_ptr(), self.mean_in.data_ptr(), self.n_bc, self.n_in,
                          t.data_ptr(), 1, c.data_ptr())
-        B.dj_mlp_forward(self.mlp, c.data_ptr(), 1, q.data_ptr())
-        B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, c.data_ptr(), 1, 1.0, 1.0,
-                          q.data_ptr())
+        if self.use_mlp:
+            B.dj_mlp_forward(self.mlp, c.data_ptr(), 1, q.data_ptr())
+        B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, c.data_ptr(), 1, 1.0,
+                          1.0 if self.use_mlp else 0.0, q.data_ptr())
         B.dj_pod_expand(self.modes_out.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
                         q.data_ptr(), 1, out.data_ptr())
         return out
