@@ -420,6 +420,11 @@ dj_status dj_pod_expand(const float* d_modes, const float* d_mean, long long row
  * with ridge = 0), DJ_ERR_CUDA. */
 dj_status dj_linear_fit(const float* d_X, const float* d_Y, int S, int n_in, int n_out, double ridge,
                         float* d_W, void* stream);
+/* Second-order features for the warm-start map (no counterpart in the paper):
+ * row s of d_F (S x (n + n (n + 1) / 2), row-major) holds the first n entries x
+ * of row s of d_X (leading dimension ld >= n) followed by x_i x_j for i <= j,
+ * row by row.  n <= 256.  Enqueued on `stream`; allocates nothing. */
+dj_status dj_quad_features(const float* d_X, int S, int ld, int n, float* d_F, void* stream);
 /* d_Y (S x n_out) = alpha X W^T + beta Y for d_X (S x n_in) and d_W (n_out x n_in),
  * row-major device arrays; enqueued on `stream`; allocates nothing. */
 dj_status dj_linear_apply(const float* d_W, int n_out, int n_in, const float* d_X, int S, float alpha, float beta,

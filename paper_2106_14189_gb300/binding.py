@@ -40,7 +40,7 @@ EXPORTS = [
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
     "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
     "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply", "dj_profile_kernels",
-    "dj_autotune_cold",
+    "dj_autotune_cold", "dj_quad_features",
 ]
 
 
@@ -140,6 +140,7 @@ def lib():
         "dj_linear_fit": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, _P, _P]),
         "dj_profile_kernels": (C.c_int, [_P, C.c_int, _P, C.c_size_t, _P, _D, _D]),
         "dj_autotune_cold": (C.c_int, [_P, C.c_int, _P, C.c_size_t, _P, C.POINTER(dj_params), _D]),
+        "dj_quad_features": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
         "dj_linear_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, C.c_float, C.c_float, _P, _P]),
         "dj_pod_expand": (C.c_int, [_P, _P, C.c_longlong, C.c_int, _P, C.c_int, _P, _P]),
         "dj_residual_norms_static": (C.c_int, [_P, _P, C.c_longlong, _P, _P]),
@@ -547,6 +548,10 @@ def dj_profile_kernels(h, launches, d_flush=None, flush_bytes=0, stream=None):
 def dj_linear_fit(d_X, d_Y, S, n_in, n_out, ridge, d_W, stream=None):
     _check(lib().dj_linear_fit(d_X, d_Y, int(S), int(n_in), int(n_out), float(ridge), d_W, _stream(stream)),
            "dj_linear_fit")
+
+
+def dj_quad_features(d_X, S, ld, n, d_F, stream=None):
+    _check(lib().dj_quad_features(d_X, int(S), int(ld), int(n), d_F, _stream(stream)), "dj_quad_features")
 
 
 def dj_linear_apply(d_W, n_out, n_in, d_X, S, alpha, beta, d_Y, stream=None):

@@ -269,6 +269,9 @@ cudaError_t clear_error_flags(dj_mesh* m, cudaStream_t s) {
   return e;
 }
 
+// byte extent of a tile's force records (n_e T float4), the largest slot byte offset + 16
+long long T_slots_bytes(const dj_mesh* m) { return (long long)m->ne * m->T * 16; }
+
 // Sliced ELL (chunks of SELL_C rows, column-major, -1 padding) of CSR lists.
 void build_sell(const std::vector<int>& ptr, const std::vector<int>& idx, long long N,
                 std::vector<int>& chunk_ptr, std::vector<int>& sell) {
@@ -798,6 +801,12 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     CK(cudaMemcpy(m->d_tile_ptr, tile_ptr.data(), tile_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(dalloc(m, &m->d_tile_nodes, tnodes_pad.size()));
     CK(cudaMemcpy(m->d_tile_nodes, tnodes_pad.data(), tnodes_pad.size() * sizeof(int), cudaMemcpyHostToDevice));
+    // the kernels index shared float4 arrays with these: stored as byte offsets
+    // (x 16), which keeps them in 16 bits for up to 4095 tile nodes / slots
+    if ((long long)m->cap * 16 > 65535 || (long long)T_slots_bytes(m) > 65535)
+      return fail(m, DJ_ERR_INVALID_ARG, "tile too large (tile_size %d, %d nodes)", m->T, m->cap);
+    for (auto& v : lconn) v = (unsigned short)(v * 16);
+    for (auto& v : lidx) v = (unsigned short)(v * 16);
     CK(dalloc(m, &m->d_lconn, lconn.size()));
     CK(cudaMemcpy(m->d_lconn, lconn.data(), lconn.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
     CK(dalloc(m, &m->d_lptr, lptr.size()));

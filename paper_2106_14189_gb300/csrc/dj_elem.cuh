@@ -662,8 +662,15 @@ __device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemC
     hex8_forces<FA, FB, MR, CMP>(d, k, x, f, inv);
 }
 
-// Per-tile reduction of the force records into one partial per local node,
-// spread over the whole block: G consecutive lanes share a node (G = the
+// element at byte offset `off` of a shared float4 array (local node and slot
+// indices are stored as byte offsets, which spares an index scaling per access)
+__device__ __forceinline__ float4 at16(const float4* base, unsigned off) {
+  return *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(base) + off);
+}
+
+// Per-tile reduction of the force records into one partial per local node
+// (li: byte offsets of the records), spread over the whole block: G
+// consecutive lanes share a node (G = the
 // largest of 1, 2, 4, 8 with G n_t <= T), lane r adds the node's records
 // r, r + G, r + 2G, ... in order, and the G lane sums are combined by an xor
 // butterfly (fixed order).  All lanes of a warp take part in every butterfly.
@@ -679,7 +686,7 @@ __device__ __forceinline__ void reduce_tile_g(const float4* sf4, const unsigned 
     if (q < n_t) {
       const int p1 = lp[q + 1];
       for (int p = lp[q] + sub; p < p1; p += G) {
-        const float4 v = sf4[li[p]];
+        const float4 v = at16(sf4, li[p]);
         fx += v.x;
         fy += v.y;
         fz += v.z;

@@ -175,18 +175,18 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
     bool inv;
     if constexpr (NE == 8) {
       const auto ldn = [&](int b, float4& h, float4& l) {
-        h = su[lc[b]];
-        l = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        h = at16(su, lc[b]);
+        l = CMP ? at16(sl, lc[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
       };
-      const auto ldx = [&](int b) { return sx[lc[b]]; };
+      const auto ldx = [&](int b) { return at16(sx, lc[b]); };
       const auto out = [&](int b, float4 f) { sf4[b * T + tid] = f; };
       hex8_forces_stream<FA, FB, MR, CMP, true>(ldn, ldx, k, hg, out, inv);
     } else {
-      const float4 x0 = sx[lc[0]];
+      const float4 x0 = at16(sx, lc[0]);
       float xd[3][3];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const float4 xi = sx[lc[i + 1]];
+        const float4 xi = at16(sx, lc[i + 1]);
         xd[i][0] = xi.x - x0.x;
         xd[i][1] = xi.y - x0.y;
         xd[i][2] = xi.z - x0.z;
@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
       float4 h[NE], l[NE];
 #pragma unroll
       for (int b = 0; b < NE; ++b) {
-        h[b] = su[lc[b]];
-        l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        h[b] = at16(su, lc[b]);
+        l[b] = CMP ? at16(sl, lc[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       float d[NE][3];
       node_deltas<NE, CMP>(h, l, d);

@@ -185,18 +185,18 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
         HgConsts hg;
         hg.load_k(ld, a.off_hg);
         const auto ldn = [&](int b, float4& h, float4& l) {
-          h = su[lc[b]];
-          l = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+          h = at16(su, lc[b]);
+          l = CMP ? at16(sl, lc[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
         };
-        const auto ldx = [&](int b) { return sx[lc[b]]; };
+        const auto ldx = [&](int b) { return at16(sx, lc[b]); };
         const auto out = [&](int b, float4 f) { sf4[b * T + tid] = f; };
         hex8_forces_stream<FA, FB, MR, CMP, true>(ldn, ldx, k, hg, out, inv);
       } else {
-        const float4 x0 = sx[lc[0]];
+        const float4 x0 = at16(sx, lc[0]);
         float xd[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-          const float4 xr = sx[lc[r + 1]];
+          const float4 xr = at16(sx, lc[r + 1]);
           xd[r][0] = xr.x - x0.x;
           xd[r][1] = xr.y - x0.y;
           xd[r][2] = xr.z - x0.z;
@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
         float4 h[NE], l[NE];
 #pragma unroll
         for (int b = 0; b < NE; ++b) {
-          h[b] = su[lc[b]];
-          l[b] = CMP ? sl[lc[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+          h[b] = at16(su, lc[b]);
+          l[b] = CMP ? at16(sl, lc[b]) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float d[NE][3];
         node_deltas<NE, CMP>(h, l, d);

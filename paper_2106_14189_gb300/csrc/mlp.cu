@@ -164,6 +164,27 @@ __global__ void adam_kernel(float* p, const float* __restrict__ g, float* m, flo
 }
 
 // row means of a column-major snapshot block: Y[r + c * rows]
+// F[s] = [x_0 .. x_{n-1}, x_i x_j for 0 <= i <= j < n] of row s of X (leading dim ld)
+__global__ void quad_features_kernel(const float* __restrict__ X, int S, int ld, int n, float* __restrict__ F) {
+  const int s = blockIdx.x;
+  const int nf = n + n * (n + 1) / 2;
+  const float* x = X + (size_t)s * ld;
+  float* f = F + (size_t)s * nf;
+  for (int q = threadIdx.x; q < nf; q += blockDim.x) {
+    if (q < n) {
+      f[q] = x[q];
+    } else {
+      // q - n enumerates (i, j), i <= j, row by row
+      int r = q - n, i = 0;
+      while (r >= n - i) {
+        r -= n - i;
+        ++i;
+      }
+      f[q] = x[i] * x[i + r];
+    }
+  }
+}
+
 __global__ void rowmean_kernel(const float* __restrict__ Y, long long rows, int cols, float* mean) {
   const long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (r >= rows) return;
@@ -636,6 +657,14 @@ dj_status dj_linear_fit(const float* d_X, const float* d_Y, int S, int n_in, int
   e = cudaMemcpyAsync(d_W, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
+}
+
+dj_status dj_quad_features(const float* d_X, int S, int ld, int n, float* d_F, void* stream) {
+  // row s of d_F (S x (n + n (n + 1) / 2), row-major): the first n entries of row s
+  // of d_X (leading dimension ld) and their pairwise products x_i x_j, i <= j
+  if (!d_X || !d_F || S <= 0 || n <= 0 || ld < n || n > 256) return DJ_ERR_INVALID_ARG;
+  quad_features_kernel<<<S, 128, 0, (cudaStream_t)stream>>>(d_X, S, ld, n, d_F);
+  return cudaGetLastError() == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
 }
 
 dj_status dj_linear_apply(const float* d_W, int n_out, int n_in, const float* d_X, int S, float alpha, float beta,

@@ -9,9 +9,11 @@ only as future work, Sec. 8).  Everything numerical runs in the CUDA library:
 * inputs: the leading POD coefficients of the prescribed-displacement vector,
   outputs: the leading POD coefficients of the relaxed field (dj_pod_fit /
   dj_pod_project / dj_pod_expand);
-* the map from input to output coefficients: a ridge least-squares linear part
-  (dj_linear_fit / dj_linear_apply) plus an MLP trained on what the linear
-  part leaves (dj_mlp_loss_grad / dj_mlp_adam_step / dj_mlp_forward).
+* the map from input to output coefficients: a ridge least-squares polynomial
+  part on the kept input coefficients and their pairwise products
+  (dj_quad_features, dj_linear_fit / dj_linear_apply) plus an MLP trained on
+  what it leaves (dj_mlp_loss_grad / dj_mlp_adam_step / dj_mlp_forward), kept
+  only when it improves the held-out error.
 
 A relaxation from the predicted field uses plain DJ-TLED relaxation both as
 fallback and as arbiter: if the predicted field inverts an element or has a
@@ -48,7 +50,8 @@ class WarmStart:
     def __init__(self, problem: W.Problem, n_in: int = 64, n_out: int = 128,
                  hidden=(256, 256, 256), seed: int = 0, alpha: float = 130.0,
                  ramp_steps: int = 400, check_every: int = 50, tol: float = 1e-5,
-                 max_steps: int = 400000, precision: int = 1, linear: bool = True):
+                 max_steps: int = 400000, precision: int = 1, linear: bool = True,
+                 quadratic: bool = True):
         import torch
         self.torch = torch
         self.p = problem
@@ -57,7 +60,7 @@ class WarmStart:
         self.seed = seed
         self.alpha, self.ramp_steps, self.check_every = alpha, ramp_steps, check_every
         self.tol, self.max_steps, self.precision = tol, max_steps, precision
-        self.linear = linear
+        self.linear, self.quadratic = linear, quadratic
         self.n_bc = problem.bc_dof.size
         self.n_dof = 3 * problem.n_nodes
         self.mlp = None
@@ -161,12 +164,18 @@ class WarmStart:
         Xv, Qv = Xc.index_select(0, val_idx).contiguous(), Qc.index_select(0, val_idx).contiguous()
         Xc, Qc = Xc.index_select(0, tr_idx).contiguous(), Qc.index_select(0, tr_idx).contiguous()
         S = S - n_val
-        # linear part of the map by ridge least squares; the MLP learns the rest
-        self.W_lin = torch.zeros((self.n_out, self.n_in), device=self.dev)
+        # polynomial part of the map by ridge least squares on the kept input
+        # coefficients and (quadratic) their pairwise products; the MLP learns
+        # the rest
+        n_k = int(self.keep_in.sum())
+        self.n_feat = n_k + (n_k * (n_k + 1) // 2 if self.quadratic else 0)
+        self.W_lin = torch.zeros((self.n_out, self.n_feat), device=self.dev)
+        self.buf_f = torch.empty((1, self.n_feat), device=self.dev)
+        Ftr, Fv = self._features(Xc, S), self._features(Xv, n_val) if n_val else None
         if self.linear:
-            B.dj_linear_fit(Xc.data_ptr(), Qc.data_ptr(), S, self.n_in, self.n_out, 1e-6,
+            B.dj_linear_fit(Ftr.data_ptr(), Qc.data_ptr(), S, self.n_feat, self.n_out, 1e-6,
                             self.W_lin.data_ptr())
-            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, Xc.data_ptr(), S, -1.0, 1.0,
+            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_feat, Ftr.data_ptr(), S, -1.0, 1.0,
                               Qc.data_ptr())
         # loss weights: output variance shares, so the loss tracks the field error
         var = np.where(self.keep_out, self.sig_out ** 2, 0.0)
@@ -196,7 +205,7 @@ class WarmStart:
         self.val_loss_linear = self.val_loss = None
         if n_val > 0:
             lin = torch.zeros((n_val, self.n_out), device=self.dev)
-            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, Xv.data_ptr(), n_val, 1.0, 0.0,
+            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_feat, Fv.data_ptr(), n_val, 1.0, 0.0,
                               lin.data_ptr())
             full = torch.empty((n_val, self.n_out), device=self.dev)
             B.dj_mlp_forward(self.mlp, Xv.data_ptr(), n_val, full.data_ptr())
@@ -216,10 +225,24 @@ class WarmStart:
                          t.data_ptr(), 1, c.data_ptr())
         if self.use_mlp:
             B.dj_mlp_forward(self.mlp, c.data_ptr(), 1, q.data_ptr())
-        B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_in, c.data_ptr(), 1, 1.0,
+        f = self._features(c, 1, out=self.buf_f)
+        B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_feat, f.data_ptr(), 1, 1.0,
                           1.0 if self.use_mlp else 0.0, q.data_ptr())
         B.dj_pod_expand(self.modes_out.data_ptr(), self.mean_out.data_ptr(), self.n_dof, self.n_out,
                         q.data_ptr(), 1, out.data_ptr())
+        return out
+
+    def _features(self, X: "torch.Tensor", rows: int, out=None) -> "torch.Tensor":
+        """Inputs of the polynomial part: the kept (leading) input coefficients
+        and, with quadratic=True, their pairwise products (dj_quad_features)."""
+        torch = self.torch
+        n_k = int(self.keep_in.sum())
+        if out is None:
+            out = torch.empty((rows, self.n_feat), device=self.dev)
+        if self.quadratic:
+            B.dj_quad_features(X.data_ptr(), rows, self.n_in, n_k, out.data_ptr())
+        else:
+            out.copy_(X[:, :n_k])
         return out
 
     def reconstruct(self, field: "torch.Tensor") -> "torch.Tensor":

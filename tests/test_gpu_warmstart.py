@@ -119,6 +119,20 @@ def test_linear_fit_and_apply_match_reference(env):
     assert np.abs(dZ.cpu().numpy() - Z_ref).max() < 1e-5 * np.abs(Z_ref).max()
 
 
+def test_quadratic_features(env):
+    torch, B = env
+    rng = np.random.default_rng(5)
+    S, ld, n = 37, 20, 7
+    X = rng.normal(size=(S, ld))
+    dX = torch.tensor(X, dtype=torch.float32, device="cuda")
+    nf = n + n * (n + 1) // 2
+    dF = torch.empty((S, nf), device="cuda")
+    B.dj_quad_features(dX.data_ptr(), S, ld, n, dF.data_ptr())
+    Xf = X.astype(np.float32).astype(np.float64)[:, :n]
+    ref = np.hstack([Xf] + [Xf[:, i:i + 1] * Xf[:, i:] for i in range(n)])
+    assert np.abs(dF.cpu().numpy() - ref).max() < 1e-6 * np.abs(ref).max()
+
+
 def test_warm_start_relaxes_faster_than_rest(env):
     """Train on the method's own relaxed solutions of seeded loads on a coarse
     brain-sized ellipsoid; on held-out loads the warm-started relaxation reaches
