@@ -253,10 +253,14 @@ def run_warmstart(args):
     from paper_2106_14189_gb300.warmstart import WarmStart, load_cases
     torch.cuda.set_device(0)
     p = W.ellipsoid_tet4(h=args.ws_h, seed=0, patch_radius=0.025, disp_range=(0.5e-3, 2.5e-3))
-    ws = WarmStart(p, n_in=64, n_out=128, alpha=130.0, ramp_steps=1500, tol=1e-5)
+    ws = WarmStart(p, n_in=64, n_out=128, alpha=130.0, ramp_steps=int(round(1500 * 3e-3 / args.ws_h)),
+                   tol=1e-5)
     t0 = time.perf_counter()
     T_train = load_cases(p, range(100000, 100000 + args.ws_train))
-    Y, kept, steps = ws.solve_batch(list(T_train), batch_size=64)
+    if args.ws_sequential:
+        Y, kept, steps = ws.solve_sequential(list(T_train))
+    else:
+        Y, kept, steps = ws.solve_batch(list(T_train), batch_size=64)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
     losses = ws.fit(T_train[kept], Y, epochs=1500, batch=128)
@@ -293,13 +297,16 @@ def run_warmstart(args):
             "prediction_rel_linf": float(np.median(pred_err)) if pred_err else None,
             "pod_reconstruction_rel_linf": float(np.median(recon_err)) if recon_err else None,
             "input_modes_kept": int(ws.keep_in.sum()),
-            "validation_loss": {"linear": ws.val_loss_linear, "linear_plus_mlp": ws.val_loss,
+            "validation_loss": {"first_order": ws.val_loss_first_order,
+                                "second_order": ws.val_loss_second_order,
+                                "polynomial_used": "second order" if ws.quadratic else "first order",
+                                "polynomial": ws.val_loss_linear, "polynomial_plus_mlp": ws.val_loss,
                                 "mlp_used": bool(ws.use_mlp)},
             "train_loads": args.ws_train, "train_loads_kept": len(kept), "test_loads": args.ws_test,
             "train_data_s": t_data, "train_fit_s": t_fit, "final_loss": losses[-1][1],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4 TI, {p.n_nodes} nodes), 6 surface patches "
-                                   f"(r = 25 mm, bump (1 - (r/R)^2)^2) 0.5-2.5 mm, ramp 1500 steps, "
+                                   f"(r = 25 mm, bump (1 - (r/R)^2)^2) 0.5-2.5 mm, ramp {ws.ramp_steps} steps, "
                                    f"compensated precision, alpha = 130 1/s, "
                                    f"MLP 64-256-256-256-128 tanh on POD coefficients"},
             "dtype": "f32", "data": "synthetic"}
@@ -436,6 +443,8 @@ def main():
     ap.add_argument("--ws-h", type=float, default=3e-3)
     ap.add_argument("--ws-train", type=int, default=512)
     ap.add_argument("--ws-test", type=int, default=32)
+    ap.add_argument("--ws-sequential", action="store_true",
+                    help="training relaxations one after the other on one mesh (large meshes)")
     ap.add_argument("--assembly", type=int, default=-1,
                     help="-1 autotune (default), 0 element slots, 1 tiles, 2 tiles with the "
                          "bulk-copy pipeline")

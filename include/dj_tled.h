@@ -414,10 +414,13 @@ dj_status dj_pod_expand(const float* d_modes, const float* d_mean, long long row
 /* Ridge least squares (the linear part of the warm-start map; no counterpart in
  * the paper): d_W (n_out x n_in, row-major) minimises
  * |X W^T - Y|^2 + ridge * tr(X^T X) / n_in * |W|^2 for d_X (S x n_in) and d_Y
- * (S x n_out), both row-major device arrays.  Products on the device, FP64
- * Cholesky solve on the host; n_in <= 1024.  Synchronous.
- * Errors: DJ_ERR_INVALID_ARG (sizes, ridge < 0, or singular normal equations
- * with ridge = 0), DJ_ERR_CUDA. */
+ * (S x n_out), both row-major device arrays.  Products on the device (FP64
+ * accumulation, FP32 storage), FP64 Cholesky solve on the host; if the
+ * regularised normal equations are not positive definite the ridge is raised
+ * tenfold, at most four times (from 1e-7 when ridge = 0).  n_in <= 1024.
+ * Synchronous.
+ * Errors: DJ_ERR_INVALID_ARG (sizes, ridge < 0, or normal equations that stay
+ * indefinite), DJ_ERR_CUDA. */
 dj_status dj_linear_fit(const float* d_X, const float* d_Y, int S, int n_in, int n_out, double ridge,
                         float* d_W, void* stream);
 /* Second-order features for the warm-start map (no counterpart in the paper):

@@ -623,22 +623,35 @@ dj_status dj_linear_fit(const float* d_X, const float* d_Y, int S, int n_in, int
   std::vector<double> L((size_t)n * n, 0.0);
   double tr = 0.0;
   for (int i = 0; i < n; ++i) tr += hG[(size_t)i * n + i];
-  const double shift = ridge * tr / n + 1e-300;
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j <= i; ++j) L[(size_t)i * n + j] = 0.5 * ((double)hG[(size_t)i * n + j] + hG[(size_t)j * n + i]);
-  for (int i = 0; i < n; ++i) L[(size_t)i * n + i] += shift;
-  for (int j = 0; j < n; ++j) {  // Cholesky, lower triangle in place
-    double d = L[(size_t)j * n + j];
-    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
-    if (!(d > 0.0)) return DJ_ERR_INVALID_ARG;  // singular normal equations (ridge = 0, rank-deficient X)
-    d = std::sqrt(d);
-    L[(size_t)j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double v = L[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
-      L[(size_t)i * n + j] = v / d;
+  // G is accumulated in FP64 but stored in FP32: if its rounding leaves the
+  // regularised normal equations indefinite, the ridge grows tenfold (at most
+  // four times) before the fit is refused
+  bool ok = false;
+  double lam = ridge;
+  for (int attempt = 0; attempt < 5 && !ok; ++attempt, lam = lam > 0.0 ? 10.0 * lam : 1e-7) {
+    const double shift = lam * tr / n + 1e-300;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j <= i; ++j)
+        L[(size_t)i * n + j] = 0.5 * ((double)hG[(size_t)i * n + j] + hG[(size_t)j * n + i]);
+    for (int i = 0; i < n; ++i) L[(size_t)i * n + i] += shift;
+    ok = true;
+    for (int j = 0; j < n && ok; ++j) {  // Cholesky, lower triangle in place
+      double d = L[(size_t)j * n + j];
+      for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+      if (!(d > 0.0)) {
+        ok = false;
+        break;
+      }
+      d = std::sqrt(d);
+      L[(size_t)j * n + j] = d;
+      for (int i = j + 1; i < n; ++i) {
+        double v = L[(size_t)i * n + j];
+        for (int k = 0; k < j; ++k) v -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+        L[(size_t)i * n + j] = v / d;
+      }
     }
   }
+  if (!ok) return DJ_ERR_INVALID_ARG;  // normal equations not positive definite
   std::vector<float> hW((size_t)n_out * n);
   std::vector<double> z(n);
   for (int o = 0; o < n_out; ++o) {

@@ -61,6 +61,7 @@ class WarmStart:
         self.alpha, self.ramp_steps, self.check_every = alpha, ramp_steps, check_every
         self.tol, self.max_steps, self.precision = tol, max_steps, precision
         self.linear, self.quadratic = linear, quadratic
+        self.quadratic_allowed = quadratic
         self.n_bc = problem.bc_dof.size
         self.n_dof = 3 * problem.n_nodes
         self.mlp = None
@@ -116,6 +117,28 @@ class WarmStart:
                         steps.append(n)
         return Y[:len(kept)], kept, steps
 
+    def solve_sequential(self, targets: List[np.ndarray]):
+        """As solve_batch, one load case after the other on a single mesh (large
+        meshes, where building a batch of copies costs more than it saves)."""
+        torch = self.torch
+        S = len(targets)
+        Y = torch.empty((S, self.n_dof), dtype=torch.float32, device=self.dev)
+        steps, kept = [], []
+        zeros = np.zeros((self.p.n_nodes, 3))
+        with B.Mesh(self.problem_for(targets[0]), **self.mesh_params()) as m:
+            for i, t in enumerate(targets):
+                B.dj_mesh_update_bc_targets(m.h, t)
+                m.set_displacements(zeros)
+                B.dj_set_step(m.h, 0)
+                st, n, r = m.relax(self.tol, self.max_steps, raise_on_fail=False)
+                if st != 0:
+                    continue
+                B.dj_get_displacements_device(m.h, Y[len(kept)].data_ptr())
+                kept.append(i)
+                steps.append(n)
+            m.sync()
+        return Y[:len(kept)], kept, steps
+
     # ---------------------------------------------------------------- fit ---
     def fit(self, T_host: np.ndarray, Y: "torch.Tensor", epochs: int = 400, batch: int = 256,
             lr: float = 1e-3, lr_final: float = 1e-5):
@@ -167,19 +190,52 @@ class WarmStart:
         # polynomial part of the map by ridge least squares on the kept input
         # coefficients and (quadratic) their pairwise products; the MLP learns
         # the rest
-        n_k = int(self.keep_in.sum())
-        self.n_feat = n_k + (n_k * (n_k + 1) // 2 if self.quadratic else 0)
-        self.W_lin = torch.zeros((self.n_out, self.n_feat), device=self.dev)
-        self.buf_f = torch.empty((1, self.n_feat), device=self.dev)
-        Ftr, Fv = self._features(Xc, S), self._features(Xv, n_val) if n_val else None
-        if self.linear:
-            B.dj_linear_fit(Ftr.data_ptr(), Qc.data_ptr(), S, self.n_feat, self.n_out, 1e-6,
-                            self.W_lin.data_ptr())
-            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_feat, Ftr.data_ptr(), S, -1.0, 1.0,
-                              Qc.data_ptr())
         # loss weights: output variance shares, so the loss tracks the field error
         var = np.where(self.keep_out, self.sig_out ** 2, 0.0)
         self.w = torch.tensor(var / var.mean(), dtype=torch.float32, device=self.dev)
+
+        def fit_poly(quadratic):
+            """ridge fit of the polynomial part; (W, features, held-out loss)"""
+            self.quadratic = quadratic
+            n_k = int(self.keep_in.sum())
+            self.n_feat = n_k + (n_k * (n_k + 1) // 2 if quadratic else 0)
+            W = torch.zeros((self.n_out, self.n_feat), device=self.dev)
+            F = self._features(Xc, S)
+            B.dj_linear_fit(F.data_ptr(), Qc.data_ptr(), S, self.n_feat, self.n_out,
+                            1e-4 if quadratic else 1e-6, W.data_ptr())
+            loss = None
+            if n_val:
+                Fv = self._features(Xv, n_val)
+                pv = torch.zeros((n_val, self.n_out), device=self.dev)
+                B.dj_linear_apply(W.data_ptr(), self.n_out, self.n_feat, Fv.data_ptr(), n_val, 1.0, 0.0,
+                                  pv.data_ptr())
+                loss = float(((pv - Qv) ** 2 * self.w).mean())
+            return W, F, loss
+
+        # polynomial part of the map by ridge least squares on the kept input
+        # coefficients and, if it does better on the held-out snapshots, their
+        # pairwise products; the MLP learns the rest
+        want_quadratic = self.quadratic_allowed
+        self.val_loss_first_order = self.val_loss_second_order = None
+        if self.linear:
+            W, Ftr, l1 = fit_poly(False)
+            self.val_loss_first_order = l1
+            if want_quadratic and S > 2 * int(self.keep_in.sum()):
+                W2, F2, l2 = fit_poly(True)
+                self.val_loss_second_order = l2
+                if l1 is None or (l2 is not None and l2 < l1):
+                    W, Ftr = W2, F2
+                else:
+                    fit_poly(False)
+            self.W_lin = W
+            B.dj_linear_apply(self.W_lin.data_ptr(), self.n_out, self.n_feat, Ftr.data_ptr(), S, -1.0, 1.0,
+                              Qc.data_ptr())
+        else:
+            self.quadratic = False
+            self.n_feat = int(self.keep_in.sum())
+            self.W_lin = torch.zeros((self.n_out, self.n_feat), device=self.dev)
+        self.buf_f = torch.empty((1, self.n_feat), device=self.dev)
+        Fv = self._features(Xv, n_val) if n_val else None
         if self.mlp is not None:
             B.dj_mlp_destroy(self.mlp)
         self.mlp = B.dj_mlp_create(self.widths, seed=self.seed)
