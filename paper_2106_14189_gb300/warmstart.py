@@ -161,7 +161,9 @@ class WarmStart:
         def spreads(sig, rel):
             keep = sig > rel * max(sig[0], 1e-300)
             return np.where(keep, sig / np.sqrt(S), 0.0), keep
-        s_in_np, self.keep_in = spreads(self.sig_in, 1e-4)
+        # (the Gram matrix of dj_pod_fit is stored in FP32, so singular values
+        # below ~3e-4 sigma_1 are rounding: the input threshold sits above that)
+        s_in_np, self.keep_in = spreads(self.sig_in, 1e-3)
         s_out_np, self.keep_out = spreads(self.sig_out, 1e-6)
         inv_in = np.where(self.keep_in, 1.0 / np.where(self.keep_in, s_in_np, 1.0), 0.0)
         self.modes_in *= torch.tensor(inv_in, dtype=torch.float32, device=self.dev)
@@ -220,7 +222,8 @@ class WarmStart:
         if self.linear:
             W, Ftr, l1 = fit_poly(False)
             self.val_loss_first_order = l1
-            if want_quadratic and S > 2 * int(self.keep_in.sum()):
+            n_k = int(self.keep_in.sum())
+            if want_quadratic and S > 2 * n_k and n_k + n_k * (n_k + 1) // 2 <= 1024:
                 W2, F2, l2 = fit_poly(True)
                 self.val_loss_second_order = l2
                 if l1 is None or (l2 is not None and l2 < l1):
