@@ -150,20 +150,24 @@ def test_warm_start_relaxes_faster_than_rest(env):
     assert losses[-1][1] < 0.1 * losses[0][1]
     T_test = load_cases(p, range(5000, 5012))
     cold, warm = [], []
-    for t in T_test:
-        with B.Mesh(ws.problem_for(t), **ws.mesh_params()) as m:
+    with B.Mesh(ws.problem_for(T_test[0]), **ws.mesh_params()) as m:
+        # one mesh for every load case, both paths warmed up (graph capture,
+        # first-use allocations), so the wall times compare the solves
+        ws.relax(T_test[0], warm=False, mesh=m)
+        ws.relax(T_test[0], warm=True, mesh=m)
+        for t in T_test:
             rc = ws.relax(t, warm=False, mesh=m)
             Uc = m.displacements()
             rw = ws.relax(t, warm=True, mesh=m)
             Uw = m.displacements()
-        assert rc.status == 0 and rw.status == 0 and rc.residual <= 1e-5 and rw.residual <= 1e-5
-        # same equilibrium: the residual bounds the force imbalance, not the
-        # displacement, so soft modes leave a small field difference
-        diff = np.abs(Uw - Uc).max() / np.abs(Uc).max()
-        print(f"warm vs cold field rel-Linf {diff:.2e}")
-        assert diff <= 1e-2
-        cold.append(rc)
-        warm.append(rw)
+            assert rc.status == 0 and rw.status == 0 and rc.residual <= 1e-5 and rw.residual <= 1e-5
+            # same equilibrium: the residual bounds the force imbalance, not the
+            # displacement, so soft modes leave a small field difference
+            diff = np.abs(Uw - Uc).max() / np.abs(Uc).max()
+            print(f"warm vs cold field rel-Linf {diff:.2e}")
+            assert diff <= 1e-2
+            cold.append(rc)
+            warm.append(rw)
     ws.close()
     n_fallback = sum(r.fallback for r in warm)
     assert n_fallback <= len(warm) // 4
@@ -172,3 +176,5 @@ def test_warm_start_relaxes_faster_than_rest(env):
     print(f"warm start: {mean_warm:.0f} vs {mean_cold:.0f} steps, "
           f"{np.mean([r.seconds for r in warm]) * 1e3:.1f} vs {np.mean([r.seconds for r in cold]) * 1e3:.1f} ms")
     assert mean_warm < 0.8 * mean_cold
+    # the gain holds in wall time, prediction and checks included
+    assert np.mean([r.seconds for r in warm]) < np.mean([r.seconds for r in cold])
