@@ -576,6 +576,8 @@ def main():
                 "kernel": ("element force (" + {0: "slots", 1: "tiles", 2: "tiles, bulk-copy pipeline"}[minfo.assembly] + ")")
                 if dominant == "force" else "node gather-update",
                 "peak_source": peak_kind,
+                "profile": "profiles/force_tma_tet4_nh_cube59.md" if dominant == "force"
+                           else "profiles/node_update_tet4_cube59.md",
                 "algorithmic_bytes_per_launch": bytes_dom,
                 "step": {"bytes_per_element_update": (force_bytes + update_bytes) / E,
                          "achieved_gbs": (force_bytes + update_bytes) / (ms_max * 1e-3 / args.steps) / 1e9},

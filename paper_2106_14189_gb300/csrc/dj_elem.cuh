@@ -8,6 +8,10 @@
 namespace dj {
 namespace elem {
 
+// x / 3 as a product (an IEEE division by a variable-free constant is not
+// contracted without fast-math; the product differs by at most an ulp)
+constexpr float kThird = 1.f / 3.f;
+
 
 __device__ __forceinline__ float ldg_stream(const float* p) { return __ldcs(p); }
 
@@ -171,7 +175,7 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
   const float D = tJ.m[0][0] * A.m[0][0] + tJ.m[0][1] * A.m[1][0] + tJ.m[0][2] * A.m[2][0];
   const float J = D * k.r0;  // Eq. 12
   bad = !(D > 0.f);
-  const float Jm23 = __powf(J, -2.f / 3.f);  // J^-2/3 (fast exp2/log2 intrinsics, ~1e-7 relative)
+  const float Jm23 = __powf(J, -2.f * kThird);  // J^-2/3 (fast exp2/log2 intrinsics, ~1e-7 relative)
   // T = tJ^T P, and P : g = tr(tJ^T P tJ) = T : tJ^T  (g = tJ tJ^T, Eq. 17)
   M3 T;
 #pragma unroll
@@ -185,7 +189,7 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) gP = fmaf(T.m[i][j], tJ.m[j][i], gP);
-  float vol_over_D = -gP / 3.f;  // multiplies Jm23 adj / D
+  float vol_over_D = -gP * kThird;  // multiplies Jm23 adj / D
   float g[6];
   if (FA || FB || MR) {
     g[0] = tJ.m[0][0] * tJ.m[0][0] + tJ.m[0][1] * tJ.m[0][1] + tJ.m[0][2] * tJ.m[0][2];
@@ -199,13 +203,13 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
     const float gQ = frob_sym(g, k.Qa);
     const float psi = Jm23 * gQ * k.sa - 1.f;  // I4bar - 1 (Eq. 31, Table 1)
     add_tJT_sym(T, tJ, k.Qa, psi);
-    vol_over_D -= psi * gQ / 3.f;
+    vol_over_D -= psi * gQ * kThird;
   }
   if (FB) {
     const float gQ = frob_sym(g, k.Qb);
     const float psi = Jm23 * gQ * k.sb - 1.f;  // I6bar - 1 (Eq. 32)
     add_tJT_sym(T, tJ, k.Qb, psi);
-    vol_over_D -= psi * gQ / 3.f;
+    vol_over_D -= psi * gQ * kThird;
   }
   float mr_vol = 0.f;
   if (MR) {
@@ -232,7 +236,7 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
 #pragma unroll
       for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
     add_tJT_sym(T, tJ, S2, Jm23);                               // extra J^-2/3 of Eq. 39
-    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;  // -2/3 2 C01 I2bar 0V
+    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) * kThird;  // -2/3 2 C01 I2bar 0V
   }
   const float invD = __fdividef(1.f, D);
   const float ca = (Jm23 * vol_over_D + mr_vol) * invD + k.kV * (J - 1.f) * k.r0;
@@ -350,8 +354,8 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
   const float D = __fdividef(1.f, k.r0) + dD;
   const float invD = __fdividef(1.f, D);
   const float lJ = log1pf(jm1);
-  const float Jm23 = expf(-2.f / 3.f * lJ);
-  const float Jm23m1 = expm1f(-2.f / 3.f * lJ);
+  const float Jm23 = __expf(-2.f * kThird * lJ);  // a factor near 1: the fast exponential suffices
+  const float Jm23m1 = expm1f(-2.f * kThird * lJ);
   // g0 = A A^T and dg = A B^T + B A^T + B B^T (symmetric, {00,11,22,01,02,12})
   const int ii[6] = {0, 1, 2, 0, 0, 1}, jj[6] = {0, 1, 2, 1, 2, 2};
   float g0[6], dg[6], g[6];
@@ -368,7 +372,7 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
     dg[q] = s1;
     g[q] = s0 + s1;
   }
-  const float mV = frob_sym(g0, k.P) / 3.f;  // mu 0V
+  const float mV = frob_sym(g0, k.P) * kThird;  // mu 0V
   const float dgP = frob_sym(dg, k.P);       // g:P - 3 mu 0V
   const M3 adjD = adj_delta(A, B);
   M3 adjT;
@@ -382,18 +386,18 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
 #pragma unroll
     for (int j = 0; j < 3; ++j) T.m[i][j] = 0.f;
   add_tJT_sym(T, B, k.P, 1.f);  // B^T P
-  float cT = -dgP / 3.f * invD;  // coefficient of adj(tJ) inside the J^-2/3 bracket
+  float cT = -dgP * kThird * invD;  // coefficient of adj(tJ) inside the J^-2/3 bracket
   if (FA) {
     const float d4 = frob_sym(dg, k.Qa);
     const float psi = Jm23m1 + Jm23 * d4 * k.sa;  // I4bar - 1
     add_tJT_sym(T, tJ, k.Qa, psi);
-    cT -= psi * frob_sym(g, k.Qa) / 3.f * invD;
+    cT -= psi * frob_sym(g, k.Qa) * kThird * invD;
   }
   if (FB) {
     const float d6 = frob_sym(dg, k.Qb);
     const float psi = Jm23m1 + Jm23 * d6 * k.sb;  // I6bar - 1
     add_tJT_sym(T, tJ, k.Qb, psi);
-    cT -= psi * frob_sym(g, k.Qb) / 3.f * invD;
+    cT -= psi * frob_sym(g, k.Qb) * kThird * invD;
   }
   float mr_vol = 0.f;
   if (MR) {
@@ -419,7 +423,7 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
 #pragma unroll
       for (int j = 0; j < 3; ++j) trPgPg += Pg[i][j] * Pg[j][i];
     add_tJT_sym(T, tJ, S2, Jm23);
-    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) / 3.f;
+    mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) * kThird;
   }
   const float cA = mV * jm1 * invD, cD = -mV * invD;
   const float cadj = mr_vol * invD + k.kV * jm1 * k.r0;  // volumetric: kappa 0V (J-1) r0 adj(tJ)
