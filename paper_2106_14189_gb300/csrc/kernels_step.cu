@@ -32,7 +32,7 @@ using namespace elem;
 
 // Element-slot assembly: one thread per element, forces to slot a * E_pad + e.
 template <int NE, bool FA, bool FB, bool MR, bool CMP>
-__global__ void __launch_bounds__(NE == 4 ? 256 : 128, NE == 8 && !CMP && !FA && !MR ? 8 : 1) force_slots_kernel(ForceArgs a) {
+__global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceArgs a) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = e < a.E;
   const int E_pad = a.E_pad;
