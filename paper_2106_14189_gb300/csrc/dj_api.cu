@@ -306,16 +306,6 @@ ForceArgs force_args(dj_mesh* m, int advance) {
   a.advance = advance;
   a.ramp_steps = m->params.ramp_steps;
   a.ramp_kind = m->params.ramp_kind;
-  a.pf_ptr[0] = a.pf_ptr[1] = nullptr;
-  a.pf_bytes[0] = a.pf_bytes[1] = 0;
-  if (advance) {  // a step: the update kernel follows
-    a.pf_ptr[0] = m->d_V;
-    a.pf_bytes[0] = (unsigned long long)m->N * sizeof(float4);
-    if (m->d_node_ptr) {
-      a.pf_ptr[1] = m->d_node_ptr;
-      a.pf_bytes[1] = (unsigned long long)(m->N + 1) * sizeof(int) / 16 * 16;
-    }
-  }
   return a;
 }
 

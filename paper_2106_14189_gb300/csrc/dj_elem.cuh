@@ -262,24 +262,6 @@ __device__ __forceinline__ void flag_inverted(DevState* st, int e, bool inverted
   }
 }
 
-// Block b of nb asks for its share of the arrays in a.pf_ptr to be brought into
-// L2 (cp.async.bulk.prefetch: no data reaches the SM, nothing to wait for);
-// shares start on 16-byte boundaries and have sizes that are multiples of 16.
-__device__ __forceinline__ void prefetch_share_l2(const ForceArgs& a, int b, int nb) {
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const unsigned long long total = a.pf_bytes[k];
-    if (!a.pf_ptr[k] || total < 16) continue;
-    const unsigned long long share = ((total + nb - 1) / nb + 15) / 16 * 16;
-    const unsigned long long beg = share * (unsigned long long)b;
-    if (beg >= total) continue;
-    const unsigned long long end = beg + share < total ? beg + share : total / 16 * 16;
-    if (end <= beg) continue;
-    const char* p = static_cast<const char*>(a.pf_ptr[k]) + beg;
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"((unsigned)(end - beg)) : "memory");
-  }
-}
-
 // griddepcontrol (programmatic dependent launch, see launch_pdl)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

@@ -60,11 +60,6 @@ struct ForceArgs {
   int advance;           // 1: this launch is a time step (bump step, ramp)
   long long ramp_steps;
   int ramp_kind;
-  // arrays the next update kernel reads and this kernel does not (node state V,
-  // partial offsets): each block asks for its share in L2 (bulk prefetch), so
-  // the update finds them there; nullptr / 0 when unused
-  const void* pf_ptr[2];
-  unsigned long long pf_bytes[2];
 };
 
 struct NodeArgs {

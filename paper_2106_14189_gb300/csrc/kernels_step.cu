@@ -54,7 +54,6 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
   // (U, V) is final once the previous update has completed
   pdl_launch_dependents();
   advance_clock(a);
-  if (threadIdx.x == 0) prefetch_share_l2(a, blockIdx.x, gridDim.x);
   if (!valid) return;
   bool inv;
   if constexpr (NE == 8) {
@@ -165,7 +164,6 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   pdl_wait();  // U of the previous update; the partials are read by it
   pdl_launch_dependents();  // see force_slots_kernel
   if (!WARP || threadIdx.x < 32) advance_clock(a);
-  if (threadIdx.x == 0) prefetch_share_l2(a, blockIdx.x, gridDim.x);
   for (int q = tid; q < n_t; q += T) {
     const int gid = __ldg(t.tnodes + (size_t)tile * t.cap + q);
     sx[q] = __ldcs(t.xloc + (size_t)tile * t.cap + q);

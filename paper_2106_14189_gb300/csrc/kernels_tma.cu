@@ -140,7 +140,6 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   pdl_wait();  // U of the previous update; the partials are read by it
   pdl_launch_dependents();
   advance_clock(a);
-  if (tid == 0) prefetch_share_l2(a, blockIdx.x, gridDim.x);
   if (first >= t.n_tiles) return;
   // prologue: the first tile's nodes
   {
