@@ -140,18 +140,23 @@ class ExplicitSolver:
         self.m = model
         self.dt = float(dt) if dt else dt_scale * model.critical_time_step()
         self.alpha = float(alpha)
-        d = self.dt
-        self.a = 2.0 * d * d / ((2.0 + self.alpha * d) * model.mass)
-        self.b = 4.0 / (2.0 + self.alpha * d)
-        self.c = (self.alpha * d - 2.0) / (2.0 + self.alpha * d)
         self.bc_dof = np.asarray(bc_dof, dtype=np.int64)
         self.bc_target = np.asarray(bc_target, dtype=np.float64)
+        self.set_damping(self.alpha)
         self.ramp_kind, self.ramp_steps = int(ramp_kind), int(ramp_steps)
         self.free = np.ones(3 * model.N, dtype=bool)
         self.free[self.bc_dof] = False
         self.U = np.zeros((model.N, 3))
         self.U_prev = np.zeros((model.N, 3))
         self.n = 0
+
+    def set_damping(self, alpha):
+        """Coefficients a, b, c of the three-level update for damping alpha."""
+        self.alpha = float(alpha)
+        d = self.dt
+        self.a = 2.0 * d * d / ((2.0 + self.alpha * d) * self.m.mass)
+        self.b = 4.0 / (2.0 + self.alpha * d)
+        self.c = (self.alpha * d - 2.0) / (2.0 + self.alpha * d)
 
     @classmethod
     def from_problem(cls, p, dt=None, alpha=None, R=None):
@@ -205,3 +210,93 @@ class ExplicitSolver:
                 if r <= tol and n >= self.ramp_steps:
                     return i + 1, r, True
         return int(max_steps), r, False
+
+
+# ---------------------------------------------------------------------------
+# Adaptive dynamic relaxation
+#
+# Sec. 6 relaxes to equilibrium with dynamic relaxation and cites the adaptive
+# form of the method without writing it out.  Reading used here (the published
+# adaptive scheme, in these steps):
+#   * the damped iteration converges fastest when the slowest mode is damped
+#     critically, alpha = 2 omega_min, omega_min^2 = lambda_min(M^-1 K);
+#   * late in the iteration the increment D = U^n - U^{n-1} is dominated by the
+#     slowest mode, so its Rayleigh quotient with the tangent stiffness,
+#     K D ~ F(U^n) - F(U^{n-1}), estimates lambda_min:
+#         lambda = D . (F(U^n) - F(U^{n-1})) / (D . M D)   over free DOFs;
+#   * the increments then shrink by a fixed factor rho per step, and the
+#     remaining distance to equilibrium is bounded by the geometric tail
+#         |U* - U^n| <= rho / (1 - rho) |D|.
+# Estimates are taken at each check (every k steps, from the last two steps of
+# the interval) once the states involved are past the ramp.
+
+def rayleigh_quotient(D, dF, mass, free):
+    """D . dF / (D . M D) over the free DOFs (D, dF: N x 3; mass: N)."""
+    d = np.asarray(D, dtype=np.float64).reshape(-1)[free]
+    f = np.asarray(dF, dtype=np.float64).reshape(-1)[free]
+    m = np.repeat(np.asarray(mass, dtype=np.float64), 3)[free]
+    den = float(np.dot(d * m, d))
+    return float(np.dot(d, f)) / den if den > 0.0 else 0.0
+
+
+def critical_damping(lam):
+    """Mass-proportional damping that damps a mode of M^-1 K eigenvalue lam
+    critically: alpha = 2 sqrt(lam)."""
+    return 2.0 * float(np.sqrt(lam))
+
+
+def convergence_rate(norm_now, norm_before, steps):
+    """Per-step contraction of the increment norm over `steps` steps."""
+    return float((norm_now / norm_before) ** (1.0 / steps))
+
+
+def error_estimate(rho, d_max):
+    """Geometric-tail bound rho / (1 - rho) |D| (inf when not contracting)."""
+    return rho / (1.0 - rho) * d_max if rho < 1.0 else np.inf
+
+
+def relax_adaptive(solver, tol, max_steps, check_every=100, alpha_min=0.0, alpha_max=None,
+                   disp_tol=0.0):
+    """Dynamic relaxation of `solver` (an ExplicitSolver) with the damping
+    re-estimated at every check.  Returns (steps, residual, converged, report)
+    with report = {alpha, lambda, rho, err_est, n_estimates, alphas}."""
+    k = int(check_every)
+    assert k >= 2
+    a_max = alpha_max if alpha_max and alpha_max > 0 else 2.0 / solver.dt
+    free = solver.free
+    rep = {"alpha": solver.alpha, "lambda": 0.0, "rho": 0.0, "err_est": np.inf, "n_estimates": 0,
+           "alphas": []}
+    norm_prev = 0.0
+    F_before = None
+    r = np.inf
+    for i in range(int(max_steps)):
+        n = solver.n                       # state whose force this step evaluates
+        D = solver.U - solver.U_prev       # D^n
+        F = solver.step(return_force=True)
+        if (i + 2) % k == 0:
+            F_before = F                   # F(U^{n}) of the step before a check
+        if (i + 1) % k == 0:
+            r = solver.residual(F)
+            past = solver.ramp_steps <= 0 or n - 1 >= solver.ramp_steps
+            d = D.reshape(-1)[free]
+            if past:
+                lam = rayleigh_quotient(D, F - F_before, solver.m.mass, free)
+                if lam > 0.0:
+                    alpha = min(max(critical_damping(lam), alpha_min), a_max)
+                    solver.set_damping(alpha)
+                    rep["lambda"] = lam
+                    rep["n_estimates"] += 1
+            rep["alpha"] = solver.alpha
+            rep["alphas"].append(solver.alpha)
+            norm = float(np.linalg.norm(d))
+            if past and norm_prev > 0.0 and norm > 0.0:
+                rho = convergence_rate(norm, norm_prev, k)
+                rep["rho"] = rho
+                rep["err_est"] = error_estimate(rho, float(np.abs(d).max()))
+            else:
+                rep["rho"], rep["err_est"] = 0.0, np.inf
+            norm_prev = norm if past else 0.0
+            if (r <= tol and n >= solver.ramp_steps
+                    and (disp_tol <= 0.0 or rep["err_est"] <= disp_tol)):
+                return i + 1, r, True, rep
+    return int(max_steps), r, False, rep
