@@ -328,7 +328,7 @@ def run_relax(args):
                          disp_range=(args.relax_dmin, args.relax_dmax))
     p.alpha = 130.0
     p.ramp_steps = int(round(1500 * args.relax_ramp_scale * 3e-3 / args.relax_h))
-    rows = []
+    rows, arows = [], {a0: [] for a0 in args.relax_adaptive}
     with B.Mesh(p, relax_check_every=50, precision=1) as m:
         info = m.info()
         for seed in range(args.relax_loads):
@@ -342,12 +342,38 @@ def run_relax(args):
             sec = time.perf_counter() - t0
             rows.append({"seed": seed, "status": st, "steps": n, "residual": r, "ms": sec * 1e3,
                          "element_updates_per_s": p.n_elems * n / sec})
+    # adaptive dynamic relaxation of the same loads, the damping estimated on
+    # the way from a start value (the tuned 130 1/s, or one a decade off)
+    for a0 in args.relax_adaptive:
+        pa = W.ellipsoid_tet4(h=args.relax_h, seed=0, patch_radius=args.relax_r,
+                              disp_range=(args.relax_dmin, args.relax_dmax))
+        pa.alpha, pa.ramp_steps = a0, p.ramp_steps
+        with B.Mesh(pa, relax_check_every=50, precision=1) as m:
+            for seed in range(args.relax_loads):
+                B.dj_mesh_update_bc_targets(m.h, W.ellipsoid_load_case(pa, seed))
+                m.set_displacements(np.zeros((p.n_nodes, 3)))
+                B.dj_set_step(m.h, 0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, n, r, rep = m.relax_adaptive(1e-5, 200000, stream=stream, raise_on_fail=False)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t0
+                arows[a0].append({"seed": seed, "status": st, "steps": n, "residual": r, "ms": sec * 1e3,
+                                  "alpha": rep["alpha"], "err_est_m": rep["err_est"],
+                                  "n_estimates": rep["n_estimates"]})
     ok = [x for x in rows if x["status"] == 0]
     line = {"metric": "dynamic relaxation to r <= 1e-5 from rest", "unit": "ms",
             "value": float(np.median([x["ms"] for x in ok])) if ok else None,
             "steps_median": float(np.median([x["steps"] for x in ok])) if ok else None,
             "element_updates_per_s": float(np.median([x["element_updates_per_s"] for x in ok])) if ok else None,
             "converged": len(ok), "loads": len(rows), "rows": rows,
+            "adaptive": [{"alpha0": a0,
+                          "ms_median": float(np.median([x["ms"] for x in v if x["status"] == 0]))
+                          if any(x["status"] == 0 for x in v) else None,
+                          "steps_median": float(np.median([x["steps"] for x in v if x["status"] == 0]))
+                          if any(x["status"] == 0 for x in v) else None,
+                          "converged": sum(x["status"] == 0 for x in v), "rows": v}
+                         for a0, v in arows.items()],
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.relax_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4, {p.n_nodes} nodes), inner mu 3 kPa / outer 1 kPa, "
                                    f"nu 0.49, TI fibres eta_a/mu 2-5, 6 surface patches (r = {args.relax_r * 1e3:.0f} mm, "
@@ -438,6 +464,8 @@ def main():
     ap.add_argument("--relax-dmin", type=float, default=0.0005)
     ap.add_argument("--relax-dmax", type=float, default=0.0025)
     ap.add_argument("--relax-ramp-scale", type=float, default=1.0)
+    ap.add_argument("--relax-adaptive", type=float, nargs="*", default=[130.0, 13.0, 1300.0],
+                    help="start damping values of the adaptive relaxations (none: skip)")
     ap.add_argument("--cutout", action="store_true",
                     help="Sec. 5.1 cut-out cube: six sizes x T4/H8 x four models, full 1 s simulations")
     ap.add_argument("--ws-h", type=float, default=3e-3)

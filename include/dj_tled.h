@@ -248,6 +248,53 @@ dj_status dj_sync(dj_mesh* mesh, void* stream);
 dj_status dj_relax_to_tol(dj_mesh* mesh, double tol, long long max_steps, long long* steps_out,
                           double* residual_out, void* stream);
 
+/* Options of adaptive dynamic relaxation (dj_relax_adaptive).
+ *   alpha_min, alpha_max  clamp of the damping estimate [1/s]; alpha_max <= 0
+ *                         selects 2 / dt (b = 1: no momentum carried over).
+ *   disp_tol              > 0: a state also needs the estimated displacement
+ *                         error err_est <= disp_tol [m] to count as converged;
+ *                         <= 0: the residual test alone. */
+typedef struct {
+  double alpha_min;
+  double alpha_max;
+  double disp_tol;
+} dj_adr_params;
+
+/* What dj_relax_adaptive measured at its last check.
+ *   alpha        damping in use at the end [1/s]
+ *   lambda       last Rayleigh quotient of M^-1 K along the increment [1/s^2]
+ *                (0: no estimate was made)
+ *   rho          per-step convergence rate from ||D|| at the last two checks
+ *                (0: none)
+ *   err_est      rho / (1 - rho) max|D| over free DOFs [m] (inf: none)
+ *   n_estimates  damping updates made */
+typedef struct {
+  double alpha;
+  double lambda;
+  double rho;
+  double err_est;
+  long long n_estimates;
+} dj_adr_report;
+
+/* Adaptive dynamic relaxation (Sec. 6 relaxes with fixed damping; this is the
+ * adaptive variant of the method it cites): dj_relax_to_tol whose damping is
+ * re-estimated at every check once the ramp is over.  With D = U^n - U^{n-1}
+ * and F the internal force, the Rayleigh quotient
+ *   lambda = D . (F(U^n) - F(U^{n-1})) / (D . M D)   (free DOFs, FP64 sums)
+ * estimates the lowest eigenvalue of M^-1 K (D tends to the slowest mode), and
+ * alpha = 2 sqrt(lambda), clamped to [alpha_min, alpha_max], damps that mode
+ * critically.  The per-step rate rho = (||D||_k / ||D||_{k-1})^(1/check) of
+ * two successive checks gives err_est = rho / (1 - rho) max|D|.  The
+ * damping starts from the mesh's alpha; the mesh's own damping (dj_step,
+ * dj_run_n, dj_relax_to_tol) is not changed.  Needs relax_check_every >= 2;
+ * not for meshes with groups (DJ_ERR_INVALID_ARG).  Synchronous.
+ *   opts        NULL: alpha_min 0, alpha_max 2 / dt, disp_tol 0
+ *   steps_out, residual_out, report  optional
+ * Errors: as dj_relax_to_tol. */
+dj_status dj_relax_adaptive(dj_mesh* mesh, double tol, long long max_steps, const dj_adr_params* opts,
+                            long long* steps_out, double* residual_out, dj_adr_report* report,
+                            void* stream);
+
 /* Warm start: U^0 = U^-1 = U0 (host, n_nodes * 3 doubles); step counter kept;
  * the error record (inverted / non-finite flags) is cleared, since the field
  * starts a new trajectory.  Synchronous. */

@@ -20,6 +20,8 @@ DJ_OK = 0
 STATUS = {0: "DJ_OK", 1: "DJ_ERR_INVALID_ARG", 2: "DJ_ERR_BAD_MESH", 3: "DJ_ERR_INVERTED_ELEMENT",
           4: "DJ_ERR_NOT_PRECOMPUTED", 5: "DJ_ERR_NONFINITE", 6: "DJ_ERR_NOT_CONVERGED",
           7: "DJ_ERR_CUDA", 8: "DJ_ERR_OOM", 9: "DJ_ERR_UNSUPPORTED"}
+(DJ_ERR_INVALID_ARG, DJ_ERR_BAD_MESH, DJ_ERR_INVERTED_ELEMENT, DJ_ERR_NOT_PRECOMPUTED, DJ_ERR_NONFINITE,
+ DJ_ERR_NOT_CONVERGED, DJ_ERR_CUDA, DJ_ERR_OOM, DJ_ERR_UNSUPPORTED) = range(1, 10)
 DJ_TET4, DJ_HEX8 = 4, 8
 DJ_NH, DJ_TI, DJ_OT, DJ_MR = 0, 1, 2, 3
 
@@ -27,7 +29,7 @@ DJ_NH, DJ_TI, DJ_OT, DJ_MR = 0, 1, 2, 3
 EXPORTS = [
     "dj_params_default", "dj_mesh_create", "dj_mesh_set_materials", "dj_mesh_set_bcs",
     "dj_mesh_update_bc_targets", "dj_mesh_set_loads", "dj_precompute", "dj_step", "dj_run_n",
-    "dj_run_n_profiled", "dj_sync", "dj_relax_to_tol", "dj_set_displacements",
+    "dj_run_n_profiled", "dj_sync", "dj_relax_to_tol", "dj_relax_adaptive", "dj_set_displacements",
     "dj_get_displacements", "dj_get_displacements_device", "dj_internal_forces",
     "dj_state_size", "dj_get_state", "dj_set_state", "dj_get_info", "dj_status_string",
     "dj_last_error", "dj_mesh_destroy", "dj_mesh_set_groups", "dj_get_group_info",
@@ -49,6 +51,17 @@ class dj_params(C.Structure):
                 ("hg_coeff", C.c_double), ("ramp_steps", C.c_longlong), ("ramp_kind", C.c_int),
                 ("relax_check_every", C.c_int), ("renumber", C.c_int), ("assembly", C.c_int),
                 ("tile_size", C.c_int), ("precision", C.c_int)]
+
+
+class dj_adr_params(C.Structure):
+    """Options of dj_relax_adaptive (include/dj_tled.h)."""
+    _fields_ = [("alpha_min", C.c_double), ("alpha_max", C.c_double), ("disp_tol", C.c_double)]
+
+
+class dj_adr_report(C.Structure):
+    """Estimates of the last check of dj_relax_adaptive (include/dj_tled.h)."""
+    _fields_ = [("alpha", C.c_double), ("lambda_", C.c_double), ("rho", C.c_double),
+                ("err_est", C.c_double), ("n_estimates", C.c_longlong)]
 
 
 class dj_info(C.Structure):
@@ -98,6 +111,8 @@ def lib():
         "dj_run_n_profiled": (C.c_int, [_P, C.c_longlong, _P, _D, _D]),
         "dj_sync": (C.c_int, [_P, _P]),
         "dj_relax_to_tol": (C.c_int, [_P, C.c_double, C.c_longlong, _LL, _D, _P]),
+        "dj_relax_adaptive": (C.c_int, [_P, C.c_double, C.c_longlong, C.POINTER(dj_adr_params), _LL, _D,
+                                        C.POINTER(dj_adr_report), _P]),
         "dj_set_displacements": (C.c_int, [_P, _D]),
         "dj_get_displacements": (C.c_int, [_P, _D]),
         "dj_get_displacements_device": (C.c_int, [_P, _P, _P]),
@@ -269,6 +284,20 @@ def dj_relax_to_tol(h, tol: float, max_steps: int, stream=None, raise_on_fail=Tr
     if raise_on_fail:
         _check(st, "dj_relax_to_tol", h)
     return st, steps.value, r.value
+
+
+def dj_relax_adaptive(h, tol: float, max_steps: int, alpha_min=0.0, alpha_max=0.0, disp_tol=0.0,
+                      stream=None, raise_on_fail=True):
+    """Adaptive dynamic relaxation; returns (status, steps, residual, report dict)."""
+    o = dj_adr_params(float(alpha_min), float(alpha_max), float(disp_tol))
+    rep = dj_adr_report()
+    steps, r = C.c_longlong(0), C.c_double(0)
+    st = lib().dj_relax_adaptive(h, float(tol), int(max_steps), C.byref(o), C.byref(steps), C.byref(r),
+                                 C.byref(rep), _stream(stream))
+    if raise_on_fail:
+        _check(st, "dj_relax_adaptive", h)
+    report = {f.rstrip("_"): getattr(rep, f) for f, _ in dj_adr_report._fields_}
+    return st, steps.value, r.value, report
 
 
 def dj_set_displacements(h, U0):
@@ -605,6 +634,11 @@ class Mesh:
 
     def relax(self, tol, max_steps, stream=None, raise_on_fail=True):
         return dj_relax_to_tol(self.h, tol, max_steps, stream, raise_on_fail)
+
+    def relax_adaptive(self, tol, max_steps, alpha_min=0.0, alpha_max=0.0, disp_tol=0.0, stream=None,
+                       raise_on_fail=True):
+        return dj_relax_adaptive(self.h, tol, max_steps, alpha_min, alpha_max, disp_tol, stream,
+                                 raise_on_fail)
 
     def info(self) -> dj_info:
         return dj_get_info(self.h)

@@ -103,6 +103,12 @@ struct dj_mesh {
   int run_chunk = 0;
   cudaGraphExec_t relax_exec = nullptr;
   int relax_k = 0;
+  // adaptive dynamic relaxation (allocated on first use)
+  AdrState* d_adr = nullptr;
+  AdrState* h_adr = nullptr;  // pinned
+  double* d_rq = nullptr;     // 4 sums per node block
+  cudaGraphExec_t adr_exec = nullptr;
+  int adr_k = 0;
   std::string last_error;
 };
 
@@ -149,15 +155,21 @@ cudaError_t dalloc(dj_mesh* m, T** p, size_t count) {
 void release_device(dj_mesh* m) {
   if (m->run_exec) cudaGraphExecDestroy(m->run_exec);
   if (m->relax_exec) cudaGraphExecDestroy(m->relax_exec);
-  m->run_exec = m->relax_exec = nullptr;
-  m->run_chunk = m->relax_k = 0;
-  void* ptrs[] = {m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
+  if (m->adr_exec) cudaGraphExecDestroy(m->adr_exec);
+  m->run_exec = m->relax_exec = m->adr_exec = nullptr;
+  m->run_chunk = m->relax_k = m->adr_k = 0;
+  if (m->h_adr) cudaFreeHost(m->h_adr);
+  m->h_adr = nullptr;
+  void* ptrs[] = {m->d_adr, m->d_rq,
+                  m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
                   m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_pdst, m->d_node_ptr, m->d_save, m->d_out64,
                   m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
                   m->d_group_node_ptr};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  m->d_adr = nullptr;
+  m->d_rq = nullptr;
   m->d_tile_ptr = m->d_tile_nodes = nullptr;
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
   m->d_xloc = nullptr;
@@ -351,6 +363,8 @@ NodeArgs node_args(dj_mesh* m) {
   a.node_resid = m->n_groups > 0 ? m->d_node_resid : nullptr;
   a.bm1_node = m->d_bm1;
   a.st = m->d_state;
+  a.adr = m->d_adr;
+  a.rq_partials = m->d_rq;
   a.N = (int)m->N;
   a.bm1 = m->bm1;
   return a;
@@ -361,12 +375,14 @@ cudaError_t launch_step(dj_mesh* m, cudaStream_t s, int mode) {
   if (e != cudaSuccess) return e;
   e = launch_node(mode, m->cmp, node_args(m), s);
   if (e != cudaSuccess) return e;
-  if (mode == NODE_UPDATE_RESID) {
+  if (mode == NODE_UPDATE_RESID || mode == NODE_ADR_RQ) {
     if (m->n_groups > 0)
       e = launch_group_resid(m->d_node_resid, m->d_group_node_ptr, m->n_groups, m->d_group_resid, s);
     else
       e = launch_resid_finalize(m->d_partials, m->n_node_blocks, m->d_state, s);
   }
+  if (e == cudaSuccess && mode == NODE_ADR_RQ)
+    e = launch_adr_finalize(m->d_rq, m->n_node_blocks, m->d_state, m->d_adr, s);
   return e;
 }
 
@@ -692,6 +708,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     lidx.assign((size_t)m->n_tiles * T * ne, 0);
     std::vector<std::vector<int>> tile_loc(m->n_tiles);
     std::vector<std::vector<unsigned short>> tile_lptr(m->n_tiles);
+    std::vector<int> tile_x0(m->n_tiles);  // smallest node id of the tile: origin of xloc
     int smax = 0;
     std::vector<int> loc;
     for (int t = 0; t < m->n_tiles; ++t) {
@@ -702,15 +719,28 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
       const int n_t = (int)loc.size();
       smax = std::max(smax, n_t);
       tile_ptr[t + 1] = tile_ptr[t] + n_t;
-      tile_nodes.insert(tile_nodes.end(), loc.begin(), loc.end());
+      tile_x0[t] = loc[0];
+      // local node order: descending record count (ties by node id), so that
+      // the lanes of a warp in the tile reduction walk lists of similar length
+      std::vector<int> deg(n_t, 0), ord(n_t), pos(n_t);
+      for (long long e = e0; e < e1; ++e)
+        for (int b = 0; b < ne; ++b)
+          deg[std::lower_bound(loc.begin(), loc.end(), cn[e * ne + b]) - loc.begin()]++;
+      for (int k = 0; k < n_t; ++k) ord[k] = k;
+      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return deg[x] > deg[y]; });
+      for (int k = 0; k < n_t; ++k) pos[ord[k]] = k;
       // local connectivity and the per-node slot lists (ascending element, then local node)
       std::vector<int> kcnt(n_t + 1, 0);
       for (long long e = e0; e < e1; ++e)
         for (int b = 0; b < ne; ++b) {
-          const int k = (int)(std::lower_bound(loc.begin(), loc.end(), cn[e * ne + b]) - loc.begin());
+          const int k = pos[std::lower_bound(loc.begin(), loc.end(), cn[e * ne + b]) - loc.begin()];
           lconn[e * ne + b] = (unsigned short)k;
           kcnt[k + 1]++;
         }
+      std::vector<int> reordered(n_t);
+      for (int k = 0; k < n_t; ++k) reordered[k] = loc[ord[k]];
+      loc.swap(reordered);
+      tile_nodes.insert(tile_nodes.end(), loc.begin(), loc.end());
       for (int k = 0; k < n_t; ++k) kcnt[k + 1] += kcnt[k];
       for (int k = 0; k <= n_t; ++k) tile_lptr[t].push_back((unsigned short)kcnt[k]);
       std::vector<int> fillk(kcnt.begin(), kcnt.end() - 1);
@@ -731,11 +761,11 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
       std::copy(tile_lptr[t].begin(), tile_lptr[t].end(), lptr.begin() + (size_t)t * (m->cap + 8));
     }
     if (m->geometric) {
-      // reference coordinates relative to the tile's first node, formed in FP64
-      // and rounded once, so that FP32 differences keep the element's scale
+      // reference coordinates relative to the tile's node of smallest id, formed
+      // in FP64 and rounded once, so that FP32 differences keep the element's scale
       xloc_pad.assign((size_t)m->n_tiles * m->cap, make_float4(0.f, 0.f, 0.f, 0.f));
       for (int t = 0; t < m->n_tiles; ++t) {
-        const double* x0 = &Xn[3 * (size_t)tile_loc[t][0]];
+        const double* x0 = &Xn[3 * (size_t)tile_x0[t]];
         for (size_t q = 0; q < tile_loc[t].size(); ++q) {
           const double* x = &Xn[3 * (size_t)tile_loc[t][q]];
           xloc_pad[(size_t)t * m->cap + q] =
@@ -1320,6 +1350,100 @@ dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long
   if (residual_out) *residual_out = r;
   if (s) return s;
   return fail(m, DJ_ERR_NOT_CONVERGED, "residual %.3e above tol %.3e after %lld steps", r, tol, done);
+}
+
+dj_status dj_relax_adaptive(dj_mesh* m, double tol, long long max_steps, const dj_adr_params* opts,
+                            long long* steps_out, double* residual_out, dj_adr_report* report, void* stream) {
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (!(tol >= 0) || max_steps < 0) return fail(m, DJ_ERR_INVALID_ARG, "bad tol or max_steps");
+  if (m->n_groups > 0) return fail(m, DJ_ERR_INVALID_ARG, "adaptive relaxation of a mesh with groups");
+  const int k = m->params.relax_check_every;
+  if (k < 2) return fail(m, DJ_ERR_INVALID_ARG, "adaptive relaxation needs relax_check_every >= 2");
+  dj_adr_params o{0.0, 0.0, 0.0};
+  if (opts) o = *opts;
+  const double dt = m->dt;
+  if (!(o.alpha_min >= 0) || !(o.alpha_max == o.alpha_max) || !(o.disp_tol == o.disp_tol))
+    return fail(m, DJ_ERR_INVALID_ARG, "bad adaptive relaxation options");
+  const double amax = o.alpha_max > 0 ? o.alpha_max : 2.0 / dt;
+  if (o.alpha_min > amax) return fail(m, DJ_ERR_INVALID_ARG, "alpha_min above alpha_max");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!m->d_adr) {
+    CK(dalloc(m, &m->d_adr, 1));
+    CK(dalloc(m, &m->d_rq, 4 * (size_t)m->n_node_blocks));
+    CK(cudaMallocHost((void**)&m->h_adr, sizeof(AdrState)));
+  }
+  // the damping starts from the mesh's alpha
+  const double a0 = m->params.alpha, adt0 = a0 * dt;
+  AdrState init{};
+  init.dt = dt;
+  init.kappa0 = 2.0 / (2.0 + adt0);
+  init.alpha_min = o.alpha_min;
+  init.alpha_max = amax;
+  init.ramp_steps = m->params.ramp_steps;
+  init.k = k;
+  init.bm1 = m->bm1;
+  init.ai_scale = 1.f;
+  init.alpha = a0;
+  init.err_est = INFINITY;
+  CK(cudaStreamSynchronize(st));  // h_adr is not in use by an earlier copy
+  *m->h_adr = init;
+  CK(cudaMemcpyAsync(m->d_adr, m->h_adr, sizeof(AdrState), cudaMemcpyHostToDevice, st));
+  if (!m->adr_exec || m->adr_k != k) {
+    if (m->adr_exec) cudaGraphExecDestroy(m->adr_exec);
+    m->adr_exec = nullptr;
+    s = capture(m, &m->adr_exec, [&](cudaStream_t cs) {
+      for (int j = 0; j < k - 2; ++j) {
+        cudaError_t e = launch_step(m, cs, NODE_ADR);
+        if (e != cudaSuccess) return e;
+      }
+      cudaError_t e = launch_step(m, cs, NODE_ADR_STOREF);
+      if (e == cudaSuccess) e = launch_step(m, cs, NODE_ADR_RQ);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_adr, m->d_adr, sizeof(AdrState), cudaMemcpyDeviceToHost, cs);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, cs);
+    });
+    if (s) return s;
+    m->adr_k = k;
+  }
+  const auto fill = [&](const AdrState& a) {
+    if (!report) return;
+    report->alpha = a.alpha;
+    report->lambda = a.lambda;
+    report->rho = a.rho;
+    report->err_est = a.err_est;
+    report->n_estimates = a.n_est;
+  };
+  long long done = 0;
+  double r = INFINITY;
+  while (done + k <= max_steps) {
+    CK(cudaGraphLaunch(m->adr_exec, st));
+    CK(cudaStreamSynchronize(st));
+    done += k;
+    fill(*m->h_adr);
+    s = check_flags(m);
+    if (s) {
+      if (steps_out) *steps_out = done;
+      return s;
+    }
+    const double num = std::sqrt(m->h_state->resid_num2), den = std::sqrt(m->h_state->resid_den2);
+    r = den > 0 ? num / den : num;
+    const long long checked = m->h_state->step - 1;
+    if (r <= tol && (m->params.ramp_steps <= 0 || checked >= m->params.ramp_steps) &&
+        (o.disp_tol <= 0 || m->h_adr->err_est <= o.disp_tol)) {
+      if (steps_out) *steps_out = done;
+      if (residual_out) *residual_out = r;
+      return DJ_OK;
+    }
+  }
+  for (; done < max_steps; ++done) CK(launch_step(m, st, NODE_ADR));
+  s = read_state(m, st);
+  if (s) return s;
+  s = check_flags(m);
+  if (steps_out) *steps_out = done;
+  if (residual_out) *residual_out = r;
+  if (s) return s;
+  return fail(m, DJ_ERR_NOT_CONVERGED, "residual %.3e above tol %.3e after %lld adaptive steps", r, tol, done);
 }
 
 dj_status dj_set_displacements(dj_mesh* m, const double* U0) {

@@ -62,6 +62,36 @@ struct ForceArgs {
   int ramp_kind;
 };
 
+// Adaptive dynamic relaxation (one per mesh, device memory).  The damping in
+// use is alpha; the update kernels of the adaptive steps take b - 1 and the
+// scale of the precomputed a_i (a_i(alpha) / a_i(alpha_0)) from here.  At every
+// check the increment D = U^n - U^{n-1} and the change of the force between
+// the last two steps give the Rayleigh quotient
+//   lambda = D . (F(U^n) - F(U^{n-1})) / (D . M D)    (free DOFs)
+// of M^-1 K along D, alpha becomes 2 sqrt(lambda) (critical damping of that
+// mode, clamped), and the ratio of ||D|| at successive checks the per-step
+// convergence rate rho, with err_est = rho / (1 - rho) max|D| the estimated
+// distance to equilibrium.
+struct AdrState {
+  // inputs, written by the host before each relaxation
+  double dt;          // time step
+  double kappa0;      // 2 / (2 + alpha_0 dt): M = kappa0 dt^2 / a_i(alpha_0)
+  double alpha_min, alpha_max;
+  long long ramp_steps;
+  int k;              // steps between checks
+  // damping in use
+  float bm1;          // (2 - alpha dt) / (2 + alpha dt)
+  float ai_scale;     // (2 + alpha_0 dt) / (2 + alpha dt)
+  double alpha;
+  // estimates of the last check
+  double lambda;      // Rayleigh quotient [1/s^2] (0: none yet)
+  double rho;         // per-step convergence rate (0: none)
+  double err_est;     // rho / (1 - rho) max|D| (inf: none)
+  double du_norm;     // ||D||_2 over free DOFs at the previous check past the ramp (0: none)
+  double du_max;      // max |D| over free DOFs
+  long long n_est;    // damping updates made
+};
+
 struct NodeArgs {
   const int* sell;        // sliced-ELL slot ids, chunks of 32 nodes, column-major
   const int* chunk_ptr;   // n_chunks + 1 offsets into sell
@@ -78,6 +108,8 @@ struct NodeArgs {
   double2* node_resid;    // grouped meshes: per-node residual sums (else nullptr)
   const float* bm1_node;  // grouped meshes with damping: per-node b - 1 (else nullptr)
   DevState* st;           // ramp value (read), error flags (written)
+  const AdrState* adr;    // adaptive modes: damping in use (else nullptr)
+  double* rq_partials;    // NODE_ADR_RQ: 4 sums per block (D.dF, D^2 / a_i, D^2, max |D|)
   int N;
   float bm1;              // b - 1 = (2 - alpha dt) / (2 + alpha dt)
 };
@@ -109,7 +141,11 @@ struct TileArgs {
   int n_tiles;
 };
 
-enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_ONLY = 3 };
+enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_ONLY = 3,
+       // adaptive dynamic relaxation: the update with the damping of AdrState,
+       // optionally storing F - R (the step before a check) or adding the
+       // Rayleigh-quotient and increment sums to the residual (the check step)
+       NODE_ADR = 4, NODE_ADR_STOREF = 5, NODE_ADR_RQ = 6 };
 
 // Programmatic dependent launch: the kernels of a step may start while the
 // kernel before them in the stream finishes; each of them reads or writes what
@@ -154,6 +190,8 @@ size_t tma_smem_bytes(int elem_type, int cmp, const TileArgs& t);
 int tma_blocks_per_sm(int elem_type, int variant, int cmp, const TileArgs& t);
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
+cudaError_t launch_adr_finalize(const double* rq_partials, int n, const DevState* st, AdrState* adr,
+                                cudaStream_t s);
 // per-group residual sums over contiguous node ranges (one block per group)
 cudaError_t launch_group_resid(const double2* node_resid, const int* group_node_ptr, int n_groups,
                                double2* out, cudaStream_t s);

@@ -217,9 +217,13 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
 
 template <int MODE, bool CMP>
 __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
+  constexpr bool ADR = MODE == NODE_ADR || MODE == NODE_ADR_STOREF || MODE == NODE_ADR_RQ;
+  constexpr bool UPD = MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID || ADR;
+  constexpr bool RESID = MODE == NODE_UPDATE_RESID || MODE == NODE_RESID_ONLY || MODE == NODE_ADR_RQ;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = i / SELL_C, lane = i % SELL_C;
   double num2 = 0.0, den2 = 0.0;
+  double rq_df = 0.0, rq_m = 0.0, rq_d2 = 0.0, rq_max = 0.0;  // NODE_ADR_RQ sums
   // node state and offsets first: the force kernel before this one does not
   // write them (and launched this kernel only after the previous update had
   // completed), so they are loaded while it finishes
@@ -227,8 +231,8 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   int beg = 0, end = 0;
   if (i < a.N) {
     V = a.V[i];
-    if (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID) U = a.U[i];
-    if (CMP && (MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID)) L = a.Ulo[i];
+    if (UPD) U = a.U[i];
+    if (CMP && UPD) L = a.Ulo[i];
     if (a.node_ptr) {
       beg = __ldg(a.node_ptr + i);
       end = __ldg(a.node_ptr + i + 1);
@@ -284,9 +288,11 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
         else num2 += f3[q] * f3[q];
       }
     } else {
-      const float ai = U.w;
-      // velocity form of the central difference: D^{n+1} = a (R - F) + (b - 1) D^n
-      const float bm1 = a.bm1_node ? __ldg(a.bm1_node + i) : a.bm1;
+      // velocity form of the central difference: D^{n+1} = a (R - F) + (b - 1) D^n;
+      // adaptive steps take b - 1 and the scale of a_i from the relaxation state
+      const float ai = ADR ? U.w * a.adr->ai_scale : U.w;
+      const float bm1 = ADR ? a.adr->bm1 : (a.bm1_node ? __ldg(a.bm1_node + i) : a.bm1);
+      const float4 D = V;  // D^n = U^n - U^{n-1}
       float dd[3] = {fmaf(-ai, fx, bm1 * V.x), fmaf(-ai, fy, bm1 * V.y), fmaf(-ai, fz, bm1 * V.z)};
       const float uh[3] = {U.x, U.y, U.z};
       float nh[3], nl[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
@@ -329,7 +335,8 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       a.U[i] = make_float4(nh[0], nh[1], nh[2], ai);
       if (CMP) a.Ulo[i] = make_float4(nl[0], nl[1], nl[2], 0.f);
       a.V[i] = make_float4(dd[0], dd[1], dd[2], V.w);
-      if (MODE == NODE_UPDATE_RESID) {
+      if (MODE == NODE_ADR_STOREF) a.fout[i] = make_float4(fx, fy, fz, 0.f);
+      if (MODE == NODE_UPDATE_RESID || MODE == NODE_ADR_RQ) {
         const double f3[3] = {fx, fy, fz};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -337,9 +344,24 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
           else num2 += f3[q] * f3[q];
         }
       }
+      if (MODE == NODE_ADR_RQ) {
+        // F(U^n) - F(U^{n-1}) along D^n over the free DOFs; the lumped mass
+        // enters as 1 / a_i(alpha_0) (times kappa0 dt^2, applied once at the end)
+        const float4 fp = a.fout[i];
+        const double df[3] = {(double)fx - fp.x, (double)fy - fp.y, (double)fz - fp.z};
+        const double d[3] = {D.x, D.y, D.z};
+        const double inv_a = U.w > 0.f ? 1.0 / (double)U.w : 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          if (!(mask & (1 << q))) {
+            rq_df += d[q] * df[q];
+            rq_m += d[q] * d[q] * inv_a;
+            rq_d2 += d[q] * d[q];
+            rq_max = fmax(rq_max, fabs(d[q]));
+          }
+      }
     }
   }
-  constexpr bool RESID = MODE == NODE_UPDATE_RESID || MODE == NODE_RESID_ONLY;
   if (RESID && a.node_resid) {
     if (i < a.N) a.node_resid[i] = make_double2(num2, den2);
     return;
@@ -366,6 +388,94 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       a.partials[blockIdx.x] = make_double2(tn, td);
     }
   }
+  if (MODE == NODE_ADR_RQ) {
+    __shared__ double sr[4][NODE_THREADS / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      rq_df += __shfl_down_sync(0xffffffffu, rq_df, o);
+      rq_m += __shfl_down_sync(0xffffffffu, rq_m, o);
+      rq_d2 += __shfl_down_sync(0xffffffffu, rq_d2, o);
+      rq_max = fmax(rq_max, __shfl_down_sync(0xffffffffu, rq_max, o));
+    }
+    const int w = threadIdx.x / 32;
+    if ((threadIdx.x & 31) == 0) {
+      sr[0][w] = rq_df;
+      sr[1][w] = rq_m;
+      sr[2][w] = rq_d2;
+      sr[3][w] = rq_max;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+      for (int q = 0; q < NODE_THREADS / 32; ++q) {
+        t0 += sr[0][q];
+        t1 += sr[1][q];
+        t2 += sr[2][q];
+        t3 = fmax(t3, sr[3][q]);
+      }
+      double* o = a.rq_partials + 4 * (size_t)blockIdx.x;
+      o[0] = t0;
+      o[1] = t1;
+      o[2] = t2;
+      o[3] = t3;
+    }
+  }
+}
+
+// Adaptive dynamic relaxation, after the check step: fixed-order sums of the
+// per-block Rayleigh-quotient terms, then (one thread) the damping update and
+// the convergence-rate estimate described at AdrState.
+__global__ void adr_finalize_kernel(const double* __restrict__ p, int n, const DevState* st, AdrState* adr) {
+  __shared__ double s[4][256];
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    t0 += p[4 * q];
+    t1 += p[4 * q + 1];
+    t2 += p[4 * q + 2];
+    t3 = fmax(t3, p[4 * q + 3]);
+  }
+  s[0][threadIdx.x] = t0;
+  s[1][threadIdx.x] = t1;
+  s[2][threadIdx.x] = t2;
+  s[3][threadIdx.x] = t3;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s[0][threadIdx.x] += s[0][threadIdx.x + o];
+      s[1][threadIdx.x] += s[1][threadIdx.x + o];
+      s[2][threadIdx.x] += s[2][threadIdx.x + o];
+      s[3][threadIdx.x] = fmax(s[3][threadIdx.x], s[3][threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double dfd = s[0][0], dmd_a = s[1][0], d2 = s[2][0], dmax = s[3][0];
+  // the force of this step was evaluated at U^n, n = step - 1; D^n and the
+  // stored force of U^{n-1} count once U^{n-1} is past the ramp
+  const long long n_eval = st->step - 1;
+  const bool past = adr->ramp_steps <= 0 || n_eval - 1 >= adr->ramp_steps;
+  const double mdd = adr->kappa0 * adr->dt * adr->dt * dmd_a;  // D . M D
+  if (past && mdd > 0.0 && dfd > 0.0) {
+    const double lam = dfd / mdd;
+    const double al = fmin(fmax(2.0 * sqrt(lam), adr->alpha_min), adr->alpha_max);
+    const double adt = al * adr->dt;
+    adr->lambda = lam;
+    adr->alpha = al;
+    adr->bm1 = (float)((2.0 - adt) / (2.0 + adt));
+    adr->ai_scale = (float)(2.0 / (2.0 + adt) / adr->kappa0);
+    adr->n_est += 1;
+  }
+  const double dn = sqrt(d2);
+  adr->du_max = dmax;
+  if (past && adr->du_norm > 0.0 && dn > 0.0) {
+    const double rho = pow(dn / adr->du_norm, 1.0 / (double)adr->k);
+    adr->rho = rho;
+    adr->err_est = rho < 1.0 ? rho / (1.0 - rho) * dmax : INFINITY;
+  } else {
+    adr->rho = 0.0;
+    adr->err_est = INFINITY;
+  }
+  adr->du_norm = past ? dn : 0.0;
 }
 
 __global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevState* st) {
@@ -494,6 +604,9 @@ cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
 
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s) {
   if (mode == NODE_UPDATE) return launch_node_m<NODE_UPDATE>(cmp, a, s);
+  if (mode == NODE_ADR) return launch_node_m<NODE_ADR>(cmp, a, s);
+  if (mode == NODE_ADR_STOREF) return launch_node_m<NODE_ADR_STOREF>(cmp, a, s);
+  if (mode == NODE_ADR_RQ) return launch_node_m<NODE_ADR_RQ>(cmp, a, s);
   if (mode == NODE_UPDATE_RESID) return launch_node_m<NODE_UPDATE_RESID>(cmp, a, s);
   if (mode == NODE_RESID_ONLY) return launch_node_m<NODE_RESID_ONLY>(cmp, a, s);
   return launch_node_m<NODE_FORCE_ONLY>(cmp, a, s);
@@ -507,6 +620,12 @@ cudaError_t launch_group_resid(const double2* node_resid, const int* group_node_
 
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s) {
   resid_finalize_kernel<<<1, 256, 0, s>>>(partials, n, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adr_finalize(const double* rq_partials, int n, const DevState* st, AdrState* adr,
+                                cudaStream_t s) {
+  adr_finalize_kernel<<<1, 256, 0, s>>>(rq_partials, n, st, adr);
   return cudaGetLastError();
 }
 
