@@ -108,7 +108,7 @@ def kinematics(u_e: np.ndarray, pre: dict):
     return out
 
 
-def element_forces(u_e: np.ndarray, pre: dict, mat: dict) -> np.ndarray:
+def element_forces(u_e: np.ndarray, pre: dict, mat: dict, pressure=None) -> np.ndarray:
     """Nodal force contributions of every element (Table 3), shape (E, n_e, 3).
 
     mat: model (E,), mu, kappa, eta_a, eta_b, c01 (E,).  For MR, C10 = mu / 2.
@@ -122,6 +122,9 @@ def element_forces(u_e: np.ndarray, pre: dict, mat: dict) -> np.ndarray:
     with Psi = mu/2 (I1-3) + C01 (I2-3) + eta_a/2 (I4-1)^2 + eta_b/2 (I6-1)^2
     + kappa/2 (J-1)^2 (all invariants modified), which gives the NH, TI, OT and
     MR rows of Table 3.  Row a of the result is the force on local node a.
+
+    pressure (E,), optional: replaces dPsi/dJ = kappa (J - 1) (average nodal
+    pressure, oracle/anp.py).
     """
     k = kinematics(u_e, pre)
     J = k["J"]
@@ -136,7 +139,7 @@ def element_forces(u_e: np.ndarray, pre: dict, mat: dict) -> np.ndarray:
     dPsi1 = 0.5 * mat["mu"]
     dPsi4 = np.where((model == TI) | (model == OT), mat["eta_a"] * (I4b - 1.0), 0.0)
     dPsi6 = np.where(model == OT, mat["eta_b"] * (I6b - 1.0), 0.0)
-    JdPsiJ = mat["kappa"] * J * (J - 1.0)
+    JdPsiJ = mat["kappa"] * J * (J - 1.0) if pressure is None else J * np.asarray(pressure)
     dev = (dPsi1[:, None, None] * pre["I1m"] + dPsi4[:, None, None] * pre["I4m"]
            + dPsi6[:, None, None] * pre["I6m"])
     vol_coef = -2.0 / 3.0 * (dPsi1 * I1b + dPsi4 * I4b + dPsi6 * I6b) + JdPsiJ

@@ -43,7 +43,7 @@ Readings (the paper is silent on these):
 """
 import numpy as np
 
-from . import djtled, elements, hourglass
+from . import anp, djtled, elements, hourglass
 
 TET4, HEX8 = elements.TET4, elements.HEX8
 
@@ -89,8 +89,11 @@ class Model:
     """Mesh + material + precomputed oracle constants; evaluates F_int(U)."""
 
     def __init__(self, elem_type, X, conn, mat, a_dir=None, b_dir=None, hg_coeff=0.1,
-                 R=None):
+                 R=None, anp=False):
         self.elem_type = int(elem_type)
+        self.anp = bool(anp)
+        if self.anp and self.elem_type != TET4:
+            raise ValueError("average nodal pressure is built for T4 meshes")
         self.X = np.asarray(X, dtype=np.float64)
         self.conn = np.asarray(conn, dtype=np.int64)
         self.mat = {k: (np.asarray(v, dtype=np.float64) if k != "model" else np.asarray(v))
@@ -110,11 +113,16 @@ class Model:
     def from_problem(cls, p, R=None):
         mat = dict(model=p.model, mu=p.mu, kappa=p.kappa, rho=p.rho, eta_a=p.eta_a,
                    eta_b=p.eta_b, c01=p.c01)
-        return cls(p.elem_type, p.X, p.conn, mat, p.a_dir, p.b_dir, p.hg_coeff, R)
+        return cls(p.elem_type, p.X, p.conn, mat, p.a_dir, p.b_dir, p.hg_coeff, R,
+                   anp=getattr(p, "anp", False))
 
     def element_forces(self, U):
         u_e = U[self.conn]
-        F = djtled.element_forces(u_e, self.pre, self.mat)
+        pbar = None
+        if self.anp:
+            J = djtled.kinematics(u_e, self.pre)["J"]
+            pbar = anp.element_pressure(J, self.pre["V0"], self.mat["kappa"], self.conn, self.N)
+        F = djtled.element_forces(u_e, self.pre, self.mat, pressure=pbar)
         if self.elem_type == HEX8:
             F = F + hourglass.hourglass_forces(u_e, self.gamma, self.k_hg)
         return F

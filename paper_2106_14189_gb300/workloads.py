@@ -89,6 +89,7 @@ class Problem:
     hg_coeff: float = 0.1
     ramp_kind: int = RAMP_SMOOTH
     ramp_steps: int = 0
+    anp: bool = False        # T4: average nodal pressure in place of the element volumetric term
     meta: dict = field(default_factory=dict)
 
     @property
