@@ -88,7 +88,16 @@ typedef struct dj_mesh dj_mesh;
  *                     two floats and the element force is evaluated from the
  *                     increment tJ - 0J so that J - 1 and the deviatoric stress
  *                     keep FP32 relative accuracy at small strain; needed to
- *                     relax stiff (kappa / mu ~ 50) meshes to residuals ~1e-5. */
+ *                     relax stiff (kappa / mu ~ 50) meshes to residuals ~1e-5.
+ *   anp               0 (default): the element volumetric term of Table 3.
+ *                     1: average nodal pressure (Sec. 7's remedy for volumetric
+ *                     locking; T4 with assembly 2 only, else
+ *                     DJ_ERR_INVALID_ARG): the nodal volume ratio J_i = V_i / V0_i
+ *                     from the element volumes shared equally by their nodes,
+ *                     p_i = kappa_i (J_i - 1) with kappa_i the volume-weighted
+ *                     bulk modulus, and each element's volumetric factor
+ *                     kappa (J - 1) replaced by the mean of its nodes' p_i.  Two
+ *                     more kernels per step (element volumes, nodal pressures). */
 typedef struct {
   double dt;
   double dt_scale;
@@ -101,6 +110,7 @@ typedef struct {
   int assembly;
   int tile_size;
   int precision;
+  int anp;
 } dj_params;
 
 /* Read-only description of a mesh after dj_precompute. */
@@ -266,7 +276,7 @@ typedef struct {
  *                (0: no estimate was made)
  *   rho          per-step convergence rate from ||D|| at the last two checks
  *                (0: none)
- *   err_est      rho / (1 - rho) max|D| over free DOFs [m] (inf: none)
+ *   err_est      r / (1 - r) max|D| over free DOFs [m], r = rho^k (inf: none)
  *   n_estimates  damping updates made */
 typedef struct {
   double alpha;
@@ -278,16 +288,17 @@ typedef struct {
 
 /* Adaptive dynamic relaxation (Sec. 6 relaxes with fixed damping; this is the
  * adaptive variant of the method it cites): dj_relax_to_tol whose damping is
- * re-estimated at every check once the ramp is over.  With D = U^n - U^{n-1}
- * and F the internal force, the Rayleigh quotient
- *   lambda = D . (F(U^n) - F(U^{n-1})) / (D . M D)   (free DOFs, FP64 sums)
- * estimates the lowest eigenvalue of M^-1 K (D tends to the slowest mode), and
- * alpha = 2 sqrt(lambda), clamped to [alpha_min, alpha_max], damps that mode
- * critically.  The per-step rate rho = (||D||_k / ||D||_{k-1})^(1/check) of
- * two successive checks gives err_est = rho / (1 - rho) max|D|.  The
- * damping starts from the mesh's alpha; the mesh's own damping (dj_step,
- * dj_run_n, dj_relax_to_tol) is not changed.  Needs relax_check_every >= 2;
- * not for meshes with groups (DJ_ERR_INVALID_ARG).  Synchronous.
+ * re-estimated at every check once the ramp is over.  With D = U^n - U^{n-k}
+ * the change over the check interval k = relax_check_every and F the internal
+ * force, the Rayleigh quotient
+ *   lambda = D . (F(U^n) - F(U^{n-k})) / (D . M D)   (free DOFs, FP64 sums)
+ * estimates the lowest eigenvalue of M^-1 K that the load excites (D tends to
+ * the slowest mode), and alpha = 2 sqrt(lambda), clamped to [alpha_min,
+ * alpha_max], damps that mode critically.  The contraction r = ||D|| / ||D of
+ * the previous interval|| gives rho = r^(1/k) and err_est = r / (1 - r) max|D|.
+ * The damping starts from the mesh's alpha; the mesh's own damping (dj_step,
+ * dj_run_n, dj_relax_to_tol) is not changed.  Not for meshes with groups
+ * (DJ_ERR_INVALID_ARG).  Synchronous.
  *   opts        NULL: alpha_min 0, alpha_max 2 / dt, disp_tol 0
  *   steps_out, residual_out, report  optional
  * Errors: as dj_relax_to_tol. */

@@ -228,15 +228,19 @@ class ExplicitSolver:
 # adaptive scheme, in these steps):
 #   * the damped iteration converges fastest when the slowest mode is damped
 #     critically, alpha = 2 omega_min, omega_min^2 = lambda_min(M^-1 K);
-#   * late in the iteration the increment D = U^n - U^{n-1} is dominated by the
-#     slowest mode, so its Rayleigh quotient with the tangent stiffness,
-#     K D ~ F(U^n) - F(U^{n-1}), estimates lambda_min:
-#         lambda = D . (F(U^n) - F(U^{n-1})) / (D . M D)   over free DOFs;
-#   * the increments then shrink by a fixed factor rho per step, and the
+#   * late in the iteration the displacement change is dominated by the
+#     slowest mode, so its Rayleigh quotient with the tangent stiffness
+#     estimates lambda_min.  The change is taken over a whole check interval,
+#     D = U^n - U^{n-k}, with K D ~ F(U^n) - F(U^{n-k}): over k steps the fast
+#     modes' oscillations cancel, and the force difference stays well above
+#     the rounding of single-precision forces near equilibrium;
+#         lambda = D . (F(U^n) - F(U^{n-k})) / (D . M D)   over free DOFs;
+#   * the changes then shrink by a fixed factor r per interval, and the
 #     remaining distance to equilibrium is bounded by the geometric tail
-#         |U* - U^n| <= rho / (1 - rho) |D|.
-# Estimates are taken at each check (every k steps, from the last two steps of
-# the interval) once the states involved are past the ramp.
+#         |U* - U^n| <= r / (1 - r) |D|,  r = ||D_now|| / ||D_previous||,
+#     the per-step rate being rho = r^(1/k).
+# Estimates are taken at each check (every k steps) once the earlier state is
+# past the ramp (prescribed values fixed between the two).
 
 def rayleigh_quotient(D, dF, mass, free):
     """D . dF / (D . M D) over the free DOFs (D, dF: N x 3; mass: N)."""
@@ -253,14 +257,14 @@ def critical_damping(lam):
     return 2.0 * float(np.sqrt(lam))
 
 
-def convergence_rate(norm_now, norm_before, steps):
-    """Per-step contraction of the increment norm over `steps` steps."""
-    return float((norm_now / norm_before) ** (1.0 / steps))
+def interval_ratio(norm_now, norm_before):
+    """Contraction of the displacement change from one interval to the next."""
+    return float(norm_now / norm_before)
 
 
-def error_estimate(rho, d_max):
-    """Geometric-tail bound rho / (1 - rho) |D| (inf when not contracting)."""
-    return rho / (1.0 - rho) * d_max if rho < 1.0 else np.inf
+def error_estimate(r, d_max):
+    """Geometric-tail bound r / (1 - r) |D| (inf when not contracting)."""
+    return r / (1.0 - r) * d_max if r < 1.0 else np.inf
 
 
 def relax_adaptive(solver, tol, max_steps, check_every=100, alpha_min=0.0, alpha_max=None,
@@ -269,41 +273,44 @@ def relax_adaptive(solver, tol, max_steps, check_every=100, alpha_min=0.0, alpha
     re-estimated at every check.  Returns (steps, residual, converged, report)
     with report = {alpha, lambda, rho, err_est, n_estimates, alphas}."""
     k = int(check_every)
-    assert k >= 2
+    assert k >= 1
     a_max = alpha_max if alpha_max and alpha_max > 0 else 2.0 / solver.dt
     free = solver.free
     rep = {"alpha": solver.alpha, "lambda": 0.0, "rho": 0.0, "err_est": np.inf, "n_estimates": 0,
            "alphas": []}
     norm_prev = 0.0
-    F_before = None
+    snap = None                            # (step index, U, F) of the previous check
     r = np.inf
     for i in range(int(max_steps)):
         n = solver.n                       # state whose force this step evaluates
-        D = solver.U - solver.U_prev       # D^n
+        U_n = solver.U.copy()
         F = solver.step(return_force=True)
-        if (i + 2) % k == 0:
-            F_before = F                   # F(U^{n}) of the step before a check
         if (i + 1) % k == 0:
             r = solver.residual(F)
-            past = solver.ramp_steps <= 0 or n - 1 >= solver.ramp_steps
-            d = D.reshape(-1)[free]
+            past = snap is not None and (solver.ramp_steps <= 0 or snap[0] >= solver.ramp_steps)
             if past:
-                lam = rayleigh_quotient(D, F - F_before, solver.m.mass, free)
+                D = U_n - snap[1]
+                lam = rayleigh_quotient(D, F - snap[2], solver.m.mass, free)
                 if lam > 0.0:
                     alpha = min(max(critical_damping(lam), alpha_min), a_max)
                     solver.set_damping(alpha)
                     rep["lambda"] = lam
                     rep["n_estimates"] += 1
-            rep["alpha"] = solver.alpha
-            rep["alphas"].append(solver.alpha)
-            norm = float(np.linalg.norm(d))
-            if past and norm_prev > 0.0 and norm > 0.0:
-                rho = convergence_rate(norm, norm_prev, k)
-                rep["rho"] = rho
-                rep["err_est"] = error_estimate(rho, float(np.abs(d).max()))
+                d = D.reshape(-1)[free]
+                norm = float(np.linalg.norm(d))
+                if norm_prev > 0.0 and norm > 0.0:
+                    ratio = interval_ratio(norm, norm_prev)
+                    rep["rho"] = ratio ** (1.0 / k)
+                    rep["err_est"] = error_estimate(ratio, float(np.abs(d).max()))
+                else:
+                    rep["rho"], rep["err_est"] = 0.0, np.inf
+                norm_prev = norm
             else:
                 rep["rho"], rep["err_est"] = 0.0, np.inf
-            norm_prev = norm if past else 0.0
+                norm_prev = 0.0
+            rep["alpha"] = solver.alpha
+            rep["alphas"].append(solver.alpha)
+            snap = (n, U_n, F)
             if (r <= tol and n >= solver.ramp_steps
                     and (disp_tol <= 0.0 or rep["err_est"] <= disp_tol)):
                 return i + 1, r, True, rep

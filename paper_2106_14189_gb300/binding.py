@@ -50,7 +50,7 @@ class dj_params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dt_scale", C.c_double), ("alpha", C.c_double),
                 ("hg_coeff", C.c_double), ("ramp_steps", C.c_longlong), ("ramp_kind", C.c_int),
                 ("relax_check_every", C.c_int), ("renumber", C.c_int), ("assembly", C.c_int),
-                ("tile_size", C.c_int), ("precision", C.c_int)]
+                ("tile_size", C.c_int), ("precision", C.c_int), ("anp", C.c_int)]
 
 
 class dj_adr_params(C.Structure):
@@ -605,6 +605,8 @@ class Mesh:
             if params is None:
                 kw = dict(dt=p.dt, dt_scale=p.dt_scale, alpha=p.alpha, hg_coeff=p.hg_coeff,
                           ramp_steps=p.ramp_steps, ramp_kind=p.ramp_kind)
+                if getattr(p, "anp", False):  # average nodal pressure runs on the bulk-copy tiles
+                    kw.update(anp=1, assembly=2)
                 kw.update(param_kw)
                 params = default_params(**kw)
             self.params = params

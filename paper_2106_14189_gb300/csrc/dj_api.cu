@@ -104,9 +104,15 @@ struct dj_mesh {
   cudaGraphExec_t relax_exec = nullptr;
   int relax_k = 0;
   // adaptive dynamic relaxation (allocated on first use)
+  // average nodal pressure (T4, bulk-copy tiles)
+  int anp = 0;
+  float* d_vparts = nullptr;  // per (tile, node): a quarter of the element volume changes
+  float* d_c1 = nullptr;      // per node: kappa_i / V0_i
+  float* d_pres = nullptr;    // per node: p_i
   AdrState* d_adr = nullptr;
   AdrState* h_adr = nullptr;  // pinned
   double* d_rq = nullptr;     // 4 sums per node block
+  double4* d_usnap = nullptr; // U of the previous check (FP64)
   cudaGraphExec_t adr_exec = nullptr;
   int adr_k = 0;
   std::string last_error;
@@ -160,7 +166,7 @@ void release_device(dj_mesh* m) {
   m->run_chunk = m->relax_k = m->adr_k = 0;
   if (m->h_adr) cudaFreeHost(m->h_adr);
   m->h_adr = nullptr;
-  void* ptrs[] = {m->d_adr, m->d_rq,
+  void* ptrs[] = {m->d_adr, m->d_rq, m->d_usnap, m->d_vparts, m->d_c1, m->d_pres,
                   m->d_conn,     m->d_consts,     m->d_slots, m->d_sell, m->d_chunk_ptr, m->d_U,
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
                   m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_pdst, m->d_node_ptr, m->d_save, m->d_out64,
@@ -170,6 +176,8 @@ void release_device(dj_mesh* m) {
     if (p) cudaFree(p);
   m->d_adr = nullptr;
   m->d_rq = nullptr;
+  m->d_usnap = nullptr;
+  m->d_vparts = m->d_c1 = m->d_pres = nullptr;
   m->d_tile_ptr = m->d_tile_nodes = nullptr;
   m->d_lconn = m->d_lptr = m->d_lidx = nullptr;
   m->d_xloc = nullptr;
@@ -318,6 +326,7 @@ ForceArgs force_args(dj_mesh* m, int advance) {
   a.advance = advance;
   a.ramp_steps = m->params.ramp_steps;
   a.ramp_kind = m->params.ramp_kind;
+  a.pres = m->d_pres;
   return a;
 }
 
@@ -339,8 +348,14 @@ TileArgs tile_args(dj_mesh* m) {
 }
 
 cudaError_t launch_force_any(dj_mesh* m, int advance, cudaStream_t s) {
+  if (m->anp) {  // nodal pressures of U^n first
+    cudaError_t e = launch_anp(m->cmp, tile_args(m), m->d_node_ptr, m->d_U, m->d_Ulo, (int)m->E, (int)m->N,
+                               m->d_vparts, m->d_c1, m->d_pres, s);
+    if (e != cudaSuccess) return e;
+  }
   if (m->assembly == ASSEMBLY_TILES_TMA)
-    return launch_force_tma(m->elem_type, m->variant, m->cmp, force_args(m, advance), tile_args(m), m->tma_grid, s);
+    return launch_force_tma(m->elem_type, m->variant, m->cmp, m->anp, force_args(m, advance), tile_args(m),
+                            m->tma_grid, s);
   if (m->assembly == ASSEMBLY_TILES)
     return launch_force_tiled(m->elem_type, m->variant, m->cmp, force_args(m, advance), tile_args(m),
                               m->n_tiles, s);
@@ -365,6 +380,7 @@ NodeArgs node_args(dj_mesh* m) {
   a.st = m->d_state;
   a.adr = m->d_adr;
   a.rq_partials = m->d_rq;
+  a.usnap = m->d_usnap;
   a.N = (int)m->N;
   a.bm1 = m->bm1;
   return a;
@@ -430,6 +446,7 @@ void dj_params_default(dj_params* p) {
   p->assembly = ASSEMBLY_TILES;
   p->tile_size = 0;
   p->precision = 0;
+  p->anp = 0;
 }
 
 const char* dj_status_string(dj_status s) {
@@ -593,8 +610,10 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   if (!(prm.dt_scale > 0) || !(prm.alpha >= 0) || !(prm.hg_coeff >= 0) || prm.relax_check_every <= 0 ||
       (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt) ||
       (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES && prm.assembly != ASSEMBLY_TILES_TMA) ||
-      (prm.precision != 0 && prm.precision != 1))
+      (prm.precision != 0 && prm.precision != 1) || (prm.anp != 0 && prm.anp != 1))
     return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
+  if (prm.anp && (m->ne != 4 || prm.assembly != ASSEMBLY_TILES_TMA))
+    return fail(m, DJ_ERR_INVALID_ARG, "average nodal pressure needs T4 elements and assembly 2");
   {
     const int tmax = prm.assembly == ASSEMBLY_TILES_TMA ? 256 : (m->ne == 4 ? 512 : 256);
     if (prm.tile_size < 0 || prm.tile_size % 32 != 0 || prm.tile_size > tmax)
@@ -854,6 +873,35 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     CK(dalloc(m, &m->d_node_ptr, node_ptr.size()));
     CK(cudaMemcpy(m->d_node_ptr, node_ptr.data(), node_ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
     m->sell_entries = (long long)node_ptr.size();
+    m->anp = prm.anp;
+    if (m->anp) {
+      // kappa_i / V0_i: V0_i = sum of 0V_e / 4 over the node's elements (FP64),
+      // kappa_i their 0V-weighted bulk modulus
+      std::vector<double> v0n(N, 0.0), kv0n(N, 0.0);
+      for (long long e = 0; e < E; ++e) {
+        const int* c = &cn[e * 4];
+        double d[3][3];
+        for (int r = 0; r < 3; ++r)
+          for (int j = 0; j < 3; ++j) d[r][j] = Xn[3 * (size_t)c[r + 1] + j] - Xn[3 * (size_t)c[0] + j];
+        const double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                           d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                           d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+        const double q = det / 6.0 / 4.0, kq = m->kappa[m->elem_old_of_new[e]] * q;
+        for (int b = 0; b < 4; ++b) {
+          v0n[c[b]] += q;
+          kv0n[c[b]] += kq;
+        }
+      }
+      std::vector<float> c1(N, 0.f);
+      for (long long i = 0; i < N; ++i)
+        if (v0n[i] > 0) c1[i] = (float)(kv0n[i] / v0n[i] / v0n[i]);
+      CK(dalloc(m, &m->d_c1, N));
+      CK(cudaMemcpy(m->d_c1, c1.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+      CK(dalloc(m, &m->d_pres, N));
+      CK(cudaMemset(m->d_pres, 0, N * sizeof(float)));
+      CK(dalloc(m, &m->d_vparts, (size_t)m->n_parts));
+      CK(cudaMemset(m->d_vparts, 0, (size_t)m->n_parts * sizeof(float)));
+    }
     CK(cudaMalloc(&d_mass_sell, (sell.size() + 1) * sizeof(int)));
     CK(cudaMemcpy(d_mass_sell, sell.data(), sell.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(cudaMalloc(&d_mass_chunk, chunk_ptr.size() * sizeof(int)));
@@ -884,7 +932,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   if (m->assembly == ASSEMBLY_TILES_TMA) {
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int per_sm = tma_blocks_per_sm(m->elem_type, m->variant, m->cmp, tile_args(m));
+    const int per_sm = tma_blocks_per_sm(m->elem_type, m->variant, m->cmp, m->anp, tile_args(m));
     if (per_sm <= 0) return fail(m, DJ_ERR_UNSUPPORTED, "tile too large for shared memory (tile_size %d)", m->T);
     m->tma_grid = std::min(m->n_tiles, per_sm * sms);
   }
@@ -1359,7 +1407,6 @@ dj_status dj_relax_adaptive(dj_mesh* m, double tol, long long max_steps, const d
   if (!(tol >= 0) || max_steps < 0) return fail(m, DJ_ERR_INVALID_ARG, "bad tol or max_steps");
   if (m->n_groups > 0) return fail(m, DJ_ERR_INVALID_ARG, "adaptive relaxation of a mesh with groups");
   const int k = m->params.relax_check_every;
-  if (k < 2) return fail(m, DJ_ERR_INVALID_ARG, "adaptive relaxation needs relax_check_every >= 2");
   dj_adr_params o{0.0, 0.0, 0.0};
   if (opts) o = *opts;
   const double dt = m->dt;
@@ -1371,6 +1418,8 @@ dj_status dj_relax_adaptive(dj_mesh* m, double tol, long long max_steps, const d
   if (!m->d_adr) {
     CK(dalloc(m, &m->d_adr, 1));
     CK(dalloc(m, &m->d_rq, 4 * (size_t)m->n_node_blocks));
+    CK(dalloc(m, &m->d_usnap, (size_t)m->N));
+    CK(cudaMemset(m->d_usnap, 0, (size_t)m->N * sizeof(double4)));
     CK(cudaMallocHost((void**)&m->h_adr, sizeof(AdrState)));
   }
   // the damping starts from the mesh's alpha
@@ -1393,12 +1442,11 @@ dj_status dj_relax_adaptive(dj_mesh* m, double tol, long long max_steps, const d
     if (m->adr_exec) cudaGraphExecDestroy(m->adr_exec);
     m->adr_exec = nullptr;
     s = capture(m, &m->adr_exec, [&](cudaStream_t cs) {
-      for (int j = 0; j < k - 2; ++j) {
+      for (int j = 0; j < k - 1; ++j) {
         cudaError_t e = launch_step(m, cs, NODE_ADR);
         if (e != cudaSuccess) return e;
       }
-      cudaError_t e = launch_step(m, cs, NODE_ADR_STOREF);
-      if (e == cudaSuccess) e = launch_step(m, cs, NODE_ADR_RQ);
+      cudaError_t e = launch_step(m, cs, NODE_ADR_RQ);
       if (e == cudaSuccess) e = cudaMemcpyAsync(m->h_adr, m->d_adr, sizeof(AdrState), cudaMemcpyDeviceToHost, cs);
       if (e != cudaSuccess) return e;
       return cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, cs);

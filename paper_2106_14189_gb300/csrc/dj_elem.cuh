@@ -69,12 +69,15 @@ __device__ __forceinline__ void add_tJT_sym(M3& acc, const M3& tJ, const float* 
     }
 }
 
-// Per-element constants of the table, loaded once into registers.
-template <bool FA, bool FB, bool MR>
+// Per-element constants of the table, loaded once into registers.  ANP: the
+// volumetric factor kappa 0V (J - 1) / det 0J is replaced by pv = pbar / 6, the
+// element's mean nodal pressure times 0V / det 0J (T4, average nodal pressure).
+template <bool FA, bool FB, bool MR, bool ANP = false>
 struct ElemConsts {
   float J0[3][3];
   float P[6];
   float kV, r0;
+  float pv;
   float Qa[FA ? 6 : 1], sa;
   float Qb[FB ? 6 : 1], sb;
   float gm;
@@ -168,8 +171,8 @@ struct HgConsts {
 };
 
 // F = J^-2/3 tJ^T (P + psi_a Q_a + psi_b Q_b + MR) + coefficient * adj(tJ)   (Table 3)
-template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA, FB, MR>& k,
+template <bool FA, bool FB, bool MR, bool ANP>
+__device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA, FB, MR, ANP>& k,
                                               bool& bad) {
   const M3 A = adj3(tJ);  // det(tJ) tJ^-1
   const float D = tJ.m[0][0] * A.m[0][0] + tJ.m[0][1] * A.m[1][0] + tJ.m[0][2] * A.m[2][0];
@@ -239,7 +242,7 @@ __device__ __forceinline__ M3 dj_force_matrix(const M3& tJ, const ElemConsts<FA,
     mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) * kThird;  // -2/3 2 C01 I2bar 0V
   }
   const float invD = __fdividef(1.f, D);
-  const float ca = (Jm23 * vol_over_D + mr_vol) * invD + k.kV * (J - 1.f) * k.r0;
+  const float ca = (Jm23 * vol_over_D + mr_vol) * invD + (ANP ? k.pv : k.kV * (J - 1.f) * k.r0);
   M3 F;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -333,8 +336,8 @@ __device__ __forceinline__ M3 adj_delta(const M3& A, const M3& B) {
 //   I4bar - 1    = (J^-2/3 - 1) + J^-2/3 (P_a : (A B^T + B A^T + B B^T)) s_a
 // Every term is of the order of the increment, so FP32 keeps its relative
 // accuracy at small strain instead of losing it to cancellation.
-template <bool FA, bool FB, bool MR>
-__device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, const ElemConsts<FA, FB, MR>& k,
+template <bool FA, bool FB, bool MR, bool ANP>
+__device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, const ElemConsts<FA, FB, MR, ANP>& k,
                                                   bool& bad) {
   M3 tJ;
 #pragma unroll
@@ -426,7 +429,7 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
     mr_vol = -Jm23 * Jm23 * k.gm * (gP * gP - trPgPg) * kThird;
   }
   const float cA = mV * jm1 * invD, cD = -mV * invD;
-  const float cadj = mr_vol * invD + k.kV * jm1 * k.r0;  // volumetric: kappa 0V (J-1) r0 adj(tJ)
+  const float cadj = mr_vol * invD + (ANP ? k.pv : k.kV * jm1 * k.r0);  // volumetric: kappa 0V (J-1) r0 adj(tJ)
   M3 F;
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -438,8 +441,8 @@ __device__ __forceinline__ M3 dj_force_matrix_cmp(const M3& A, const M3& B, cons
   return F;
 }
 
-template <bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ M3 force_matrix(const M3& A, const M3& B, const ElemConsts<FA, FB, MR>& k,
+template <bool FA, bool FB, bool MR, bool CMP, bool ANP>
+__device__ __forceinline__ M3 force_matrix(const M3& A, const M3& B, const ElemConsts<FA, FB, MR, ANP>& k,
                                            bool& bad) {
   if constexpr (CMP) {
     return dj_force_matrix_cmp<FA, FB, MR>(A, B, k, bad);
@@ -470,8 +473,8 @@ __device__ __forceinline__ float node_diff(float hb, float h0, float lb, float l
 // Nodal forces of one T4 element from d_b = u_b - u_0 (b = 1..3):
 // tJ = 0J + H_xi u has rows d_1, d_2, d_3 (Eq. 11); F H_xi gives node b = 1..3
 // column b-1 and node 0 minus their sum (Sec. 7).
-template <bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ void tet4_forces(const float (&d)[4][3], const ElemConsts<FA, FB, MR>& k,
+template <bool FA, bool FB, bool MR, bool CMP, bool ANP>
+__device__ __forceinline__ void tet4_forces(const float (&d)[4][3], const ElemConsts<FA, FB, MR, ANP>& k,
                                             const ElemExtra<4>&, float (&f)[4][3], bool& inv) {
   M3 A, B;
 #pragma unroll
@@ -657,8 +660,8 @@ __device__ __forceinline__ void hex8_forces_stream(Ld ld, LdX ldx, ElemConsts<FA
   }
 }
 
-template <int NE, bool FA, bool FB, bool MR, bool CMP>
-__device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemConsts<FA, FB, MR>& k,
+template <int NE, bool FA, bool FB, bool MR, bool CMP, bool ANP>
+__device__ __forceinline__ void elem_forces(const float (&d)[NE][3], const ElemConsts<FA, FB, MR, ANP>& k,
                                             const ElemExtra<NE>& x, float (&f)[NE][3], bool& inv) {
   if constexpr (NE == 4)
     tet4_forces<FA, FB, MR, CMP>(d, k, x, f, inv);

@@ -60,17 +60,18 @@ struct ForceArgs {
   int advance;           // 1: this launch is a time step (bump step, ramp)
   long long ramp_steps;
   int ramp_kind;
+  const float* pres;     // average nodal pressure: p_i of every node (else unused)
 };
 
 // Adaptive dynamic relaxation (one per mesh, device memory).  The damping in
 // use is alpha; the update kernels of the adaptive steps take b - 1 and the
 // scale of the precomputed a_i (a_i(alpha) / a_i(alpha_0)) from here.  At every
-// check the increment D = U^n - U^{n-1} and the change of the force between
-// the last two steps give the Rayleigh quotient
-//   lambda = D . (F(U^n) - F(U^{n-1})) / (D . M D)    (free DOFs)
+// check (every k steps) the change over the interval, D = U^n - U^{n-k}, and
+// that of the force give the Rayleigh quotient
+//   lambda = D . (F(U^n) - F(U^{n-k})) / (D . M D)    (free DOFs)
 // of M^-1 K along D, alpha becomes 2 sqrt(lambda) (critical damping of that
-// mode, clamped), and the ratio of ||D|| at successive checks the per-step
-// convergence rate rho, with err_est = rho / (1 - rho) max|D| the estimated
+// mode, clamped), and the ratio r of ||D|| at successive checks gives the
+// per-step rate rho = r^(1/k) and err_est = r / (1 - r) max|D|, the estimated
 // distance to equilibrium.
 struct AdrState {
   // inputs, written by the host before each relaxation
@@ -90,6 +91,8 @@ struct AdrState {
   double du_norm;     // ||D||_2 over free DOFs at the previous check past the ramp (0: none)
   double du_max;      // max |D| over free DOFs
   long long n_est;    // damping updates made
+  long long snap_step;  // step index of the snapshot (U, F - R) of the previous check
+  int has_prev;         // 0 until the first check has stored a snapshot
 };
 
 struct NodeArgs {
@@ -110,6 +113,7 @@ struct NodeArgs {
   DevState* st;           // ramp value (read), error flags (written)
   const AdrState* adr;    // adaptive modes: damping in use (else nullptr)
   double* rq_partials;    // NODE_ADR_RQ: 4 sums per block (D.dF, D^2 / a_i, D^2, max |D|)
+  double4* usnap;         // NODE_ADR_RQ: U of the previous check (FP64, hi + lo); F - R of it in fout
   int N;
   float bm1;              // b - 1 = (2 - alpha dt) / (2 + alpha dt)
 };
@@ -142,10 +146,10 @@ struct TileArgs {
 };
 
 enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_ONLY = 3,
-       // adaptive dynamic relaxation: the update with the damping of AdrState,
-       // optionally storing F - R (the step before a check) or adding the
-       // Rayleigh-quotient and increment sums to the residual (the check step)
-       NODE_ADR = 4, NODE_ADR_STOREF = 5, NODE_ADR_RQ = 6 };
+       // adaptive dynamic relaxation: the update with the damping of AdrState;
+       // at a check also the Rayleigh-quotient and interval sums against the
+       // previous check's snapshot (U, F - R), which it then replaces
+       NODE_ADR = 4, NODE_ADR_RQ = 5 };
 
 // Programmatic dependent launch: the kernels of a step may start while the
 // kernel before them in the stream finishes; each of them reads or writes what
@@ -184,12 +188,17 @@ cudaError_t launch_force(int elem_type, int variant, int cmp, const ForceArgs& a
 cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceArgs& a,
                                const TileArgs& t, int n_tiles, cudaStream_t s);
 // kernels_tma.cu: persistent, double-buffered tiles staged with bulk async copies
-cudaError_t launch_force_tma(int elem_type, int variant, int cmp, const ForceArgs& a,
+// anp: average nodal pressure (T4 only; reads ForceArgs::pres)
+cudaError_t launch_force_tma(int elem_type, int variant, int cmp, int anp, const ForceArgs& a,
                              const TileArgs& t, int grid, cudaStream_t s);
-size_t tma_smem_bytes(int elem_type, int cmp, const TileArgs& t);
-int tma_blocks_per_sm(int elem_type, int variant, int cmp, const TileArgs& t);
+size_t tma_smem_bytes(int elem_type, int cmp, int anp, const TileArgs& t);
+int tma_blocks_per_sm(int elem_type, int variant, int cmp, int anp, const TileArgs& t);
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s);
 cudaError_t launch_resid_finalize(const double2* partials, int n, DevState* st, cudaStream_t s);
+// average nodal pressure (T4, tiles): volume pass and nodal pressures
+size_t anp_volume_smem(int cmp, const TileArgs& t);
+cudaError_t launch_anp(int cmp, const TileArgs& t, const int* node_ptr, const float4* U, const float4* Ulo, int E,
+                       int N, float* vparts, const float* c1, float* pres, cudaStream_t s);
 cudaError_t launch_adr_finalize(const double* rq_partials, int n, const DevState* st, AdrState* adr,
                                 cudaStream_t s);
 // per-group residual sums over contiguous node ranges (one block per group)

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
 
 template <int MODE, bool CMP>
 __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
-  constexpr bool ADR = MODE == NODE_ADR || MODE == NODE_ADR_STOREF || MODE == NODE_ADR_RQ;
+  constexpr bool ADR = MODE == NODE_ADR || MODE == NODE_ADR_RQ;
   constexpr bool UPD = MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID || ADR;
   constexpr bool RESID = MODE == NODE_UPDATE_RESID || MODE == NODE_RESID_ONLY || MODE == NODE_ADR_RQ;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,7 +292,6 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       // adaptive steps take b - 1 and the scale of a_i from the relaxation state
       const float ai = ADR ? U.w * a.adr->ai_scale : U.w;
       const float bm1 = ADR ? a.adr->bm1 : (a.bm1_node ? __ldg(a.bm1_node + i) : a.bm1);
-      const float4 D = V;  // D^n = U^n - U^{n-1}
       float dd[3] = {fmaf(-ai, fx, bm1 * V.x), fmaf(-ai, fy, bm1 * V.y), fmaf(-ai, fz, bm1 * V.z)};
       const float uh[3] = {U.x, U.y, U.z};
       float nh[3], nl[3] = {0.f, 0.f, 0.f}, ul[3] = {0.f, 0.f, 0.f};
@@ -332,10 +331,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       // a non-finite element force reaches U^{n+1} of its nodes (NaN and Inf
       // propagate through the update), or the reaction of prescribed ones
       if (!isfinite(nh[0] + nh[1] + nh[2] + fx + fy + fz)) flag_nonfinite(a.st, i);
-      a.U[i] = make_float4(nh[0], nh[1], nh[2], ai);
+      a.U[i] = make_float4(nh[0], nh[1], nh[2], U.w);  // w keeps the precomputed a_i
       if (CMP) a.Ulo[i] = make_float4(nl[0], nl[1], nl[2], 0.f);
       a.V[i] = make_float4(dd[0], dd[1], dd[2], V.w);
-      if (MODE == NODE_ADR_STOREF) a.fout[i] = make_float4(fx, fy, fz, 0.f);
       if (MODE == NODE_UPDATE_RESID || MODE == NODE_ADR_RQ) {
         const double f3[3] = {fx, fy, fz};
 #pragma unroll
@@ -345,11 +343,15 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
         }
       }
       if (MODE == NODE_ADR_RQ) {
-        // F(U^n) - F(U^{n-1}) along D^n over the free DOFs; the lumped mass
-        // enters as 1 / a_i(alpha_0) (times kappa0 dt^2, applied once at the end)
+        // D = U^n - U^{n-k} and F(U^n) - F(U^{n-k}) against the previous
+        // check's snapshot, over the free DOFs; the lumped mass enters as
+        // 1 / a_i(alpha_0) (times kappa0 dt^2, applied once at the end).  Then
+        // this check's U^n and F - R become the snapshot.
         const float4 fp = a.fout[i];
+        const double4 us = a.usnap[i];
+        const double un[3] = {(double)uh[0] + ul[0], (double)uh[1] + ul[1], (double)uh[2] + ul[2]};
         const double df[3] = {(double)fx - fp.x, (double)fy - fp.y, (double)fz - fp.z};
-        const double d[3] = {D.x, D.y, D.z};
+        const double d[3] = {un[0] - us.x, un[1] - us.y, un[2] - us.z};
         const double inv_a = U.w > 0.f ? 1.0 / (double)U.w : 0.0;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
@@ -359,6 +361,8 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
             rq_d2 += d[q] * d[q];
             rq_max = fmax(rq_max, fabs(d[q]));
           }
+        a.usnap[i] = make_double4(un[0], un[1], un[2], 0.0);
+        a.fout[i] = make_float4(fx, fy, fz, 0.f);
       }
     }
   }
@@ -450,10 +454,10 @@ __global__ void adr_finalize_kernel(const double* __restrict__ p, int n, const D
   }
   if (threadIdx.x != 0) return;
   const double dfd = s[0][0], dmd_a = s[1][0], d2 = s[2][0], dmax = s[3][0];
-  // the force of this step was evaluated at U^n, n = step - 1; D^n and the
-  // stored force of U^{n-1} count once U^{n-1} is past the ramp
+  // the force of this step was evaluated at U^n, n = step - 1; the interval
+  // counts once the previous check's state is past the ramp
   const long long n_eval = st->step - 1;
-  const bool past = adr->ramp_steps <= 0 || n_eval - 1 >= adr->ramp_steps;
+  const bool past = adr->has_prev && (adr->ramp_steps <= 0 || adr->snap_step >= adr->ramp_steps);
   const double mdd = adr->kappa0 * adr->dt * adr->dt * dmd_a;  // D . M D
   if (past && mdd > 0.0 && dfd > 0.0) {
     const double lam = dfd / mdd;
@@ -468,14 +472,16 @@ __global__ void adr_finalize_kernel(const double* __restrict__ p, int n, const D
   const double dn = sqrt(d2);
   adr->du_max = dmax;
   if (past && adr->du_norm > 0.0 && dn > 0.0) {
-    const double rho = pow(dn / adr->du_norm, 1.0 / (double)adr->k);
-    adr->rho = rho;
-    adr->err_est = rho < 1.0 ? rho / (1.0 - rho) * dmax : INFINITY;
+    const double r = dn / adr->du_norm;  // contraction over one interval
+    adr->rho = pow(r, 1.0 / (double)adr->k);
+    adr->err_est = r < 1.0 ? r / (1.0 - r) * dmax : INFINITY;
   } else {
     adr->rho = 0.0;
     adr->err_est = INFINITY;
   }
   adr->du_norm = past ? dn : 0.0;
+  adr->snap_step = n_eval;
+  adr->has_prev = 1;
 }
 
 __global__ void resid_finalize_kernel(const double2* __restrict__ p, int n, DevState* st) {
@@ -605,7 +611,6 @@ cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s) {
   if (mode == NODE_UPDATE) return launch_node_m<NODE_UPDATE>(cmp, a, s);
   if (mode == NODE_ADR) return launch_node_m<NODE_ADR>(cmp, a, s);
-  if (mode == NODE_ADR_STOREF) return launch_node_m<NODE_ADR_STOREF>(cmp, a, s);
   if (mode == NODE_ADR_RQ) return launch_node_m<NODE_ADR_RQ>(cmp, a, s);
   if (mode == NODE_UPDATE_RESID) return launch_node_m<NODE_UPDATE_RESID>(cmp, a, s);
   if (mode == NODE_RESID_ONLY) return launch_node_m<NODE_RESID_ONLY>(cmp, a, s);

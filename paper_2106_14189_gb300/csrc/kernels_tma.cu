@@ -97,16 +97,21 @@ __device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t
 __device__ __forceinline__ void async_copy16(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void async_copy4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 __device__ __forceinline__ void async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// stage the tile's nodal U (and low parts) into su / sl with cp.async
-template <bool CMP>
+// stage the tile's nodal U (and low parts, and nodal pressures) into su / sl /
+// sp with cp.async
+template <bool CMP, bool ANP>
 __device__ __forceinline__ void gather_nodes(const ForceArgs& a, const int* tnodes, int n_t, float4* su,
-                                             float4* sl, int tid, int T) {
+                                             float4* sl, float* sp, int tid, int T) {
   for (int q = tid; q < n_t; q += T) {
     const int gid = tnodes[q];
     async_copy16(su + q, a.U + gid);
     if (CMP) async_copy16(sl + q, a.Ulo + gid);
+    if (ANP) async_copy4(sp + q, a.pres + gid);
   }
 }
 
@@ -114,7 +119,7 @@ __device__ __forceinline__ void gather_nodes(const ForceArgs& a, const int* tnod
 //   bulk copies of a tile's segments are issued two tiles ahead (stages 0/1),
 //   the nodal gather of tile k+1 (cp.async) is in flight while tile k's
 //   element forces are reduced, and a tile costs two block barriers.
-template <int NE, bool FA, bool FB, bool MR, bool CMP>
+template <int NE, bool FA, bool FB, bool MR, bool CMP, bool ANP>
 __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t) {
   extern __shared__ __align__(128) char smem[];
   const StageLayout<NE> L(t);
@@ -124,7 +129,8 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   float4* su2 = sbase;                              // [2][cap] staged U, by tile parity
   float4* sl2 = sbase + 2 * cap;                    // [2][cap] staged low parts (compensated)
   float4* sf4 = sbase + (CMP ? 4 : 2) * cap;        // NE T force records (slot a T + e)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sf4 + NE * T);
+  float* sp2 = reinterpret_cast<float*>(sf4 + NE * T);  // [2][cap] nodal pressures (ANP)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sp2 + (ANP ? 2 * cap : 0));
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     }
     const int* tn = reinterpret_cast<const int*>(smem + L.tnodes);
     const int n0 = __ldg(t.tile_ptr + first + 1) - __ldg(t.tile_ptr + first);
-    gather_nodes<CMP>(a, tn, n0, su2, sl2, tid, T);
+    gather_nodes<CMP, ANP>(a, tn, n0, su2, sl2, sp2, tid, T);
     async_wait_all();
     __syncthreads();
   }
@@ -169,17 +175,24 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     const int* pdst = reinterpret_cast<const int*>(st + L.pdst);
     const float4* su = su2 + s * cap;
     const float4* sl = sl2 + s * cap;
+    const float* sp = sp2 + s * cap;
     const int base = __ldg(t.tile_ptr + tile);
     const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
     // 1. element forces of this tile into shared memory
     const int e = tile * T + tid;
     if (e < a.E) {
       const auto ld = [&](int r) { return tab[r * T + tid]; };
-      ElemConsts<FA, FB, MR> k;
+      ElemConsts<FA, FB, MR, ANP> k;
       int lc[NE];
 #pragma unroll
       for (int b = 0; b < NE; ++b) lc[b] = lconn[tid * NE + b];
       k.load_geometric(ld, a);
+      if constexpr (ANP) {  // mean nodal pressure times 0V / det 0J = 1 / 6
+        float ps = sp[lc[0] >> 4];
+#pragma unroll
+        for (int b = 1; b < NE; ++b) ps += sp[lc[b] >> 4];
+        k.pv = ps * (1.f / 24.f);
+      }
       bool inv;
       if constexpr (NE == 8) {
         HgConsts hg;
@@ -235,7 +248,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     if (has_next) {
       const int* tn = reinterpret_cast<const int*>(smem + (s ^ 1) * stage_bytes + L.tnodes);
       const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
-      gather_nodes<CMP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, tid, T);
+      gather_nodes<CMP, ANP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, sp2 + (s ^ 1) * cap, tid, T);
     }
     reduce_tile(sf4, lidx, lptr, n_t, tid, T, [&](int q, float4 f) { t.partials[pdst[q]] = f; });
     async_wait_all();
@@ -245,72 +258,83 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   }
 }
 
-template <int NE, bool CMP>
+template <int NE, bool CMP, bool ANP>
 size_t smem_bytes_t(const TileArgs& t) {
   const StageLayout<NE> L(t);
   const size_t stage = (L.bytes + 127) & ~size_t(127);
-  return 2 * stage + (size_t)(CMP ? 4 : 2) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) + 16;
+  return 2 * stage + (size_t)(CMP ? 4 : 2) * t.cap * sizeof(float4) + (size_t)NE * t.T * sizeof(float4) +
+         (ANP ? 2 * (size_t)t.cap * sizeof(float) : 0) + 16;
 }
 
-template <int NE, bool FA, bool FB, bool MR, bool CMP>
+template <int NE, bool FA, bool FB, bool MR, bool CMP, bool ANP>
 cudaError_t launch_t(const ForceArgs& a, const TileArgs& t, int grid, cudaStream_t s) {
-  const size_t smem = smem_bytes_t<NE, CMP>(t);
-  return launch_pdl(force_tma_kernel<NE, FA, FB, MR, CMP>, dim3(grid), dim3(t.T), smem, s, a, t);
+  const size_t smem = smem_bytes_t<NE, CMP, ANP>(t);
+  return launch_pdl(force_tma_kernel<NE, FA, FB, MR, CMP, ANP>, dim3(grid), dim3(t.T), smem, s, a, t);
 }
 
-template <int NE, bool FA, bool FB, bool MR, bool CMP>
+template <int NE, bool FA, bool FB, bool MR, bool CMP, bool ANP>
 int occupancy_t(const TileArgs& t) {
-  const size_t smem = smem_bytes_t<NE, CMP>(t);
+  const size_t smem = smem_bytes_t<NE, CMP, ANP>(t);
   // allow the largest dynamic shared memory once, outside any stream capture
-  if (cudaFuncSetAttribute(force_tma_kernel<NE, FA, FB, MR, CMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(force_tma_kernel<NE, FA, FB, MR, CMP, ANP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            227 * 1024) != cudaSuccess)
     return 0;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, force_tma_kernel<NE, FA, FB, MR, CMP>, t.T, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, force_tma_kernel<NE, FA, FB, MR, CMP, ANP>, t.T, smem) !=
       cudaSuccess)
     return 0;
   return n;
 }
 
-template <int NE, bool CMP>
+template <int NE, bool CMP, bool ANP>
 cudaError_t launch_v(int variant, const ForceArgs& a, const TileArgs& t, int grid, cudaStream_t s) {
   switch (variant) {
-    case VAR_NH: return launch_t<NE, false, false, false, CMP>(a, t, grid, s);
-    case VAR_TI: return launch_t<NE, true, false, false, CMP>(a, t, grid, s);
-    case VAR_OT: return launch_t<NE, true, true, false, CMP>(a, t, grid, s);
-    case VAR_MR: return launch_t<NE, false, false, true, CMP>(a, t, grid, s);
-    default: return launch_t<NE, true, true, true, CMP>(a, t, grid, s);
+    case VAR_NH: return launch_t<NE, false, false, false, CMP, ANP>(a, t, grid, s);
+    case VAR_TI: return launch_t<NE, true, false, false, CMP, ANP>(a, t, grid, s);
+    case VAR_OT: return launch_t<NE, true, true, false, CMP, ANP>(a, t, grid, s);
+    case VAR_MR: return launch_t<NE, false, false, true, CMP, ANP>(a, t, grid, s);
+    default: return launch_t<NE, true, true, true, CMP, ANP>(a, t, grid, s);
   }
 }
 
-template <int NE, bool CMP>
+template <int NE, bool CMP, bool ANP>
 int occupancy_v(int variant, const TileArgs& t) {
   switch (variant) {
-    case VAR_NH: return occupancy_t<NE, false, false, false, CMP>(t);
-    case VAR_TI: return occupancy_t<NE, true, false, false, CMP>(t);
-    case VAR_OT: return occupancy_t<NE, true, true, false, CMP>(t);
-    case VAR_MR: return occupancy_t<NE, false, false, true, CMP>(t);
-    default: return occupancy_t<NE, true, true, true, CMP>(t);
+    case VAR_NH: return occupancy_t<NE, false, false, false, CMP, ANP>(t);
+    case VAR_TI: return occupancy_t<NE, true, false, false, CMP, ANP>(t);
+    case VAR_OT: return occupancy_t<NE, true, true, false, CMP, ANP>(t);
+    case VAR_MR: return occupancy_t<NE, false, false, true, CMP, ANP>(t);
+    default: return occupancy_t<NE, true, true, true, CMP, ANP>(t);
   }
 }
 
 }  // namespace
 
-size_t tma_smem_bytes(int elem_type, int cmp, const TileArgs& t) {
-  if (elem_type == DJ_TET4) return cmp ? smem_bytes_t<4, true>(t) : smem_bytes_t<4, false>(t);
-  return cmp ? smem_bytes_t<8, true>(t) : smem_bytes_t<8, false>(t);
+// anp (average nodal pressure) is built for T4 only; H8 ignores it
+size_t tma_smem_bytes(int elem_type, int cmp, int anp, const TileArgs& t) {
+  if (elem_type == DJ_TET4) {
+    if (anp) return cmp ? smem_bytes_t<4, true, true>(t) : smem_bytes_t<4, false, true>(t);
+    return cmp ? smem_bytes_t<4, true, false>(t) : smem_bytes_t<4, false, false>(t);
+  }
+  return cmp ? smem_bytes_t<8, true, false>(t) : smem_bytes_t<8, false, false>(t);
 }
 
-int tma_blocks_per_sm(int elem_type, int variant, int cmp, const TileArgs& t) {
-  if (elem_type == DJ_TET4) return cmp ? occupancy_v<4, true>(variant, t) : occupancy_v<4, false>(variant, t);
-  return cmp ? occupancy_v<8, true>(variant, t) : occupancy_v<8, false>(variant, t);
+int tma_blocks_per_sm(int elem_type, int variant, int cmp, int anp, const TileArgs& t) {
+  if (elem_type == DJ_TET4) {
+    if (anp) return cmp ? occupancy_v<4, true, true>(variant, t) : occupancy_v<4, false, true>(variant, t);
+    return cmp ? occupancy_v<4, true, false>(variant, t) : occupancy_v<4, false, false>(variant, t);
+  }
+  return cmp ? occupancy_v<8, true, false>(variant, t) : occupancy_v<8, false, false>(variant, t);
 }
 
-cudaError_t launch_force_tma(int elem_type, int variant, int cmp, const ForceArgs& a, const TileArgs& t,
+cudaError_t launch_force_tma(int elem_type, int variant, int cmp, int anp, const ForceArgs& a, const TileArgs& t,
                              int grid, cudaStream_t s) {
-  if (elem_type == DJ_TET4)
-    return cmp ? launch_v<4, true>(variant, a, t, grid, s) : launch_v<4, false>(variant, a, t, grid, s);
-  return cmp ? launch_v<8, true>(variant, a, t, grid, s) : launch_v<8, false>(variant, a, t, grid, s);
+  if (elem_type == DJ_TET4) {
+    if (anp)
+      return cmp ? launch_v<4, true, true>(variant, a, t, grid, s) : launch_v<4, false, true>(variant, a, t, grid, s);
+    return cmp ? launch_v<4, true, false>(variant, a, t, grid, s) : launch_v<4, false, false>(variant, a, t, grid, s);
+  }
+  return cmp ? launch_v<8, true, false>(variant, a, t, grid, s) : launch_v<8, false, false>(variant, a, t, grid, s);
 }
 
 }  // namespace dj

@@ -3,8 +3,8 @@ oracle's adaptive relaxation (oracle/dynamics.py relax_adaptive).
 
 Tolerances: the relaxed fields within 2e-4 rel-Linf of the oracle's (both
 stop at r <= 1e-5, compensated precision, as for the plain relaxation
-tests); the damping estimates within 1 % (FP32 increments and force
-differences against FP64); step counts within two check intervals.
+tests); the damping estimates within 2 % (FP32 forces against FP64 over a
+check interval); step counts within two check intervals.
 """
 import numpy as np
 import pytest
@@ -46,22 +46,22 @@ def test_adaptive_relaxation_matches_oracle(B, et, alpha0, assembly):
     assert ok and st == 0 and r <= 1e-5
     assert abs(steps - n_ref) <= 100
     assert rel_linf(U, s.U) < 2e-4
-    assert rep["alpha"] == pytest.approx(ref["alpha"], rel=1e-2)
-    assert rep["lambda"] == pytest.approx(ref["lambda"], rel=2e-2)
+    assert rep["alpha"] == pytest.approx(ref["alpha"], rel=2e-2)
+    assert rep["lambda"] == pytest.approx(ref["lambda"], rel=4e-2)
     assert abs(rep["n_estimates"] - ref["n_estimates"]) <= 2
     assert np.isfinite(rep["err_est"]) and 0.0 < rep["rho"] < 1.0
 
 
 def test_first_estimate_matches_oracle(B):
-    """The first damping update (the first check past the ramp) from identical
-    trajectories: FP32 increments against FP64 ones."""
+    """The first damping update (the first check whose previous check is past
+    the ramp) from identical trajectories: FP32 against FP64."""
     p = W.cube_shear(W.TET4, 5, shear=0.1)
     p.alpha, p.ramp_steps = 40.0, 200
     with B.Mesh(p, relax_check_every=50, precision=1) as m:
-        st, steps, r, rep = m.relax_adaptive(0.0, 250, raise_on_fail=False)
+        st, steps, r, rep = m.relax_adaptive(0.0, 300, raise_on_fail=False)
     s = dynamics.ExplicitSolver.from_problem(p)
-    n_ref, r_ref, ok, ref = dynamics.relax_adaptive(s, 0.0, 250, check_every=50)
-    assert steps == n_ref == 250
+    n_ref, r_ref, ok, ref = dynamics.relax_adaptive(s, 0.0, 300, check_every=50)
+    assert steps == n_ref == 300
     assert rep["n_estimates"] == ref["n_estimates"] == 1
     print(f"lambda {rep['lambda']:.6f} / {ref['lambda']:.6f}")
     assert rep["lambda"] == pytest.approx(ref["lambda"], rel=1e-3)
@@ -75,7 +75,8 @@ def test_adaptive_beats_fixed_damping(B):
         p = W.cube_shear(W.TET4, 6, shear=0.1)
         p.alpha, p.ramp_steps = alpha0, 200
         with B.Mesh(p, relax_check_every=50, precision=1) as m:
-            _, fixed, _ = m.relax(1e-5, 60000)
+            # the under-damped start may not converge at all within the cap
+            _, fixed, _ = m.relax(1e-5, 60000, raise_on_fail=False)
         with B.Mesh(p, relax_check_every=50, precision=1) as m:
             _, adaptive, _, rep = m.relax_adaptive(1e-5, 60000)
         print(f"alpha0 {alpha0}: fixed {fixed} steps, adaptive {adaptive} (alpha {rep['alpha']:.3f})")
@@ -126,9 +127,6 @@ def test_adaptive_runs_are_deterministic_and_leave_damping(B):
 
 def test_adaptive_argument_checks(B):
     p = W.cube_shear(W.TET4, 3, shear=0.1)
-    with B.Mesh(p, relax_check_every=1) as m:
-        st, *_ = m.relax_adaptive(1e-5, 100, raise_on_fail=False)
-        assert st == B.DJ_ERR_INVALID_ARG
     with B.Mesh(p, relax_check_every=50) as m:
         st, *_ = m.relax_adaptive(1e-5, 100, alpha_min=5.0, alpha_max=1.0, raise_on_fail=False)
         assert st == B.DJ_ERR_INVALID_ARG

@@ -88,13 +88,13 @@ def test_error_estimate_is_exact_on_a_geometric_sequence():
     u_star = rng.normal(size=30)
     C = rng.normal(size=30)
     rho, k = 0.97, 25
-    u = [u_star + C * rho ** n for n in range(0, 3 * k + 2)]
-    n = 3 * k + 1
-    D_now = u[n] - u[n - 1]
-    D_before = u[n - k] - u[n - k - 1]
-    r = dynamics.convergence_rate(np.linalg.norm(D_now), np.linalg.norm(D_before), k)
-    assert r == pytest.approx(rho, rel=1e-12)
-    # |u* - u_n| = sum_{j > n} |D_j| = rho / (1 - rho) |D_n| componentwise
+    u = [u_star + C * rho ** n for n in range(0, 3 * k + 1)]
+    n = 3 * k
+    D_now = u[n] - u[n - k]             # change over the last interval
+    D_before = u[n - k] - u[n - 2 * k]  # and over the one before
+    r = dynamics.interval_ratio(np.linalg.norm(D_now), np.linalg.norm(D_before))
+    assert r == pytest.approx(rho ** k, rel=1e-12)
+    # |u* - u_n| = sum of all later intervals = r / (1 - r) |D_now| componentwise
     est = dynamics.error_estimate(r, np.abs(D_now).max())
     assert est == pytest.approx(np.abs(u_star - u[n]).max(), rel=1e-10)
     assert dynamics.error_estimate(1.0, 1.0) == np.inf

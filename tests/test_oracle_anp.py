@@ -112,3 +112,25 @@ def test_anp_relieves_volumetric_locking():
         assert r[(True, nu)][0] < 1.0 and r[(True, nu)][1] > 0.0
     assert r[(False, 0.3)][0] > 20 * r[(False, 0.499)][0]     # the element formulation locks
     assert r[(True, 0.3)][0] < 1.5 * r[(True, 0.499)][0]      # ANP does not
+
+
+def test_anp_keeps_the_critical_step():
+    """Averaging lowers the volumetric stiffness: the highest eigenvalue of
+    M^-1 K with ANP stays below the element formulation's, so the element
+    formulation's critical step (Eq. 14) remains stable."""
+    from scipy.linalg import eigh
+    lam_max = {}
+    for on in (False, True):
+        p = W.cube_compression_tet4(n=3)
+        p.anp = on
+        m = dynamics.Model.from_problem(p)
+        N, h = p.n_nodes, 1e-7
+        K = np.zeros((3 * N, 3 * N))
+        for j in range(3 * N):
+            Up = np.zeros(3 * N)
+            Up[j] = h
+            K[:, j] = (m.internal_forces(Up.reshape(-1, 3)) - m.internal_forces(-Up.reshape(-1, 3))).reshape(-1) / (2 * h)
+        lam_max[on] = eigh(0.5 * (K + K.T), np.diag(np.repeat(m.mass, 3)), eigvals_only=True)[-1]
+        dt = m.critical_time_step()
+    assert lam_max[True] < lam_max[False]
+    assert dt < 2.0 / np.sqrt(lam_max[False])
