@@ -96,12 +96,16 @@ def workload(name):
     return p, desc
 
 
+# the sources that make the step kernels and their launch / tile layout: a
+# change to any of them invalidates the stored ncu traffic
+STEP_SOURCES = ("dj_api.cu", "dj_elem.cuh", "dj_internal.h", "kernels_step.cu", "kernels_tma.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2106_14189_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -254,7 +258,7 @@ def run_warmstart(args):
     torch.cuda.set_device(0)
     p = W.ellipsoid_tet4(h=args.ws_h, seed=0, patch_radius=0.025, disp_range=(0.5e-3, 2.5e-3))
     ws = WarmStart(p, n_in=64, n_out=128, alpha=130.0, ramp_steps=int(round(1500 * 3e-3 / args.ws_h)),
-                   tol=1e-5)
+                   tol=1e-5, adaptive=args.ws_adaptive)
     t0 = time.perf_counter()
     T_train = load_cases(p, range(100000, 100000 + args.ws_train))
     if args.ws_sequential:
@@ -307,7 +311,8 @@ def run_warmstart(args):
             "config": {"workload": f"ellipsoid 70/55/45 mm, h = {args.ws_h * 1e3:.2f} mm "
                                    f"({p.n_elems} T4 TI, {p.n_nodes} nodes), 6 surface patches "
                                    f"(r = 25 mm, bump (1 - (r/R)^2)^2) 0.5-2.5 mm, ramp {ws.ramp_steps} steps, "
-                                   f"compensated precision, alpha = 130 1/s, "
+                                   f"compensated precision, alpha = 130 1/s"
+                                   f"{' (start of the adaptive damping)' if args.ws_adaptive else ''}, "
                                    f"MLP 64-256-256-256-128 tanh on POD coefficients"},
             "dtype": "f32", "data": "synthetic"}
     print(json.dumps(line), flush=True)
@@ -471,6 +476,8 @@ def main():
     ap.add_argument("--ws-h", type=float, default=3e-3)
     ap.add_argument("--ws-train", type=int, default=512)
     ap.add_argument("--ws-test", type=int, default=32)
+    ap.add_argument("--ws-adaptive", action="store_true",
+                    help="both timed relaxations (warm and from rest) with adaptive damping")
     ap.add_argument("--ws-sequential", action="store_true",
                     help="training relaxations one after the other on one mesh (large meshes)")
     ap.add_argument("--assembly", type=int, default=-1,

@@ -59,6 +59,20 @@ __global__ void __launch_bounds__(kAnpMaxThreads) anp_volume_kernel(TileArgs t, 
   float4* sl = sm + cap;
   float4* sx = sm + (CMP ? 2 : 1) * cap;
   float* sv = reinterpret_cast<float*>(sx + cap);  // 4 T records
+  // the tile's slot lists, staged with the nodes (16-byte loads)
+  unsigned short* sidx = reinterpret_cast<unsigned short*>(sv + 4 * T);  // 4 T local slot ids
+  unsigned short* sptr = sidx + 4 * T;                                   // cap + 8 list offsets
+  {
+    const uint4* gi = reinterpret_cast<const uint4*>(t.lidx + (size_t)tile * T * 4);
+    const uint4* gp = reinterpret_cast<const uint4*>(t.lptr + (size_t)tile * (cap + 8));
+    uint4* di = reinterpret_cast<uint4*>(sidx);
+    uint4* dp = reinterpret_cast<uint4*>(sptr);
+    const int ni = T / 2, np = (cap + 8) / 8;  // 4 T and cap + 8 uint16 values
+    for (int q = tid; q < ni + np; q += T) {
+      if (q < ni) di[q] = __ldg(gi + q);
+      else dp[q - ni] = __ldg(gp + (q - ni));
+    }
+  }
   const int n_t = __ldg(t.tile_ptr + tile + 1) - __ldg(t.tile_ptr + tile);
   for (int q = tid; q < n_t; q += T) {
     const int gid = __ldg(t.tnodes + (size_t)tile * cap + q);
@@ -103,10 +117,9 @@ __global__ void __launch_bounds__(kAnpMaxThreads) anp_volume_kernel(TileArgs t, 
 #pragma unroll
   for (int b = 0; b < 4; ++b) sv[b * T + tid] = v;
   __syncthreads();
-  const unsigned short* li = t.lidx + (size_t)tile * T * 4;
-  const unsigned short* lp = t.lptr + (size_t)tile * (cap + 8);
+  const unsigned short* li = sidx;
+  const unsigned short* lp = sptr;
   const int* pd = t.pdst + (size_t)tile * cap;
-  // the lists are read from global memory here (one pass, no reuse)
   if (8 * n_t <= T) reduce_tile_scalar_g<8>(sv, li, lp, n_t, tid, T, vparts, pd);
   else if (4 * n_t <= T) reduce_tile_scalar_g<4>(sv, li, lp, n_t, tid, T, vparts, pd);
   else if (2 * n_t <= T) reduce_tile_scalar_g<2>(sv, li, lp, n_t, tid, T, vparts, pd);
@@ -126,7 +139,8 @@ __global__ void anp_pressure_kernel(const int* __restrict__ node_ptr, const floa
 }  // namespace
 
 size_t anp_volume_smem(int cmp, const TileArgs& t) {
-  return (size_t)((cmp ? 3 : 2) * t.cap) * sizeof(float4) + (size_t)4 * t.T * sizeof(float);
+  return (size_t)((cmp ? 3 : 2) * t.cap) * sizeof(float4) + (size_t)4 * t.T * sizeof(float) +
+         (size_t)(4 * t.T + t.cap + 8) * sizeof(unsigned short);
 }
 
 cudaError_t launch_anp(int cmp, const TileArgs& t, const int* node_ptr, const float4* U, const float4* Ulo, int E,

@@ -51,7 +51,7 @@ class WarmStart:
                  hidden=(256, 256, 256), seed: int = 0, alpha: float = 130.0,
                  ramp_steps: int = 400, check_every: int = 50, tol: float = 1e-5,
                  max_steps: int = 400000, precision: int = 1, linear: bool = True,
-                 quadratic: bool = True):
+                 quadratic: bool = True, adaptive: bool = False):
         import torch
         self.torch = torch
         self.p = problem
@@ -60,6 +60,7 @@ class WarmStart:
         self.seed = seed
         self.alpha, self.ramp_steps, self.check_every = alpha, ramp_steps, check_every
         self.tol, self.max_steps, self.precision = tol, max_steps, precision
+        self.adaptive = adaptive  # relax with dj_relax_adaptive (damping estimated on the way)
         self.linear, self.quadratic = linear, quadratic
         self.quadratic_allowed = quadratic
         self.n_bc = problem.bc_dof.size
@@ -345,14 +346,14 @@ class WarmStart:
         if warm:
             torch.cuda.synchronize()
             t_pred = time.perf_counter() - t0
-        st, n, r = mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
+        st, n, r = self._relax(mesh)
         if warm and not fallback and st != 0:
             # the relaxation from the prediction failed (an element inverted on
             # the way): the same solve from rest decides
             fallback = True
             mesh.set_displacements(np.zeros((self.p.n_nodes, 3)))
             B.dj_set_step(mesh.h, 0)
-            st, n2, r = mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
+            st, n2, r = self._relax(mesh)
             n += n2
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
@@ -360,6 +361,12 @@ class WarmStart:
             mesh.close()
         return RelaxResult(steps=n, residual=r, seconds=sec, warm=warm and not fallback,
                            fallback=fallback, status=st, predict_seconds=t_pred)
+
+    def _relax(self, mesh):
+        if self.adaptive:
+            st, n, r, _ = mesh.relax_adaptive(self.tol, self.max_steps, raise_on_fail=False)
+            return st, n, r
+        return mesh.relax(self.tol, self.max_steps, raise_on_fail=False)
 
     def close(self):
         if self.mlp is not None:
