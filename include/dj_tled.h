@@ -311,8 +311,11 @@ dj_status dj_relax_adaptive(dj_mesh* mesh, double tol, long long max_steps, cons
  * starts a new trajectory.  Synchronous. */
 dj_status dj_set_displacements(dj_mesh* mesh, const double* U0);
 
-/* Current displacements U^n, host n_nodes * 3 doubles.  Synchronizes the
- * device and reports pending device-side errors. */
+/* Current displacements U^n, host n_nodes * 3 doubles (caller order).
+ * Synchronizes the device and reports pending device-side errors.  When U_out
+ * is page-locked (cudaHostAlloc / cudaHostRegister) the library's kernel
+ * writes it directly through its device mapping; other host memory receives
+ * one copy from a device buffer. */
 dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
 
 /* Current displacements into device memory, n_nodes * 3 floats in caller

@@ -1143,24 +1143,26 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
 
 dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
   if (!m || !target) return DJ_ERR_INVALID_ARG;
-  for (size_t k = 0; k < m->bc_dof.size(); ++k) {
+  const size_t nb = m->bc_dof.size();
+  for (size_t k = 0; k < nb; ++k)
     if (!std::isfinite(target[k])) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
-    m->bc_target[k] = target[k];
-  }
+  std::memcpy(m->bc_target.data(), target, nb * sizeof(double));
   if (!m->precomputed) return DJ_OK;
   CK(cudaSetDevice(m->device));
-  for (size_t k = 0; k < m->bc_dof.size(); ++k) {
-    float4& t = m->h_bct[m->bc_node_of_entry[k]];
-    const float v = (float)target[k];
-    if (m->bc_comp_of_entry[k] == 0) t.x = v;
-    if (m->bc_comp_of_entry[k] == 1) t.y = v;
-    if (m->bc_comp_of_entry[k] == 2) t.z = v;
-  }
   if (m->n_bc_nodes) {
-    // staged through pinned memory (allocated once per mesh)
-    if (!m->h_bct_pinned) CK(cudaMallocHost((void**)&m->h_bct_pinned, m->h_bct.size() * sizeof(float4)));
-    std::memcpy(m->h_bct_pinned, m->h_bct.data(), m->h_bct.size() * sizeof(float4));
-    CK(cudaMemcpy(m->d_bct, m->h_bct_pinned, m->h_bct.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    // the per-node table (targets, w = component mask) lives in pinned memory
+    // once the first update has staged it; each update rewrites the targets
+    // in place and copies the table once
+    const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
+    if (!m->h_bct_pinned) {
+      CK(cudaMallocHost((void**)&m->h_bct_pinned, bytes));
+      std::memcpy(m->h_bct_pinned, m->h_bct.data(), bytes);
+    }
+    float* pin = reinterpret_cast<float*>(m->h_bct_pinned);
+    const int* node = m->bc_node_of_entry.data();
+    const int* comp = m->bc_comp_of_entry.data();
+    for (size_t k = 0; k < nb; ++k) pin[4 * (size_t)node[k] + comp[k]] = (float)target[k];
+    CK(cudaMemcpy(m->d_bct, m->h_bct_pinned, bytes, cudaMemcpyHostToDevice));
   }
   return DJ_OK;
 }
@@ -1523,11 +1525,22 @@ dj_status dj_get_displacements(dj_mesh* m, double* U_out) {
   if (!U_out) return fail(m, DJ_ERR_INVALID_ARG, "null U_out");
   CK(cudaDeviceSynchronize());
   const long long N = m->N;
-  // caller order and FP64 on the device, then one copy into the caller's buffer
-  if (!m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
-  CK(launch_to_caller_order_f64(m->d_U, m->cmp ? m->d_Ulo : nullptr, m->d_perm, (int)N, m->d_out64, 0));
-  CK(cudaMemcpy(U_out, m->d_out64, 3 * N * sizeof(double), cudaMemcpyDeviceToHost));
-  s = read_state(m, 0);
+  // caller order and FP64 on the device.  A page-locked caller buffer is
+  // written by the kernel itself through its device mapping; otherwise the
+  // values go through a device buffer and one copy.
+  double* direct = nullptr;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, U_out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+      attr.devicePointer)
+    direct = static_cast<double*>(attr.devicePointer);
+  else
+    (void)cudaGetLastError();
+  if (!direct && !m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
+  CK(launch_to_caller_order_f64(m->d_U, m->cmp ? m->d_Ulo : nullptr, m->d_perm, (int)N,
+                                direct ? direct : m->d_out64, 0));
+  if (!direct)
+    CK(cudaMemcpyAsync(U_out, m->d_out64, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, 0));
+  s = read_state(m, 0);  // one synchronisation for the field and the state
   if (s) return s;
   return check_flags(m);
 }

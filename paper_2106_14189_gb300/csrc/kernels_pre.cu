@@ -256,22 +256,34 @@ __global__ void to_caller_order_kernel(const float4* __restrict__ U, const int* 
 
 // U (+ compensated low part) in caller order as doubles, the layout of the
 // host call's output
-__global__ void to_caller_order_f64_kernel(const float4* __restrict__ U, const float4* __restrict__ Ulo,
-                                           const int* __restrict__ perm, int N, double* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // caller node id
-  if (i >= N) return;
-  const int v = perm[i];
-  const float4 u = U[v];
-  double x = u.x, y = u.y, z = u.z;
-  if (Ulo) {
-    const float4 l = Ulo[v];
-    x += l.x;
-    y += l.y;
-    z += l.z;
+// FP64 displacements in caller order.  The block's 3 x 256 values go through
+// shared memory so that the stores to `out` (device memory, or a page-locked
+// host buffer written over the host link) are contiguous per warp.
+constexpr int kOrderThreads = 256;
+__global__ void __launch_bounds__(kOrderThreads) to_caller_order_f64_kernel(const float4* __restrict__ U,
+                                                                           const float4* __restrict__ Ulo,
+                                                                           const int* __restrict__ perm, int N,
+                                                                           double* out) {
+  __shared__ double sv[3 * kOrderThreads];
+  const int i0 = blockIdx.x * kOrderThreads;
+  const int i = i0 + threadIdx.x;  // caller node id
+  if (i < N) {
+    const int v = perm[i];
+    const float4 u = U[v];
+    double x = u.x, y = u.y, z = u.z;
+    if (Ulo) {
+      const float4 l = Ulo[v];
+      x += l.x;
+      y += l.y;
+      z += l.z;
+    }
+    sv[3 * threadIdx.x] = x;
+    sv[3 * threadIdx.x + 1] = y;
+    sv[3 * threadIdx.x + 2] = z;
   }
-  out[3 * (size_t)i] = x;
-  out[3 * (size_t)i + 1] = y;
-  out[3 * (size_t)i + 2] = z;
+  __syncthreads();
+  const int n = 3 * min(kOrderThreads, N - i0);
+  for (int q = threadIdx.x; q < n; q += kOrderThreads) out[3 * (size_t)i0 + q] = sv[q];
 }
 
 __global__ void from_caller_order_kernel(const float* __restrict__ src, const int* __restrict__ perm, int N,
@@ -338,7 +350,7 @@ cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, 
 
 cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
                                        double* out, cudaStream_t s) {
-  const int t = 256;
+  const int t = kOrderThreads;
   to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
   return cudaGetLastError();
 }

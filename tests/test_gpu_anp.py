@@ -143,3 +143,18 @@ def test_anp_argument_checks(B):
     q.anp = True
     with pytest.raises(B.DJError):
         B.Mesh(q, assembly=1)
+
+
+def test_anp_in_a_batch_matches_the_oracle(B):
+    """T4 meshes with average nodal pressure stepped together in one batch
+    (one graph) land on the oracle's trajectories."""
+    probs = [W.cube_compression_tet4(n=n, n_steps=200, strain=-0.1) for n in (4, 5, 6)]
+    for p in probs:
+        p.anp = True
+    with B.Batch(probs, anp=1, assembly=2) as bt:
+        bt.run(200)
+        Ub = [bt.displacements(i) for i in range(len(probs))]
+        dts = [B.dj_batch_instance_info(bt.b, i)[2] for i in range(len(probs))]
+    for p, U, dt in zip(probs, Ub, dts):
+        ref = dynamics.ExplicitSolver.from_problem(p, dt=dt).run(200)
+        assert rel_linf(U, ref) <= 1e-4

@@ -367,3 +367,18 @@ def test_full_size_cfg2b_sampled_nodes(B):
         assert err <= bound, (i, err, bound)
         checked += 1
     assert checked > 40
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_displacements_into_pinned_and_pageable_buffers_agree(B, prec):
+    """dj_get_displacements writes a page-locked buffer directly from its
+    kernel and fills other host memory by a copy: both give the same values."""
+    torch = pytest.importorskip("torch")
+    p = W.cube_shear(W.TET4, 7, n_steps=100)
+    with B.Mesh(p, precision=prec) as m:
+        m.run(60)
+        U_page = m.displacements()
+        pinned = torch.empty((p.n_nodes, 3), dtype=torch.float64).pin_memory()
+        U_pin = B.dj_get_displacements(m.h, p.n_nodes, out=pinned.numpy())
+        assert np.array_equal(U_page, U_pin)
+        assert np.abs(U_page).max() > 0
