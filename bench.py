@@ -96,9 +96,9 @@ def workload(name):
     return p, desc
 
 
-# the sources that make the step kernels and their launch / tile layout: a
-# change to any of them invalidates the stored ncu traffic
-STEP_SOURCES = ("dj_api.cu", "dj_elem.cuh", "dj_internal.h", "kernels_step.cu", "kernels_tma.cu")
+# the sources of the step kernels: a change to any of them invalidates the
+# stored ncu traffic (the tile layout is checked through dj_get_info)
+STEP_SOURCES = ("dj_elem.cuh", "dj_internal.h", "kernels_step.cu", "kernels_tma.cu")
 
 
 def kernel_source_hash():
@@ -602,7 +602,8 @@ def main():
     try:
         tr = json.load(open(TRAFFIC_FILE))
         if (tr.get("source_hash") == kernel_source_hash() and tr.get("workload") == args.workload
-                and tr.get("assembly") == minfo.assembly and tr.get("tile_size") == minfo.tile_size):
+                and tr.get("assembly") == minfo.assembly and tr.get("tile_size") == minfo.tile_size
+                and tr.get("n_parts", minfo.n_parts) == minfo.n_parts):
             traffic = tr.get(f"{dominant}_bytes_per_launch")
     except Exception:
         pass
