@@ -298,6 +298,8 @@ def run_warmstart(args):
             "steps_warm": float(np.mean([r.steps for r in warm])),
             "steps_plain": float(np.mean([r.steps for r in cold])),
             "fallbacks": int(sum(r.fallback for r in warm)), "all_converged": ok,
+            "converged_plain": int(sum(r.status == 0 for r in cold)),
+            "converged_warm": int(sum(r.status == 0 for r in warm)),
             "prediction_rel_linf": float(np.median(pred_err)) if pred_err else None,
             "pod_reconstruction_rel_linf": float(np.median(recon_err)) if recon_err else None,
             "input_modes_kept": int(ws.keep_in.sum()),

@@ -10,6 +10,7 @@
 //   bct       float4[n_bc_nodes]: target displacement, w = component mask
 //   state     DevState (step counter, ramp value, error flags, residual sums)
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <climits>
@@ -150,6 +151,12 @@ dj_status fail(dj_mesh* m, dj_status s, const char* fmt, ...) {
       return fail(m, _e == cudaErrorMemoryAllocation ? DJ_ERR_OOM : DJ_ERR_CUDA, "%s: %s (%s:%d)", \
                   #call, cudaGetErrorString(_e), __FILE__, __LINE__);                          \
   } while (0)
+
+// a named range around a library call for profilers (NVTX; no cost without a tool)
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 template <class T>
 cudaError_t dalloc(dj_mesh* m, T** p, size_t count) {
@@ -600,6 +607,7 @@ dj_status dj_mesh_set_loads(dj_mesh* m, const double* R) {
 }
 
 dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
+  const Range range("dj_precompute");
   if (!m) return DJ_ERR_INVALID_ARG;
   if (!m->materials_set) return fail(m, DJ_ERR_INVALID_ARG, "call dj_mesh_set_materials first");
   dj_params prm;
@@ -802,6 +810,38 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     for (int t = 0; t < m->n_tiles; ++t)
       for (int q = 0; q < tile_ptr[t + 1] - tile_ptr[t]; ++q)
         pdst_pad[(size_t)t * m->cap + q] = fillp[tile_nodes[tile_ptr[t] + q]]++;
+    // every index the kernels follow, checked once on the host: a table that
+    // would send a kernel out of bounds is refused before anything runs
+    std::vector<char> seen(m->T * ne);
+    for (int t = 0; t < m->n_tiles; ++t) {
+      const int n_t = tile_ptr[t + 1] - tile_ptr[t];
+      const long long e0 = (long long)t * m->T, e1 = std::min(E, e0 + m->T);
+      const int R = (int)((e1 - e0) * ne);
+      const unsigned short* lp = &lptr[(size_t)t * (m->cap + 8)];
+      bool ok = n_t >= 1 && n_t <= m->cap && lp[0] == 0 && lp[n_t] == R;
+      for (int q = 0; ok && q < n_t; ++q) {
+        ok = lp[q] <= lp[q + 1] && tnodes_pad[(size_t)t * m->cap + q] >= 0 &&
+             tnodes_pad[(size_t)t * m->cap + q] < N && pdst_pad[(size_t)t * m->cap + q] >= 0 &&
+             pdst_pad[(size_t)t * m->cap + q] < m->n_parts;
+      }
+      std::fill(seen.begin(), seen.end(), 0);
+      for (long long e = e0; ok && e < e1; ++e)
+        for (int b = 0; ok && b < ne; ++b) ok = lconn[e * ne + b] < n_t;
+      // node k's list holds each of its records (slot b T + e_local) once
+      const unsigned short* li = &lidx[(size_t)t * m->T * ne];
+      for (int k = 0; ok && k < n_t; ++k)
+        for (int p = lp[k]; ok && p < lp[k + 1]; ++p) {
+          const int slot = li[p], b = slot / m->T, el = slot % m->T;
+          ok = b < ne && e0 + el < e1 && !seen[slot] && lconn[(e0 + el) * ne + b] == k;
+          if (ok) seen[slot] = 1;
+        }
+      if (!ok) {
+        return fail(m, DJ_ERR_BAD_MESH, "internal error: tile %d tables out of range", t);
+      }
+    }
+    for (long long i = 0; i < N; ++i)
+      if (node_ptr[i] > node_ptr[i + 1]) return fail(m, DJ_ERR_BAD_MESH, "internal error: node offsets");
+    if (node_ptr[N] != m->n_parts) return fail(m, DJ_ERR_BAD_MESH, "internal error: partial count");
   }
   m->sell_entries = (long long)sell.size();
   // ---- prescribed nodes ----------------------------------------------------
@@ -1168,6 +1208,7 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
 }
 
 dj_status dj_step(dj_mesh* m, void* stream) {
+  const Range range("dj_step");
   dj_status s = need_ready(m);
   if (s) return s;
   CK(launch_step(m, (cudaStream_t)stream, NODE_UPDATE));
@@ -1175,6 +1216,7 @@ dj_status dj_step(dj_mesh* m, void* stream) {
 }
 
 dj_status dj_run_n(dj_mesh* m, long long n, void* stream) {
+  const Range range("dj_run_n");
   dj_status s = need_ready(m);
   if (s) return s;
   if (n < 0) return fail(m, DJ_ERR_INVALID_ARG, "n < 0");
@@ -1334,6 +1376,7 @@ dj_status dj_sync(dj_mesh* m, void* stream) {
 
 dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long* steps_out,
                           double* residual_out, void* stream) {
+  const Range range("dj_relax_to_tol");
   dj_status s = need_ready(m);
   if (s) return s;
   if (!(tol >= 0) || max_steps < 0) return fail(m, DJ_ERR_INVALID_ARG, "bad tol or max_steps");
@@ -1404,6 +1447,7 @@ dj_status dj_relax_to_tol(dj_mesh* m, double tol, long long max_steps, long long
 
 dj_status dj_relax_adaptive(dj_mesh* m, double tol, long long max_steps, const dj_adr_params* opts,
                             long long* steps_out, double* residual_out, dj_adr_report* report, void* stream) {
+  const Range range("dj_relax_adaptive");
   dj_status s = need_ready(m);
   if (s) return s;
   if (!(tol >= 0) || max_steps < 0) return fail(m, DJ_ERR_INVALID_ARG, "bad tol or max_steps");
@@ -2020,6 +2064,7 @@ dj_status dj_batch_precompute(dj_batch* b, const dj_params* params) {
 }
 
 dj_status dj_batch_run_n(dj_batch* b, long long n, void* stream) {
+  const Range range("dj_batch_run_n");
   if (!b || n < 0) return DJ_ERR_INVALID_ARG;
   if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
   (void)cudaGetLastError();
@@ -2063,6 +2108,7 @@ dj_status dj_batch_sync(dj_batch* b, void* stream) {
 
 dj_status dj_batch_relax_to_tol(dj_batch* b, double tol, long long max_steps, long long* steps_out,
                                 double* residual_out, void* stream) {
+  const Range range("dj_batch_relax_to_tol");
   if (!b || !(tol >= 0) || max_steps < 0) return DJ_ERR_INVALID_ARG;
   if (!b->precomputed) return bfail(b, DJ_ERR_NOT_PRECOMPUTED, "call dj_batch_precompute first");
   (void)cudaGetLastError();

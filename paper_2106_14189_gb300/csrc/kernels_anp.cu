@@ -147,6 +147,13 @@ cudaError_t launch_anp(int cmp, const TileArgs& t, const int* node_ptr, const fl
                        int N, float* vparts, const float* c1, float* pres, cudaStream_t s) {
   if (t.T > kAnpMaxThreads) return cudaErrorInvalidValue;
   const size_t smem = anp_volume_smem(cmp, t);
+  if (smem > 48 * 1024) {  // tiles with many distinct nodes: opt in to more shared memory
+    cudaError_t e = cmp ? cudaFuncSetAttribute(anp_volume_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem)
+                        : cudaFuncSetAttribute(anp_volume_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   if (cmp)
     anp_volume_kernel<true><<<t.n_tiles, t.T, smem, s>>>(t, U, Ulo, E, vparts);
   else

@@ -131,7 +131,7 @@ class WarmStart:
                 B.dj_mesh_update_bc_targets(m.h, t)
                 m.set_displacements(zeros)
                 B.dj_set_step(m.h, 0)
-                st, n, r = m.relax(self.tol, self.max_steps, raise_on_fail=False)
+                st, n, r = self._relax(m)
                 if st != 0:
                     continue
                 B.dj_get_displacements_device(m.h, Y[len(kept)].data_ptr())
