@@ -77,6 +77,7 @@ struct dj_mesh {
   int n_bc_nodes = 0;
   std::vector<int> bc_node_of_entry;  // per bc entry: prescribed-node row
   std::vector<int> bc_comp_of_entry;
+  std::vector<int> bc_flat_of_entry;  // per bc entry: float index 4 row + comp in the node table
   std::vector<float4> h_bct;
   float4* h_bct_pinned = nullptr;  // pinned staging of h_bct for target updates
   std::vector<float> h_ai;
@@ -849,6 +850,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   m->h_bct.clear();
   m->bc_node_of_entry.assign(m->bc_dof.size(), 0);
   m->bc_comp_of_entry.assign(m->bc_dof.size(), 0);
+  m->bc_flat_of_entry.assign(m->bc_dof.size(), 0);
   for (size_t k = 0; k < m->bc_dof.size(); ++k) {
     const int node = m->node_new_of_old[m->bc_dof[k] / 3];
     const int comp = (int)(m->bc_dof[k] % 3);
@@ -864,6 +866,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     t.w = bits_to_float(mask);
     m->bc_node_of_entry[k] = bcidx[node];
     m->bc_comp_of_entry[k] = comp;
+    m->bc_flat_of_entry[k] = 4 * bcidx[node] + comp;
   }
   m->n_bc_nodes = (int)m->h_bct.size();
   m->h_bcidx = bcidx;
@@ -1184,8 +1187,9 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
 dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
   if (!m || !target) return DJ_ERR_INVALID_ARG;
   const size_t nb = m->bc_dof.size();
-  for (size_t k = 0; k < nb; ++k)
-    if (!std::isfinite(target[k])) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
+  bool finite = true;
+  for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
+  if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
   std::memcpy(m->bc_target.data(), target, nb * sizeof(double));
   if (!m->precomputed) return DJ_OK;
   CK(cudaSetDevice(m->device));
@@ -1199,9 +1203,8 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
       std::memcpy(m->h_bct_pinned, m->h_bct.data(), bytes);
     }
     float* pin = reinterpret_cast<float*>(m->h_bct_pinned);
-    const int* node = m->bc_node_of_entry.data();
-    const int* comp = m->bc_comp_of_entry.data();
-    for (size_t k = 0; k < nb; ++k) pin[4 * (size_t)node[k] + comp[k]] = (float)target[k];
+    const int* flat = m->bc_flat_of_entry.data();
+    for (size_t k = 0; k < nb; ++k) pin[flat[k]] = (float)target[k];
     CK(cudaMemcpy(m->d_bct, m->h_bct_pinned, bytes, cudaMemcpyHostToDevice));
   }
   return DJ_OK;
