@@ -382,3 +382,22 @@ def test_displacements_into_pinned_and_pageable_buffers_agree(B, prec):
         U_pin = B.dj_get_displacements(m.h, p.n_nodes, out=pinned.numpy())
         assert np.array_equal(U_page, U_pin)
         assert np.abs(U_page).max() > 0
+
+
+def test_brain_shift_configuration_matches_oracle(B):
+    """Sec. 6's brain-shift setting at the paper's mesh size (28,770 T4 on the
+    brain-sized ellipsoid; the paper's mesh has 28,764): neo-Hookean brain
+    tissue, rho 1060, dt = 1.6e-4 s; 300 steps with the surface loads ramped
+    over them, FP32 GPU against the FP64 oracle."""
+    p = W.ellipsoid_tet4(h=5.35e-3, seed=0, patch_radius=0.025, disp_range=(0.5e-3, 2.5e-3), fibres=False)
+    p.model[:] = W.NH
+    p.mu[:], p.kappa[:], p.rho[:] = 1006.712, 50000.0, 1060.0
+    p.eta_a[:], p.eta_b[:], p.c01[:] = 0.0, 0.0, 0.0
+    p.dt, p.alpha, p.ramp_steps = 1.6e-4, 130.0, 300
+    with B.Mesh(p) as m:
+        m.run(300)
+        U = m.displacements()
+    ref = dynamics.ExplicitSolver.from_problem(p).run(300)
+    err = rel_linf(U, ref)
+    print(f"brain-shift setting, 300 steps: rel-Linf {err:.2e}")
+    assert err < DISP_TOL
