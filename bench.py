@@ -412,6 +412,8 @@ def run_brain(args):
     n = 62500
     p.dt, p.alpha, p.ramp_steps = 1.6e-4, 130.0, n // 2
     with B.Mesh(p, precision=int(args.brain_precision)) as m:
+        # the schedule for this size (the mesh stays in L2 through the run)
+        sched, _ = B.dj_autotune(m.h, 200, stream)
         m.run(2000, stream)                     # warm-up (graph capture, clocks)
         m.sync(stream)
         B.dj_set_step(m.h, 0)
@@ -436,7 +438,8 @@ def run_brain(args):
                                    f"neo-Hookean mu 1006.712 Pa, kappa 50 kPa, rho 1060, six 25 mm surface "
                                    f"patches 0.5-2.5 mm ramped over {p.ramp_steps} steps, base fixed, "
                                    f"alpha 130 1/s, dt 1.6e-4 s",
-                       "assembly": info.assembly, "tile_size": info.tile_size, "precision": info.precision},
+                       "assembly": info.assembly, "tile_size": info.tile_size, "precision": info.precision,
+                       "graph_pdl": int(sched.graph_pdl), "schedule": "dj_autotune"},
             "dtype": "f32" + (" (compensated)" if int(args.brain_precision) else ""), "data": "synthetic"}
     print(json.dumps(line), flush=True)
 
@@ -462,6 +465,9 @@ def run_cutout(args):
             for model in (W.NH, W.TI, W.OT, W.MR):
                 p = W.cutout_cube(et, n, model)
                 with B.Mesh(p) as m:
+                    sched = None
+                    if args.cutout_tune:  # the schedule for this mesh (it stays in L2)
+                        sched, _ = B.dj_autotune(m.h, 200, stream)
                     m.run(200, stream)
                     m.sync(stream)
                     B.dj_set_step(m.h, 0)
@@ -478,7 +484,10 @@ def run_cutout(args):
                 rows.append({"elem": "T4" if et == W.TET4 else "H8", "n": n, "dofs": 3 * p.n_nodes,
                              "elements": p.n_elems, "model": names[model], "steps": p.n_steps,
                              "solve_ms": ms, "us_per_step": 1e3 * ms / p.n_steps,
-                             "max_uz": uz})
+                             "max_uz": uz,
+                             "schedule": None if sched is None else
+                             {"assembly": sched.assembly, "tile_size": sched.tile_size,
+                              "graph_pdl": sched.graph_pdl}})
     over = {}
     for el in ("T4", "H8"):
         for mo in ("TI", "OT", "MR"):
@@ -492,7 +501,8 @@ def run_cutout(args):
                                          "H8_TI": 0.019, "H8_OT": 0.037, "H8_MR": 0.139},
             "config": {"workload": "cube 0.1 m with four cylindrical recesses (r = 25 mm, depth 30 mm), "
                                    "back face fixed, front face u_z -> 0.05 m linear ramp, "
-                                   "dt = 5e-5 s, Sec. 5.1 materials"},
+                                   "dt = 5e-5 s, Sec. 5.1 materials",
+                       "schedule": "dj_autotune per mesh" if args.cutout_tune else "default (tiles, 256)"},
             "dtype": "f32", "data": "synthetic"}
     print(json.dumps(line), flush=True)
 
@@ -525,6 +535,8 @@ def main():
     ap.add_argument("--relax-ramp-scale", type=float, default=1.0)
     ap.add_argument("--relax-adaptive", type=float, nargs="*", default=[130.0, 13.0, 1300.0],
                     help="start damping values of the adaptive relaxations (none: skip)")
+    ap.add_argument("--cutout-tune", action="store_true",
+                    help="with --cutout: autotune the schedule of every mesh")
     ap.add_argument("--cutout", action="store_true",
                     help="Sec. 5.1 cut-out cube: six sizes x T4/H8 x four models, full 1 s simulations")
     ap.add_argument("--ws-h", type=float, default=3e-3)

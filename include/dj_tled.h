@@ -97,7 +97,12 @@ typedef struct dj_mesh dj_mesh;
  *                     p_i = kappa_i (J_i - 1) with kappa_i the volume-weighted
  *                     bulk modulus, and each element's volumetric factor
  *                     kappa (J - 1) replaced by the mean of its nodes' p_i.  Two
- *                     more kernels per step (element volumes, nodal pressures). */
+ *                     more kernels per step (element volumes, nodal pressures).
+ *   graph_pdl         0 (default): the steps captured into CUDA graphs
+ *                     (dj_run_n, relaxation) are joined by ordinary edges;
+ *                     1: by programmatic-launch edges, as directly launched
+ *                     steps are (faster on small meshes; dj_autotune tries
+ *                     both). */
 typedef struct {
   double dt;
   double dt_scale;
@@ -111,6 +116,7 @@ typedef struct {
   int tile_size;
   int precision;
   int anp;
+  int graph_pdl;
 } dj_params;
 
 /* Read-only description of a mesh after dj_precompute. */

@@ -423,7 +423,9 @@ template <class F>
 dj_status capture(dj_mesh* m, cudaGraphExec_t* out, F body) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+  tl_graph_pdl = m->params.graph_pdl != 0;
   cudaError_t be = body(m->cap_stream);
+  tl_graph_pdl = false;
   cudaError_t ee = cudaStreamEndCapture(m->cap_stream, &g);
   if (be != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -455,6 +457,7 @@ void dj_params_default(dj_params* p) {
   p->tile_size = 0;
   p->precision = 0;
   p->anp = 0;
+  p->graph_pdl = 0;
 }
 
 const char* dj_status_string(dj_status s) {
@@ -619,7 +622,8 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   if (!(prm.dt_scale > 0) || !(prm.alpha >= 0) || !(prm.hg_coeff >= 0) || prm.relax_check_every <= 0 ||
       (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt) ||
       (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES && prm.assembly != ASSEMBLY_TILES_TMA) ||
-      (prm.precision != 0 && prm.precision != 1) || (prm.anp != 0 && prm.anp != 1))
+      (prm.precision != 0 && prm.precision != 1) || (prm.anp != 0 && prm.anp != 1) ||
+      (prm.graph_pdl != 0 && prm.graph_pdl != 1))
     return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
   if (prm.anp && (m->ne != 4 || prm.assembly != ASSEMBLY_TILES_TMA))
     return fail(m, DJ_ERR_INVALID_ARG, "average nodal pressure needs T4 elements and assembly 2");
@@ -1844,32 +1848,46 @@ dj_status dj_autotune_cold(dj_mesh* m, int steps, void* d_flush, size_t flush_by
   CK(cudaEventCreate(&e1));
   double best = INFINITY;
   dj_params best_p = base;
+  // time one schedule from the saved state: ms over `steps` steps, or +inf
+  const auto time_schedule = [&](const dj_params& p) -> double {
+    if (dj_precompute(m, &p, nullptr) != DJ_OK) return INFINITY;  // e.g. a tile too large for shared memory
+    if (dj_set_state(m, blob.data(), bytes) != DJ_OK) return INFINITY;
+    if (dj_run_n(m, 8, stream) != DJ_OK) return INFINITY;  // graph capture and warm-up
+    float ms = 0;
+    if (!d_flush) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) return INFINITY;
+      if (dj_run_n(m, steps, stream) != DJ_OK) return INFINITY;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return INFINITY;
+      cudaEventElapsedTime(&ms, e0, e1);
+    } else {
+      // every step alone after an L2 eviction
+      for (int k = 0; k < steps; ++k) {
+        float mk = 0;
+        if (launch_l2_flush(d_flush, flush_bytes, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
+            launch_step(m, st, NODE_UPDATE) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&mk, e0, e1) != cudaSuccess)
+          return INFINITY;
+        ms += mk;
+      }
+    }
+    if (read_state(m, st) != DJ_OK || check_flags(m) != DJ_OK) return INFINITY;
+    return ms;
+  };
   for (const Cand& c : cands) {
     dj_params p = base;
     p.assembly = c.assembly;
     p.tile_size = c.tile;
-    if (dj_precompute(m, &p, nullptr) != DJ_OK) continue;  // e.g. a tile too large for shared memory
-    if (dj_set_state(m, blob.data(), bytes) != DJ_OK) continue;
-    if (dj_run_n(m, 8, stream) != DJ_OK) continue;  // graph capture and warm-up
-    float ms = 0;
-    if (!d_flush) {
-      if (cudaEventRecord(e0, st) != cudaSuccess) break;
-      if (dj_run_n(m, steps, stream) != DJ_OK) continue;
-      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) break;
-      cudaEventElapsedTime(&ms, e0, e1);
-    } else {
-      // every step alone after an L2 eviction
-      bool bad = false;
-      for (int k = 0; k < steps && !bad; ++k) {
-        float mk = 0;
-        bad = launch_l2_flush(d_flush, flush_bytes, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess ||
-              launch_step(m, st, NODE_UPDATE) != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
-              cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&mk, e0, e1) != cudaSuccess;
-        ms += mk;
-      }
-      if (bad) break;
+    const double ms = time_schedule(p);
+    if (ms < best) {
+      best = ms;
+      best_p = p;
     }
-    if (read_state(m, st) != DJ_OK || check_flags(m) != DJ_OK) continue;
+  }
+  // graph replays: the best schedule with the other kind of edges between steps
+  if (!d_flush && std::isfinite(best)) {
+    dj_params p = best_p;
+    p.graph_pdl = !best_p.graph_pdl;
+    const double ms = time_schedule(p);
     if (ms < best) {
       best = ms;
       best_p = p;

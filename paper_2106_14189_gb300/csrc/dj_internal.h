@@ -157,7 +157,12 @@ enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_O
 // returns once that kernel has completed and its writes are visible (and at
 // once when there is no programmatic dependency).  Used for launches made
 // directly on a stream; kernels captured into a CUDA graph keep ordinary
-// edges (graph replays of back-to-back steps were measured faster that way).
+// edges unless tl_graph_pdl is set (graph replays of back-to-back steps of a
+// large mesh were measured faster with ordinary edges).
+// Set by the host around a graph capture when the mesh's schedule keeps the
+// programmatic edges inside graphs (dj_params.graph_pdl).
+inline thread_local bool tl_graph_pdl = false;
+
 template <class... KArgs, class... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {
@@ -173,7 +178,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = cs == cudaStreamCaptureStatusNone ? 1 : 0;
+  cfg.numAttrs = (cs == cudaStreamCaptureStatusNone || tl_graph_pdl) ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 enum { ASSEMBLY_SLOTS = 0, ASSEMBLY_TILES = 1, ASSEMBLY_TILES_TMA = 2 };

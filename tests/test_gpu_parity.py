@@ -401,3 +401,20 @@ def test_brain_shift_configuration_matches_oracle(B):
     err = rel_linf(U, ref)
     print(f"brain-shift setting, 300 steps: rel-Linf {err:.2e}")
     assert err < DISP_TOL
+
+
+@pytest.mark.parametrize("assembly", [0, 1, 2])
+def test_graph_programmatic_edges_bit_identical(B, assembly):
+    """Graph replays with programmatic-launch edges between the steps give the
+    same trajectory, bit for bit, as ordinary edges (and so does relaxation)."""
+    p = W.cube_shear(W.TET4, 7, n_steps=200)
+    p.alpha, p.ramp_steps = 40.0, 100
+    out = []
+    for pdl in (0, 1):
+        with B.Mesh(p, assembly=assembly, graph_pdl=pdl, relax_check_every=50) as m:
+            m.run(130)
+            U = m.displacements()
+            st, n, r = m.relax(1e-3, 3000, raise_on_fail=False)
+            out.append((U, m.displacements(), n))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
