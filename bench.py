@@ -75,6 +75,10 @@ def algorithmic_bytes(info, n_nodes):
 # through HBM (force write + per-node gather) and node state is read once:
 # T4 neo-Hookean, T4 transversely isotropic, H8 neo-Hookean with hourglass.
 SLOT_MODEL_BYTES = {(4, 1): 209.0, (4, 2): 237.0, (8, 1): 536.0}  # keys: (n_e, model bit mask)
+# the same model's element-force kernel alone (connectivity, stored 0J and
+# constants, I1m / I4m, hourglass, element-force write; the gather belongs to
+# the node kernel there)
+SLOT_MODEL_FORCE_BYTES = {(4, 1): 132.0, (4, 2): 160.0, (8, 1): 328.0}
 
 
 def workload(name):
@@ -694,6 +698,11 @@ def main():
         gbs = slot_model * E / (ms_max * 1e-3 / args.steps) / 1e9
         roofline["slot_model"] = {"bytes_per_element_update": slot_model, "achieved_gbs": gbs,
                                   "frac": gbs / peak}
+        fm = SLOT_MODEL_FORCE_BYTES.get((minfo.elem_type, minfo.model_flags))
+        if fm and dominant == "force":
+            gf = fm * E / t_force / 1e9
+            roofline["slot_model"]["force_kernel"] = {"bytes_per_element": fm, "achieved_gbs": gf,
+                                                      "frac": gf / peak}
 
     # end to end through the public C ABI with host buffers: every step uploads
     # the prescribed-displacement targets of that step and reads U back
