@@ -5,11 +5,11 @@
 // connectivity, local slot index, node list, partial destinations, node
 // offsets; see TileArgs) are
 // copied with cp.async.bulk into one of two shared-memory stages, two tiles
-// ahead; an mbarrier per stage counts the arriving bytes.  The nodal values of
-// the next tile are gathered with cp.async while the current tile's element
-// forces are reduced.  Every wait is bounded: on timeout the kernel records
-// ERR_TIMEOUT, waits once more (bounded) for the copy that timed out, the only
-// one in flight, and returns.
+// ahead; an mbarrier per stage counts the arriving bytes.  A tile's stage
+// carries the node list of the block's next tile, so the nodal values of the
+// next tile are gathered with cp.async while the current tile's element forces
+// are computed and reduced.  Every wait is bounded: on timeout the kernel
+// records ERR_TIMEOUT, lets the copies in flight land (bounded) and returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -79,16 +79,21 @@ struct StageLayout {
 };
 
 // issue the bulk copies of tile `tile` into `stage` (one thread)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// the stage of `tile` carries the node list of `tnext` (the block's next tile)
 template <int NE>
 __device__ __forceinline__ void issue_tile(const ForceArgs& a, const TileArgs& t, const StageLayout<NE>& L,
-                                           char* stage, uint64_t* bar, int tile) {
+                                           char* stage, uint64_t* bar, int tile, int tnext) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   mbar_arrive_expect_tx(bar, L.bytes);
   bulk_copy(stage + L.xloc, t.xloc + (size_t)tile * t.cap, L.tab - L.xloc, bar);
   bulk_copy(stage + L.tab, a.consts + (size_t)tile * t.n_consts * t.T, L.lconn - L.tab, bar);
   bulk_copy(stage + L.lconn, t.lconn + (size_t)tile * t.T * NE, L.lidx - L.lconn, bar);
   bulk_copy(stage + L.lidx, t.lidx + (size_t)tile * t.T * NE, L.tnodes - L.lidx, bar);
-  bulk_copy(stage + L.tnodes, t.tnodes + (size_t)tile * t.cap, L.pdst - L.tnodes, bar);
+  bulk_copy(stage + L.tnodes, t.tnodes + (size_t)(tnext < t.n_tiles ? tnext : tile) * t.cap, L.pdst - L.tnodes, bar);
   bulk_copy(stage + L.pdst, t.pdst + (size_t)tile * t.cap, L.lptr - L.pdst, bar);
   bulk_copy(stage + L.lptr, t.lptr + (size_t)tile * (t.cap + 8), L.bytes - L.lptr, bar);
 }
@@ -117,8 +122,9 @@ __device__ __forceinline__ void gather_nodes(const ForceArgs& a, const int* tnod
 
 // Software pipeline per block, tiles blockIdx.x + k gridDim.x:
 //   bulk copies of a tile's segments are issued two tiles ahead (stages 0/1),
-//   the nodal gather of tile k+1 (cp.async) is in flight while tile k's
-//   element forces are reduced, and a tile costs two block barriers.
+//   the nodal gather of tile k+1 (cp.async, from the node list that came with
+//   tile k's stage) is in flight while tile k's element forces are computed
+//   and reduced, and a tile costs two block barriers.
 template <int NE, bool FA, bool FB, bool MR, bool CMP, bool ANP>
 __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t) {
   extern __shared__ __align__(128) char smem[];
@@ -140,8 +146,11 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   const int first = blockIdx.x, stride = gridDim.x;
   const bool second = first + stride < t.n_tiles;
   if (tid == 0 && first < t.n_tiles) {  // constant tables: before the wait
-    issue_tile<NE>(a, t, L, smem, &bars[0], first);
-    if (second) issue_tile<NE>(a, t, L, smem + stage_bytes, &bars[1], first + stride);
+    // the first tile's own node list goes to the (still unused) record area
+    mbar_expect_tx(&bars[0], (uint32_t)cap * 4);
+    bulk_copy(sf4, t.tnodes + (size_t)first * cap, (uint32_t)cap * 4, &bars[0]);
+    issue_tile<NE>(a, t, L, smem, &bars[0], first, first + stride);
+    if (second) issue_tile<NE>(a, t, L, smem + stage_bytes, &bars[1], first + stride, first + 2 * stride);
   }
   pdl_wait();  // U of the previous update; the partials are read by it
   pdl_launch_dependents();
@@ -151,13 +160,15 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
   {
     const bool ok = mbar_wait(&bars[0], 0u);
     if (__syncthreads_or(!ok)) {
+      // both stages' copies may still be in flight: bounded waits for them
       if (tid == 0) {
         atomicOr(&a.st->err_flags, ERR_TIMEOUT);
+        mbar_wait(&bars[0], 0u);
         if (second) mbar_wait(&bars[1], 0u);
       }
       return;
     }
-    const int* tn = reinterpret_cast<const int*>(smem + L.tnodes);
+    const int* tn = reinterpret_cast<const int*>(sf4);
     const int n0 = __ldg(t.tile_ptr + first + 1) - __ldg(t.tile_ptr + first);
     gather_nodes<CMP, ANP>(a, tn, n0, su2, sl2, sp2, tid, T);
     async_wait_all();
@@ -178,6 +189,14 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     const float* sp = sp2 + s * cap;
     const int base = __ldg(t.tile_ptr + tile);
     const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
+    const int next = tile + stride;
+    const bool has_next = next < t.n_tiles;
+    // 0. the next tile's nodes: its list came with this tile's stage
+    if (has_next) {
+      const int* tn = reinterpret_cast<const int*>(st + L.tnodes);
+      const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
+      gather_nodes<CMP, ANP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, sp2 + (s ^ 1) * cap, tid, T);
+    }
     // 1. element forces of this tile into shared memory
     const int e = tile * T + tid;
     if (e < a.E) {
@@ -232,29 +251,23 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
       flag_inverted(a.st, e, inv);
     }
     // 2. the next tile's segments must have landed; barrier: records complete
-    const int next = tile + stride;
-    const bool has_next = next < t.n_tiles;
     const bool ok = has_next ? mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1)) : true;
     if (__syncthreads_or(!ok)) {
-      // the only copy in flight is the one that timed out: give it one more
-      // bounded wait before the block's shared memory is released
+      // the next tile's gather and the copy that timed out are in flight:
+      // let both land (bounded) before the block's shared memory is released
+      async_wait_all();
       if (tid == 0) {
         atomicOr(&a.st->err_flags, ERR_TIMEOUT);
         mbar_wait(&bars[s ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
       }
       return;
     }
-    // 3. gather the next tile's nodes (async) while this tile is reduced
-    if (has_next) {
-      const int* tn = reinterpret_cast<const int*>(smem + (s ^ 1) * stage_bytes + L.tnodes);
-      const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
-      gather_nodes<CMP, ANP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, sp2 + (s ^ 1) * cap, tid, T);
-    }
     reduce_tile(sf4, lidx, lptr, n_t, tid, T, [&](int q, float4 f) { t.partials[pdst[q]] = f; });
     async_wait_all();
     // 4. barrier: stage s and the records are free, the next tile's nodes staged
     __syncthreads();
-    if (tid == 0 && next + stride < t.n_tiles) issue_tile<NE>(a, t, L, smem + s * stage_bytes, &bars[s], next + stride);
+    if (tid == 0 && next + stride < t.n_tiles)
+      issue_tile<NE>(a, t, L, smem + s * stage_bytes, &bars[s], next + stride, next + 2 * stride);
   }
 }
 
