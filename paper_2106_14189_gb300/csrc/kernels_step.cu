@@ -246,8 +246,22 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   if (i < a.N) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (a.node_ptr) {
-      // node-major partials: one contiguous run per node, ascending tile
-      for (int p = beg; p < end; ++p) {
+      // node-major partials: one contiguous run per node, ascending tile.  The
+      // first kBatch loads are issued together (most nodes have fewer
+      // partials), then added in the run's order
+      constexpr int kBatch = 4;
+      float4 f0[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k)
+        if (beg + k < end) f0[k] = __ldcs(a.slots + beg + k);
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k)
+        if (beg + k < end) {
+          fx += f0[k].x;
+          fy += f0[k].y;
+          fz += f0[k].z;
+        }
+      for (int p = beg + kBatch; p < end; ++p) {
         const float4 f = __ldcs(a.slots + p);
         fx += f.x;
         fy += f.y;
