@@ -177,7 +177,13 @@ dj_status dj_mesh_set_bcs(dj_mesh* mesh, const long long* dof, const double* tar
 
 /* Replace the target values of the current prescribed-DOF list (same order as
  * the last dj_mesh_set_bcs).  Allowed after dj_precompute; takes effect on the
- * next step.  Host array of n_bc_dofs doubles. */
+ * next step.  Host array of n_bc_dofs doubles, read before the call returns:
+ * a page-locked, 8-byte aligned array is read by the library's kernel through
+ * its device mapping (one launch on the legacy default stream, then a
+ * synchronisation of that stream); other host memory is staged in a
+ * page-locked copy of the per-node table and copied once.  Steps still in
+ * flight on a non-blocking stream are not waited for.
+ * Errors: DJ_ERR_INVALID_ARG (null or non-finite target; nothing changes). */
 dj_status dj_mesh_update_bc_targets(dj_mesh* mesh, const double* target);
 
 /* Independent bodies in one mesh (used for batches of problems).  elem_group:
@@ -319,9 +325,9 @@ dj_status dj_set_displacements(dj_mesh* mesh, const double* U0);
 
 /* Current displacements U^n, host n_nodes * 3 doubles (caller order).
  * Synchronizes the device and reports pending device-side errors.  When U_out
- * is page-locked (cudaHostAlloc / cudaHostRegister) the library's kernel
- * writes it directly through its device mapping; other host memory receives
- * one copy from a device buffer. */
+ * is page-locked (cudaHostAlloc / cudaHostRegister) and 8-byte aligned the
+ * library's kernel writes it directly through its device mapping; other host
+ * memory receives one copy from a device buffer. */
 dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
 
 /* Current displacements into device memory, n_nodes * 3 floats in caller

@@ -16,6 +16,7 @@
 #include <climits>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <numeric>
@@ -23,6 +24,7 @@
 #include <vector>
 
 #include "dj_internal.h"
+#include "dj_io.h"
 
 using namespace dj;
 
@@ -55,6 +57,7 @@ struct dj_mesh {
   float4* d_U = nullptr;
   float4* d_V = nullptr;
   float4* d_bct = nullptr;
+  int* d_bc_flat = nullptr;  // bc_flat_of_entry on the device (target updates)
   float4* d_R = nullptr;
   float4* d_fout = nullptr;
   float4* d_Ulo = nullptr;  // compensated mode: low part of U
@@ -179,7 +182,7 @@ void release_device(dj_mesh* m) {
                   m->d_V,        m->d_bct,        m->d_R,     m->d_fout, m->d_perm,      m->d_state,
                   m->d_partials, m->d_tile_ptr,   m->d_tile_nodes, m->d_lconn, m->d_lptr, m->d_lidx, m->d_xloc, m->d_pdst, m->d_node_ptr, m->d_save, m->d_out64,
                   m->d_parts,    m->d_Ulo,        m->d_bm1,   m->d_node_resid, m->d_group_resid,
-                  m->d_group_node_ptr};
+                  m->d_group_node_ptr, m->d_bc_flat};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   m->d_adr = nullptr;
@@ -197,6 +200,7 @@ void release_device(dj_mesh* m) {
   m->d_bm1 = nullptr;
   m->d_node_resid = m->d_group_resid = nullptr;
   m->d_group_node_ptr = nullptr;
+  m->d_bc_flat = nullptr;
   if (m->h_group_resid) cudaFreeHost(m->h_group_resid);
   m->h_group_resid = nullptr;
   if (m->h_state) cudaFreeHost(m->h_state);
@@ -963,8 +967,12 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   }
   CK(dalloc(m, &m->d_fout, N));
   CK(dalloc(m, &m->d_bct, std::max(1, m->n_bc_nodes)));
-  if (m->n_bc_nodes)
+  if (m->n_bc_nodes) {
     CK(cudaMemcpy(m->d_bct, m->h_bct.data(), m->h_bct.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    const size_t nb = m->bc_flat_of_entry.size();
+    CK(dalloc(m, &m->d_bc_flat, nb));
+    CK(cudaMemcpy(m->d_bc_flat, m->bc_flat_of_entry.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+  }
   CK(dalloc(m, &m->d_perm, N));
   CK(cudaMemcpy(m->d_perm, m->node_new_of_old.data(), N * sizeof(int), cudaMemcpyHostToDevice));
   if (!m->R.empty()) {
@@ -1198,9 +1206,25 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
   if (!m->precomputed) return DJ_OK;
   CK(cudaSetDevice(m->device));
   if (m->n_bc_nodes) {
-    // the per-node table (targets, w = component mask) lives in pinned memory
-    // once the first update has staged it; each update rewrites the targets
-    // in place and copies the table once
+    // a page-locked caller array (8-byte aligned) is read by the scatter kernel
+    // through its device mapping: one launch, no host pass over the table
+    cudaPointerAttributes attr;
+    const double* mapped = nullptr;
+    if (reinterpret_cast<uintptr_t>(target) % alignof(double) == 0 &&
+        cudaPointerGetAttributes(&attr, target) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+        attr.devicePointer)
+      mapped = static_cast<const double*>(attr.devicePointer);
+    else
+      (void)cudaGetLastError();
+    if (mapped) {
+      CK(launch_bc_targets(mapped, m->d_bc_flat, (int)nb, m->d_bct, 0));
+      CK(cudaStreamSynchronize(0));  // the caller may reuse the array on return
+      return DJ_OK;
+    }
+    // otherwise the per-node table (targets, w = component mask) lives in
+    // pinned memory once the first update has staged it; each update rewrites
+    // the targets in place and copies the table once (every target entry is
+    // rewritten, so the staged copy never goes stale)
     const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
     if (!m->h_bct_pinned) {
       CK(cudaMallocHost((void**)&m->h_bct_pinned, bytes));
@@ -1576,12 +1600,13 @@ dj_status dj_get_displacements(dj_mesh* m, double* U_out) {
   if (!U_out) return fail(m, DJ_ERR_INVALID_ARG, "null U_out");
   CK(cudaDeviceSynchronize());
   const long long N = m->N;
-  // caller order and FP64 on the device.  A page-locked caller buffer is
-  // written by the kernel itself through its device mapping; otherwise the
-  // values go through a device buffer and one copy.
+  // caller order and FP64 on the device.  A page-locked caller buffer
+  // (8-byte aligned) is written by the kernel itself through its device
+  // mapping; otherwise the values go through a device buffer and one copy.
   double* direct = nullptr;
   cudaPointerAttributes attr;
-  if (cudaPointerGetAttributes(&attr, U_out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+  if (reinterpret_cast<uintptr_t>(U_out) % alignof(double) == 0 &&
+      cudaPointerGetAttributes(&attr, U_out) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
       attr.devicePointer)
     direct = static_cast<double*>(attr.devicePointer);
   else

@@ -14,6 +14,7 @@
 #include <float.h>
 
 #include "dj_internal.h"
+#include "dj_io.h"
 
 namespace dj {
 
@@ -298,6 +299,15 @@ __global__ void from_caller_order_kernel(const float* __restrict__ src, const in
   if (Ulo) Ulo[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// one step's prescribed targets (Sec. 5.1, Sec. 6) into the per-node table:
+// entry k of the caller's FP64 array goes to float index flat[k] of the table
+// (4 floats per prescribed node: x, y, z targets and the component mask)
+__global__ void bc_targets_kernel(const double* __restrict__ target, const int* __restrict__ flat, int n,
+                                  float* __restrict__ table) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) table[__ldg(flat + k)] = (float)target[k];
+}
+
 }  // namespace
 
 cudaError_t launch_from_caller_order(const float* src, const int* node_new_of_old, int N, float4* U,
@@ -352,6 +362,12 @@ cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const
                                        double* out, cudaStream_t s) {
   const int t = kOrderThreads;
   to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  bc_targets_kernel<<<(n + 255) / 256, 256, 0, s>>>(target, flat, n, reinterpret_cast<float*>(table));
   return cudaGetLastError();
 }
 
