@@ -130,10 +130,21 @@ __global__ void anp_pressure_kernel(const int* __restrict__ node_ptr, const floa
                                     const float* __restrict__ c1, float* __restrict__ pres, int N) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  // the node's run in ascending tile order; the first kBatch loads are issued
+  // together, then added in that order
+  constexpr int kBatch = 4;
+  const int p0 = __ldg(node_ptr + i), p1 = __ldg(node_ptr + i + 1);
+  const float c = __ldg(c1 + i);
+  float v[kBatch];
+#pragma unroll
+  for (int k = 0; k < kBatch; ++k)
+    if (p0 + k < p1) v[k] = __ldg(vparts + p0 + k);
   float s = 0.f;
-  const int p1 = __ldg(node_ptr + i + 1);
-  for (int p = __ldg(node_ptr + i); p < p1; ++p) s += __ldg(vparts + p);
-  pres[i] = __ldg(c1 + i) * s;
+#pragma unroll
+  for (int k = 0; k < kBatch; ++k)
+    if (p0 + k < p1) s += v[k];
+  for (int p = p0 + kBatch; p < p1; ++p) s += __ldg(vparts + p);
+  pres[i] = c * s;
 }
 
 }  // namespace
