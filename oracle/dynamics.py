@@ -17,10 +17,17 @@ g(t_{n+1}) after the update; fixed DOFs are prescribed DOFs with target 0.
 
 Readings (the paper is silent on these):
 * lumped mass: m_i = sum over elements containing node i of rho 0V / n_e.
-* critical step (Eq. 14): dt_crit = min_e L_e / c_e with c_e the dilatational
-  wave speed sqrt(M_e / rho_e), M_e = kappa + 4/3 mu_eff + 4 (eta_a + eta_b)
-  (mu_eff = mu + 2 C01 for Mooney-Rivlin, the small-strain shear modulus; the
-  fibre terms are the small-strain stiffening along the fibre).  L_e is the
+* critical step (Eq. 14): dt_crit = min_e L_e / c_e with c_e the fastest
+  (dilatational) wave speed sqrt(M_e / rho_e) of the material linearised at
+  rest, M_e the largest eigenvalue of its acoustic tensor over all directions:
+  M_e = kappa + 4/3 mu_eff + 16/9 (eta_a + eta_b).  mu_eff = mu + 2 C01 is the
+  small-strain shear modulus (Mooney-Rivlin).  A fibre family adds
+  eta (dI4bar)^2 to the second variation of Psi at rest (Table 3: the term
+  eta / 2 (I4bar - 1)^2 has zero slope there), with dI4bar = 2 H : (A - I/3) for
+  a displacement gradient H (the J^-2/3 of the modified invariant removes the
+  trace); its acoustic contribution 4 eta ((A - I/3) n)^2 is largest along the
+  fibre, 4 eta (2/3)^2 = 16/9 eta.  So M_e is exact for NH, MR and TI, and for
+  OT an upper bound (exact when the two fibres coincide).  L_e is the
   length that makes Eq. 14 the central-difference limit 2 / omega_e of the
   element's highest frequency under lumped mass, bounded as for uniform-strain
   elements: omega_e^2 <= n_e c_e^2 sum_{i,a} 0B_ia^2 (+ n_e k lmax(Gamma Gamma^T)
@@ -60,7 +67,7 @@ def wave_modulus(mat):
     mu_eff = mat["mu"] + np.where(model == djtled.MR, 2.0 * mat["c01"], 0.0)
     fib = np.where((model == djtled.TI) | (model == djtled.OT), mat["eta_a"], 0.0) \
         + np.where(model == djtled.OT, mat["eta_b"], 0.0)
-    return mat["kappa"] + 4.0 / 3.0 * mu_eff + 4.0 * fib
+    return mat["kappa"] + 4.0 / 3.0 * mu_eff + 16.0 / 9.0 * fib
 
 
 def critical_time_step(X, conn, elem_type, mat, V0, gamma=None, k_hg=None):

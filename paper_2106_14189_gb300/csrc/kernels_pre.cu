@@ -9,7 +9,10 @@
 // Critical step (Eq. 14, dt <= L_e / c): L_e is taken as the length for which
 // Eq. 14 equals 2 / omega_e, with the uniform-strain bound
 //   omega_e^2 <= n_e c^2 sum_{i,a} 0B_ia^2  (+ n_e k lmax(Gamma Gamma^T) / (rho 0V), H8)
-// c^2 = (kappa + 4/3 mu_eff + 4 (eta_a + eta_b)) / rho, lmax by Gershgorin.
+// c^2 = (kappa + 4/3 mu_eff + 16/9 (eta_a + eta_b)) / rho, lmax by Gershgorin:
+// the largest acoustic modulus of the material linearised at rest (a fibre
+// family adds 4 eta ((A - I/3) n)^2, largest along the fibre; an upper bound
+// for two fibre families).
 #include <cuda_runtime.h>
 #include <float.h>
 
@@ -165,7 +168,7 @@ __global__ void precompute_elements_kernel(PreArgs a) {
       sumB2 += B0[i][b] * B0[i][b];
     }
   const double mu_eff = mu + 2.0 * c01;
-  const double Mw = kappa + 4.0 / 3.0 * mu_eff + 4.0 * (eta_a + eta_b);
+  const double Mw = kappa + 4.0 / 3.0 * mu_eff + 16.0 / 9.0 * (eta_a + eta_b);
   double w2 = ne * (Mw / rho) * sumB2;
   if (ne == 8) {
     double cq[4][3];

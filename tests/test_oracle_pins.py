@@ -410,49 +410,174 @@ def test_central_difference_discrete_frequency_damping_and_stability():
 
 
 # ---------------------------------------------------------------- mass, dt -
-def test_lumped_mass_and_critical_step():
+def _one_material(model, mu=1000.0, kappa=20000.0, eta_a=0.0, eta_b=0.0, c01=0.0, rho=1000.0, E=1):
+    f = lambda v: np.full(E, float(v))
+    return dict(model=np.full(E, model), mu=f(mu), kappa=f(kappa), rho=f(rho), eta_a=f(eta_a),
+                eta_b=f(eta_b), c01=f(c01))
+
+
+def _stiffness(mdl, N, h=1e-7):
+    """Assembled stiffness at rest by central differences of the oracle forces."""
+    K = np.zeros((3 * N, 3 * N))
+    for j in range(3 * N):
+        u = np.zeros(3 * N)
+        u[j] = h
+        fp = mdl.internal_forces(u.reshape(-1, 3)).ravel()
+        fm = mdl.internal_forces(-u.reshape(-1, 3)).ravel()
+        K[:, j] = (fp - fm) / (2 * h)
+    return 0.5 * (K + K.T)
+
+
+def _omega_max(mdl, N):
+    ms = 1.0 / np.sqrt(np.repeat(mdl.mass, 3))
+    return float(np.sqrt(np.linalg.eigvalsh(_stiffness(mdl, N) * ms[:, None] * ms[None, :]).max()))
+
+
+def _first_piola_tangent(mat, a, b, h=1e-6):
+    """dP/dF at F = I of the oracle's element, from its nodal forces: on one T4
+    under a homogeneous deformation gradient F the forces are f_a = 0V P 0b_a."""
+    X = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]])
+    conn = np.array([[0, 1, 2, 3]])
+    pre = djtled.precompute(X, conn, 4, a[None], b[None], with_mr=bool(mat["model"][0] == djtled.MR))
+    J0 = elements.reference_jacobian(X, conn, 4)[0]
+    B0 = np.linalg.solve(J0, elements.Hxi(4))
+    V0 = np.linalg.det(J0) / 6.0
+
+    def P(F):
+        f = djtled.element_forces((X @ (F - np.eye(3)).T)[conn], pre, mat)[0]
+        return f.T @ np.linalg.pinv(B0) / V0
+
+    A = np.zeros((3, 3, 3, 3))
+    for k in range(3):
+        for l in range(3):
+            E = np.zeros((3, 3))
+            E[k, l] = h
+            A[:, :, k, l] = (P(np.eye(3) + E) - P(np.eye(3) - E)) / (2 * h)
+    return A
+
+
+def _largest_acoustic_modulus(A, hints):
+    """max over unit n of the largest eigenvalue of Q_ik = A_iJkL n_J n_L."""
+    from scipy.optimize import minimize
+    rng = np.random.default_rng(0)
+    ns = np.vstack([rng.normal(size=(4000, 3))] + [np.asarray(v)[None] for v in hints])
+    ns /= np.linalg.norm(ns, axis=1, keepdims=True)
+
+    def lam(n):
+        n = n / np.linalg.norm(n)
+        q = np.einsum("iJkL,J,L->ik", A, n, n)
+        return np.linalg.eigvalsh(0.5 * (q + q.T))[-1]
+
+    vals = np.array([lam(n) for n in ns])
+    best = max(vals.max(), *[-minimize(lambda x: -lam(x), ns[i], method="Nelder-Mead",
+                                       options=dict(xatol=1e-10, fatol=1e-12, maxiter=4000)).fun
+                             for i in np.argsort(vals)[-3:]])
+    return float(best)
+
+
+@pytest.mark.parametrize("case", ["NH", "TI", "OT_same_fibre", "OT", "MR"])
+def test_wave_modulus_is_the_largest_acoustic_modulus(case):
+    """The modulus of the critical step's wave speed (Eq. 14) equals the largest
+    eigenvalue of the acoustic tensor of the oracle's own material, linearised at
+    rest from its element forces (pinned to classical TLED and to the energy
+    gradient above), over all directions: exact for NH, MR and TI; for OT an upper
+    bound that is reached when both fibres coincide."""
+    rng = np.random.default_rng({"NH": 1, "TI": 2, "OT_same_fibre": 3, "OT": 4, "MR": 5}[case])
+    a = rng.normal(size=3)
+    a /= np.linalg.norm(a)
+    b = rng.normal(size=3)
+    b /= np.linalg.norm(b)
+    mu, kappa = 1300.0, 9000.0
+    if case == "NH":
+        mat = _one_material(djtled.NH, mu, kappa)
+    elif case == "TI":
+        mat = _one_material(djtled.TI, mu, kappa, eta_a=4.0 * mu)
+    elif case == "MR":
+        mat = _one_material(djtled.MR, mu, kappa, c01=0.4 * mu)
+    else:
+        mat = _one_material(djtled.OT, mu, kappa, eta_a=3.0 * mu, eta_b=2.0 * mu)
+        if case == "OT_same_fibre":
+            b = a
+    M = dynamics.wave_modulus(mat)[0]
+    Mmax = _largest_acoustic_modulus(_first_piola_tangent(mat, a, b), [a, b])
+    if case == "OT":
+        assert Mmax <= M * (1 + 1e-7) and Mmax > 0.8 * M
+    else:
+        assert abs(M - Mmax) < 1e-6 * M, (M, Mmax)
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_lumped_mass_and_critical_step(model):
+    """Lumped mass sums to rho V; the critical step of a cube mesh equals the
+    hand-derived uniform-strain bound with the largest acoustic modulus
+    (NH: kappa + 4/3 mu; MR: mu + 2 C01 in place of mu; a fibre: + 16/9 eta)."""
     n, L, rho = 4, 0.5, 1060.0
+    mu, kappa = 1006.712, 50000.0
+    eta_a = 3.0 * mu if model in (djtled.TI, djtled.OT) else 0.0
+    eta_b = 2.0 * mu if model == djtled.OT else 0.0
+    c01 = 0.3 * mu if model == djtled.MR else 0.0
+    modulus = kappa + 4.0 / 3.0 * (mu + 2.0 * c01) + 16.0 / 9.0 * (eta_a + eta_b)
     for et in (4, 8):
         X, conn = (W.cube_tet4(n, L) if et == 4 else W.cube_hex8(n, L))
         E = conn.shape[0]
-        mat = dict(model=np.zeros(E), mu=np.full(E, 1006.712), kappa=np.full(E, 50000.0),
-                   rho=np.full(E, rho), eta_a=np.zeros(E), eta_b=np.zeros(E), c01=np.zeros(E))
-        mdl = dynamics.Model(et, X, conn, mat)
+        mat = _one_material(model, mu, kappa, eta_a, eta_b, c01, rho, E)
+        rng = np.random.default_rng(et)
+        mdl = dynamics.Model(et, X, conn, mat, a_dir=rng.normal(size=(E, 3)), b_dir=rng.normal(size=(E, 3)))
         assert abs(mdl.mass.sum() - rho * L ** 3) < 1e-12 * rho * L ** 3
-        c = np.sqrt((50000.0 + 4.0 / 3.0 * 1006.712) / rho)
+        c = np.sqrt(modulus / rho)
         h = L / n
         # uniform-strain bound omega^2 <= n_e c^2 sum 0B^2: a Kuhn tet of a cube of
         # side h has barycentric gradients (-1,0,0), (1,-1,0), (0,1,-1), (0,0,1) / h,
         # sum 0B^2 = 6 / h^2; a brick has 0B = xi_a / (4h), sum = 1.5 / h^2, and its
-        # hourglass Gram matrix is 8 I with k = 0.1 c^2 rho h^3 1.5 / h^2 / 8
+        # hourglass Gram matrix is 8 I with k = 0.1 (kappa + 4/3 mu) h^3 1.5 / h^2 / 8
         if et == 4:
             dt = 2.0 / np.sqrt(4 * c * c * 6.0 / h ** 2)
         else:
-            w2 = 8 * c * c * 1.5 / h ** 2 + 8 * (0.1 * c * c * rho * h ** 3 * 1.5 / h ** 2 / 8) * 8 \
-                / (rho * h ** 3)
+            k_hg = 0.1 * (kappa + 4.0 / 3.0 * mu) * h ** 3 * 1.5 / h ** 2 / 8
+            w2 = 8 * c * c * 1.5 / h ** 2 + 8 * k_hg * 8 / (rho * h ** 3)
             dt = 2.0 / np.sqrt(w2)
         assert abs(mdl.critical_time_step() - dt) < 1e-12 * dt
 
 
 @pytest.mark.parametrize("et", [4, 8])
-def test_critical_step_bounds_the_global_highest_frequency(et):
-    """2 / omega_max of the assembled, linearised, unconstrained mesh >= dt_crit."""
+@pytest.mark.parametrize("model", MODELS)
+def test_critical_step_bounds_the_global_highest_frequency(et, model):
+    """2 / omega_max of the assembled, linearised, unconstrained mesh >= dt_crit,
+    with a compressible matrix (nu = 0.3) and stiff fibres so that the fibre and
+    Mooney-Rivlin terms dominate the highest frequency."""
     X, conn = (W.box_tet4(3, 2, 2, 1.0, 0.7, 0.9) if et == 4 else W.box_hex8(3, 2, 2, 1.0, 0.7, 0.9))
     rng = np.random.default_rng(2)
     X = X + rng.uniform(-0.03, 0.03, size=X.shape)
     E = conn.shape[0]
-    mat = dict(model=np.zeros(E), mu=np.full(E, 1006.7), kappa=np.full(E, 50000.0),
-               rho=np.full(E, 1000.0), eta_a=np.zeros(E), eta_b=np.zeros(E), c01=np.zeros(E))
-    mdl = dynamics.Model(et, X, conn, mat, hg_coeff=0.1)
-    N = X.shape[0]
-    K = np.zeros((3 * N, 3 * N))
-    h = 1e-7
-    for j in range(3 * N):
-        u = np.zeros(3 * N)
-        u[j] = h
-        K[:, j] = mdl.internal_forces(u.reshape(-1, 3)).ravel() / h
-    ms = 1.0 / np.sqrt(np.repeat(mdl.mass, 3))
-    wmax = np.sqrt(np.linalg.eigvalsh(0.5 * (K + K.T) * ms[:, None] * ms[None, :]).max())
+    mu, kappa = 1153.8, 2500.0
+    mat = _one_material(model, mu, kappa, eta_a=5.0 * mu if model in (djtled.TI, djtled.OT) else 0.0,
+                        eta_b=4.0 * mu if model == djtled.OT else 0.0,
+                        c01=0.5 * mu if model == djtled.MR else 0.0, E=E)
+    mdl = dynamics.Model(et, X, conn, mat, a_dir=rng.normal(size=(E, 3)), b_dir=rng.normal(size=(E, 3)),
+                         hg_coeff=0.1)
+    wmax = _omega_max(mdl, X.shape[0])
+    dt = mdl.critical_time_step()
+    assert dt <= 2.0 / wmax
+    assert dt > 0.3 * 2.0 / wmax  # a bound, but not a vacuous one
+
+
+def test_single_brick_with_fibre_along_an_edge_highest_frequency():
+    """One cube brick (side h, 1-point rule), fibre along the x edge, free.  Its
+    uniform-strain modes u_a = G xi_a have gradient 2 G / h and Rayleigh quotient
+    4 / (rho h^2) G:C:G / |G|^2, C the linearised material: volumetric 3 kappa,
+    the deviatoric stretch along the fibre D = e_x e_x - I/3: 2 mu + 4 eta |D|^2 =
+    2 mu + 8/3 eta.  With a stiff fibre and a soft hourglass the latter is the
+    highest frequency; the critical step stays below 2 / omega_max."""
+    h, rho, mu, kappa, eta = 0.01, 1000.0, 1000.0, 1500.0, 6000.0
+    X, conn = W.cube_hex8(1, h)
+    mat = _one_material(djtled.TI, mu, kappa, eta_a=eta, rho=rho)
+    mdl = dynamics.Model(8, X, conn, mat, a_dir=np.array([[1.0, 0.0, 0.0]]), b_dir=np.array([[0.0, 1, 0]]),
+                         hg_coeff=0.05)
+    w_hand = np.sqrt(4.0 / (rho * h * h) * (2.0 * mu + 8.0 / 3.0 * eta))
+    w_vol = np.sqrt(4.0 / (rho * h * h) * 3.0 * kappa)
+    assert w_hand > 1.5 * w_vol
+    wmax = _omega_max(mdl, X.shape[0])
+    assert abs(wmax - w_hand) < 1e-6 * w_hand, (wmax, w_hand)
     assert mdl.critical_time_step() <= 2.0 / wmax
 
 
