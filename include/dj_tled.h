@@ -102,7 +102,13 @@ typedef struct dj_mesh dj_mesh;
  *                     (dj_run_n, relaxation) are joined by ordinary edges;
  *                     1: by programmatic-launch edges, as directly launched
  *                     steps are (faster on small meshes; dj_autotune tries
- *                     both). */
+ *                     both).
+ *   max_blocks        assembly 2 only: upper limit on the blocks of the
+ *                     persistent kernel, each of which walks the tiles
+ *                     b, b + grid, b + 2 grid, ...; 0 (default) = SMs x resident
+ *                     blocks per SM (one wave).  A small value makes every block
+ *                     walk many tiles, the steady state of its copy pipeline.
+ *                     Negative values are rejected (DJ_ERR_INVALID_ARG). */
 typedef struct {
   double dt;
   double dt_scale;
@@ -117,6 +123,7 @@ typedef struct {
   int precision;
   int anp;
   int graph_pdl;
+  int max_blocks;
 } dj_params;
 
 /* Read-only description of a mesh after dj_precompute. */
@@ -136,6 +143,8 @@ typedef struct {
   int tile_size;            /* elements per tile (tiled assembly) */
   int n_consts;             /* floats per element in the element table */
   int precision;            /* precision mode in use (see dj_params) */
+  int grid;                 /* assembly 2: blocks of the persistent kernel (else 0) */
+  long long n_tiles;        /* tiled assembly: number of tiles (else 0) */
 } dj_info;
 
 /* Fill *p with the defaults listed above. */

@@ -627,7 +627,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
       (prm.ramp_kind != DJ_RAMP_LINEAR && prm.ramp_kind != DJ_RAMP_SMOOTH) || !std::isfinite(prm.dt) ||
       (prm.assembly != ASSEMBLY_SLOTS && prm.assembly != ASSEMBLY_TILES && prm.assembly != ASSEMBLY_TILES_TMA) ||
       (prm.precision != 0 && prm.precision != 1) || (prm.anp != 0 && prm.anp != 1) ||
-      (prm.graph_pdl != 0 && prm.graph_pdl != 1))
+      (prm.graph_pdl != 0 && prm.graph_pdl != 1) || prm.max_blocks < 0)
     return fail(m, DJ_ERR_INVALID_ARG, "invalid dj_params");
   if (prm.anp && (m->ne != 4 || prm.assembly != ASSEMBLY_TILES_TMA))
     return fail(m, DJ_ERR_INVALID_ARG, "average nodal pressure needs T4 elements and assembly 2");
@@ -990,6 +990,7 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     const int per_sm = tma_blocks_per_sm(m->elem_type, m->variant, m->cmp, m->anp, tile_args(m));
     if (per_sm <= 0) return fail(m, DJ_ERR_UNSUPPORTED, "tile too large for shared memory (tile_size %d)", m->T);
     m->tma_grid = std::min(m->n_tiles, per_sm * sms);
+    if (prm.max_blocks > 0) m->tma_grid = std::min(m->tma_grid, prm.max_blocks);
   }
   m->n_node_blocks = (int)((N + NODE_THREADS - 1) / NODE_THREADS);
   CK(dalloc(m, &m->d_partials, m->n_node_blocks));
@@ -1838,6 +1839,8 @@ dj_status dj_get_info(const dj_mesh* mc, dj_info* info) {
   info->tile_size = m->T;
   info->n_consts = m->n_consts;
   info->precision = m->cmp;
+  info->grid = m->assembly == ASSEMBLY_TILES_TMA ? m->tma_grid : 0;
+  info->n_tiles = m->assembly != ASSEMBLY_SLOTS ? m->n_tiles : 0;
   return DJ_OK;
 }
 

@@ -275,6 +275,64 @@ def test_tma_pipeline_equals_per_tile_blocks(B, et, tile):
         b.sync()
 
 
+# The persistent bulk-copy kernel (assembly 2) walks tiles b, b + grid, ...:
+# from the second tile of a block on, the stage ring is reused, the mbarrier
+# phases flip and the node list of the next tile rides in the current stage.
+# A grid cap (dj_params.max_blocks) makes every block walk several tiles on
+# meshes small enough for the oracle.
+STEADY = [(4, 0, 3), (4, 64, 4), (8, 0, 2), (8, 64, 3)]  # (element, tile size, blocks)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("model", [W.NH, W.TI, W.OT, W.MR])
+@pytest.mark.parametrize("et,tile,blocks", STEADY)
+def test_tma_steady_state_forces_match_oracle(B, et, tile, blocks, model, prec):
+    """Bulk-copy pipeline with several tiles per block: every nodal force against
+    the oracle within the force tolerance."""
+    if et == 4:
+        p = W.random_tet_mesh_problem(2058, seed=31 + model, model=model)
+        U = np.random.default_rng(7).normal(size=(p.n_nodes, 3)) * 0.005
+    else:
+        p = W.random_hex_mesh_problem(9, seed=41 + model, model=model)
+        p.hg_coeff = 0.15
+        U = np.random.default_rng(8).normal(size=(p.n_nodes, 3)) * 0.004
+    with B.Mesh(p, assembly=2, tile_size=tile, precision=prec, max_blocks=blocks) as m:
+        info = m.info()
+        F = m.internal_forces(U)
+    assert info.grid == blocks and info.n_tiles >= 3 * info.grid, (info.grid, info.n_tiles)
+    ref = dynamics.Model.from_problem(p).internal_forces(U)
+    assert rel_linf(F, ref) < FORCE_TOL
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("model", [W.NH, W.TI])
+@pytest.mark.parametrize("et,tile,blocks", STEADY)
+def test_tma_steady_state_trajectory_matches_oracle(B, et, tile, blocks, model, prec):
+    """Bulk-copy pipeline with several tiles per block, stepped: every DOF against
+    the FP64 oracle's trajectory within rel-Linf 1e-4 (Algorithm 1 run-time loop,
+    Eq. 13), and bit-identical to the one-block-per-tile kernel (same tiles, same
+    summation order)."""
+    if et == 4:
+        p = W.random_tet_mesh_problem(4374, seed=51 + model, model=model)
+    else:
+        p = W.random_hex_mesh_problem(10, seed=61 + model, model=model)
+    p.ramp_steps, p.alpha = 200, 2.0
+    n = 300
+    with B.Mesh(p, assembly=2, tile_size=tile, precision=prec, max_blocks=blocks) as m, \
+            B.Mesh(p, assembly=1, tile_size=tile, precision=prec) as t:
+        info = m.info()
+        m.run(n)
+        t.run(n)
+        U, Ut = m.displacements(), t.displacements()
+    assert info.grid == blocks and info.n_tiles >= 3 * info.grid, (info.grid, info.n_tiles)
+    assert np.array_equal(U, Ut)
+    ref = dynamics.ExplicitSolver.from_problem(p).run(n)
+    e = rel_linf(U, ref)
+    print(f"steady-state bulk-copy T{et} model {model} prec {prec}: {info.n_tiles} tiles on "
+          f"{info.grid} blocks, {n} steps, rel-Linf {e:.2e}")
+    assert e < DISP_TOL
+
+
 def test_relaxation_matches_oracle(B):
     """Plain FP32 stepping stalls near r ~ 1e-4 on this stiff (kappa / mu = 50) cube,
     so the tolerance here is 3e-4; the compensated mode reaches 1e-5 (below)."""
@@ -324,16 +382,20 @@ def test_cfg1_trajectory_compensated(B, cfg1_reference):
     assert rel_linf(U, ref[2000]) < DISP_TOL
 
 
-def test_full_size_cfg2b_sampled_nodes(B):
-    """1.23M-tet cube (59^3 x 6) in the benchmark's configuration (plain FP32, tiled
-    assembly): one update at sampled nodes against the oracle, which evaluates only
+def test_full_size_cfg2b_sampled_nodes_bulk_copy_tiles_256(B):
+    """1.23M-tet cube (59^3 x 6) in the benchmark's schedule (plain FP32, the
+    persistent bulk-copy kernel with tiles of 256 on one wave of blocks, so every
+    block walks several tiles): one update at sampled nodes against the oracle,
+    which evaluates only
     their incident elements.  FP32 error model of the force at node i: 1e-4 of the
     largest incident element force, plus the volumetric term's absolute error
     kappa 0V |0B| dJ with dJ = 8 ulp(1) (J - 1 is formed as det(tJ) / det(0J) - 1)."""
     from oracle import tled
     p = W.cube_shear(W.TET4, 59, n_steps=5000)
     rng = np.random.default_rng(0)
-    with B.Mesh(p) as m:
+    with B.Mesh(p, assembly=2, tile_size=256) as m:
+        info = m.info()
+        assert info.assembly == 2 and info.n_tiles > info.grid > 0, (info.n_tiles, info.grid)
         m.run(2000)
         U0 = m.displacements()
         m.step()
