@@ -478,13 +478,31 @@ const char* dj_mlp_last_error(const dj_mlp* mlp);
 void dj_mlp_destroy(dj_mlp* mlp);
 
 /* POD of cols snapshots of length rows (d_Y column-major: snapshot c at
- * d_Y + c * rows; cols <= 4096): d_mean (rows) the snapshot mean, d_modes
- * (rows x r, row-major) the r leading orthonormal modes of the centred
- * snapshots (method of snapshots: Gram matrix on the GPU with FP64 slab
- * accumulation, FP64 Householder + QL eigen-decomposition on the host), sigma_out (host,
- * optional, r) the singular values.  Synchronous. */
+ * d_Y + c * rows; cols <= 65536, r <= min(cols, 1024)): d_mean (rows) the
+ * snapshot mean, d_modes (rows x r, row-major) the r leading orthonormal modes
+ * of the centred snapshots Yc, sigma_out (host, optional, r) their singular
+ * values.  Method: randomised range finder on the GPU, Z = Yc Omega with a
+ * seeded normal Omega of l = min(cols, r + max(32, r / 2)) columns, three
+ * subspace-iteration steps (none when l = cols, where the result is the exact
+ * truncated SVD), each product orthonormalised through the eigen-decomposition
+ * of its l x l Gram matrix, then a Rayleigh-Ritz step on (Yc^T Z)^T (Yc^T Z);
+ * products with FP64 slab accumulation, the l x l eigenproblems in FP64 on
+ * the host (dj_symmetric_eigen).  Modes beyond the numerical rank of the
+ * snapshots are zero with sigma 0.  Allocates about (cols + 2 l) rows floats
+ * of device scratch; synchronous.
+ * Errors: DJ_ERR_INVALID_ARG (sizes), DJ_ERR_OOM, DJ_ERR_CUDA. */
 dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d_mean, float* d_modes,
                      double* sigma_out, void* stream);
+/* Eigen-decomposition of a symmetric n x n matrix (host, FP64, no device
+ * work; no counterpart in the paper): the cyclic Jacobi method, sweeping the
+ * pairs (p, q) row by row with the plane rotation that zeroes a_pq, until the
+ * off-diagonal part is below 1e-15 of the matrix in Frobenius norm.  A
+ * (row-major, host) is read and symmetrised as (A + A^T) / 2; w (host, n) gets
+ * the eigenvalues in descending order, V (host, row-major n x n, optional) the
+ * orthonormal eigenvectors as columns in the same order.  n <= 4096 (cost
+ * grows as n^3 per sweep: meant for the POD's small Rayleigh-Ritz problems).
+ * Errors: DJ_ERR_INVALID_ARG (null pointer, size, non-finite entry). */
+dj_status dj_symmetric_eigen(const double* A, int n, double* w, double* V);
 /* d_Q (cols x r) = (X - mean)^T modes for column-major d_X (rows x cols);
  * d_mean may be NULL.  Enqueued on `stream`; allocates nothing. */
 dj_status dj_pod_project(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_X,

@@ -42,7 +42,7 @@ EXPORTS = [
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
     "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
     "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply", "dj_profile_kernels",
-    "dj_autotune_cold", "dj_quad_features",
+    "dj_autotune_cold", "dj_quad_features", "dj_symmetric_eigen",
 ]
 
 
@@ -164,6 +164,7 @@ def lib():
         "dj_batch_set_step": (C.c_int, [_P, C.c_longlong]),
         "dj_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(dj_params), _D]),
         "dj_batch_autotune": (C.c_int, [_P, C.c_int, _P]),
+        "dj_symmetric_eigen": (C.c_int, [_D, C.c_int, _D, _D]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -726,3 +727,13 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def dj_symmetric_eigen(A):
+    """Eigenvalues (descending) and eigenvectors (columns) of a symmetric matrix."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.empty(n)
+    V = np.empty((n, n))
+    _check(lib().dj_symmetric_eigen(_dptr(A), n, _dptr(w), _dptr(V)), "dj_symmetric_eigen")
+    return w, V

@@ -5,7 +5,7 @@
 //
 //   gemm_kernel<ACC>   C = alpha op(A) op(B) + beta C, 64 x 64 tiles, 4 x 4 per
 //                      thread, FP32 products; ACC = double adds each 16-wide
-//                      K-slab into an FP64 accumulator (POD Gram matrices over
+//                      K-slab into an FP64 accumulator (POD products over
 //                      ~1e5-1e6 long columns)
 //   bias_act_kernel    Z + b, then tanh (hidden layers) or identity (output)
 //   mse_grad_kernel    weighted squared error and dL/dY
@@ -218,96 +218,62 @@ cudaError_t gemm(int M, int N, int K, float alpha, const float* A, long long sar
 
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Symmetric eigen-decomposition (FP64, host): Householder reduction to
-// tridiagonal form T = Q^T A Q, then the QL iteration with implicit Wilkinson
-// shifts on T, accumulating the plane rotations into Q.  On return w holds the
-// eigenvalues and V (row-major n x n) the eigenvectors as columns.
-void symmetric_eigen(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& V) {
+// Symmetric eigen-decomposition (FP64, host) by the cyclic Jacobi method: sweeps
+// over the pairs (p, q), p < q, row by row; each pair is annihilated by the plane
+// rotation J = [[c, s], [-s, c]] in the (p, q) plane with t = s / c the root of
+// t^2 + 2 theta t - 1 = 0 of smaller magnitude, theta = (a_qq - a_pp) / (2 a_pq)
+// (A <- J^T A J, V <- V J).  Sweeps stop when the off-diagonal Frobenius norm is
+// below 1e-15 of the whole matrix's (at most 60 sweeps).  Used for small
+// matrices only (the POD's Rayleigh-Ritz and orthonormalisation steps, sizes
+// of a few hundred).  A (row-major n x n) is overwritten; w gets the
+// eigenvalues in descending order, V (row-major n x n) the eigenvectors as
+// columns in the same order.
+void jacobi_eigen(std::vector<double>& A, int n, std::vector<double>& w, std::vector<double>& V) {
   auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
+  std::vector<double> Vw((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Vw[(size_t)i * n + i] = 1.0;
+  double total = 0.0;
+  for (size_t q = 0; q < A.size(); ++q) total += A[q] * A[q];
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += 2.0 * a(i, j) * a(i, j);
+    if (!(off > 1e-30 * total)) break;
+    for (int p = 0; p + 1 < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a(p, q);
+        if (apq == 0.0) continue;
+        const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(1.0 + theta * theta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q of A J
+          const double kp = a(k, p), kq = a(k, q);
+          a(k, p) = c * kp - sn * kq;
+          a(k, q) = sn * kp + c * kq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q of J^T (A J)
+          const double pk = a(p, k), qk = a(q, k);
+          a(p, k) = c * pk - sn * qk;
+          a(q, k) = sn * pk + c * qk;
+        }
+        a(p, q) = a(q, p) = 0.0;
+        for (int k = 0; k < n; ++k) {
+          double* vr = &Vw[(size_t)k * n];
+          const double kp = vr[p], kq = vr[q];
+          vr[p] = c * kp - sn * kq;
+          vr[q] = sn * kp + c * kq;
+        }
+      }
+  }
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return a(x, x) > a(y, y); });
+  w.resize(n);
   V.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  std::vector<double> v(n), p(n), wv(n);
-  for (int k = 0; k + 2 < n; ++k) {
-    // Householder vector of column k below the diagonal
-    double nx = 0.0;
-    for (int i = k + 1; i < n; ++i) nx += a(i, k) * a(i, k);
-    nx = std::sqrt(nx);
-    if (nx == 0.0) continue;
-    const double alpha = a(k + 1, k) > 0 ? -nx : nx;
-    for (int i = 0; i < n; ++i) v[i] = 0.0;
-    for (int i = k + 1; i < n; ++i) v[i] = a(i, k);
-    v[k + 1] -= alpha;
-    double nv = 0.0;
-    for (int i = k + 1; i < n; ++i) nv += v[i] * v[i];
-    nv = std::sqrt(nv);
-    if (nv == 0.0) continue;
-    for (int i = k + 1; i < n; ++i) v[i] /= nv;
-    // A <- H A H with H = I - 2 v v^T:  p = 2 A v, K = v^T p, w = p - K v, A -= v w^T + w v^T
-    for (int i = k; i < n; ++i) {
-      double s = 0.0;
-      for (int j = k + 1; j < n; ++j) s += a(i, j) * v[j];
-      p[i] = 2.0 * s;
-    }
-    double K = 0.0;
-    for (int i = k + 1; i < n; ++i) K += v[i] * p[i];
-    for (int i = k; i < n; ++i) wv[i] = p[i] - K * v[i];
-    for (int i = k; i < n; ++i)
-      for (int j = k; j < n; ++j) a(i, j) -= v[i] * wv[j] + wv[i] * v[j];
-    // Q <- Q H
-    for (int i = 0; i < n; ++i) {
-      double s = 0.0;
-      for (int j = k + 1; j < n; ++j) s += V[(size_t)i * n + j] * v[j];
-      for (int j = k + 1; j < n; ++j) V[(size_t)i * n + j] -= 2.0 * s * v[j];
-    }
+  for (int c = 0; c < n; ++c) {
+    w[c] = a(order[c], order[c]);
+    for (int k = 0; k < n; ++k) V[(size_t)k * n + c] = Vw[(size_t)k * n + order[c]];
   }
-  std::vector<double> d(n), e(n, 0.0);
-  for (int i = 0; i < n; ++i) d[i] = a(i, i);
-  for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
-  // QL with implicit shifts: deflate from the top, e[i] couples d[i] and d[i+1]
-  for (int l = 0; l < n; ++l) {
-    for (int iter = 0; iter < 60; ++iter) {
-      int m = l;
-      for (; m + 1 < n; ++m) {
-        const double dd = std::fabs(d[m]) + std::fabs(d[m + 1]);
-        if (std::fabs(e[m]) <= 1e-15 * dd) break;
-      }
-      if (m == l) break;
-      // Wilkinson shift from the leading 2 x 2 block
-      double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-      double r = std::hypot(g, 1.0);
-      g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
-      double s = 1.0, c = 1.0, pp = 0.0;
-      int i = m - 1;
-      for (; i >= l; --i) {
-        double f = s * e[i];
-        const double b = c * e[i];
-        r = std::hypot(f, g);
-        e[i + 1] = r;
-        if (r == 0.0) {
-          d[i + 1] -= pp;
-          e[m] = 0.0;
-          break;
-        }
-        s = f / r;
-        c = g / r;
-        g = d[i + 1] - pp;
-        r = (d[i] - g) * s + 2.0 * c * b;
-        pp = s * r;
-        d[i + 1] = g + pp;
-        g = c * r - b;
-        for (int k = 0; k < n; ++k) {  // rotate eigenvector columns i, i+1
-          f = V[(size_t)k * n + i + 1];
-          V[(size_t)k * n + i + 1] = s * V[(size_t)k * n + i] + c * f;
-          V[(size_t)k * n + i] = c * V[(size_t)k * n + i] - s * f;
-        }
-      }
-      if (r == 0.0 && i >= l) continue;
-      d[l] -= pp;
-      e[l] = g;
-      e[m] = 0.0;
-    }
-  }
-  w = d;
 }
 
 }  // namespace
@@ -521,57 +487,161 @@ void dj_mlp_destroy(dj_mlp* m) {
   delete m;
 }
 
+namespace {
+
+// standard normal numbers from a counter (splitmix64 of seed + index, two
+// uniforms, Box-Muller); the same on every host
+double normal_at(unsigned long long seed, unsigned long long i) {
+  auto mix = [](unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  const double u1 = ((mix(seed + 2 * i) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((mix(seed + 2 * i + 1) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+// Device scratch of one POD fit, freed on every exit path.
+struct PodWork {
+  std::vector<float*> bufs;
+  float* get(size_t n) {
+    float* p = nullptr;
+    if (cudaMalloc(&p, n * sizeof(float)) != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    return p;
+  }
+  ~PodWork() {
+    for (float* p : bufs) cudaFree(p);
+  }
+};
+
+// Orthonormalise the k columns of Z (n x k, row-major, leading dimension ld) in
+// place by the eigen-decomposition of its Gram matrix G = Z^T Z = V L V^T:
+// Z <- Z V_k L_k^-1/2 over the eigenvalues above 1e-10 of the largest (columns
+// that FP32 rounding cannot tell apart from a combination of the others are
+// dropped).  k is updated to the number of columns kept.  tmp: n x ld floats.
+cudaError_t orthonormalise(float* Z, long long n, int ld, int& k, float* tmp, float* d_small, cudaStream_t s) {
+  cudaError_t e = gemm<double>(k, k, (int)std::min<long long>(n, 0x7fffffff), 1.f, Z, 1, ld, Z, ld, 1, 0.f,
+                               d_small, k, s);
+  std::vector<float> hG((size_t)k * k);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hG.data(), d_small, hG.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  std::vector<double> G((size_t)k * k), w, V;
+  for (int i = 0; i < k; ++i)
+    for (int j = 0; j < k; ++j) G[(size_t)i * k + j] = 0.5 * ((double)hG[(size_t)i * k + j] + hG[(size_t)j * k + i]);
+  jacobi_eigen(G, k, w, V);
+  int kept = 0;
+  while (kept < k && w[kept] > 1e-10 * w[0] && w[kept] > 0.0) ++kept;
+  std::vector<float> T((size_t)k * ld, 0.f);  // k x kept, leading dimension ld
+  for (int i = 0; i < k; ++i)
+    for (int c = 0; c < kept; ++c) T[(size_t)i * ld + c] = (float)(V[(size_t)i * k + c] / std::sqrt(w[c]));
+  e = cudaMemcpyAsync(d_small, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && kept > 0)
+    e = gemm<double>((int)n, kept, k, 1.f, Z, ld, 1, d_small, ld, 1, 0.f, tmp, ld, s);
+  if (e == cudaSuccess && kept > 0)
+    e = cudaMemcpyAsync(Z, tmp, (size_t)n * ld * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // T is host memory of this frame
+  k = kept;
+  return e;
+}
+
+}  // namespace
+
+// POD by a randomised range finder with subspace iteration and a Rayleigh-Ritz
+// step (no Gram matrix of the snapshots is formed):
+//   Yc = Y - mean 1^T (rows x cols), Omega (cols x l) seeded normal, l = r + p
+//   Z = orth(Yc Omega); q times: W = orth(Yc^T Z), Z = orth(Yc W)
+//   B^T = Yc^T Z, B B^T = U S^2 U^T (l x l, Jacobi on the host)
+//   modes = Z U_r, sigma = S_r
+// With l >= cols the range of Z is that of Yc and the result is the exact
+// truncated SVD; otherwise q = 3 power steps (subspace iteration) with
+// oversampling p = max(32, r / 2) resolve the leading r modes.
 dj_status dj_pod_fit(const float* d_Y, long long rows, int cols, int r, float* d_mean, float* d_modes,
                      double* sigma_out, void* stream) {
-  dj_mlp* m = nullptr;  // for MCK
-  if (!d_Y || !d_mean || !d_modes || rows <= 0 || cols <= 0 || r <= 0 || r > cols || cols > 4096)
+  if (!d_Y || !d_mean || !d_modes || rows <= 0 || cols <= 0 || r <= 0 || r > cols || cols > 65536 || r > 1024)
     return DJ_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  float *Yc = nullptr, *G = nullptr, *Vr = nullptr;
-  MCK(cudaMalloc(&Yc, (size_t)rows * cols * sizeof(float)));
-  cudaError_t e = cudaMalloc(&G, (size_t)cols * cols * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&Vr, (size_t)cols * r * sizeof(float));
-  auto cleanup = [&]() {
-    if (Yc) cudaFree(Yc);
-    if (G) cudaFree(G);
-    if (Vr) cudaFree(Vr);
-  };
-  if (e == cudaSuccess) {
-    rowmean_kernel<<<blocks(rows, 256), 256, 0, s>>>(d_Y, rows, cols, d_mean);
-    center_kernel<<<blocks(rows * (long long)cols, 256), 256, 0, s>>>(d_Y, d_mean, rows, cols, Yc);
-    e = cudaGetLastError();
+  const int p_over = std::max(32, r / 2);
+  const int l = std::min(cols, r + p_over);
+  const int q_steps = l >= cols ? 0 : 3;
+  const int Kr = (int)std::min<long long>(rows, 0x7fffffff);
+  PodWork wk;
+  float* Yc = wk.get((size_t)rows * cols);
+  float* Z = wk.get((size_t)rows * l);
+  float* Zt = wk.get((size_t)rows * l);
+  float* W = wk.get((size_t)cols * l);
+  float* Wt = wk.get((size_t)cols * l);
+  float* sm = wk.get((size_t)l * l);
+  if (!Yc || !Z || !Zt || !W || !Wt || !sm) return DJ_ERR_OOM;
+  rowmean_kernel<<<blocks(rows, 256), 256, 0, s>>>(d_Y, rows, cols, d_mean);
+  center_kernel<<<blocks(rows * (long long)cols, 256), 256, 0, s>>>(d_Y, d_mean, rows, cols, Yc);
+  cudaError_t e = cudaGetLastError();
+  // Omega: cols x l, row-major (staged through W)
+  {
+    std::vector<float> om((size_t)cols * l);
+    for (size_t i = 0; i < om.size(); ++i) om[i] = (float)normal_at(0x5EEDull + (unsigned long long)cols, i);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(W, om.data(), om.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
-  // Gram G = Yc^T Yc (cols x cols), Yc column-major: Yc(k, j) = Yc[k + j * rows]
-  if (e == cudaSuccess) e = gemm<double>(cols, cols, (int)std::min<long long>(rows, 0x7fffffff), 1.f, Yc, rows, 1,
-                                         Yc, 1, rows, 0.f, G, cols, s);
-  std::vector<float> hG((size_t)cols * cols);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+  // Yc(i, c) = Yc[i + c rows]: as A(i, k) with sar = 1, sac = rows; as A^T with sar = rows, sac = 1
+  int k = l;
+  if (e == cudaSuccess) e = gemm<double>((int)rows, k, cols, 1.f, Yc, 1, rows, W, l, 1, 0.f, Z, l, s);
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) e = orthonormalise(Z, rows, l, k, Zt, sm, s);
+  for (int it = 0; it < q_steps && e == cudaSuccess && k > 0; ++it) {
+    e = gemm<double>(cols, k, Kr, 1.f, Yc, rows, 1, Z, l, 1, 0.f, W, l, s);
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) e = orthonormalise(W, cols, l, k, Wt, sm, s);
+    if (e == cudaSuccess && k > 0) e = gemm<double>((int)rows, k, cols, 1.f, Yc, 1, rows, W, l, 1, 0.f, Z, l, s);
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) e = orthonormalise(Z, rows, l, k, Zt, sm, s);
+  }
+  // Rayleigh-Ritz: B^T = Yc^T Z (cols x k), C = B B^T (k x k)
+  std::vector<double> wv, U;
+  if (e == cudaSuccess && k > 0) e = gemm<double>(cols, k, Kr, 1.f, Yc, rows, 1, Z, l, 1, 0.f, W, l, s);
+  if (e == cudaSuccess && k > 0) e = gemm<double>(k, k, cols, 1.f, W, 1, l, W, l, 1, 0.f, sm, k, s);
+  if (e == cudaSuccess && k > 0) {
+    std::vector<float> hC((size_t)k * k);
+    e = cudaMemcpyAsync(hC.data(), sm, hC.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::vector<double> C((size_t)k * k);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) C[(size_t)i * k + j] = 0.5 * ((double)hC[(size_t)i * k + j] + hC[(size_t)j * k + i]);
+    if (e == cudaSuccess) jacobi_eigen(C, k, wv, U);
+  }
+  if (e != cudaSuccess) return DJ_ERR_CUDA;
+  // modes = Z U_r (rows x r, row-major); columns beyond the rank found are zero
+  std::vector<float> hU((size_t)std::max(k, 1) * r, 0.f);
+  for (int c = 0; c < r; ++c) {
+    const double lam = c < k ? wv[c] : 0.0;
+    if (sigma_out) sigma_out[c] = lam > 0 ? std::sqrt(lam) : 0.0;
+    if (c < k && lam > 0)
+      for (int i = 0; i < k; ++i) hU[(size_t)i * r + c] = (float)U[(size_t)i * k + c];
+  }
+  if (k > 0) {
+    e = cudaMemcpyAsync(sm, hU.data(), (size_t)k * r * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = gemm<double>((int)rows, r, k, 1.f, Z, l, 1, sm, r, 1, 0.f, d_modes, r, s);
+  } else {
+    e = cudaMemsetAsync(d_modes, 0, (size_t)rows * r * sizeof(float), s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    cleanup();
-    return DJ_ERR_CUDA;
-  }
-  std::vector<double> a(hG.begin(), hG.end()), w, V;
-  for (int i = 0; i < cols; ++i)
-    for (int j = 0; j < i; ++j) a[(size_t)i * cols + j] = a[(size_t)j * cols + i] = 0.5 * (a[(size_t)i * cols + j] + a[(size_t)j * cols + i]);
-  symmetric_eigen(a, cols, w, V);
-  std::vector<int> order(cols);
-  for (int i = 0; i < cols; ++i) order[i] = i;
-  std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
-  // modes = Yc V_r diag(lambda^-1/2): V_r scaled on the host (cols x r, row-major)
-  std::vector<float> hV((size_t)cols * r, 0.f);
-  for (int q = 0; q < r; ++q) {
-    const double lam = w[order[q]];
-    const double sc = lam > 1e-30 ? 1.0 / std::sqrt(lam) : 0.0;
-    if (sigma_out) sigma_out[q] = lam > 0 ? std::sqrt(lam) : 0.0;
-    for (int k = 0; k < cols; ++k) hV[(size_t)k * r + q] = (float)(V[(size_t)k * cols + order[q]] * sc);
-  }
-  e = cudaMemcpyAsync(Vr, hV.data(), hV.size() * sizeof(float), cudaMemcpyHostToDevice, s);
-  // d_modes row-major rows x r
-  if (e == cudaSuccess) e = gemm<float>((int)rows, r, cols, 1.f, Yc, 1, rows, Vr, r, 1, 0.f, d_modes, r, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cleanup();
   return e == cudaSuccess ? DJ_OK : DJ_ERR_CUDA;
+}
+
+// Host-only symmetric eigen-decomposition (the cyclic Jacobi method the POD uses).
+dj_status dj_symmetric_eigen(const double* A, int n, double* w, double* V) {
+  if (!A || !w || n <= 0 || n > 4096) return DJ_ERR_INVALID_ARG;
+  std::vector<double> a(A, A + (size_t)n * n), wv, Vv;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double m = 0.5 * (a[(size_t)i * n + j] + a[(size_t)j * n + i]);
+      if (!std::isfinite(m)) return DJ_ERR_INVALID_ARG;
+      a[(size_t)i * n + j] = a[(size_t)j * n + i] = m;
+    }
+  jacobi_eigen(a, n, wv, Vv);
+  std::copy(wv.begin(), wv.end(), w);
+  if (V) std::copy(Vv.begin(), Vv.end(), V);
+  return DJ_OK;
 }
 
 dj_status dj_pod_project(const float* d_modes, const float* d_mean, long long rows, int r, const float* d_X,

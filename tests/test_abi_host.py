@@ -97,3 +97,45 @@ def test_state_size_is_known_before_device_work(lib):
         assert info.n_nodes == X.shape[0] and info.n_elems == conn.shape[0] and info.elem_type == 8
     finally:
         binding.dj_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["random", "clustered", "degenerate"])
+def test_symmetric_eigen_matches_numpy(lib, kind):
+    """The host eigensolver behind the POD (cyclic Jacobi, no device work)
+    against LAPACK's through numpy: eigenvalues to 1e-12 of the largest,
+    orthonormal eigenvectors that satisfy A v = w v, and, inside a cluster of
+    nearly equal eigenvalues, the same invariant subspace."""
+    rng = np.random.default_rng({"random": 1, "clustered": 2, "degenerate": 3}[kind])
+    n = 60
+    Q = np.linalg.qr(rng.normal(size=(n, n)))[0]
+    if kind == "random":
+        lam = rng.uniform(0.1, 10.0, size=n)
+    elif kind == "clustered":  # SPD, three tight clusters and a spread tail
+        lam = np.concatenate([5.0 + 1e-9 * rng.normal(size=10), 2.0 + 1e-7 * rng.normal(size=15),
+                              1.0 + 1e-12 * rng.normal(size=5), rng.uniform(1e-6, 0.5, size=30)])
+    else:  # exactly repeated eigenvalues and a null space
+        lam = np.concatenate([np.full(20, 3.0), np.full(20, 1.0), np.zeros(20)])
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    w, V = binding.dj_symmetric_eigen(A)
+    w_ref, V_ref = np.linalg.eigh(A)
+    assert np.all(np.diff(w) <= 0)
+    assert np.abs(w - w_ref[::-1]).max() < 1e-12 * np.abs(w_ref).max()
+    assert np.abs(V.T @ V - np.eye(n)).max() < 1e-12
+    assert np.abs(A @ V - V * w).max() < 1e-12 * np.abs(w_ref).max()
+    # clusters: projectors onto the eigenvectors of each group agree
+    for lo, hi in [(4.0, 6.0), (1.5, 2.5), (0.9, 1.1), (2.9, 3.1)]:
+        sel = (w > lo) & (w < hi)
+        sel_ref = (w_ref > lo) & (w_ref < hi)
+        assert sel.sum() == sel_ref.sum()
+        if sel.any():
+            P = V[:, sel] @ V[:, sel].T
+            P_ref = V_ref[:, sel_ref] @ V_ref[:, sel_ref].T
+            assert np.abs(P - P_ref).max() < 1e-6
+
+
+def test_symmetric_eigen_rejects_bad_input(lib):
+    A = np.eye(3)
+    A[0, 1] = np.nan
+    with pytest.raises(binding.DJError):
+        binding.dj_symmetric_eigen(A)
