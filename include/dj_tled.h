@@ -533,6 +533,156 @@ dj_status dj_quad_features(const float* d_X, int S, int ld, int n, float* d_F, v
 dj_status dj_linear_apply(const float* d_W, int n_out, int n_in, const float* d_X, int S, float alpha, float beta,
                           float* d_Y, void* stream);
 
+/* BF16 variant of an MLP (no counterpart in the paper): precision 1 rounds
+ * the weights and the activations entering every product to bfloat16 (8-bit
+ * significand) and accumulates in FP32; the master weights, Adam moments,
+ * biases, tanh and loss stay FP32.  precision 0 (default) is plain FP32.
+ * Errors: DJ_ERR_INVALID_ARG. */
+dj_status dj_mlp_set_precision(dj_mlp* mlp, int precision);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start for dynamic relaxation (no counterpart in the paper,
+ * which names learning methods only as future work, Sec. 8; the relaxation
+ * it serves is that of Sec. 6).  A dj_ws maps the prescribed values t of a
+ * load case (n_bc floats, in the order of dj_mesh_set_bcs) to an initial
+ * nodal field:
+ *   c  = Phi_in^T (t - mean_in)       leading n_in POD coefficients of the
+ *                                     targets, scaled to unit spread over the
+ *                                     training loads (modes below 1e-4 of the
+ *                                     largest singular value are switched off)
+ *   q  = W f(c) [+ MLP(x)]            f(c): the kept coefficients (first order)
+ *                                     or those and their pairwise products
+ *                                     (second order); W by ridge least squares;
+ *                                     the MLP (input x = c or f(c)) is trained
+ *                                     on what W leaves
+ *   U0 = mean_out + Phi_out q         leading n_out POD modes of the relaxed
+ *                                     fields, scaled by their spread
+ * A seeded share of the loads is held out: it chooses the polynomial order
+ * and (mlp = -1) whether the MLP is kept.  Training uses the library's
+ * kernels only (POD, features, normal equations, MLP forward / backward /
+ * Adam); the held-out losses are computed on the host from at most a few
+ * hundred rows.
+ * ---------------------------------------------------------------------- */
+typedef struct dj_ws dj_ws;
+
+enum { DJ_WS_MLP_ON_COEFFS = 0, DJ_WS_MLP_ON_FEATURES = 1 };    /* MLP input */
+enum { DJ_WS_PARTS_FITTED = 0, DJ_WS_PARTS_POLYNOMIAL = 1, DJ_WS_PARTS_MLP = 2 };  /* prediction parts (bits) */
+enum { DJ_WS_ARM_REST = 0, DJ_WS_ARM_POLYNOMIAL = 1, DJ_WS_ARM_FITTED = 2 };  /* dj_ws_relax_to_tol */
+
+/* Warm-start options (dj_ws_params_default fills the defaults):
+ *   n_in, n_out     POD modes of targets / relaxed fields (64, 128; <= 256 / 1024)
+ *   hidden[4]       MLP hidden widths, 0 ends the list (256, 256, 256, 0); tanh
+ *   epochs, batch   MLP training: passes over the training loads, minibatch rows
+ *                   (1500, 128); one seeded permutation of the rows per epoch
+ *   lr, lr_final    Adam step, decayed exponentially over the iterations (1e-3, 1e-5)
+ *   quadratic       1: the second-order polynomial part may be chosen (1)
+ *   mlp             -1: train the MLP and keep it only if it lowers the held-out
+ *                   loss (default); 1: train and keep it; 0: no MLP
+ *   mlp_input       DJ_WS_MLP_ON_COEFFS (default) or DJ_WS_MLP_ON_FEATURES
+ *   mlp_bf16        1: BF16 products in the MLP (dj_mlp_set_precision)
+ *   holdout         share of the loads held out (0.1; none below 20 loads)
+ *   seed            split, minibatch and MLP initialisation seed
+ *   adaptive        1: relaxations use dj_relax_adaptive (default), 0: dj_relax_to_tol */
+typedef struct {
+  int n_in, n_out;
+  int hidden[4];
+  int epochs, batch;
+  double lr, lr_final;
+  int quadratic;
+  int mlp;
+  int mlp_input;
+  int mlp_bf16;
+  double holdout;
+  unsigned long long seed;
+  int adaptive;
+} dj_ws_params;
+
+/* What the fit found (held-out losses: the weighted mean squared error of the
+ * output coefficients, weights = variance shares of the output modes; NaN
+ * when not computed). */
+typedef struct {
+  int n_loads, n_kept;           /* loads given / relaxed successfully */
+  int n_train, n_holdout;
+  int n_in, n_out, n_in_kept, n_out_kept, n_features, n_bc;
+  long long n_dof;
+  int quadratic_used, mlp_used;
+  long long mlp_params, mlp_iterations;
+  double val_loss_first_order, val_loss_second_order;
+  double val_loss_polynomial;     /* of the polynomial part chosen */
+  double val_loss_polynomial_mlp; /* polynomial part + MLP */
+  double final_train_loss;        /* MLP loss on the last minibatch */
+  double mean_training_steps;     /* dj_ws_train: mean relaxation steps of the kept loads */
+  double data_seconds, fit_seconds, fit_seconds_polynomial;
+} dj_ws_info;
+
+/* Outcome of dj_ws_relax_to_tol. */
+typedef struct {
+  long long steps;                 /* relaxation steps in total (incl. a failed warm attempt) */
+  long long steps_warm_attempt;    /* steps of a warm relaxation that failed, else 0 */
+  double residual;                 /* residual reached */
+  int started_warm;                /* 1: the answer was relaxed from the prediction */
+  int fallback;                    /* 1: the prediction was rejected or its relaxation failed */
+  double residual_predicted;       /* residual of the predicted field (inf if inverted) */
+  double residual_prescribed_only; /* residual of the field with only the prescribed values */
+  double predict_seconds;          /* wall time up to the start of the relaxation */
+  double seconds;                  /* wall time of the whole call */
+} dj_ws_result;
+
+void dj_ws_params_default(dj_ws_params* p);
+
+/* Train a warm start on `mesh` (precomputed, with its prescribed DOFs set):
+ * every load case (targets: host, n_loads x n_bc doubles, row by row, each in
+ * the order of dj_mesh_set_bcs) is relaxed from rest to `tol` with the mesh's
+ * parameters (dj_relax_adaptive or dj_relax_to_tol, see params.adaptive);
+ * cases that fail (an element inverts, no convergence in max_steps) are
+ * dropped; the method's own relaxed fields are the training data of the fit
+ * described above.  The mesh's targets and state are left at the last case.
+ * Synchronous; allocates n_loads x (3 n_nodes + n_bc) floats of device memory
+ * for the training data (freed before return) and the model's own buffers.
+ * Errors: DJ_ERR_INVALID_ARG (arguments, options), DJ_ERR_NOT_CONVERGED (fewer
+ * than two cases relaxed), DJ_ERR_OOM, DJ_ERR_CUDA; *out stays NULL. */
+dj_status dj_ws_train(dj_mesh* mesh, const double* targets, int n_loads, double tol, long long max_steps,
+                      const dj_ws_params* params, dj_ws** out, void* stream);
+
+/* The same fit from caller-supplied training data: d_targets (device,
+ * n_loads x n_bc floats) and d_fields (device, n_loads x 3 n_nodes floats, each
+ * a relaxed field in caller node order), bc_dof (host, n_bc flat DOF indices
+ * 3 node + component, the order of the targets).  Synchronous. */
+dj_status dj_ws_fit(const long long* bc_dof, int n_bc, long long n_nodes, const float* d_targets,
+                    const float* d_fields, int n_loads, const dj_ws_params* params, dj_ws** out, void* stream);
+
+/* Predicted field for targets (host, n_bc doubles) into d_field (device,
+ * 3 n_nodes floats, caller order): parts = DJ_WS_PARTS_FITTED (what the fit
+ * kept), DJ_WS_PARTS_POLYNOMIAL, DJ_WS_PARTS_MLP or both bits.  Synchronous. */
+dj_status dj_ws_predict(dj_ws* ws, const double* targets, int parts, float* d_field, void* stream);
+
+/* Relax `mesh` for the load case `targets` (host, n_bc doubles) to `tol`:
+ *   DJ_WS_ARM_REST        from rest (the plain method; the reference arm);
+ *   DJ_WS_ARM_POLYNOMIAL  from the polynomial part's prediction;
+ *   DJ_WS_ARM_FITTED      from the fitted map (polynomial part + MLP if kept).
+ * A prediction is used only if it inverts no element and its residual is below
+ * that of the field holding the prescribed values alone; then the state is set
+ * to it with the step counter at the end of the ramp.  Otherwise, or if the
+ * warm relaxation fails, the case is relaxed from rest (fallback).  The mesh
+ * must be the one the warm start was trained for (same nodes and prescribed
+ * DOFs).  res (optional) receives the outcome.  Synchronous.
+ * Errors: DJ_ERR_INVALID_ARG, the relaxation's status (e.g.
+ * DJ_ERR_NOT_CONVERGED), DJ_ERR_CUDA. */
+dj_status dj_ws_relax_to_tol(dj_mesh* mesh, dj_ws* ws, const double* targets, int arm, double tol,
+                             long long max_steps, dj_ws_result* res, void* stream);
+
+/* Serialised model (bases, polynomial part, MLP weights, options, info):
+ * dj_ws_save writes at most `capacity` bytes to buf and the size to *bytes
+ * (buf NULL: the size only; a smaller capacity: DJ_ERR_INVALID_ARG);
+ * dj_ws_load builds a dj_ws from such a buffer (host memory) on the current
+ * device.  Errors: DJ_ERR_INVALID_ARG (size, format), DJ_ERR_OOM, DJ_ERR_CUDA. */
+dj_status dj_ws_save(const dj_ws* ws, void* buf, size_t capacity, size_t* bytes);
+dj_status dj_ws_load(const void* buf, size_t bytes, dj_ws** out);
+
+dj_status dj_ws_get_info(const dj_ws* ws, dj_ws_info* info);
+const char* dj_ws_last_error(const dj_ws* ws);
+void dj_ws_destroy(dj_ws* ws);
+
 #ifdef __cplusplus
 }
 #endif

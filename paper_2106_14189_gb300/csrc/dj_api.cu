@@ -444,6 +444,13 @@ dj_status capture(dj_mesh* m, cudaGraphExec_t* out, F body) {
 
 }  // namespace
 
+namespace dj {
+// accessors for the warm-start layer (warmstart.cu)
+const std::vector<long long>& mesh_bc_dofs(const dj_mesh* m) { return m->bc_dof; }
+long long mesh_ramp_steps(const dj_mesh* m) { return m->params.ramp_steps; }
+long long mesh_n_nodes(const dj_mesh* m) { return m->N; }
+}  // namespace dj
+
 extern "C" {
 
 void dj_params_default(dj_params* p) {

@@ -15,6 +15,7 @@
 //
 // The dense products here take milliseconds (batch <= 1024, widths <= 256);
 // they are SIMT FP32, not tensor-core kernels.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,7 +39,7 @@ template <typename ACC>
 __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, float alpha, const float* __restrict__ A,
                                                    long long sar, long long sac, const float* __restrict__ B,
                                                    long long sbr, long long sbc, float beta, float* __restrict__ C,
-                                                   long long ldc, const float* __restrict__ subA) {
+                                                   long long ldc, const float* __restrict__ subA, int bf16) {
   __shared__ float As[TK][TM + 4];
   __shared__ float Bs[TK][TN + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -50,12 +51,14 @@ __global__ void __launch_bounds__(256) gemm_kernel(int M, int N, int K, float al
     for (int q = threadIdx.x; q < TM * TK; q += 256) {
       const int ii = q / TK, kk = q % TK;
       const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < M && k < K) ? A[i * sar + k * sac] - (subA ? subA[k] : 0.f) : 0.f;
+      const float v = (i < M && k < K) ? A[i * sar + k * sac] - (subA ? subA[k] : 0.f) : 0.f;
+      As[kk][ii] = bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
     }
     for (int q = threadIdx.x; q < TN * TK; q += 256) {
       const int jj = q % TN, kk = q / TN;
       const int j = j0 + jj, k = k0 + kk;
-      Bs[kk][jj] = (j < N && k < K) ? B[k * sbr + j * sbc] : 0.f;
+      const float v = (j < N && k < K) ? B[k * sbr + j * sbc] : 0.f;
+      Bs[kk][jj] = bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
     }
     __syncthreads();
     float part[4][4];
@@ -209,10 +212,10 @@ __global__ void add_mean_kernel(float* X, const float* __restrict__ mean, long l
 template <typename ACC>
 cudaError_t gemm(int M, int N, int K, float alpha, const float* A, long long sar, long long sac, const float* B,
                  long long sbr, long long sbc, float beta, float* C, long long ldc, cudaStream_t s,
-                 const float* subA = nullptr) {
+                 const float* subA = nullptr, int bf16 = 0) {
   if (M <= 0 || N <= 0) return cudaSuccess;
   dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
-  gemm_kernel<ACC><<<grid, 256, 0, s>>>(M, N, K, alpha, A, sar, sac, B, sbr, sbc, beta, C, ldc, subA);
+  gemm_kernel<ACC><<<grid, 256, 0, s>>>(M, N, K, alpha, A, sar, sac, B, sbr, sbc, beta, C, ldc, subA, bf16);
   return cudaGetLastError();
 }
 
@@ -294,6 +297,7 @@ struct dj_mlp {
   double* d_loss = nullptr;
   int batch_cap = 0;
   long long t = 0;  // Adam step
+  int bf16 = 0;     // 1: products with bfloat16-rounded operands, FP32 accumulation
   std::string last_error;
 };
 
@@ -337,7 +341,7 @@ dj_status mlp_forward(dj_mlp* m, const float* X, int batch, cudaStream_t s) {
     const int in = m->widths[l], out = m->widths[l + 1];
     const float* W = m->d_p + m->w_off[l];
     // Z = A_l W^T : (batch x in)(in x out), W row-major out x in -> B(k, j) = W[j * in + k]
-    MCK(gemm<float>(batch, out, in, 1.f, m->act[l], in, 1, W, 1, in, 0.f, m->act[l + 1], out, s));
+    MCK(gemm<float>(batch, out, in, 1.f, m->act[l], in, 1, W, 1, in, 0.f, m->act[l + 1], out, s, nullptr, m->bf16));
     const long long n = (long long)batch * out;
     bias_act_kernel<<<blocks(n, 256), 256, 0, s>>>(m->act[l + 1], m->d_p + m->b_off[l], batch, out,
                                                    l + 1 < m->L ? 1 : 0);
@@ -443,12 +447,13 @@ dj_status dj_mlp_loss_grad(dj_mlp* m, const float* d_X, const float* d_T, const 
     float* gW = m->d_g + m->w_off[l];
     float* gb = m->d_g + m->b_off[l];
     // dW = dZ^T A_l : (out x batch)(batch x in)
-    MCK(gemm<float>(out, in, batch, 1.f, dcur, 1, out, m->act[l], in, 1, 0.f, gW, in, s));
+    MCK(gemm<float>(out, in, batch, 1.f, dcur, 1, out, m->act[l], in, 1, 0.f, gW, in, s, nullptr, m->bf16));
     colsum_kernel<<<blocks(out, 128), 128, 0, s>>>(dcur, batch, out, gb);
     MCK(cudaGetLastError());
     if (l > 0) {
       // dA_l = dZ W : (batch x out)(out x in), then through tanh
-      MCK(gemm<float>(batch, in, out, 1.f, dcur, out, 1, m->d_p + m->w_off[l], in, 1, 0.f, dnext, in, s));
+      MCK(gemm<float>(batch, in, out, 1.f, dcur, out, 1, m->d_p + m->w_off[l], in, 1, 0.f, dnext, in, s, nullptr,
+                      m->bf16));
       const long long n = (long long)batch * in;
       act_bwd_kernel<<<blocks(n, 256), 256, 0, s>>>(dnext, m->act[l], n);
       MCK(cudaGetLastError());
@@ -475,6 +480,12 @@ dj_status dj_mlp_adam_step(dj_mlp* m, float lr, float beta1, float beta2, float 
   return DJ_OK;
 }
 
+dj_status dj_mlp_set_precision(dj_mlp* m, int precision) {
+  if (!m || (precision != 0 && precision != 1)) return DJ_ERR_INVALID_ARG;
+  m->bf16 = precision;
+  return DJ_OK;
+}
+
 const char* dj_mlp_last_error(const dj_mlp* m) { return m ? m->last_error.c_str() : "null mlp"; }
 
 void dj_mlp_destroy(dj_mlp* m) {
@@ -486,6 +497,8 @@ void dj_mlp_destroy(dj_mlp* m) {
     if (p) cudaFree(p);
   delete m;
 }
+
+}  // extern "C"
 
 namespace {
 
@@ -549,6 +562,8 @@ cudaError_t orthonormalise(float* Z, long long n, int ld, int& k, float* tmp, fl
 }
 
 }  // namespace
+
+extern "C" {
 
 // POD by a randomised range finder with subspace iteration and a Rayleigh-Ritz
 // step (no Gram matrix of the snapshots is formed):
