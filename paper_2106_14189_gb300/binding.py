@@ -42,8 +42,14 @@ EXPORTS = [
     "dj_mlp_last_error", "dj_mlp_destroy", "dj_pod_fit", "dj_pod_project", "dj_pod_expand",
     "dj_residual_norms_static", "dj_set_step", "dj_batch_set_step", "dj_autotune",
     "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply", "dj_profile_kernels",
-    "dj_autotune_cold", "dj_quad_features", "dj_symmetric_eigen",
+    "dj_autotune_cold", "dj_quad_features", "dj_symmetric_eigen", "dj_mlp_set_precision",
+    "dj_ws_params_default", "dj_ws_train", "dj_ws_fit", "dj_ws_predict", "dj_ws_relax_to_tol",
+    "dj_ws_save", "dj_ws_load", "dj_ws_get_info", "dj_ws_last_error", "dj_ws_destroy",
 ]
+
+DJ_WS_MLP_ON_COEFFS, DJ_WS_MLP_ON_FEATURES = 0, 1
+DJ_WS_PARTS_FITTED, DJ_WS_PARTS_POLYNOMIAL, DJ_WS_PARTS_MLP = 0, 1, 2
+DJ_WS_ARM_REST, DJ_WS_ARM_POLYNOMIAL, DJ_WS_ARM_FITTED = 0, 1, 2
 
 
 class dj_params(C.Structure):
@@ -74,6 +80,41 @@ class dj_info(C.Structure):
                 ("node_bytes_per_node", C.c_longlong), ("n_parts", C.c_longlong),
                 ("assembly", C.c_int), ("tile_size", C.c_int), ("n_consts", C.c_int),
                 ("precision", C.c_int), ("grid", C.c_int), ("n_tiles", C.c_longlong)]
+
+
+class dj_ws_params(C.Structure):
+    """Options of the learned warm start (include/dj_tled.h)."""
+    _fields_ = [("n_in", C.c_int), ("n_out", C.c_int), ("hidden", C.c_int * 4), ("epochs", C.c_int),
+                ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double), ("quadratic", C.c_int),
+                ("mlp", C.c_int), ("mlp_input", C.c_int), ("mlp_bf16", C.c_int), ("holdout", C.c_double),
+                ("seed", C.c_ulonglong), ("adaptive", C.c_int)]
+
+
+class dj_ws_info(C.Structure):
+    _fields_ = [("n_loads", C.c_int), ("n_kept", C.c_int), ("n_train", C.c_int), ("n_holdout", C.c_int),
+                ("n_in", C.c_int), ("n_out", C.c_int), ("n_in_kept", C.c_int), ("n_out_kept", C.c_int),
+                ("n_features", C.c_int), ("n_bc", C.c_int), ("n_dof", C.c_longlong),
+                ("quadratic_used", C.c_int), ("mlp_used", C.c_int), ("mlp_params", C.c_longlong),
+                ("mlp_iterations", C.c_longlong), ("val_loss_first_order", C.c_double),
+                ("val_loss_second_order", C.c_double), ("val_loss_polynomial", C.c_double),
+                ("val_loss_polynomial_mlp", C.c_double), ("final_train_loss", C.c_double),
+                ("mean_training_steps", C.c_double), ("data_seconds", C.c_double),
+                ("fit_seconds", C.c_double), ("fit_seconds_polynomial", C.c_double)]
+
+
+class dj_ws_result(C.Structure):
+    _fields_ = [("steps", C.c_longlong), ("steps_warm_attempt", C.c_longlong), ("residual", C.c_double),
+                ("started_warm", C.c_int), ("fallback", C.c_int), ("residual_predicted", C.c_double),
+                ("residual_prescribed_only", C.c_double), ("predict_seconds", C.c_double),
+                ("seconds", C.c_double)]
+
+
+def _struct_dict(st):
+    out = {}
+    for f, _ in st._fields_:
+        v = getattr(st, f)
+        out[f] = list(v) if hasattr(v, "__len__") else v
+    return out
 
 
 class DJError(RuntimeError):
@@ -165,6 +206,20 @@ def lib():
         "dj_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(dj_params), _D]),
         "dj_batch_autotune": (C.c_int, [_P, C.c_int, _P]),
         "dj_symmetric_eigen": (C.c_int, [_D, C.c_int, _D, _D]),
+        "dj_mlp_set_precision": (C.c_int, [_P, C.c_int]),
+        "dj_ws_params_default": (None, [C.POINTER(dj_ws_params)]),
+        "dj_ws_train": (C.c_int, [_P, _D, C.c_int, C.c_double, C.c_longlong, C.POINTER(dj_ws_params),
+                                  C.POINTER(_P), _P]),
+        "dj_ws_fit": (C.c_int, [_LL, C.c_int, C.c_longlong, _P, _P, C.c_int, C.POINTER(dj_ws_params),
+                                C.POINTER(_P), _P]),
+        "dj_ws_predict": (C.c_int, [_P, _D, C.c_int, _P, _P]),
+        "dj_ws_relax_to_tol": (C.c_int, [_P, _P, _D, C.c_int, C.c_double, C.c_longlong,
+                                         C.POINTER(dj_ws_result), _P]),
+        "dj_ws_save": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "dj_ws_load": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
+        "dj_ws_get_info": (C.c_int, [_P, C.POINTER(dj_ws_info)]),
+        "dj_ws_last_error": (C.c_char_p, [_P]),
+        "dj_ws_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -737,3 +792,88 @@ def dj_symmetric_eigen(A):
     V = np.empty((n, n))
     _check(lib().dj_symmetric_eigen(_dptr(A), n, _dptr(w), _dptr(V)), "dj_symmetric_eigen")
     return w, V
+
+
+def dj_mlp_set_precision(m, precision):
+    _mcheck(lib().dj_mlp_set_precision(m, int(precision)), "dj_mlp_set_precision", m)
+
+
+# ------------------------------------------------------------ warm start --
+def ws_params(**kw) -> dj_ws_params:
+    p = dj_ws_params()
+    lib().dj_ws_params_default(C.byref(p))
+    for k, v in kw.items():
+        if k == "hidden":
+            v = list(v) + [0] * (4 - len(v))
+            p.hidden = (C.c_int * 4)(*v)
+            continue
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _wcheck(st, where, ws=None):
+    if st != DJ_OK:
+        msg = lib().dj_ws_last_error(ws) if ws else b""
+        raise DJError(st, where, msg.decode() if msg else "")
+
+
+def dj_ws_train(mesh_h, targets, tol, max_steps, params=None, stream=None):
+    T = np.ascontiguousarray(targets, dtype=np.float64)
+    w = _P()
+    st = lib().dj_ws_train(mesh_h, _dptr(T), int(T.shape[0]), float(tol), int(max_steps),
+                           C.byref(params) if params is not None else None, C.byref(w), _stream(stream))
+    if st != DJ_OK:
+        raise DJError(st, "dj_ws_train", dj_last_error(mesh_h))
+    return w
+
+
+def dj_ws_fit(bc_dof, n_nodes, d_targets, d_fields, n_loads, params=None, stream=None):
+    dof = np.ascontiguousarray(bc_dof, dtype=np.int64)
+    w = _P()
+    _wcheck(lib().dj_ws_fit(dof.ctypes.data_as(_LL), int(dof.size), int(n_nodes), d_targets, d_fields,
+                            int(n_loads), C.byref(params) if params is not None else None, C.byref(w),
+                            _stream(stream)), "dj_ws_fit")
+    return w
+
+
+def dj_ws_predict(ws, targets, d_field, parts=DJ_WS_PARTS_FITTED, stream=None):
+    t = _f64(targets)
+    _wcheck(lib().dj_ws_predict(ws, _dptr(t), int(parts), d_field, _stream(stream)), "dj_ws_predict", ws)
+
+
+def dj_ws_relax_to_tol(mesh_h, ws, targets, arm, tol, max_steps, stream=None, raise_on_fail=True):
+    """Returns (status, result dict)."""
+    t = _f64(targets)
+    res = dj_ws_result()
+    st = lib().dj_ws_relax_to_tol(mesh_h, ws, _dptr(t), int(arm), float(tol), int(max_steps), C.byref(res),
+                                  _stream(stream))
+    if raise_on_fail:
+        _wcheck(st, "dj_ws_relax_to_tol", ws)
+    return st, _struct_dict(res)
+
+
+def dj_ws_save(ws) -> bytes:
+    n = C.c_size_t(0)
+    _wcheck(lib().dj_ws_save(ws, None, 0, C.byref(n)), "dj_ws_save", ws)
+    buf = C.create_string_buffer(n.value)
+    _wcheck(lib().dj_ws_save(ws, C.cast(buf, _P), n.value, C.byref(n)), "dj_ws_save", ws)
+    return buf.raw[:n.value]
+
+
+def dj_ws_load(blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    w = _P()
+    _wcheck(lib().dj_ws_load(C.cast(buf, _P), len(blob), C.byref(w)), "dj_ws_load")
+    return w
+
+
+def dj_ws_get_info(ws) -> dict:
+    info = dj_ws_info()
+    _wcheck(lib().dj_ws_get_info(ws, C.byref(info)), "dj_ws_get_info", ws)
+    return _struct_dict(info)
+
+
+def dj_ws_destroy(ws):
+    lib().dj_ws_destroy(ws)
