@@ -339,6 +339,23 @@ dj_status dj_set_displacements(dj_mesh* mesh, const double* U0);
  * memory receives one copy from a device buffer. */
 dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
 
+/* One time step with its input and output in host memory, for callers that
+ * drive the solver from the host every step (Eq. 13 with the prescribed
+ * values of Sec. 5.1 / Sec. 6): the prescribed targets of this step (host,
+ * n_bc doubles in the order of dj_mesh_set_bcs, as dj_mesh_update_bc_targets;
+ * NULL keeps the current ones), one step (as dj_step), then U^{n+1} in caller
+ * order into U_out (host, n_nodes * 3 values, doubles when out_f64 = 1, floats
+ * when out_f64 = 0; NULL skips the read-back).  Everything is enqueued on
+ * `stream` and the call synchronises once, at its end, so the caller may
+ * reuse both buffers on return.  Page-locked (cudaHostAlloc /
+ * cudaHostRegister), 8-byte aligned buffers are read and written by the
+ * library's kernels through their device mappings; other host memory goes
+ * through one copy each way.  The FP32 output holds U + low part rounded once
+ * (exactly U in the plain FP32 precision mode).
+ * Errors: as dj_step and dj_mesh_update_bc_targets; device-side flags
+ * (inverted element, non-finite value) are reported by this call. */
+dj_status dj_step_host(dj_mesh* mesh, const double* targets, void* U_out, int out_f64, void* stream);
+
 /* Current displacements into device memory, n_nodes * 3 floats in caller
  * order, enqueued on `stream`. */
 dj_status dj_get_displacements_device(dj_mesh* mesh, float* d_U_out, void* stream);

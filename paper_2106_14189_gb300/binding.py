@@ -44,7 +44,7 @@ EXPORTS = [
     "dj_batch_autotune", "dj_linear_fit", "dj_linear_apply", "dj_profile_kernels",
     "dj_autotune_cold", "dj_quad_features", "dj_symmetric_eigen", "dj_mlp_set_precision",
     "dj_ws_params_default", "dj_ws_train", "dj_ws_fit", "dj_ws_predict", "dj_ws_relax_to_tol",
-    "dj_ws_save", "dj_ws_load", "dj_ws_get_info", "dj_ws_last_error", "dj_ws_destroy",
+    "dj_ws_save", "dj_ws_load", "dj_ws_get_info", "dj_ws_last_error", "dj_ws_destroy", "dj_step_host",
 ]
 
 DJ_WS_MLP_ON_COEFFS, DJ_WS_MLP_ON_FEATURES = 0, 1
@@ -207,6 +207,7 @@ def lib():
         "dj_batch_autotune": (C.c_int, [_P, C.c_int, _P]),
         "dj_symmetric_eigen": (C.c_int, [_D, C.c_int, _D, _D]),
         "dj_mlp_set_precision": (C.c_int, [_P, C.c_int]),
+        "dj_step_host": (C.c_int, [_P, _D, _P, C.c_int, _P]),
         "dj_ws_params_default": (None, [C.POINTER(dj_ws_params)]),
         "dj_ws_train": (C.c_int, [_P, _D, C.c_int, C.c_double, C.c_longlong, C.POINTER(dj_ws_params),
                                   C.POINTER(_P), _P]),
@@ -877,3 +878,16 @@ def dj_ws_get_info(ws) -> dict:
 
 def dj_ws_destroy(ws):
     lib().dj_ws_destroy(ws)
+
+
+def dj_step_host(h, targets, U_out, stream=None):
+    """One step with host input and output (include/dj_tled.h): targets (n_bc
+    float64 or None), U_out a C-contiguous float64 or float32 array of
+    n_nodes x 3 (or None)."""
+    t = None if targets is None else _f64(targets)
+    if U_out is not None and (not U_out.flags.c_contiguous or U_out.dtype not in (np.float64, np.float32)):
+        raise ValueError("U_out must be a C-contiguous float64 or float32 array")
+    _check(lib().dj_step_host(h, _dptr(t), None if U_out is None else U_out.ctypes.data_as(_P),
+                              1 if U_out is None or U_out.dtype == np.float64 else 0, _stream(stream)),
+           "dj_step_host", h)
+    return U_out

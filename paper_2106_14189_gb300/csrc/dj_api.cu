@@ -1246,6 +1246,67 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
   return DJ_OK;
 }
 
+namespace {
+// device address of a page-locked host array (8-byte aligned), else nullptr
+void* mapped_host(const void* p) {
+  cudaPointerAttributes attr;
+  if (reinterpret_cast<uintptr_t>(p) % alignof(double) == 0 && cudaPointerGetAttributes(&attr, p) == cudaSuccess &&
+      attr.type == cudaMemoryTypeHost && attr.devicePointer)
+    return attr.devicePointer;
+  (void)cudaGetLastError();
+  return nullptr;
+}
+}  // namespace
+
+dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f64, void* stream) {
+  const Range range("dj_step_host");
+  dj_status s = need_ready(m);
+  if (s) return s;
+  if (out_f64 != 0 && out_f64 != 1) return fail(m, DJ_ERR_INVALID_ARG, "out_f64 must be 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nb = m->bc_dof.size();
+  if (target && nb) {
+    bool finite = true;
+    for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
+    if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
+    std::memcpy(m->bc_target.data(), target, nb * sizeof(double));
+    if (const void* mt = mapped_host(target)) {
+      CK(launch_bc_targets(static_cast<const double*>(mt), m->d_bc_flat, (int)nb, m->d_bct, st));
+    } else {
+      const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
+      if (!m->h_bct_pinned) {
+        CK(cudaMallocHost((void**)&m->h_bct_pinned, bytes));
+        std::memcpy(m->h_bct_pinned, m->h_bct.data(), bytes);
+      }
+      // the staging table is free: every call ends with a synchronisation
+      float* pin = reinterpret_cast<float*>(m->h_bct_pinned);
+      const int* flat = m->bc_flat_of_entry.data();
+      for (size_t k = 0; k < nb; ++k) pin[flat[k]] = (float)target[k];
+      CK(cudaMemcpyAsync(m->d_bct, m->h_bct_pinned, bytes, cudaMemcpyHostToDevice, st));
+    }
+  }
+  CK(launch_step(m, st, NODE_UPDATE));
+  if (U_out) {
+    const long long N = m->N;
+    void* direct = mapped_host(U_out);
+    const float4* lo = m->cmp ? m->d_Ulo : nullptr;
+    if (out_f64) {
+      if (!direct && !m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
+      double* dst = direct ? static_cast<double*>(direct) : m->d_out64;
+      CK(launch_to_caller_order_f64(m->d_U, lo, m->d_perm, (int)N, dst, st));
+      if (!direct) CK(cudaMemcpyAsync(U_out, m->d_out64, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
+    } else {
+      if (!direct && !m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
+      float* dst = direct ? static_cast<float*>(direct) : reinterpret_cast<float*>(m->d_out64);
+      CK(launch_to_caller_order_f32(m->d_U, lo, m->d_perm, (int)N, dst, st));
+      if (!direct) CK(cudaMemcpyAsync(U_out, m->d_out64, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  s = read_state(m, st);  // the only synchronisation of the call
+  if (s) return s;
+  return check_flags(m);
+}
+
 dj_status dj_step(dj_mesh* m, void* stream) {
   const Range range("dj_step");
   dj_status s = need_ready(m);

@@ -251,6 +251,9 @@ cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const
                                        double* out, cudaStream_t s);
 cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, int N, float* out,
                                    cudaStream_t s);
+// FP32 caller-order output (U + low part when Ulo is given), stores contiguous per warp
+cudaError_t launch_to_caller_order_f32(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
+                                       float* out, cudaStream_t s);
 // U (internal) = caller-order field (N x 3 floats); w of U and of V kept,
 // U^n - U^{n-1} = 0, low part = 0
 cudaError_t launch_from_caller_order(const float* src, const int* node_new_of_old, int N, float4* U,

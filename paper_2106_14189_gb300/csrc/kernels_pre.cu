@@ -290,6 +290,33 @@ __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f64_kernel(cons
   for (int q = threadIdx.x; q < n; q += kOrderThreads) out[3 * (size_t)i0 + q] = sv[q];
 }
 
+// FP32 displacements (high + low part in the compensated mode, rounded once)
+// in caller order, staged through shared memory like the FP64 kernel above.
+__global__ void __launch_bounds__(kOrderThreads) to_caller_order_f32_kernel(const float4* __restrict__ U,
+                                                                           const float4* __restrict__ Ulo,
+                                                                           const int* __restrict__ perm, int N,
+                                                                           float* out) {
+  __shared__ float sv[3 * kOrderThreads];
+  const int i0 = blockIdx.x * kOrderThreads;
+  const int i = i0 + threadIdx.x;  // caller node id
+  if (i < N) {
+    const int v = perm[i];
+    float4 u = U[v];
+    if (Ulo) {
+      const float4 l = Ulo[v];
+      u.x += l.x;
+      u.y += l.y;
+      u.z += l.z;
+    }
+    sv[3 * threadIdx.x] = u.x;
+    sv[3 * threadIdx.x + 1] = u.y;
+    sv[3 * threadIdx.x + 2] = u.z;
+  }
+  __syncthreads();
+  const int n = 3 * min(kOrderThreads, N - i0);
+  for (int q = threadIdx.x; q < n; q += kOrderThreads) out[3 * (size_t)i0 + q] = sv[q];
+}
+
 __global__ void from_caller_order_kernel(const float* __restrict__ src, const int* __restrict__ perm, int N,
                                          float4* U, float4* V, float4* Ulo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // caller node id
@@ -365,6 +392,13 @@ cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const
                                        double* out, cudaStream_t s) {
   const int t = kOrderThreads;
   to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_caller_order_f32(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
+                                       float* out, cudaStream_t s) {
+  const int t = kOrderThreads;
+  to_caller_order_f32_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
   return cudaGetLastError();
 }
 

@@ -161,3 +161,34 @@ def test_batch_autotune(B):
         for i, p in enumerate(probs):
             ref = dynamics.ExplicitSolver.from_problem(p).run(200)
             assert rel_linf(bt.displacements(i), ref) < DISP_TOL
+
+
+def test_benchmarked_batch_sampled_instances_match_oracle(B):
+    """The benchmark's batch itself (256 seeded instances, 10.8M elements, T4 / H8,
+    schedules chosen by dj_batch_autotune as the benchmark does): after 400
+    steps, eight seeded instances among those the oracle steps in seconds
+    (<= 20k elements) each match the FP64 oracle run on that instance alone
+    within rel-Linf 1e-4."""
+    probs = W.batch_instances(256, seed=0, n_steps=2000)
+    n_steps = 400
+    with B.Batch(probs) as bt:
+        bt.run(20)
+        bt.sync()
+        B.dj_batch_autotune(bt.b, steps=20)
+        # the autotuner restores the state it found; start the timed trajectory from rest
+        for i in range(len(probs)):
+            B.dj_batch_set_displacements(bt.b, i, np.zeros((probs[i].n_nodes, 3)))
+        B.dj_batch_set_step(bt.b, 0)
+        bt.run(n_steps)
+        bt.sync()
+        small = [i for i, p in enumerate(probs) if p.n_elems <= 20000]
+        rng = np.random.default_rng(0)
+        sample = sorted(rng.choice(small, size=8, replace=False))
+        assert {probs[i].elem_type for i in sample} == {4, 8}
+        for i in sample:
+            p = probs[i]
+            U = bt.displacements(i)
+            ref = dynamics.ExplicitSolver.from_problem(p).run(n_steps)
+            e = rel_linf(U, ref)
+            print(f"batch instance {i} (T{p.elem_type}, {p.n_elems} elements): rel-Linf {e:.2e}")
+            assert e < DISP_TOL, (i, e)

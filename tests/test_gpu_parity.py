@@ -528,3 +528,88 @@ def test_graph_programmatic_edges_bit_identical(B, assembly):
             out.append((U, m.displacements(), n))
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_full_size_brain_ellipsoid_sampled_nodes(B, prec):
+    """The 0.8M-T4 anisotropic brain-sized ellipsoid of the relaxation workload
+    (h = 1.76 mm, two materials, TI fibres, six surface patches, alpha = 130 1/s,
+    the schedule a mesh of this size gets by default) part way up its ramp: one
+    damped update (Eq. 13) at 64 sampled free nodes against the oracle, which
+    evaluates only their incident elements.  Error model of the FP32 force at a
+    node as in the cube test: 1e-4 of the largest incident element force plus
+    the volumetric term's rounding kappa 0V |0B| 8 ulp(1)."""
+    from oracle import tled
+    p = W.ellipsoid_tet4(h=1.76e-3, seed=0, patch_radius=0.025, disp_range=(0.5e-3, 2.5e-3))
+    p.alpha, p.ramp_steps = 130.0, 2557
+    p.bc_target = W.ellipsoid_load_case(p, 3)
+    with B.Mesh(p, relax_check_every=50, precision=prec) as m:
+        m.run(1200)
+        U0 = m.displacements()
+        m.step()
+        U1 = m.displacements()
+        m.step()
+        U2 = m.displacements()
+        dt = m.dt
+        info = m.info()
+    assert info.n_elems == p.n_elems and np.abs(U2).max() > 1e-4
+    free = np.ones(3 * p.n_nodes, dtype=bool)
+    free[p.bc_dof] = False
+    cand = np.nonzero(free.reshape(-1, 3).all(axis=1) & (np.abs(U2).max(axis=1) > 1e-6))[0]
+    sample = np.random.default_rng(1).choice(cand, size=64, replace=False)
+    eps = float(np.finfo(np.float32).eps)
+    ad = p.alpha * dt
+    worst = 0.0
+    for i in sample:
+        els = np.nonzero((p.conn == i).any(axis=1))[0]
+        sub = W.Problem(name="sub", elem_type=4, X=p.X, conn=p.conn[els], model=p.model[els],
+                        mu=p.mu[els], kappa=p.kappa[els], rho=p.rho[els], eta_a=p.eta_a[els],
+                        eta_b=p.eta_b[els], c01=p.c01[els], a_dir=p.a_dir[els], b_dir=p.b_dir[els],
+                        bc_dof=np.zeros(0, dtype=np.int64), bc_target=np.zeros(0))
+        mdl = dynamics.Model.from_problem(sub)
+        Fe = mdl.element_forces(U1)
+        F = mdl.internal_forces(U1)[i]
+        B0, V0 = tled.shape_derivatives(p.X, p.conn[els], 4)
+        vol_scale = np.sum(p.kappa[els] * V0 * np.abs(B0).max(axis=(1, 2)))
+        a_i = 2 * dt * dt / ((2 + ad) * mdl.mass[i])
+        U2_ref = -a_i * F + 4 / (2 + ad) * U1[i] + (ad - 2) / (2 + ad) * U0[i]
+        err = np.abs(U2[i] - U2_ref).max()
+        bound = a_i * (1e-4 * np.abs(Fe).max() + 8 * eps * vol_scale) \
+            + 4 * np.spacing(np.float32(np.abs(U2[i]).max()))
+        worst = max(worst, err / bound)
+        assert err <= bound, (i, err, bound)
+    print(f"brain ellipsoid 0.8M T4 TI, precision {prec}: worst error / bound {worst:.2f} over 64 nodes")
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_step_host_matches_separate_calls(B, prec):
+    """dj_step_host (targets in, one step, displacements out, one
+    synchronisation) gives bit for bit the trajectory of dj_mesh_update_bc_targets
+    + dj_step + dj_get_displacements, with page-locked and pageable buffers, and
+    its FP32 output is the FP64 output rounded once."""
+    torch = pytest.importorskip("torch")
+    p = W.cube_shear(W.TET4, 6, n_steps=40)
+    base = np.asarray(p.bc_target, dtype=np.float64)
+    N = p.n_nodes
+    ref, outs = [], {}
+    with B.Mesh(p, precision=prec) as m:
+        for k in range(25):
+            B.dj_mesh_update_bc_targets(m.h, base * (0.5 + 0.02 * k))
+            B.dj_step(m.h)
+            ref.append(m.displacements())
+    for layout in ("pageable", "pinned"):
+        if layout == "pinned":
+            tgt = torch.empty(base.size, dtype=torch.float64).pin_memory().numpy()
+            U64 = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            U32 = torch.empty((N, 3), dtype=torch.float32).pin_memory().numpy()
+        else:
+            tgt, U64, U32 = np.empty(base.size), np.empty((N, 3)), np.empty((N, 3), dtype=np.float32)
+        with B.Mesh(p, precision=prec) as m, B.Mesh(p, precision=prec) as m2:
+            for k in range(25):
+                tgt[:] = base * (0.5 + 0.02 * k)
+                B.dj_step_host(m.h, tgt, U64)
+                B.dj_step_host(m2.h, tgt, U32)
+                assert np.array_equal(U64, ref[k]), (layout, k)
+                assert np.array_equal(U32, U64.astype(np.float32)), (layout, k)
+        outs[layout] = U64.copy()
+    assert np.abs(outs["pinned"]).max() > 0
