@@ -873,31 +873,38 @@ def main():
                                                       "frac": gf / peak}
 
     # end to end through the public C ABI with host buffers: every step uploads
-    # the prescribed-displacement targets of that step and reads U back
+    # the prescribed-displacement targets of that step and reads U back, in one
+    # library call (dj_step_host: targets in, one step, U out, one
+    # synchronisation).  The state is FP32 (precision 0), so the read-back is
+    # FP32; the FP64 read-back of the same call is reported beside it.
     e2e = None
     if args.e2e_steps > 0:
         # the step's inputs and result live in pinned host memory
         targets_t = torch.tensor(p.bc_target, dtype=torch.float64).pin_memory()
         targets = targets_t.numpy()
-        U_host_t = torch.empty((N, 3), dtype=torch.float64).pin_memory()
-        U_host = U_host_t.numpy()
-        n_e2e = args.e2e_steps
-        t_e2e = 0.0
-        for k in range(n_e2e):
-            l2_flush()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            B.dj_mesh_update_bc_targets(mesh.h, targets)
-            B.dj_step(mesh.h, stream)
-            B.dj_get_displacements(mesh.h, N, out=U_host)
-            t_e2e += time.perf_counter() - t0
-        e2e_value, _ = replica_throughput(E * n_e2e, t_e2e * 1e3, dist, device="cuda")
-        # bytes that cross the host link per step: the FP64 targets (read by the
-        # library's kernel from the page-locked array), U in FP64 and the
-        # 40-byte device state read with it
-        e2e = {"value": e2e_value, "unit": "element-updates/s",
-               "h2d_bytes_per_step": int(targets.nbytes), "d2h_bytes_per_step": int(U_host.nbytes + 40),
-               "steps": n_e2e}
+        U32_t = torch.empty((N, 3), dtype=torch.float32).pin_memory()
+        U64_t = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+        res = {}
+        for name, U_host in (("f32", U32_t.numpy()), ("f64", U64_t.numpy())):
+            n_e2e = args.e2e_steps
+            t_e2e = 0.0
+            for k in range(n_e2e + 3):
+                l2_flush()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                B.dj_step_host(mesh.h, targets, U_host, stream)
+                if k >= 3:  # three untimed calls first
+                    t_e2e += time.perf_counter() - t0
+            val, _ = replica_throughput(E * n_e2e, t_e2e * 1e3, dist, device="cuda")
+            # bytes that cross the host link per step: the FP64 targets (read by
+            # the library's kernel from the page-locked array), U and the 48-byte
+            # device state read with it
+            res[name] = {"value": val, "unit": "element-updates/s", "ms_per_step": t_e2e * 1e3 / n_e2e,
+                         "h2d_bytes_per_step": int(targets.nbytes),
+                         "d2h_bytes_per_step": int(U_host.nbytes + 48), "steps": n_e2e}
+        e2e = dict(res["f32"])
+        e2e["call"] = "dj_step_host (targets in, one step, FP32 displacements out, one synchronisation)"
+        e2e["f64_output"] = res["f64"]
 
     # secondary workload: the hex8 cube (same metric)
     also = None

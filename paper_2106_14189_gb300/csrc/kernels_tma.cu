@@ -174,6 +174,10 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     async_wait_all();
     __syncthreads();
   }
+  // node counts of the current and the next tile, carried from tile to tile;
+  // the one after next is loaded a tile ahead of its use
+  int n_cur = __ldg(t.tile_ptr + first + 1) - __ldg(t.tile_ptr + first);
+  int n_nxt = second ? __ldg(t.tile_ptr + first + stride + 1) - __ldg(t.tile_ptr + first + stride) : 0;
   int i = 0;
   for (int tile = first; tile < t.n_tiles; tile += stride, ++i) {
     const int s = i & 1;
@@ -187,15 +191,15 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     const float4* su = su2 + s * cap;
     const float4* sl = sl2 + s * cap;
     const float* sp = sp2 + s * cap;
-    const int base = __ldg(t.tile_ptr + tile);
-    const int n_t = __ldg(t.tile_ptr + tile + 1) - base;
+    const int n_t = n_cur;
     const int next = tile + stride;
     const bool has_next = next < t.n_tiles;
+    const int after = next + stride;
+    const int n_after = after < t.n_tiles ? __ldg(t.tile_ptr + after + 1) - __ldg(t.tile_ptr + after) : 0;
     // 0. the next tile's nodes: its list came with this tile's stage
     if (has_next) {
       const int* tn = reinterpret_cast<const int*>(st + L.tnodes);
-      const int nn = __ldg(t.tile_ptr + next + 1) - __ldg(t.tile_ptr + next);
-      gather_nodes<CMP, ANP>(a, tn, nn, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, sp2 + (s ^ 1) * cap, tid, T);
+      gather_nodes<CMP, ANP>(a, tn, n_nxt, su2 + (s ^ 1) * cap, sl2 + (s ^ 1) * cap, sp2 + (s ^ 1) * cap, tid, T);
     }
     // 1. element forces of this tile into shared memory
     const int e = tile * T + tid;
@@ -268,6 +272,8 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     __syncthreads();
     if (tid == 0 && next + stride < t.n_tiles)
       issue_tile<NE>(a, t, L, smem + s * stage_bytes, &bars[s], next + stride, next + 2 * stride);
+    n_cur = n_nxt;
+    n_nxt = n_after;
   }
 }
 
