@@ -599,7 +599,13 @@ enum { DJ_WS_ARM_REST = 0, DJ_WS_ARM_POLYNOMIAL = 1, DJ_WS_ARM_FITTED = 2 };  /*
  *   mlp_bf16        1: BF16 products in the MLP (dj_mlp_set_precision)
  *   holdout         share of the loads held out (0.1; none below 20 loads)
  *   seed            split, minibatch and MLP initialisation seed
- *   adaptive        1: relaxations use dj_relax_adaptive (default), 0: dj_relax_to_tol */
+ *   adaptive        1: relaxations use dj_relax_adaptive (default), 0: dj_relax_to_tol
+ *   bootstrap       dj_ws_train only: 0 (default) relaxes every training load
+ *                   from rest; k >= 20 fits a warm start to the first k loads
+ *                   relaxed, relaxes the following ones from it
+ *                   (dj_ws_relax_to_tol, fitted arm, same tolerance: the
+ *                   training fields are still the method's relaxations) and
+ *                   refits each time the number of loads relaxed doubles */
 typedef struct {
   int n_in, n_out;
   int hidden[4];
@@ -612,6 +618,7 @@ typedef struct {
   double holdout;
   unsigned long long seed;
   int adaptive;
+  int bootstrap;
 } dj_ws_params;
 
 /* What the fit found (held-out losses: the weighted mean squared error of the

@@ -87,7 +87,7 @@ class dj_ws_params(C.Structure):
     _fields_ = [("n_in", C.c_int), ("n_out", C.c_int), ("hidden", C.c_int * 4), ("epochs", C.c_int),
                 ("batch", C.c_int), ("lr", C.c_double), ("lr_final", C.c_double), ("quadratic", C.c_int),
                 ("mlp", C.c_int), ("mlp_input", C.c_int), ("mlp_bf16", C.c_int), ("holdout", C.c_double),
-                ("seed", C.c_ulonglong), ("adaptive", C.c_int)]
+                ("seed", C.c_ulonglong), ("adaptive", C.c_int), ("bootstrap", C.c_int)]
 
 
 class dj_ws_info(C.Structure):

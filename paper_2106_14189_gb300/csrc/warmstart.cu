@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -436,7 +437,8 @@ dj_status new_ws(const dj_ws_params* prm, dj_ws** out) {
   if (P.n_in <= 0 || P.n_in > 256 || P.n_out <= 0 || P.n_out > 1024 || P.epochs < 0 || P.batch <= 0 ||
       !(P.lr > 0) || !(P.lr_final > 0) || !(P.holdout >= 0 && P.holdout < 0.9) ||
       (P.mlp_input != DJ_WS_MLP_ON_COEFFS && P.mlp_input != DJ_WS_MLP_ON_FEATURES) ||
-      (P.mlp_bf16 != 0 && P.mlp_bf16 != 1) || P.mlp < -1 || P.mlp > 1)
+      (P.mlp_bf16 != 0 && P.mlp_bf16 != 1) || P.mlp < -1 || P.mlp > 1 || P.bootstrap < 0 ||
+      (P.bootstrap > 0 && P.bootstrap < 20))
     return DJ_ERR_INVALID_ARG;
   for (int l = 0; l < 4; ++l)
     if (P.hidden[l] < 0 || P.hidden[l] > 4096) return DJ_ERR_INVALID_ARG;
@@ -482,6 +484,7 @@ void dj_ws_params_default(dj_ws_params* p) {
   p->holdout = 0.1;
   p->seed = 0;
   p->adaptive = 1;
+  p->bootstrap = 0;
 }
 
 dj_status dj_ws_fit(const long long* bc_dof, int n_bc, long long n_nodes, const float* d_targets,
@@ -545,19 +548,50 @@ dj_status dj_ws_train(dj_mesh* mesh, const double* targets, int n_loads, double 
     delete w;
     return e == cudaErrorMemoryAllocation ? DJ_ERR_OOM : DJ_ERR_CUDA;
   }
-  // training data: every load relaxed from rest; loads that fail are dropped
+  // training data: every load relaxed by the method to `tol`, from rest or
+  // (bootstrap) from a fit to the loads relaxed so far, refitted whenever
+  // their number doubles; loads that fail are dropped
   int kept = 0;
   long long steps_sum = 0;
   std::vector<float> tf(n_bc);
+  dj_ws* boot = nullptr;  // the current intermediate fit
+  int next_fit = w->prm.bootstrap > 0 ? w->prm.bootstrap : INT_MAX;
   for (int i = 0; i < n_loads && st == DJ_OK; ++i) {
     const double* t = targets + (size_t)i * n_bc;
-    st = dj_mesh_update_bc_targets(mesh, t);
-    if (st) break;
-    st = start_from_rest(mesh, d_zero, s);
-    if (st) break;
+    if (kept >= next_fit && kept < n_loads) {
+      if (boot) dj_ws_destroy(boot);
+      boot = nullptr;
+      st = new_ws(&w->prm, &boot);
+      if (st) break;
+      boot->n_bc = n_bc;
+      boot->n_dof = n_dof;
+      boot->bc_dof = bc;
+      st = ws_fit(boot, d_T, d_Y, kept, s);
+      if (st) {
+        w->last_error = boot->last_error;
+        break;
+      }
+      next_fit = 2 * kept;
+    }
     long long n = 0;
     double r = 0;
-    const dj_status rs = relax(mesh, w, tol, max_steps, &n, &r, s);
+    dj_status rs;
+    if (boot) {
+      dj_ws_result res{};
+      rs = dj_ws_relax_to_tol(mesh, boot, t, DJ_WS_ARM_FITTED, tol, max_steps, &res, stream);
+      n = res.steps;
+      if (rs == DJ_ERR_INVALID_ARG) {
+        st = rs;
+        w->last_error = boot->last_error;
+        break;
+      }
+    } else {
+      st = dj_mesh_update_bc_targets(mesh, t);
+      if (st) break;
+      st = start_from_rest(mesh, d_zero, s);
+      if (st) break;
+      rs = relax(mesh, w, tol, max_steps, &n, &r, s);
+    }
     if (rs == DJ_ERR_CUDA || rs == DJ_ERR_OOM) {
       st = rs;
       break;
@@ -575,6 +609,7 @@ dj_status dj_ws_train(dj_mesh* mesh, const double* targets, int n_loads, double 
     steps_sum += n;
     ++kept;
   }
+  if (boot) dj_ws_destroy(boot);
   w->info.n_kept = kept;
   w->info.data_seconds = seconds_since(t0);
   w->info.mean_training_steps = kept ? (double)steps_sum / kept : 0.0;
