@@ -176,7 +176,7 @@ def coarse_ws(env):
     torch, B = env
     from paper_2106_14189_gb300.warmstart import WarmStart, load_cases
     p = W.ellipsoid_tet4(h=6e-3, seed=0, disp_range=(1e-3, 4e-3))
-    ws = WarmStart(p, alpha=140.0, ramp_steps=500, tol=1e-5, epochs=1500, batch=128, mlp=-1)
+    ws = WarmStart(p, alpha=140.0, ramp_steps=750, tol=1e-5, epochs=1500, batch=128, mlp=-1)
     info = ws.train(load_cases(p, range(1000, 3048)))
     yield ws, info, p, load_cases(p, range(5000, 5016))
     ws.close()
