@@ -696,6 +696,47 @@ def run_cutout(args):
     print(json.dumps(line), flush=True)
 
 
+def batch_eval(args, stream):
+    """Batched solves: args.batch_instances seeded instances (T4 / H8 50/50,
+    5k-150k elements each) advanced in one CUDA graph with two kernel chains,
+    schedules chosen by dj_batch_autotune; element-updates/s over
+    args.batch_steps steps."""
+    import torch
+    from paper_2106_14189_gb300 import binding as B
+    n_inst = args.batch_instances
+    probs = W.batch_instances(n_inst, seed=0, n_steps=2000)
+    t_setup = time.perf_counter()
+    bt = B.Batch(probs)
+    t_setup = time.perf_counter() - t_setup
+    bt.run(20, stream)
+    bt.sync(stream)
+    t_tune = time.perf_counter()
+    B.dj_batch_autotune(bt.b, steps=20, stream=stream)
+    t_tune = time.perf_counter() - t_tune
+    bt.run(20, stream)
+    bt.sync(stream)
+    kb = args.batch_steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    bt.run(kb, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bt.sync(stream)
+    msb = e0.elapsed_time(e1)
+    n_i, n_nodes_b, n_el_b, n_tet_b, n_hex_b = bt.info()
+    bt.close()
+    return {"workload": f"{n_i} seeded instances, T4/H8 50/50, element count log-uniform in "
+                        f"[5k, 150k]: {n_el_b} elements ({n_tet_b} T4, {n_hex_b} H8), "
+                        f"{n_nodes_b} nodes, each its own dt = 0.9 dt_crit",
+            "value": n_el_b * kb / (msb * 1e-3), "unit": "element-updates/s",
+            "ms_per_step": msb / kb, "steps": kb, "setup_s": t_setup, "autotune_s": t_tune,
+            "schedule": "two kernel chains (T4 part, H8 part) in one CUDA graph, "
+                        "schedules chosen by dj_batch_autotune",
+            "l2": "working set ~1.5 GB > 129 MB L2 (no eviction needed)" if n_i >= 64 else
+                  "working set of this batch size may fit in L2"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -709,6 +750,9 @@ def main():
     ap.add_argument("--no-also", action="store_true", help="skip the secondary hex8 workload")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch workload")
     ap.add_argument("--batch-steps", type=int, default=400)
+    ap.add_argument("--batch-instances", type=int, default=256)
+    ap.add_argument("--batch-only", action="store_true",
+                    help="only the batched solves (for profiling): one JSON line")
     ap.add_argument("--warmstart", action="store_true",
                     help="learned warm start evaluation instead of the step benchmark")
     ap.add_argument("--brain", action="store_true",
@@ -765,6 +809,13 @@ def main():
         return
     if args.brain:
         run_brain(args)
+        return
+    if args.batch_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"batch": batch_eval(args, torch.cuda.current_stream())}), flush=True)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -991,36 +1042,7 @@ def main():
     # batched solves: 256 seeded instances, T4 / H8 50/50, 5k-150k elements each
     batch = None
     if world == 1 and not args.no_batch and not args.no_also:
-        probs = W.batch_instances(256, seed=0, n_steps=2000)
-        t_setup = time.perf_counter()
-        bt = B.Batch(probs)
-        t_setup = time.perf_counter() - t_setup
-        bt.run(20, stream)
-        bt.sync(stream)
-        t_tune = time.perf_counter()
-        B.dj_batch_autotune(bt.b, steps=20, stream=stream)
-        t_tune = time.perf_counter() - t_tune
-        bt.run(20, stream)
-        bt.sync(stream)
-        kb = args.batch_steps
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        bt.run(kb, stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        bt.sync(stream)
-        msb = e0.elapsed_time(e1)
-        n_inst, n_nodes_b, n_el_b, n_tet_b, n_hex_b = bt.info()
-        batch = {"workload": f"256 seeded instances, T4/H8 50/50, element count log-uniform in "
-                             f"[5k, 150k]: {n_el_b} elements ({n_tet_b} T4, {n_hex_b} H8), "
-                             f"{n_nodes_b} nodes, each its own dt = 0.9 dt_crit",
-                 "value": n_el_b * kb / (msb * 1e-3), "unit": "element-updates/s",
-                 "ms_per_step": msb / kb, "steps": kb, "setup_s": t_setup, "autotune_s": t_tune,
-                 "schedule": "two kernel chains (T4 part, H8 part) in one CUDA graph, "
-                             "schedules chosen by dj_batch_autotune",
-                 "l2": "working set ~1.5 GB > 129 MB L2 (no eviction needed)"}
-        bt.close()
+        batch = batch_eval(args, stream)
 
     # relaxation to tolerance, learned warm start against rest (the second half
     # of the metric): 3 mm ellipsoid, library training on seeded loads

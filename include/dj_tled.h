@@ -352,8 +352,12 @@ dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
  * library's kernels through their device mappings; other host memory goes
  * through one copy each way.  The FP32 output holds U + low part rounded once
  * (exactly U in the plain FP32 precision mode).
- * Errors: as dj_step and dj_mesh_update_bc_targets; device-side flags
- * (inverted element, non-finite value) are reported by this call. */
+ * Errors: as dj_step; device-side flags (inverted element, non-finite value)
+ * are reported by this call.  A non-finite target: with pageable targets
+ * DJ_ERR_INVALID_ARG before anything runs; with page-locked targets (checked
+ * on the host while the step runs) that entry is not applied -- the DOF keeps
+ * its previous target for the step -- and the call returns
+ * DJ_ERR_INVALID_ARG after the step. */
 dj_status dj_step_host(dj_mesh* mesh, const double* targets, void* U_out, int out_f64, void* stream);
 
 /* Current displacements into device memory, n_nodes * 3 floats in caller

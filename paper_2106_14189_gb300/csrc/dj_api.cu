@@ -1265,13 +1265,20 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   if (out_f64 != 0 && out_f64 != 1) return fail(m, DJ_ERR_INVALID_ARG, "out_f64 must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nb = m->bc_dof.size();
-  if (target && nb) {
+  // page-locked targets: the scatter kernel reads them through the device
+  // mapping and the host's own pass over them (finiteness, the host copy)
+  // runs while the step executes; a non-finite target is not applied (the
+  // kernel keeps the previous one) and the call reports it after the step
+  const bool mapped_targets = target && nb && mapped_host(target);
+  if (target && nb && !mapped_targets) {
     bool finite = true;
     for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
     if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
     std::memcpy(m->bc_target.data(), target, nb * sizeof(double));
-    if (const void* mt = mapped_host(target)) {
-      CK(launch_bc_targets(static_cast<const double*>(mt), m->d_bc_flat, (int)nb, m->d_bct, st));
+  }
+  if (target && nb) {
+    if (mapped_targets) {
+      CK(launch_bc_targets(static_cast<const double*>(mapped_host(target)), m->d_bc_flat, (int)nb, m->d_bct, st));
     } else {
       const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
       if (!m->h_bct_pinned) {
@@ -1302,9 +1309,21 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
       if (!direct) CK(cudaMemcpyAsync(U_out, m->d_out64, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, st));
     }
   }
-  s = read_state(m, st);  // the only synchronisation of the call
+  CK(cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  bool finite = true;
+  if (mapped_targets) {  // overlaps the step
+    for (size_t k = 0; k < nb; ++k) {
+      if (std::isfinite(target[k]))
+        m->bc_target[k] = target[k];
+      else
+        finite = false;
+    }
+  }
+  CK(cudaStreamSynchronize(st));  // the only synchronisation of the call
+  s = check_flags(m);
   if (s) return s;
-  return check_flags(m);
+  if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target (not applied; the step kept its previous value)");
+  return DJ_OK;
 }
 
 dj_status dj_step(dj_mesh* m, void* stream) {

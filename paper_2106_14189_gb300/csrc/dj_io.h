@@ -10,7 +10,8 @@ namespace dj {
 // of the per-node prescribed-displacement table (float4 per prescribed node:
 // x, y, z targets, w = component mask).  flat[k] < 4 * (table rows) and
 // flat[k] % 4 < 3 for every k (the host builds and checks the list); n <= 0
-// launches nothing.
+// launches nothing.  A non-finite target[k] is skipped (the entry keeps its
+// previous value); the host reports it.
 cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s);
 
 }  // namespace dj

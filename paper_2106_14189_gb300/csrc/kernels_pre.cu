@@ -335,7 +335,10 @@ __global__ void from_caller_order_kernel(const float* __restrict__ src, const in
 __global__ void bc_targets_kernel(const double* __restrict__ target, const int* __restrict__ flat, int n,
                                   float* __restrict__ table) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) table[__ldg(flat + k)] = (float)target[k];
+  if (k < n) {
+    const double v = target[k];
+    if (isfinite(v)) table[__ldg(flat + k)] = (float)v;  // a non-finite target keeps the previous one
+  }
 }
 
 }  // namespace

@@ -613,3 +613,32 @@ def test_step_host_matches_separate_calls(B, prec):
                 assert np.array_equal(U32, U64.astype(np.float32)), (layout, k)
         outs[layout] = U64.copy()
     assert np.abs(outs["pinned"]).max() > 0
+
+
+def test_step_host_non_finite_pinned_target_is_not_applied(B):
+    """A NaN among page-locked targets: the step runs with that DOF's previous
+    target, the other targets are applied, and the call reports
+    DJ_ERR_INVALID_ARG; pageable targets are refused before the step."""
+    torch = pytest.importorskip("torch")
+    p = W.cube_shear(W.TET4, 4, n_steps=10)
+    p.ramp_steps = 0
+    base = np.asarray(p.bc_target, dtype=np.float64)
+    moved = int(np.nonzero(np.abs(base) > 0)[0][0])
+    tgt = torch.empty(base.size, dtype=torch.float64).pin_memory().numpy()
+    U = np.empty((p.n_nodes, 3))
+    with B.Mesh(p) as m:
+        tgt[:] = base
+        B.dj_step_host(m.h, tgt, U)
+        before = U.reshape(-1)[p.bc_dof].copy()
+        tgt[:] = 2 * base
+        tgt[moved] = np.nan
+        with pytest.raises(B.DJError) as e:
+            B.dj_step_host(m.h, tgt, U)
+        assert e.value.status == B.DJ_ERR_INVALID_ARG
+        after = U.reshape(-1)[p.bc_dof]
+        assert after[moved] == np.float32(before[moved])
+        others = np.abs(base) > 0
+        others[moved] = False
+        assert np.allclose(after[others], 2 * base[others], rtol=1e-6)
+        with pytest.raises(B.DJError):
+            B.dj_step_host(m.h, np.full(base.size, np.nan), U)
