@@ -677,10 +677,12 @@ __device__ __forceinline__ float4 at16(const float4* base, unsigned off) {
 
 // Per-tile reduction of the force records into one partial per local node
 // (li: byte offsets of the records), spread over the whole block: G
-// consecutive lanes share a node (G = the
-// largest of 1, 2, 4, 8 with G n_t <= T), lane r adds the node's records
-// r, r + G, r + 2G, ... in order, and the G lane sums are combined by an xor
-// butterfly (fixed order).  All lanes of a warp take part in every butterfly.
+// consecutive lanes share a node (G = 8 or 4 when G n_t <= T, else 2, in
+// passes of T / G nodes: a tile of more than T / 2 nodes takes two passes, the
+// second over its lightest nodes, rather than one lane per node), lane r adds
+// the node's records r, r + G, r + 2G, ... in order, and the G lane sums are
+// combined by an xor butterfly (fixed order).  All lanes of a warp take part
+// in every butterfly.
 // store(q, f) receives node q's partial.  The choice of G depends only on n_t
 // and T, so every kernel that uses this gives bit-identical partials.
 template <int G, class Store>
@@ -714,8 +716,7 @@ __device__ __forceinline__ void reduce_tile(const float4* sf4, const unsigned sh
                                             int n_t, int tid, int T, Store store) {
   if (8 * n_t <= T) reduce_tile_g<8>(sf4, li, lp, n_t, tid, T, store);
   else if (4 * n_t <= T) reduce_tile_g<4>(sf4, li, lp, n_t, tid, T, store);
-  else if (2 * n_t <= T) reduce_tile_g<2>(sf4, li, lp, n_t, tid, T, store);
-  else reduce_tile_g<1>(sf4, li, lp, n_t, tid, T, store);
+  else reduce_tile_g<2>(sf4, li, lp, n_t, tid, T, store);
 }
 
 // d_b = u_b - u_0 from the nodal records (hi, lo)
