@@ -1269,7 +1269,12 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   // mapping and the host's own pass over them (finiteness, the host copy)
   // runs while the step executes; a non-finite target is not applied (the
   // kernel keeps the previous one) and the call reports it after the step
-  const bool mapped_targets = target && nb && mapped_host(target);
+  const void* mt = (target && nb) ? mapped_host(target) : nullptr;
+  const bool mapped_targets = mt != nullptr;
+  // the device state reaches the host through the mapping of its page-locked
+  // copy, written by the last kernel of the call (no separate copy)
+  DevState* st_map = nullptr;
+  CK(cudaHostGetDevicePointer((void**)&st_map, m->h_state, 0));
   if (target && nb && !mapped_targets) {
     bool finite = true;
     for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
@@ -1278,7 +1283,7 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   }
   if (target && nb) {
     if (mapped_targets) {
-      CK(launch_bc_targets(static_cast<const double*>(mapped_host(target)), m->d_bc_flat, (int)nb, m->d_bct, st));
+      CK(launch_bc_targets(static_cast<const double*>(mt), m->d_bc_flat, (int)nb, m->d_bct, st));
     } else {
       const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
       if (!m->h_bct_pinned) {
@@ -1300,16 +1305,17 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
     if (out_f64) {
       if (!direct && !m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
       double* dst = direct ? static_cast<double*>(direct) : m->d_out64;
-      CK(launch_to_caller_order_f64(m->d_U, lo, m->d_perm, (int)N, dst, st));
+      CK(launch_to_caller_order_f64(m->d_U, lo, m->d_perm, (int)N, dst, st, m->d_state, st_map));
       if (!direct) CK(cudaMemcpyAsync(U_out, m->d_out64, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, st));
     } else {
       if (!direct && !m->d_out64) CK(cudaMalloc(&m->d_out64, 3 * N * sizeof(double)));
       float* dst = direct ? static_cast<float*>(direct) : reinterpret_cast<float*>(m->d_out64);
-      CK(launch_to_caller_order_f32(m->d_U, lo, m->d_perm, (int)N, dst, st));
+      CK(launch_to_caller_order_f32(m->d_U, lo, m->d_perm, (int)N, dst, st, m->d_state, st_map));
       if (!direct) CK(cudaMemcpyAsync(U_out, m->d_out64, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, st));
     }
+  } else {
+    CK(launch_copy_state(m->d_state, st_map, st));
   }
-  CK(cudaMemcpyAsync(m->h_state, m->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, st));
   bool finite = true;
   if (mapped_targets) {  // overlaps the step
     for (size_t k = 0; k < nb; ++k) {

@@ -247,13 +247,18 @@ cudaError_t launch_node_mass(const int* sell, const int* chunk_ptr, const double
 cudaError_t launch_min_reduce(const double* v, int n, double* out, cudaStream_t s);
 // evict the L2 cache: write the first half of buf, read the second (bytes >= 2 x L2)
 cudaError_t launch_l2_flush(void* buf, size_t bytes, cudaStream_t s);
+// st_out (optional): block 0 also copies the device state *st there (e.g. a
+// mapped page-locked host copy), so one synchronisation returns both
 cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
-                                       double* out, cudaStream_t s);
+                                       double* out, cudaStream_t s, const DevState* st = nullptr,
+                                       DevState* st_out = nullptr);
+cudaError_t launch_copy_state(const DevState* st, DevState* st_out, cudaStream_t s);
 cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, int N, float* out,
                                    cudaStream_t s);
 // FP32 caller-order output (U + low part when Ulo is given), stores contiguous per warp
 cudaError_t launch_to_caller_order_f32(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
-                                       float* out, cudaStream_t s);
+                                       float* out, cudaStream_t s, const DevState* st = nullptr,
+                                       DevState* st_out = nullptr);
 // U (internal) = caller-order field (N x 3 floats); w of U and of V kept,
 // U^n - U^{n-1} = 0, low part = 0
 cudaError_t launch_from_caller_order(const float* src, const int* node_new_of_old, int N, float4* U,

@@ -267,8 +267,10 @@ constexpr int kOrderThreads = 256;
 __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f64_kernel(const float4* __restrict__ U,
                                                                            const float4* __restrict__ Ulo,
                                                                            const int* __restrict__ perm, int N,
-                                                                           double* out) {
-  __shared__ double sv[3 * kOrderThreads];
+                                                                           double* out, const DevState* st,
+                                                                           DevState* st_out) {
+  __shared__ __align__(16) double sv[3 * kOrderThreads];
+  if (st_out && blockIdx.x == 0 && threadIdx.x == 0) *st_out = *st;
   const int i0 = blockIdx.x * kOrderThreads;
   const int i = i0 + threadIdx.x;  // caller node id
   if (i < N) {
@@ -287,7 +289,14 @@ __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f64_kernel(cons
   }
   __syncthreads();
   const int n = 3 * min(kOrderThreads, N - i0);
-  for (int q = threadIdx.x; q < n; q += kOrderThreads) out[3 * (size_t)i0 + q] = sv[q];
+  double* o = out + 3 * (size_t)i0;
+  if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {  // 16-byte stores (pairs of values)
+    for (int q = threadIdx.x; q < n / 2; q += kOrderThreads)
+      reinterpret_cast<double2*>(o)[q] = reinterpret_cast<const double2*>(sv)[q];
+    if ((n & 1) && threadIdx.x == 0) o[n - 1] = sv[n - 1];
+  } else {
+    for (int q = threadIdx.x; q < n; q += kOrderThreads) o[q] = sv[q];
+  }
 }
 
 // FP32 displacements (high + low part in the compensated mode, rounded once)
@@ -295,8 +304,10 @@ __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f64_kernel(cons
 __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f32_kernel(const float4* __restrict__ U,
                                                                            const float4* __restrict__ Ulo,
                                                                            const int* __restrict__ perm, int N,
-                                                                           float* out) {
-  __shared__ float sv[3 * kOrderThreads];
+                                                                           float* out, const DevState* st,
+                                                                           DevState* st_out) {
+  __shared__ __align__(16) float sv[3 * kOrderThreads];
+  if (st_out && blockIdx.x == 0 && threadIdx.x == 0) *st_out = *st;
   const int i0 = blockIdx.x * kOrderThreads;
   const int i = i0 + threadIdx.x;  // caller node id
   if (i < N) {
@@ -314,8 +325,17 @@ __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f32_kernel(cons
   }
   __syncthreads();
   const int n = 3 * min(kOrderThreads, N - i0);
-  for (int q = threadIdx.x; q < n; q += kOrderThreads) out[3 * (size_t)i0 + q] = sv[q];
+  float* o = out + 3 * (size_t)i0;
+  if ((reinterpret_cast<uintptr_t>(o) & 15) == 0) {  // 16-byte stores (quads of values)
+    for (int q = threadIdx.x; q < n / 4; q += kOrderThreads)
+      reinterpret_cast<float4*>(o)[q] = reinterpret_cast<const float4*>(sv)[q];
+    for (int q = (n / 4) * 4 + threadIdx.x; q < n; q += kOrderThreads) o[q] = sv[q];
+  } else {
+    for (int q = threadIdx.x; q < n; q += kOrderThreads) o[q] = sv[q];
+  }
 }
+
+__global__ void copy_state_kernel(const DevState* st, DevState* st_out) { *st_out = *st; }
 
 __global__ void from_caller_order_kernel(const float* __restrict__ src, const int* __restrict__ perm, int N,
                                          float4* U, float4* V, float4* Ulo) {
@@ -392,16 +412,21 @@ cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, 
 }
 
 cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
-                                       double* out, cudaStream_t s) {
+                                       double* out, cudaStream_t s, const DevState* st, DevState* st_out) {
   const int t = kOrderThreads;
-  to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
+  to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out, st, st_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_state(const DevState* st, DevState* st_out, cudaStream_t s) {
+  copy_state_kernel<<<1, 1, 0, s>>>(st, st_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_to_caller_order_f32(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
-                                       float* out, cudaStream_t s) {
+                                       float* out, cudaStream_t s, const DevState* st, DevState* st_out) {
   const int t = kOrderThreads;
-  to_caller_order_f32_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out);
+  to_caller_order_f32_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out, st, st_out);
   return cudaGetLastError();
 }
 
