@@ -554,9 +554,11 @@ dj_status dj_quad_features(const float* d_X, int S, int ld, int n, float* d_F, v
 dj_status dj_linear_apply(const float* d_W, int n_out, int n_in, const float* d_X, int S, float alpha, float beta,
                           float* d_Y, void* stream);
 
-/* BF16 variant of an MLP (no counterpart in the paper): precision 1 rounds
- * the weights and the activations entering every product to bfloat16 (8-bit
- * significand) and accumulates in FP32; the master weights, Adam moments,
+/* BF16 variant of an MLP (no counterpart in the paper): precision 1 runs the
+ * forward and backward products on the tensor cores (tcgen05.mma, BF16
+ * operands rounded from the FP32 values, FP32 accumulation in tensor memory);
+ * precision 2 rounds the same operands to BF16 but multiplies on the CUDA
+ * cores (a reference for the first); the master weights, Adam moments,
  * biases, tanh and loss stay FP32.  precision 0 (default) is plain FP32.
  * Errors: DJ_ERR_INVALID_ARG. */
 dj_status dj_mlp_set_precision(dj_mlp* mlp, int precision);

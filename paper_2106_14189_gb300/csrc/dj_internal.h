@@ -210,6 +210,14 @@ cudaError_t launch_adr_finalize(const double* rq_partials, int n, const DevState
 cudaError_t launch_group_resid(const double2* node_resid, const int* group_node_ptr, int n_groups,
                                double2* out, cudaStream_t s);
 
+// gemm_tc.cu: C = alpha op(A) op(B) + beta C (strided FP32 operands, rounded
+// to BF16 in shared memory; FP32 accumulation in tensor memory, tcgen05)
+cudaError_t gemm_bf16_tc(int M, int N, int K, float alpha, const float* A, long long sar, long long sac,
+                         const float* B, long long sbr, long long sbc, float beta, float* C, long long ldc,
+                         cudaStream_t s);
+// true (and the flag cleared) if a bounded wait of that kernel gave up
+bool gemm_tc_timed_out();
+
 // force kernel variants
 enum { VAR_NH = 0, VAR_TI = 1, VAR_OT = 2, VAR_MR = 3, VAR_ALL = 4 };
 

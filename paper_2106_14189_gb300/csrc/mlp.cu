@@ -13,8 +13,9 @@
 //   colsum_kernel      bias gradients (fixed-order column sums)
 //   adam_kernel        Adam update with bias correction
 //
-// The dense products here take milliseconds (batch <= 1024, widths <= 256);
-// they are SIMT FP32, not tensor-core kernels.
+// The dense products here take milliseconds (batch <= 1024, widths <= 256):
+// SIMT FP32 by default; the MLP's BF16 variant runs its products on the
+// tensor cores (gemm_tc.cu).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -221,6 +222,14 @@ cudaError_t gemm(int M, int N, int K, float alpha, const float* A, long long sar
 
 inline unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// the MLP's products: FP32 on CUDA cores (precision 0), BF16 operands on the
+// tensor cores (1, gemm_tc.cu), BF16-rounded operands on CUDA cores (2)
+cudaError_t mlp_gemm(int precision, int M, int N, int K, const float* A, long long sar, long long sac,
+                     const float* B, long long sbr, long long sbc, float* C, long long ldc, cudaStream_t s) {
+  if (precision == 1) return gemm_bf16_tc(M, N, K, 1.f, A, sar, sac, B, sbr, sbc, 0.f, C, ldc, s);
+  return gemm<float>(M, N, K, 1.f, A, sar, sac, B, sbr, sbc, 0.f, C, ldc, s, nullptr, precision == 2 ? 1 : 0);
+}
+
 // Symmetric eigen-decomposition (FP64, host) by the cyclic Jacobi method: sweeps
 // over the pairs (p, q), p < q, row by row; each pair is annihilated by the plane
 // rotation J = [[c, s], [-s, c]] in the (p, q) plane with t = s / c the root of
@@ -297,7 +306,7 @@ struct dj_mlp {
   double* d_loss = nullptr;
   int batch_cap = 0;
   long long t = 0;  // Adam step
-  int bf16 = 0;     // 1: products with bfloat16-rounded operands, FP32 accumulation
+  int bf16 = 0;     // products: 0 FP32, 1 BF16 tensor cores, 2 BF16-rounded operands on CUDA cores
   std::string last_error;
 };
 
@@ -341,7 +350,7 @@ dj_status mlp_forward(dj_mlp* m, const float* X, int batch, cudaStream_t s) {
     const int in = m->widths[l], out = m->widths[l + 1];
     const float* W = m->d_p + m->w_off[l];
     // Z = A_l W^T : (batch x in)(in x out), W row-major out x in -> B(k, j) = W[j * in + k]
-    MCK(gemm<float>(batch, out, in, 1.f, m->act[l], in, 1, W, 1, in, 0.f, m->act[l + 1], out, s, nullptr, m->bf16));
+    MCK(mlp_gemm(m->bf16, batch, out, in, m->act[l], in, 1, W, 1, in, m->act[l + 1], out, s));
     const long long n = (long long)batch * out;
     bias_act_kernel<<<blocks(n, 256), 256, 0, s>>>(m->act[l + 1], m->d_p + m->b_off[l], batch, out,
                                                    l + 1 < m->L ? 1 : 0);
@@ -447,13 +456,12 @@ dj_status dj_mlp_loss_grad(dj_mlp* m, const float* d_X, const float* d_T, const 
     float* gW = m->d_g + m->w_off[l];
     float* gb = m->d_g + m->b_off[l];
     // dW = dZ^T A_l : (out x batch)(batch x in)
-    MCK(gemm<float>(out, in, batch, 1.f, dcur, 1, out, m->act[l], in, 1, 0.f, gW, in, s, nullptr, m->bf16));
+    MCK(mlp_gemm(m->bf16, out, in, batch, dcur, 1, out, m->act[l], in, 1, gW, in, s));
     colsum_kernel<<<blocks(out, 128), 128, 0, s>>>(dcur, batch, out, gb);
     MCK(cudaGetLastError());
     if (l > 0) {
       // dA_l = dZ W : (batch x out)(out x in), then through tanh
-      MCK(gemm<float>(batch, in, out, 1.f, dcur, out, 1, m->d_p + m->w_off[l], in, 1, 0.f, dnext, in, s, nullptr,
-                      m->bf16));
+      MCK(mlp_gemm(m->bf16, batch, in, out, dcur, out, 1, m->d_p + m->w_off[l], in, 1, dnext, in, s));
       const long long n = (long long)batch * in;
       act_bwd_kernel<<<blocks(n, 256), 256, 0, s>>>(dnext, m->act[l], n);
       MCK(cudaGetLastError());
@@ -463,6 +471,7 @@ dj_status dj_mlp_loss_grad(dj_mlp* m, const float* d_X, const float* d_T, const 
   if (loss_out) {
     MCK(cudaMemcpyAsync(loss_out, m->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
     MCK(cudaStreamSynchronize(s));
+    if (m->bf16 == 1 && gemm_tc_timed_out()) return mfail(m, DJ_ERR_CUDA, "a tensor-core wait timed out");
   }
   return DJ_OK;
 }
@@ -481,7 +490,7 @@ dj_status dj_mlp_adam_step(dj_mlp* m, float lr, float beta1, float beta2, float 
 }
 
 dj_status dj_mlp_set_precision(dj_mlp* m, int precision) {
-  if (!m || (precision != 0 && precision != 1)) return DJ_ERR_INVALID_ARG;
+  if (!m || precision < 0 || precision > 2) return DJ_ERR_INVALID_ARG;
   m->bf16 = precision;
   return DJ_OK;
 }

@@ -134,10 +134,10 @@ def test_quadratic_features(env):
 
 
 def test_bf16_mlp_matches_reference_at_bf16_tolerance(env):
-    """BF16 variant: forward output and gradients against the FP64 MLP; every
-    product operand is rounded to bfloat16 (8-bit significand, relative
-    spacing 2^-8), so the tolerance is a few times that spacing, against
-    1e-5 for FP32 (test above)."""
+    """BF16 variant (products on the tensor cores): forward output and
+    gradients against the FP64 MLP; every product operand is rounded to
+    bfloat16 (8-bit significand, relative spacing 2^-8), so the tolerance is a
+    few times that spacing, against 1e-5 for FP32 (test above)."""
     torch, B = env
     rng = np.random.default_rng(3)
     widths = [64, 256, 256, 256, 128]
@@ -165,6 +165,34 @@ def test_bf16_mlp_matches_reference_at_bf16_tolerance(env):
         assert np.abs(dY.cpu().numpy() - Y_ref).max() < 1e-5 * np.abs(Y_ref).max()
     finally:
         B.dj_mlp_destroy(m)
+
+
+@pytest.mark.parametrize("shape", [(200, 300, 150), (1, 64, 128), (256, 256, 256), (77, 40, 9)])
+def test_tensor_core_products_match_cuda_core_bf16(env, shape):
+    """The BF16 products on the tensor cores (tcgen05, precision 1) against the
+    same BF16-rounded operands multiplied on the CUDA cores (precision 2): one
+    linear layer (batch x in -> out; ragged sizes, a single row), forward and
+    weight gradient, agree to FP32 accumulation-order rounding."""
+    torch, B = env
+    batch, n_in, n_out = shape
+    rng = np.random.default_rng(11)
+    X = rng.normal(size=(batch, n_in))
+    T = rng.normal(size=(batch, n_out))
+    dX = torch.tensor(X, dtype=torch.float32, device="cuda")
+    dT = torch.tensor(T, dtype=torch.float32, device="cuda")
+    out = {}
+    for prec in (1, 2):
+        m = B.dj_mlp_create([n_in, n_out], seed=2)
+        try:
+            B.dj_mlp_set_precision(m, prec)
+            dY = torch.empty((batch, n_out), device="cuda")
+            B.dj_mlp_forward(m, dX.data_ptr(), batch, dY.data_ptr())
+            B.dj_mlp_loss_grad(m, dX.data_ptr(), dT.data_ptr(), 0, batch)
+            out[prec] = (dY.cpu().numpy().astype(np.float64), B.dj_mlp_get_grads(m).astype(np.float64))
+        finally:
+            B.dj_mlp_destroy(m)
+    for a, b in zip(out[1], out[2]):
+        assert np.abs(a - b).max() <= 2e-5 * np.abs(b).max()
 
 
 @pytest.fixture(scope="module")
