@@ -243,76 +243,10 @@ def host_cpu():
     return n, f"{model or 'unknown'} ({platform.machine()})"
 
 
-def _oracle_block_worker(conn, problem, e0, e1):
-    """Worker of the all-cores oracle timing: the FP64 oracle's element forces
-    of elements [e0, e1) of `problem`, assembled over all nodes, for every U
-    received (None ends it)."""
-    from oracle import dynamics
-    import copy as _copy
-    sub = _copy.copy(problem)
-    for k in ("conn", "model", "mu", "kappa", "rho", "eta_a", "eta_b", "c01", "a_dir", "b_dir"):
-        v = getattr(problem, k)
-        if v is not None:
-            setattr(sub, k, np.asarray(v)[e0:e1])
-    m = dynamics.Model.from_problem(sub)
-    conn.send(True)
-    while True:
-        U = conn.recv()
-        if U is None:
-            break
-        conn.send(m.internal_forces(U))
-
-
-class ParallelOracle:
-    """The FP64 oracle stepped with its element forces split over host processes
-    (spawned, one contiguous element block each, forces summed in block order);
-    the update is the oracle's own (dynamics.ExplicitSolver.step)."""
-
-    def __init__(self, problem, n_proc):
-        import multiprocessing as mp
-        from oracle import dynamics
-        ctx = mp.get_context("spawn")
-        self.solver = dynamics.ExplicitSolver.from_problem(problem)
-        E = problem.n_elems
-        cuts = np.linspace(0, E, n_proc + 1).astype(int)
-        self.pipes, self.procs = [], []
-        for i in range(n_proc):
-            a, b = ctx.Pipe()
-            pr = ctx.Process(target=_oracle_block_worker, args=(b, problem, int(cuts[i]), int(cuts[i + 1])),
-                             daemon=True)
-            pr.start()
-            self.pipes.append(a)
-            self.procs.append(pr)
-        for a in self.pipes:
-            a.recv()
-        self.solver.m.internal_forces = self._forces
-
-    def _forces(self, U):
-        for a in self.pipes:
-            a.send(U)
-        F = self.pipes[0].recv()
-        for a in self.pipes[1:]:
-            F = F + a.recv()
-        return F
-
-    def step(self):
-        self.solver.step()
-
-    def close(self):
-        for a in self.pipes:
-            try:
-                a.send(None)
-            except Exception:
-                pass
-        for pr in self.procs:
-            pr.join(timeout=10)
-            if pr.is_alive():
-                pr.terminate()
-
-
 def oracle_rate_all_cores(p_small, n_proc, min_seconds):
     """As oracle_rate, with the element forces split over n_proc processes."""
-    po = ParallelOracle(p_small, n_proc)
+    from oracle.parallel import ParallelSolver
+    po = ParallelSolver(p_small, n_proc)
     try:
         po.step()
         t = time.perf_counter()
@@ -368,7 +302,8 @@ def run_reference(args, world, rank):
         n = max(2, int(round(per_step_elems ** (1 / 3))))
         sample = W.cube_shear(W.HEX8, n, n_steps=5000)
     if cores > 1:
-        s = ParallelOracle(sample, cores)
+        from oracle.parallel import ParallelSolver
+        s = ParallelSolver(sample, cores)
     else:
         from oracle import dynamics
         s = dynamics.ExplicitSolver.from_problem(sample)

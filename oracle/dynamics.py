@@ -50,7 +50,7 @@ Readings (the paper is silent on these):
 """
 import numpy as np
 
-from . import anp, djtled, elements, hourglass
+from . import anp, djtled, elements, hourglass, tled
 
 TET4, HEX8 = elements.TET4, elements.HEX8
 
@@ -96,9 +96,19 @@ class Model:
     """Mesh + material + precomputed oracle constants; evaluates F_int(U)."""
 
     def __init__(self, elem_type, X, conn, mat, a_dir=None, b_dir=None, hg_coeff=0.1,
-                 R=None, anp=False):
+                 R=None, anp=False, formulation="djtled"):
+        """formulation: "djtled" (O-A, the paper's Jacobian-operator forces,
+        Table 3) or "tled" (O-B, classical TLED through the deformation
+        gradient and the second Piola-Kirchhoff stress, Eq. 4 and 54-55): the
+        same discretisation, so both give the same trajectory up to rounding
+        (the paper's Fig. 4 compares the two)."""
+        if formulation not in ("djtled", "tled"):
+            raise ValueError(formulation)
+        self.formulation = formulation
         self.elem_type = int(elem_type)
         self.anp = bool(anp)
+        if self.anp and formulation != "djtled":
+            raise ValueError("average nodal pressure is built on the DJ-TLED forces")
         if self.anp and self.elem_type != TET4:
             raise ValueError("average nodal pressure is built for T4 meshes")
         self.X = np.asarray(X, dtype=np.float64)
@@ -117,14 +127,19 @@ class Model:
         self.mass = lumped_mass(self.pre["V0"], self.mat["rho"], self.conn, self.N)
 
     @classmethod
-    def from_problem(cls, p, R=None):
+    def from_problem(cls, p, R=None, formulation="djtled"):
         mat = dict(model=p.model, mu=p.mu, kappa=p.kappa, rho=p.rho, eta_a=p.eta_a,
                    eta_b=p.eta_b, c01=p.c01)
         return cls(p.elem_type, p.X, p.conn, mat, p.a_dir, p.b_dir, p.hg_coeff, R,
-                   anp=getattr(p, "anp", False))
+                   anp=getattr(p, "anp", False), formulation=formulation)
 
     def element_forces(self, U):
         u_e = U[self.conn]
+        if self.formulation == "tled":
+            F = tled.element_forces(u_e, self.X, self.conn, self.elem_type, self.mat, self.a_dir, self.b_dir)
+            if self.elem_type == HEX8:
+                F = F + hourglass.hourglass_forces(u_e, self.gamma, self.k_hg)
+            return F
         pbar = None
         if self.anp:
             J = djtled.kinematics(u_e, self.pre)["J"]
@@ -174,10 +189,10 @@ class ExplicitSolver:
         self.c = (self.alpha * d - 2.0) / (2.0 + self.alpha * d)
 
     @classmethod
-    def from_problem(cls, p, dt=None, alpha=None, R=None):
+    def from_problem(cls, p, dt=None, alpha=None, R=None, formulation="djtled"):
         if dt is None and getattr(p, "dt", 0.0) > 0.0:
             dt = p.dt
-        return cls(Model.from_problem(p, R), p.bc_dof, p.bc_target, dt=dt,
+        return cls(Model.from_problem(p, R, formulation), p.bc_dof, p.bc_target, dt=dt,
                    dt_scale=p.dt_scale, alpha=p.alpha if alpha is None else alpha,
                    ramp_kind=p.ramp_kind, ramp_steps=p.ramp_steps)
 

@@ -104,6 +104,11 @@ struct dj_mesh {
   int geometric = 0;
   float4* d_parts = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // dj_step_host: side stream and events for the target scatter that runs
+  // beside the element-force kernel (created on first use)
+  cudaStream_t io_stream = nullptr;
+  cudaEvent_t io_before = nullptr, io_done = nullptr;
+  DevState* h_state_map = nullptr;  // device address of the page-locked state copy
   cudaGraphExec_t run_exec = nullptr;
   int run_chunk = 0;
   cudaGraphExec_t relax_exec = nullptr;
@@ -207,6 +212,12 @@ void release_device(dj_mesh* m) {
   if (m->h_bct_pinned) cudaFreeHost(m->h_bct_pinned);
   m->h_bct_pinned = nullptr;
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+  if (m->io_stream) cudaStreamDestroy(m->io_stream);
+  if (m->io_before) cudaEventDestroy(m->io_before);
+  if (m->io_done) cudaEventDestroy(m->io_done);
+  m->io_stream = nullptr;
+  m->io_before = m->io_done = nullptr;
+  m->h_state_map = nullptr;
   m->d_conn = nullptr;
   m->d_consts = nullptr;
   m->d_slots = nullptr;
@@ -1273,8 +1284,8 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   const bool mapped_targets = mt != nullptr;
   // the device state reaches the host through the mapping of its page-locked
   // copy, written by the last kernel of the call (no separate copy)
-  DevState* st_map = nullptr;
-  CK(cudaHostGetDevicePointer((void**)&st_map, m->h_state, 0));
+  if (!m->h_state_map) CK(cudaHostGetDevicePointer((void**)&m->h_state_map, m->h_state, 0));
+  DevState* st_map = m->h_state_map;
   if (target && nb && !mapped_targets) {
     bool finite = true;
     for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
@@ -1283,7 +1294,18 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   }
   if (target && nb) {
     if (mapped_targets) {
-      CK(launch_bc_targets(static_cast<const double*>(mt), m->d_bc_flat, (int)nb, m->d_bct, st));
+      // the scatter reads the targets over the host link on a side stream,
+      // beside the element-force kernel; the node update (the only reader of
+      // the prescribed-value table) waits for it
+      if (!m->io_stream) {
+        CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&m->io_done, cudaEventDisableTiming));
+      }
+      CK(cudaEventRecord(m->io_before, st));
+      CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
+      CK(launch_bc_targets(static_cast<const double*>(mt), m->d_bc_flat, (int)nb, m->d_bct, m->io_stream));
+      CK(cudaEventRecord(m->io_done, m->io_stream));
     } else {
       const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
       if (!m->h_bct_pinned) {
@@ -1297,7 +1319,13 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
       CK(cudaMemcpyAsync(m->d_bct, m->h_bct_pinned, bytes, cudaMemcpyHostToDevice, st));
     }
   }
-  CK(launch_step(m, st, NODE_UPDATE));
+  if (mapped_targets) {
+    CK(launch_force_any(m, 1, st));
+    CK(cudaStreamWaitEvent(st, m->io_done, 0));
+    CK(launch_node(NODE_UPDATE, m->cmp, node_args(m), st));
+  } else {
+    CK(launch_step(m, st, NODE_UPDATE));
+  }
   if (U_out) {
     const long long N = m->N;
     void* direct = mapped_host(U_out);
