@@ -171,8 +171,12 @@ def test_bf16_mlp_matches_reference_at_bf16_tolerance(env):
 def test_tensor_core_products_match_cuda_core_bf16(env, shape):
     """The BF16 products on the tensor cores (tcgen05, precision 1) against the
     same BF16-rounded operands multiplied on the CUDA cores (precision 2): one
-    linear layer (batch x in -> out; ragged sizes, a single row), forward and
-    weight gradient, agree to FP32 accumulation-order rounding."""
+    linear layer (batch x in -> out; ragged sizes, a single row).  The forward
+    product sees identical operands and agrees to FP32 accumulation-order
+    rounding (2e-5); the weight gradient's operand dL/dY comes from that
+    forward output, whose last-bit differences can move a value to the
+    neighbouring bfloat16, so it agrees to a fraction of one BF16 spacing
+    (1e-3 against 2^-8 = 3.9e-3)."""
     torch, B = env
     batch, n_in, n_out = shape
     rng = np.random.default_rng(11)
@@ -191,8 +195,9 @@ def test_tensor_core_products_match_cuda_core_bf16(env, shape):
             out[prec] = (dY.cpu().numpy().astype(np.float64), B.dj_mlp_get_grads(m).astype(np.float64))
         finally:
             B.dj_mlp_destroy(m)
-    for a, b in zip(out[1], out[2]):
-        assert np.abs(a - b).max() <= 2e-5 * np.abs(b).max()
+    (y1, g1), (y2, g2) = out[1], out[2]
+    assert np.abs(y1 - y2).max() <= 2e-5 * np.abs(y2).max()
+    assert np.abs(g1 - g2).max() <= 1e-3 * np.abs(g2).max()
 
 
 @pytest.fixture(scope="module")
