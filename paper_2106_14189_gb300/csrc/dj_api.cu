@@ -107,7 +107,9 @@ struct dj_mesh {
   // dj_step_host: side stream and events for the target scatter that runs
   // beside the element-force kernel (created on first use)
   cudaStream_t io_stream = nullptr;
-  cudaEvent_t io_before = nullptr, io_done = nullptr;
+  cudaEvent_t io_before = nullptr, io_done = nullptr, io_copied = nullptr;
+  int4* d_bc_entry = nullptr;    // per prescribed-node row: target entries of x, y, z (-1: free), mask
+  double* d_tgt_stage = nullptr; // device copy of the caller's targets (allocated on first use)
   DevState* h_state_map = nullptr;  // device address of the page-locked state copy
   cudaGraphExec_t run_exec = nullptr;
   int run_chunk = 0;
@@ -215,8 +217,13 @@ void release_device(dj_mesh* m) {
   if (m->io_stream) cudaStreamDestroy(m->io_stream);
   if (m->io_before) cudaEventDestroy(m->io_before);
   if (m->io_done) cudaEventDestroy(m->io_done);
+  if (m->io_copied) cudaEventDestroy(m->io_copied);
+  if (m->d_bc_entry) cudaFree(m->d_bc_entry);
+  if (m->d_tgt_stage) cudaFree(m->d_tgt_stage);
   m->io_stream = nullptr;
-  m->io_before = m->io_done = nullptr;
+  m->io_before = m->io_done = m->io_copied = nullptr;
+  m->d_bc_entry = nullptr;
+  m->d_tgt_stage = nullptr;
   m->h_state_map = nullptr;
   m->d_conn = nullptr;
   m->d_consts = nullptr;
@@ -401,6 +408,8 @@ NodeArgs node_args(dj_mesh* m) {
   a.node_resid = m->n_groups > 0 ? m->d_node_resid : nullptr;
   a.bm1_node = m->d_bm1;
   a.st = m->d_state;
+  a.tgt = nullptr;
+  a.bc_entry = m->d_bc_entry;
   a.adr = m->d_adr;
   a.rq_partials = m->d_rq;
   a.usnap = m->d_usnap;
@@ -990,6 +999,17 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
     const size_t nb = m->bc_flat_of_entry.size();
     CK(dalloc(m, &m->d_bc_flat, nb));
     CK(cudaMemcpy(m->d_bc_flat, m->bc_flat_of_entry.data(), nb * sizeof(int), cudaMemcpyHostToDevice));
+    // per prescribed-node row, the target entries of its components (read by
+    // the node update when dj_step_host hands it the targets directly)
+    std::vector<int4> ent(m->n_bc_nodes, make_int4(-1, -1, -1, 0));
+    for (size_t k = 0; k < nb; ++k) {
+      int4& e = ent[m->bc_node_of_entry[k]];
+      const int c = m->bc_comp_of_entry[k];
+      (c == 0 ? e.x : (c == 1 ? e.y : e.z)) = (int)k;
+      e.w |= 1 << c;
+    }
+    CK(dalloc(m, &m->d_bc_entry, ent.size()));
+    CK(cudaMemcpy(m->d_bc_entry, ent.data(), ent.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
   CK(dalloc(m, &m->d_perm, N));
   CK(cudaMemcpy(m->d_perm, m->node_new_of_old.data(), N * sizeof(int), cudaMemcpyHostToDevice));
@@ -1294,17 +1314,22 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   }
   if (target && nb) {
     if (mapped_targets) {
-      // the scatter reads the targets over the host link on a side stream,
-      // beside the element-force kernel; the node update (the only reader of
-      // the prescribed-value table) waits for it
+      // page-locked targets are copied by a copy engine on a side stream
+      // beside the element-force kernel; the node update reads that device
+      // copy directly, and the per-node table is brought up to date from it
+      // on the side stream for later calls
       if (!m->io_stream) {
         CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&m->io_done, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&m->io_copied, cudaEventDisableTiming));
       }
+      if (!m->d_tgt_stage) CK(cudaMalloc(&m->d_tgt_stage, nb * sizeof(double)));
       CK(cudaEventRecord(m->io_before, st));
       CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
-      CK(launch_bc_targets(static_cast<const double*>(mt), m->d_bc_flat, (int)nb, m->d_bct, m->io_stream));
+      CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
+      CK(cudaEventRecord(m->io_copied, m->io_stream));
+      CK(launch_bc_targets(m->d_tgt_stage, m->d_bc_flat, (int)nb, m->d_bct, m->io_stream));
       CK(cudaEventRecord(m->io_done, m->io_stream));
     } else {
       const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
@@ -1321,8 +1346,11 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   }
   if (mapped_targets) {
     CK(launch_force_any(m, 1, st));
-    CK(cudaStreamWaitEvent(st, m->io_done, 0));
-    CK(launch_node(NODE_UPDATE, m->cmp, node_args(m), st));
+    CK(cudaStreamWaitEvent(st, m->io_copied, 0));
+    NodeArgs na = node_args(m);
+    na.tgt = m->d_tgt_stage;
+    CK(launch_node(NODE_UPDATE, m->cmp, na, st));
+    CK(cudaStreamWaitEvent(st, m->io_done, 0));  // the table update, before the call's synchronisation
   } else {
     CK(launch_step(m, st, NODE_UPDATE));
   }

@@ -112,6 +112,12 @@ struct NodeArgs {
   const float* bm1_node;  // grouped meshes with damping: per-node b - 1 (else nullptr)
   DevState* st;           // ramp value (read), error flags (written)
   const AdrState* adr;    // adaptive modes: damping in use (else nullptr)
+  // NODE_UPDATE only: prescribed targets read from a device copy of the
+  // caller's FP64 array (entry bc_entry[b].{x,y,z} of prescribed-node row b,
+  // -1 if that component is free; .w the component mask) instead of the
+  // per-node table; a non-finite entry keeps the table's value.  nullptr: table
+  const double* tgt;
+  const int4* bc_entry;
   double* rq_partials;    // NODE_ADR_RQ: 4 sums per block (D.dF, D^2 / a_i, D^2, max |D|)
   double4* usnap;         // NODE_ADR_RQ: U of the previous check (FP64, hi + lo); F - R of it in fout
   int N;

@@ -330,10 +330,28 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       }
       int mask = 0;
       if (bc >= 0) {
-        const float4 t = __ldg(a.bct + bc);
-        mask = __float_as_int(t.w);
+        float tv[3];
+        if (MODE == NODE_UPDATE && a.tgt) {
+          const int4 en = __ldg(a.bc_entry + bc);
+          mask = en.w;
+          const int ek[3] = {en.x, en.y, en.z};
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const double v = ek[q] >= 0 ? __ldg(a.tgt + ek[q]) : 0.0;
+            tv[q] = (float)v;
+            if (!isfinite(v)) {  // not applied: the table keeps the previous target
+              const float4 t = __ldg(a.bct + bc);
+              tv[q] = q == 0 ? t.x : (q == 1 ? t.y : t.z);
+            }
+          }
+        } else {
+          const float4 t = __ldg(a.bct + bc);
+          mask = __float_as_int(t.w);
+          tv[0] = t.x;
+          tv[1] = t.y;
+          tv[2] = t.z;
+        }
         const float rs = a.st->ramp_s;
-        const float tv[3] = {t.x, t.y, t.z};
 #pragma unroll
         for (int q = 0; q < 3; ++q)
           if (mask & (1 << q)) {
