@@ -347,17 +347,16 @@ dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
  * order into U_out (host, n_nodes * 3 values, doubles when out_f64 = 1, floats
  * when out_f64 = 0; NULL skips the read-back).  Everything is enqueued on
  * `stream` and the call synchronises once, at its end, so the caller may
- * reuse both buffers on return.  Page-locked (cudaHostAlloc /
- * cudaHostRegister), 8-byte aligned buffers are read and written by the
- * library's kernels through their device mappings; other host memory goes
- * through one copy each way.  The FP32 output holds U + low part rounded once
+ * reuse both buffers on return.  The targets are copied to the device on a
+ * side stream while the element forces are computed (page-locked buffers by
+ * a copy engine directly); a page-locked, 8-byte aligned U_out is written by
+ * the library's kernel through its device mapping, other host memory
+ * through one copy.  The FP32 output holds U + low part rounded once
  * (exactly U in the plain FP32 precision mode).
  * Errors: as dj_step; device-side flags (inverted element, non-finite value)
- * are reported by this call.  A non-finite target: with pageable targets
- * DJ_ERR_INVALID_ARG before anything runs; with page-locked targets (checked
- * on the host while the step runs) that entry is not applied -- the DOF keeps
- * its previous target for the step -- and the call returns
- * DJ_ERR_INVALID_ARG after the step. */
+ * are reported by this call.  A non-finite target is detected on the device:
+ * that entry is not applied -- the DOF keeps its previous target for the
+ * step -- and the call returns DJ_ERR_INVALID_ARG after the step. */
 dj_status dj_step_host(dj_mesh* mesh, const double* targets, void* U_out, int out_f64, void* stream);
 
 /* Current displacements into device memory, n_nodes * 3 floats in caller

@@ -110,6 +110,7 @@ struct dj_mesh {
   cudaEvent_t io_before = nullptr, io_done = nullptr, io_copied = nullptr;
   int4* d_bc_entry = nullptr;    // per prescribed-node row: target entries of x, y, z (-1: free), mask
   double* d_tgt_stage = nullptr; // device copy of the caller's targets (allocated on first use)
+  bool targets_on_device = false;  // bc_target lags d_tgt_stage (dj_step_host)
   DevState* h_state_map = nullptr;  // device address of the page-locked state copy
   cudaGraphExec_t run_exec = nullptr;
   int run_chunk = 0;
@@ -294,7 +295,7 @@ dj_status read_state(dj_mesh* m, cudaStream_t s) {
 
 dj_status check_flags(dj_mesh* m) {
   const DevState& st = *m->h_state;
-  if (st.err_flags) {
+  if (st.err_flags & ~ERR_BAD_TARGET) {
     const int be = st.bad_elem;
     const int caller = (be >= 0 && be < (int)m->E) ? m->elem_old_of_new[be] : -1;
     if (st.err_flags & ERR_INVERTED)
@@ -464,6 +465,25 @@ dj_status capture(dj_mesh* m, cudaGraphExec_t* out, F body) {
 
 }  // namespace
 
+namespace {
+// After dj_step_host the host copy of the targets lags the device copy: bring
+// it up to date (non-finite entries, which were not applied, keep their value).
+dj_status sync_host_targets(dj_mesh* m) {
+  if (!m->targets_on_device || !m->d_tgt_stage) {
+    m->targets_on_device = false;
+    return DJ_OK;
+  }
+  const size_t nb = m->bc_dof.size();
+  std::vector<double> t(nb);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(t.data(), m->d_tgt_stage, nb * sizeof(double), cudaMemcpyDeviceToHost));
+  for (size_t k = 0; k < nb; ++k)
+    if (std::isfinite(t[k])) m->bc_target[k] = t[k];
+  m->targets_on_device = false;
+  return DJ_OK;
+}
+}  // namespace
+
 namespace dj {
 // accessors for the warm-start layer (warmstart.cu)
 const std::vector<long long>& mesh_bc_dofs(const dj_mesh* m) { return m->bc_dof; }
@@ -598,6 +618,7 @@ dj_status dj_mesh_set_bcs(dj_mesh* m, const long long* dof, const double* target
   }
   m->bc_dof.assign(dof, dof + n);
   m->bc_target.assign(target, target + n);
+  m->targets_on_device = false;
   m->precomputed = false;
   return DJ_OK;
 }
@@ -645,6 +666,10 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
   const Range range("dj_precompute");
   if (!m) return DJ_ERR_INVALID_ARG;
   if (!m->materials_set) return fail(m, DJ_ERR_INVALID_ARG, "call dj_mesh_set_materials first");
+  if (m->precomputed) {
+    dj_status ts = sync_host_targets(m);
+    if (ts) return ts;
+  }
   dj_params prm;
   if (p)
     prm = *p;
@@ -1242,6 +1267,7 @@ dj_status dj_mesh_update_bc_targets(dj_mesh* m, const double* target) {
   for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
   if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
   std::memcpy(m->bc_target.data(), target, nb * sizeof(double));
+  m->targets_on_device = false;
   if (!m->precomputed) return DJ_OK;
   CK(cudaSetDevice(m->device));
   if (m->n_bc_nodes) {
@@ -1296,55 +1322,34 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   if (out_f64 != 0 && out_f64 != 1) return fail(m, DJ_ERR_INVALID_ARG, "out_f64 must be 0 or 1");
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nb = m->bc_dof.size();
-  // page-locked targets: the scatter kernel reads them through the device
-  // mapping and the host's own pass over them (finiteness, the host copy)
-  // runs while the step executes; a non-finite target is not applied (the
-  // kernel keeps the previous one) and the call reports it after the step
-  const void* mt = (target && nb) ? mapped_host(target) : nullptr;
-  const bool mapped_targets = mt != nullptr;
   // the device state reaches the host through the mapping of its page-locked
   // copy, written by the last kernel of the call (no separate copy)
   if (!m->h_state_map) CK(cudaHostGetDevicePointer((void**)&m->h_state_map, m->h_state, 0));
   DevState* st_map = m->h_state_map;
-  if (target && nb && !mapped_targets) {
-    bool finite = true;
-    for (size_t k = 0; k < nb; ++k) finite &= std::isfinite(target[k]);
-    if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target");
-    std::memcpy(m->bc_target.data(), target, nb * sizeof(double));
-  }
-  if (target && nb) {
-    if (mapped_targets) {
-      // page-locked targets are copied by a copy engine on a side stream
-      // beside the element-force kernel; the node update reads that device
-      // copy directly, and the per-node table is brought up to date from it
-      // on the side stream for later calls
-      if (!m->io_stream) {
-        CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&m->io_done, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&m->io_copied, cudaEventDisableTiming));
-      }
-      if (!m->d_tgt_stage) CK(cudaMalloc(&m->d_tgt_stage, nb * sizeof(double)));
-      CK(cudaEventRecord(m->io_before, st));
-      CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
-      CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
-      CK(cudaEventRecord(m->io_copied, m->io_stream));
-      CK(launch_bc_targets(m->d_tgt_stage, m->d_bc_flat, (int)nb, m->d_bct, m->io_stream));
-      CK(cudaEventRecord(m->io_done, m->io_stream));
-    } else {
-      const size_t bytes = (size_t)m->n_bc_nodes * sizeof(float4);
-      if (!m->h_bct_pinned) {
-        CK(cudaMallocHost((void**)&m->h_bct_pinned, bytes));
-        std::memcpy(m->h_bct_pinned, m->h_bct.data(), bytes);
-      }
-      // the staging table is free: every call ends with a synchronisation
-      float* pin = reinterpret_cast<float*>(m->h_bct_pinned);
-      const int* flat = m->bc_flat_of_entry.data();
-      for (size_t k = 0; k < nb; ++k) pin[flat[k]] = (float)target[k];
-      CK(cudaMemcpyAsync(m->d_bct, m->h_bct_pinned, bytes, cudaMemcpyHostToDevice, st));
+  const bool with_targets = target && nb;
+  if (with_targets) {
+    // the targets are copied to the device on a side stream beside the
+    // element-force kernel (a copy engine; page-locked buffers directly,
+    // others through the driver's staging); the node update reads that copy,
+    // and the per-node table is brought up to date from it on the side
+    // stream.  Non-finite entries are found on the device: not applied (the
+    // previous target stays) and reported after the step.  The host's own
+    // copy of the targets is refreshed from the device copy when it is next
+    // needed (sync_host_targets).
+    if (!m->io_stream) {
+      CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&m->io_done, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&m->io_copied, cudaEventDisableTiming));
     }
-  }
-  if (mapped_targets) {
+    if (!m->d_tgt_stage) CK(cudaMalloc(&m->d_tgt_stage, nb * sizeof(double)));
+    CK(cudaEventRecord(m->io_before, st));
+    CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
+    CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
+    CK(cudaEventRecord(m->io_copied, m->io_stream));
+    CK(launch_bc_targets(m->d_tgt_stage, m->d_bc_flat, (int)nb, m->d_bct, m->io_stream, &m->d_state->err_flags));
+    CK(cudaEventRecord(m->io_done, m->io_stream));
+    m->targets_on_device = true;
     CK(launch_force_any(m, 1, st));
     CK(cudaStreamWaitEvent(st, m->io_copied, 0));
     NodeArgs na = node_args(m);
@@ -1352,7 +1357,7 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
     CK(launch_node(NODE_UPDATE, m->cmp, na, st));
     CK(cudaStreamWaitEvent(st, m->io_done, 0));  // the table update, before the call's synchronisation
   } else {
-    CK(launch_step(m, st, NODE_UPDATE));
+  CK(launch_step(m, st, NODE_UPDATE));
   }
   if (U_out) {
     const long long N = m->N;
@@ -1372,20 +1377,17 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   } else {
     CK(launch_copy_state(m->d_state, st_map, st));
   }
-  bool finite = true;
-  if (mapped_targets) {  // overlaps the step
-    for (size_t k = 0; k < nb; ++k) {
-      if (std::isfinite(target[k]))
-        m->bc_target[k] = target[k];
-      else
-        finite = false;
-    }
-  }
   CK(cudaStreamSynchronize(st));  // the only synchronisation of the call
-  s = check_flags(m);
-  if (s) return s;
-  if (!finite) return fail(m, DJ_ERR_INVALID_ARG, "non-finite target (not applied; the step kept its previous value)");
-  return DJ_OK;
+  if (m->h_state->err_flags & ERR_BAD_TARGET) {
+    // not applied: clear the record so that later calls do not report it again
+    const int keep = m->h_state->err_flags & ~ERR_BAD_TARGET;
+    CK(cudaMemcpy(&m->d_state->err_flags, &keep, sizeof(int), cudaMemcpyHostToDevice));
+    m->h_state->err_flags = keep;
+    s = check_flags(m);
+    if (s) return s;
+    return fail(m, DJ_ERR_INVALID_ARG, "non-finite target (not applied; the step kept its previous value)");
+  }
+  return check_flags(m);
 }
 
 dj_status dj_step(dj_mesh* m, void* stream) {
@@ -2169,6 +2171,10 @@ dj_status dj_batch_create(dj_mesh* const* inst, int n, dj_batch** out) {
   if (!inst || n <= 0) return DJ_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i)
     if (!inst[i] || !inst[i]->materials_set) return DJ_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    const dj_status ts = sync_host_targets(inst[i]);
+    if (ts) return ts;
+  }
   dj_batch* b = new (std::nothrow) dj_batch();
   if (!b) return DJ_ERR_OOM;
   b->n = n;

@@ -39,14 +39,16 @@ enum { KG_CP = 0, KG_KV = 1, KG_COMMON = 2 };
 struct DevState {
   long long step;     // n of the current displacement U^n
   float ramp_s;       // s(tau) for the step being computed (U^{n+1})
-  int err_flags;      // bit 0: det tJ <= 0, bit 1: non-finite value, bit 2: wait timeout
+  int err_flags;      // bit 0: det tJ <= 0, bit 1: non-finite value, bit 2: wait timeout, bit 3: bad target
   int bad_elem;       // smallest internal element id with det tJ <= 0
   int bad_node;       // smallest internal node id with a non-finite force or displacement
   double resid_num2;  // sum of squared residual over free DOFs
   double resid_den2;  // sum of squared reaction over prescribed DOFs
 };
 
-enum { ERR_INVERTED = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4 };
+// ERR_BAD_TARGET: a non-finite prescribed target was handed to dj_step_host
+// and not applied (reported and cleared by that call)
+enum { ERR_INVERTED = 1, ERR_NONFINITE = 2, ERR_TIMEOUT = 4, ERR_BAD_TARGET = 8 };
 
 struct ForceArgs {
   const int4* conn;      // tet: E_pad int4; hex: 2 E_pad int4 (nodes 0-3, 4-7)

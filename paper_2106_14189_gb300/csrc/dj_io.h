@@ -11,7 +11,9 @@ namespace dj {
 // x, y, z targets, w = component mask).  flat[k] < 4 * (table rows) and
 // flat[k] % 4 < 3 for every k (the host builds and checks the list); n <= 0
 // launches nothing.  A non-finite target[k] is skipped (the entry keeps its
-// previous value); the host reports it.
-cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s);
+// previous value) and, when bad_flags is given (a device int, e.g. the
+// mesh state's error flags), ERR_BAD_TARGET is or-ed into it.
+cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s,
+                              int* bad_flags = nullptr);
 
 }  // namespace dj

@@ -353,11 +353,14 @@ __global__ void from_caller_order_kernel(const float* __restrict__ src, const in
 // entry k of the caller's FP64 array goes to float index flat[k] of the table
 // (4 floats per prescribed node: x, y, z targets and the component mask)
 __global__ void bc_targets_kernel(const double* __restrict__ target, const int* __restrict__ flat, int n,
-                                  float* __restrict__ table) {
+                                  float* __restrict__ table, int* bad_flags) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) {
     const double v = target[k];
-    if (isfinite(v)) table[__ldg(flat + k)] = (float)v;  // a non-finite target keeps the previous one
+    if (isfinite(v))
+      table[__ldg(flat + k)] = (float)v;
+    else if (bad_flags)  // a non-finite target keeps the previous one
+      atomicOr(bad_flags, ERR_BAD_TARGET);
   }
 }
 
@@ -430,9 +433,10 @@ cudaError_t launch_to_caller_order_f32(const float4* U, const float4* Ulo, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s) {
+cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s,
+                              int* bad_flags) {
   if (n <= 0) return cudaSuccess;
-  bc_targets_kernel<<<(n + 255) / 256, 256, 0, s>>>(target, flat, n, reinterpret_cast<float*>(table));
+  bc_targets_kernel<<<(n + 255) / 256, 256, 0, s>>>(target, flat, n, reinterpret_cast<float*>(table), bad_flags);
   return cudaGetLastError();
 }
 

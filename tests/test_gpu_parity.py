@@ -616,9 +616,9 @@ def test_step_host_matches_separate_calls(B, prec):
 
 
 def test_step_host_non_finite_pinned_target_is_not_applied(B):
-    """A NaN among page-locked targets: the step runs with that DOF's previous
-    target, the other targets are applied, and the call reports
-    DJ_ERR_INVALID_ARG; pageable targets are refused before the step."""
+    """A NaN among the targets (page-locked or pageable): the step runs with
+    that DOF's previous target, the other targets are applied, and the call
+    reports DJ_ERR_INVALID_ARG; the next call with finite targets succeeds."""
     torch = pytest.importorskip("torch")
     p = W.cube_shear(W.TET4, 4, n_steps=10)
     p.ramp_steps = 0
@@ -642,3 +642,7 @@ def test_step_host_non_finite_pinned_target_is_not_applied(B):
         assert np.allclose(after[others], 2 * base[others], rtol=1e-6)
         with pytest.raises(B.DJError):
             B.dj_step_host(m.h, np.full(base.size, np.nan), U)
+        assert np.array_equal(U.reshape(-1)[p.bc_dof], after)  # nothing applied
+        tgt[:] = 3 * base
+        B.dj_step_host(m.h, tgt, U)
+        assert np.allclose(U.reshape(-1)[p.bc_dof][np.abs(base) > 0], 3 * base[np.abs(base) > 0], rtol=1e-6)
