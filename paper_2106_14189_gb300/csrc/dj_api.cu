@@ -1343,14 +1343,16 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
       CK(cudaEventCreateWithFlags(&m->io_copied, cudaEventDisableTiming));
     }
     if (!m->d_tgt_stage) CK(cudaMalloc(&m->d_tgt_stage, nb * sizeof(double)));
+    // the element forces go first (they do not read the targets); the side
+    // stream's copy follows whatever the stream held before this call
     CK(cudaEventRecord(m->io_before, st));
+    CK(launch_force_any(m, 1, st));
     CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
     CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
     CK(cudaEventRecord(m->io_copied, m->io_stream));
     CK(launch_bc_targets(m->d_tgt_stage, m->d_bc_flat, (int)nb, m->d_bct, m->io_stream, &m->d_state->err_flags));
     CK(cudaEventRecord(m->io_done, m->io_stream));
     m->targets_on_device = true;
-    CK(launch_force_any(m, 1, st));
     CK(cudaStreamWaitEvent(st, m->io_copied, 0));
     NodeArgs na = node_args(m);
     na.tgt = m->d_tgt_stage;
