@@ -1328,14 +1328,14 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   DevState* st_map = m->h_state_map;
   const bool with_targets = target && nb;
   if (with_targets) {
-    // the targets are copied to the device on a side stream beside the
-    // element-force kernel (a copy engine; page-locked buffers directly,
-    // others through the driver's staging); the node update reads that copy,
-    // and the per-node table is brought up to date from it on the side
-    // stream.  Non-finite entries are found on the device: not applied (the
-    // previous target stays) and reported after the step.  The host's own
-    // copy of the targets is refreshed from the device copy when it is next
-    // needed (sync_host_targets).
+    // The node update reads this step's targets itself: page-locked arrays
+    // through their device mapping (no copy, no cross-stream wait, so the
+    // update keeps its programmatic launch behind the element forces), other
+    // host memory from a device copy made ahead of the step.  The per-node
+    // table is brought up to date on a side stream for later calls; non-finite
+    // entries are not applied (the previous target stays) and are reported
+    // after the step.  The host's own copy of the targets is refreshed from the
+    // device when it is next needed (sync_host_targets).
     if (!m->io_stream) {
       CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
@@ -1343,23 +1343,26 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
       CK(cudaEventCreateWithFlags(&m->io_copied, cudaEventDisableTiming));
     }
     if (!m->d_tgt_stage) CK(cudaMalloc(&m->d_tgt_stage, nb * sizeof(double)));
-    // the element forces go first (they do not read the targets); the side
-    // stream's copy follows whatever the stream held before this call
+    const double* src = static_cast<const double*>(mapped_host(target));
+    if (!src) {
+      CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, st));
+      src = m->d_tgt_stage;
+    }
     CK(cudaEventRecord(m->io_before, st));
     CK(launch_force_any(m, 1, st));
+    NodeArgs na = node_args(m);
+    na.tgt = src;
+    CK(launch_node(NODE_UPDATE, m->cmp, na, st));
     CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
-    CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
-    CK(cudaEventRecord(m->io_copied, m->io_stream));
+    if (src != m->d_tgt_stage)  // keep a device copy for sync_host_targets
+      CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
     CK(launch_bc_targets(m->d_tgt_stage, m->d_bc_flat, (int)nb, m->d_bct, m->io_stream, &m->d_state->err_flags));
     CK(cudaEventRecord(m->io_done, m->io_stream));
     m->targets_on_device = true;
-    CK(cudaStreamWaitEvent(st, m->io_copied, 0));
-    NodeArgs na = node_args(m);
-    na.tgt = m->d_tgt_stage;
-    CK(launch_node(NODE_UPDATE, m->cmp, na, st));
-    CK(cudaStreamWaitEvent(st, m->io_done, 0));  // the table update, before the call's synchronisation
+    // the table update (and its non-finite flag) lands before the state is read
+    CK(cudaStreamWaitEvent(st, m->io_done, 0));
   } else {
-  CK(launch_step(m, st, NODE_UPDATE));
+    CK(launch_step(m, st, NODE_UPDATE));
   }
   if (U_out) {
     const long long N = m->N;

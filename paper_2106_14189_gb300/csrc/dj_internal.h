@@ -114,10 +114,11 @@ struct NodeArgs {
   const float* bm1_node;  // grouped meshes with damping: per-node b - 1 (else nullptr)
   DevState* st;           // ramp value (read), error flags (written)
   const AdrState* adr;    // adaptive modes: damping in use (else nullptr)
-  // NODE_UPDATE only: prescribed targets read from a device copy of the
-  // caller's FP64 array (entry bc_entry[b].{x,y,z} of prescribed-node row b,
-  // -1 if that component is free; .w the component mask) instead of the
-  // per-node table; a non-finite entry keeps the table's value.  nullptr: table
+  // NODE_UPDATE only: prescribed targets read from the caller's FP64 array
+  // (a device copy, or page-locked host memory through its device mapping;
+  // entry bc_entry[b].{x,y,z} of prescribed-node row b, -1 if that component
+  // is free; .w the component mask) instead of the per-node table; a
+  // non-finite entry keeps the table's value.  nullptr: the table
   const double* tgt;
   const int4* bc_entry;
   double* rq_partials;    // NODE_ADR_RQ: 4 sums per block (D.dF, D^2 / a_i, D^2, max |D|)

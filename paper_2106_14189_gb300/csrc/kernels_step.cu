@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
           const int ek[3] = {en.x, en.y, en.z};
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            const double v = ek[q] >= 0 ? __ldg(a.tgt + ek[q]) : 0.0;
+            const double v = ek[q] >= 0 ? a.tgt[ek[q]] : 0.0;  // may be host memory read through its mapping
             tv[q] = (float)v;
             if (!isfinite(v)) {  // not applied: the table keeps the previous target
               const float4 t = __ldg(a.bct + bc);
