@@ -1328,14 +1328,15 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   DevState* st_map = m->h_state_map;
   const bool with_targets = target && nb;
   if (with_targets) {
-    // The node update reads this step's targets itself: page-locked arrays
-    // through their device mapping (no copy, no cross-stream wait, so the
-    // update keeps its programmatic launch behind the element forces), other
-    // host memory from a device copy made ahead of the step.  The per-node
-    // table is brought up to date on a side stream for later calls; non-finite
-    // entries are not applied (the previous target stays) and are reported
-    // after the step.  The host's own copy of the targets is refreshed from the
-    // device when it is next needed (sync_host_targets).
+    // The node update reads this step's targets itself and stores them into
+    // its prescribed-node rows of the table: page-locked arrays through their
+    // device mapping (no copy, no wait on another stream, so the update keeps
+    // its programmatic launch behind the element forces), other host memory
+    // from a device copy made ahead of the step.  Non-finite entries are not
+    // applied (the previous target stays) and are reported after the step.
+    // A device copy of the targets, for the host's own copy of them, is made
+    // by a copy engine on a side stream (sync_host_targets reads it when the
+    // host copy is next needed).
     if (!m->io_stream) {
       CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
       CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
@@ -1347,20 +1348,20 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
     if (!src) {
       CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, st));
       src = m->d_tgt_stage;
+    } else {
+      CK(cudaEventRecord(m->io_before, st));
     }
-    CK(cudaEventRecord(m->io_before, st));
     CK(launch_force_any(m, 1, st));
     NodeArgs na = node_args(m);
     na.tgt = src;
     CK(launch_node(NODE_UPDATE, m->cmp, na, st));
-    CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
-    if (src != m->d_tgt_stage)  // keep a device copy for sync_host_targets
+    if (src != m->d_tgt_stage) {
+      CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
       CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
-    CK(launch_bc_targets(m->d_tgt_stage, m->d_bc_flat, (int)nb, m->d_bct, m->io_stream, &m->d_state->err_flags));
-    CK(cudaEventRecord(m->io_done, m->io_stream));
+      CK(cudaEventRecord(m->io_done, m->io_stream));
+      CK(cudaStreamWaitEvent(st, m->io_done, 0));  // the device copy lands before the call returns
+    }
     m->targets_on_device = true;
-    // the table update (and its non-finite flag) lands before the state is read
-    CK(cudaStreamWaitEvent(st, m->io_done, 0));
   } else {
     CK(launch_step(m, st, NODE_UPDATE));
   }

@@ -269,6 +269,9 @@ __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f64_kernel(cons
                                                                            const int* __restrict__ perm, int N,
                                                                            double* out, const DevState* st,
                                                                            DevState* st_out) {
+  // launched behind the node update with a programmatic dependency: U only
+  // after that kernel has completed (at once for an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ __align__(16) double sv[3 * kOrderThreads];
   if (st_out && blockIdx.x == 0 && threadIdx.x == 0) *st_out = *st;
   const int i0 = blockIdx.x * kOrderThreads;
@@ -306,6 +309,9 @@ __global__ void __launch_bounds__(kOrderThreads) to_caller_order_f32_kernel(cons
                                                                            const int* __restrict__ perm, int N,
                                                                            float* out, const DevState* st,
                                                                            DevState* st_out) {
+  // launched behind the node update with a programmatic dependency: U only
+  // after that kernel has completed (at once for an ordinary launch)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   __shared__ __align__(16) float sv[3 * kOrderThreads];
   if (st_out && blockIdx.x == 0 && threadIdx.x == 0) *st_out = *st;
   const int i0 = blockIdx.x * kOrderThreads;
@@ -417,8 +423,8 @@ cudaError_t launch_to_caller_order(const float4* U, const int* node_new_of_old, 
 cudaError_t launch_to_caller_order_f64(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
                                        double* out, cudaStream_t s, const DevState* st, DevState* st_out) {
   const int t = kOrderThreads;
-  to_caller_order_f64_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out, st, st_out);
-  return cudaGetLastError();
+  return launch_pdl(to_caller_order_f64_kernel, dim3((N + t - 1) / t), dim3(t), 0, s, U, Ulo, node_new_of_old, N,
+                    out, st, st_out);
 }
 
 cudaError_t launch_copy_state(const DevState* st, DevState* st_out, cudaStream_t s) {
@@ -429,8 +435,8 @@ cudaError_t launch_copy_state(const DevState* st, DevState* st_out, cudaStream_t
 cudaError_t launch_to_caller_order_f32(const float4* U, const float4* Ulo, const int* node_new_of_old, int N,
                                        float* out, cudaStream_t s, const DevState* st, DevState* st_out) {
   const int t = kOrderThreads;
-  to_caller_order_f32_kernel<<<(N + t - 1) / t, t, 0, s>>>(U, Ulo, node_new_of_old, N, out, st, st_out);
-  return cudaGetLastError();
+  return launch_pdl(to_caller_order_f32_kernel, dim3((N + t - 1) / t), dim3(t), 0, s, U, Ulo, node_new_of_old, N,
+                    out, st, st_out);
 }
 
 cudaError_t launch_bc_targets(const double* target, const int* flat, int n, float4* table, cudaStream_t s,

@@ -332,18 +332,29 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       if (bc >= 0) {
         float tv[3];
         if (MODE == NODE_UPDATE && a.tgt) {
+          // this step's targets from the caller's array (host memory through
+          // its mapping, or a device copy); the node's table row takes them
+          // for later steps.  A non-finite entry is not applied: the row's
+          // previous target stays and the step records ERR_BAD_TARGET.
           const int4 en = __ldg(a.bc_entry + bc);
           mask = en.w;
           const int ek[3] = {en.x, en.y, en.z};
+          float4 row = a.bct[bc];
+          float* rv[3] = {&row.x, &row.y, &row.z};
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            const double v = ek[q] >= 0 ? a.tgt[ek[q]] : 0.0;  // may be host memory read through its mapping
-            tv[q] = (float)v;
-            if (!isfinite(v)) {  // not applied: the table keeps the previous target
-              const float4 t = __ldg(a.bct + bc);
-              tv[q] = q == 0 ? t.x : (q == 1 ? t.y : t.z);
+            tv[q] = *rv[q];
+            if (ek[q] >= 0) {
+              const double v = a.tgt[ek[q]];
+              if (isfinite(v)) {
+                tv[q] = (float)v;
+                *rv[q] = tv[q];
+              } else {
+                atomicOr(&a.st->err_flags, ERR_BAD_TARGET);
+              }
             }
           }
+          const_cast<float4*>(a.bct)[bc] = row;
         } else {
           const float4 t = __ldg(a.bct + bc);
           mask = __float_as_int(t.w);
