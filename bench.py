@@ -901,11 +901,14 @@ def main():
         for name, U_host in (("f32", U32_t.numpy()), ("f64", U64_t.numpy())):
             n_e2e = args.e2e_steps
             t_e2e = 0.0
+            # the binding's form for a host-driven loop: buffers bound once,
+            # the caller refills the targets in place before every call
+            host_step = B.HostStep(mesh, targets, U_host, stream)
             for k in range(n_e2e + 3):
                 l2_flush()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                B.dj_step_host(mesh.h, targets, U_host, stream)
+                host_step()
                 if k >= 3:  # three untimed calls first
                     t_e2e += time.perf_counter() - t0
             val, _ = replica_throughput(E * n_e2e, t_e2e * 1e3, dist, device="cuda")
@@ -916,7 +919,8 @@ def main():
                          "h2d_bytes_per_step": int(targets.nbytes),
                          "d2h_bytes_per_step": int(U_host.nbytes + 48), "steps": n_e2e}
         e2e = dict(res["f32"])
-        e2e["call"] = "dj_step_host (targets in, one step, FP32 displacements out, one synchronisation)"
+        e2e["call"] = ("dj_step_host through binding.HostStep (targets in, one step, FP32 displacements out, "
+                       "one synchronisation)")
         e2e["f64_output"] = res["f64"]
 
     # secondary workload: the hex8 cube (same metric)

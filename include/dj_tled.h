@@ -347,9 +347,11 @@ dj_status dj_get_displacements(dj_mesh* mesh, double* U_out);
  * order into U_out (host, n_nodes * 3 values, doubles when out_f64 = 1, floats
  * when out_f64 = 0; NULL skips the read-back).  Everything is enqueued on
  * `stream` and the call synchronises once, at its end, so the caller may
- * reuse both buffers on return.  The targets are copied to the device on a
- * side stream while the element forces are computed (page-locked buffers by
- * a copy engine directly); a page-locked, 8-byte aligned U_out is written by
+ * reuse both buffers on return.  Page-locked targets are read by the
+ * element-force kernel through their device mapping (coalesced, beside its
+ * own work) into a device copy that the update kernel applies; other host
+ * memory is copied to the device before the step.  A page-locked, 8-byte
+ * aligned U_out is written by
  * the library's kernel through its device mapping, other host memory
  * through one copy.  The FP32 output holds U + low part rounded once
  * (exactly U in the plain FP32 precision mode).

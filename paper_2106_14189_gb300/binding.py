@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from typing import Optional
 
 import numpy as np
@@ -207,7 +208,7 @@ def lib():
         "dj_batch_autotune": (C.c_int, [_P, C.c_int, _P]),
         "dj_symmetric_eigen": (C.c_int, [_D, C.c_int, _D, _D]),
         "dj_mlp_set_precision": (C.c_int, [_P, C.c_int]),
-        "dj_step_host": (C.c_int, [_P, _D, _P, C.c_int, _P]),
+        "dj_step_host": (C.c_int, [_P, _P, _P, C.c_int, _P]),
         "dj_ws_params_default": (None, [C.POINTER(dj_ws_params)]),
         "dj_ws_train": (C.c_int, [_P, _D, C.c_int, C.c_double, C.c_longlong, C.POINTER(dj_ws_params),
                                   C.POINTER(_P), _P]),
@@ -880,14 +881,85 @@ def dj_ws_destroy(ws):
     lib().dj_ws_destroy(ws)
 
 
+def _addr(a: np.ndarray) -> int:
+    """Address of an array's first element (the cheap route for writable
+    buffers; the array interface otherwise)."""
+    try:
+        return C.addressof(C.c_char.from_buffer(a))
+    except (TypeError, ValueError, BufferError):
+        return a.__array_interface__["data"][0]
+
+
+_F64, _F32 = np.dtype(np.float64), np.dtype(np.float32)
+_HOST_ADDR = {}  # id(array) -> (weak reference, address) of recent host buffers
+
+
+def _host_addr(a: np.ndarray) -> int:
+    """_addr with a small cache for buffers passed again and again (a host
+    loop's targets and output); a weak reference tells a live entry from a
+    reused id."""
+    e = _HOST_ADDR.get(id(a))
+    if e is not None and e[0]() is a:
+        return e[1]
+    addr = _addr(a)
+    if len(_HOST_ADDR) >= 16:
+        _HOST_ADDR.clear()
+    _HOST_ADDR[id(a)] = (weakref.ref(a), addr)
+    return addr
+
+
 def dj_step_host(h, targets, U_out, stream=None):
     """One step with host input and output (include/dj_tled.h): targets (n_bc
     float64 or None), U_out a C-contiguous float64 or float32 array of
-    n_nodes x 3 (or None)."""
-    t = None if targets is None else _f64(targets)
-    if U_out is not None and (not U_out.flags.c_contiguous or U_out.dtype not in (np.float64, np.float32)):
-        raise ValueError("U_out must be a C-contiguous float64 or float32 array")
-    _check(lib().dj_step_host(h, _dptr(t), None if U_out is None else U_out.ctypes.data_as(_P),
-                              1 if U_out is None or U_out.dtype == np.float64 else 0, _stream(stream)),
-           "dj_step_host", h)
+    n_nodes x 3 (or None).  Called once per step by a host-driven loop, so
+    the marshalling takes the cheap routes (no ctypes pointer objects, cached
+    addresses).  HostStep binds the buffers once and validates their sizes."""
+    ta = None
+    if targets is not None:
+        if not (type(targets) is np.ndarray and targets.dtype is _F64 and targets.flags.c_contiguous):
+            targets = _f64(targets)
+        ta = _host_addr(targets) if targets.size else None
+    ua, out_f64 = None, 1
+    if U_out is not None:
+        dt = U_out.dtype
+        if not U_out.flags.c_contiguous or (dt is not _F32 and dt is not _F64 and dt not in (_F32, _F64)):
+            raise ValueError("U_out must be a C-contiguous float64 or float32 array")
+        out_f64 = 0 if dt == _F32 else 1
+        ua = _host_addr(U_out) if U_out.size else None
+    st = lib().dj_step_host(h, ta, ua, out_f64, _stream(stream))
+    if st != DJ_OK:
+        _check(st, "dj_step_host", h)
     return U_out
+
+
+class HostStep:
+    """dj_step_host bound to a mesh, a target array and an output array (the
+    form for a loop that drives the solver from the host every step: the
+    caller refills `targets` in place, calls the object, reads `U_out`).
+    Types, layout and sizes are checked once, here; each call only passes
+    the addresses.  Page-locked arrays (e.g. numpy views of pinned torch
+    tensors) take the library's mapped paths."""
+
+    def __init__(self, mesh, targets: Optional[np.ndarray], U_out: Optional[np.ndarray], stream=None):
+        info = mesh.info()
+        if targets is not None:
+            if not (isinstance(targets, np.ndarray) and targets.dtype == _F64 and targets.flags.c_contiguous):
+                raise ValueError("targets must be a C-contiguous float64 array (it is refilled in place)")
+            if targets.size != info.n_bc_dofs:
+                raise ValueError(f"targets has {targets.size} values, the mesh {info.n_bc_dofs} prescribed DOFs")
+        if U_out is not None:
+            if not (isinstance(U_out, np.ndarray) and U_out.flags.c_contiguous and U_out.dtype in (_F32, _F64)):
+                raise ValueError("U_out must be a C-contiguous float64 or float32 array")
+            if U_out.size != 3 * info.n_nodes:
+                raise ValueError(f"U_out has {U_out.size} values, the mesh 3 x {info.n_nodes}")
+        self.mesh, self.targets, self.U_out = mesh, targets, U_out  # held: the addresses stay valid
+        self._args = (mesh.h, _addr(targets) if targets is not None and targets.size else None,
+                      _addr(U_out) if U_out is not None and U_out.size else None,
+                      0 if U_out is not None and U_out.dtype == _F32 else 1, _stream(stream))
+        self._f = lib().dj_step_host
+
+    def __call__(self) -> Optional[np.ndarray]:
+        st = self._f(*self._args)
+        if st != DJ_OK:
+            _check(st, "dj_step_host", self.mesh.h)
+        return self.U_out

@@ -104,12 +104,8 @@ struct dj_mesh {
   int geometric = 0;
   float4* d_parts = nullptr;
   cudaStream_t cap_stream = nullptr;
-  // dj_step_host: side stream and events for the target scatter that runs
-  // beside the element-force kernel (created on first use)
-  cudaStream_t io_stream = nullptr;
-  cudaEvent_t io_before = nullptr, io_done = nullptr, io_copied = nullptr;
   int4* d_bc_entry = nullptr;    // per prescribed-node row: target entries of x, y, z (-1: free), mask
-  double* d_tgt_stage = nullptr; // device copy of the caller's targets (allocated on first use)
+  double* d_tgt_stage = nullptr; // device copy of the caller's targets (dj_step_host; allocated on first use)
   bool targets_on_device = false;  // bc_target lags d_tgt_stage (dj_step_host)
   DevState* h_state_map = nullptr;  // device address of the page-locked state copy
   cudaGraphExec_t run_exec = nullptr;
@@ -215,14 +211,8 @@ void release_device(dj_mesh* m) {
   if (m->h_bct_pinned) cudaFreeHost(m->h_bct_pinned);
   m->h_bct_pinned = nullptr;
   if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
-  if (m->io_stream) cudaStreamDestroy(m->io_stream);
-  if (m->io_before) cudaEventDestroy(m->io_before);
-  if (m->io_done) cudaEventDestroy(m->io_done);
-  if (m->io_copied) cudaEventDestroy(m->io_copied);
   if (m->d_bc_entry) cudaFree(m->d_bc_entry);
   if (m->d_tgt_stage) cudaFree(m->d_tgt_stage);
-  m->io_stream = nullptr;
-  m->io_before = m->io_done = m->io_copied = nullptr;
   m->d_bc_entry = nullptr;
   m->d_tgt_stage = nullptr;
   m->h_state_map = nullptr;
@@ -358,6 +348,9 @@ ForceArgs force_args(dj_mesh* m, int advance) {
   a.ramp_steps = m->params.ramp_steps;
   a.ramp_kind = m->params.ramp_kind;
   a.pres = m->d_pres;
+  a.tgt_src = nullptr;
+  a.tgt_dst = nullptr;
+  a.n_tgt = 0;
   return a;
 }
 
@@ -378,19 +371,25 @@ TileArgs tile_args(dj_mesh* m) {
   return t;
 }
 
-cudaError_t launch_force_any(dj_mesh* m, int advance, cudaStream_t s) {
+// tgt_src: the step's targets in the caller's page-locked array (device
+// address of its mapping), copied by the force kernel into d_tgt_stage
+cudaError_t launch_force_any(dj_mesh* m, int advance, cudaStream_t s, const double* tgt_src = nullptr) {
   if (m->anp) {  // nodal pressures of U^n first
     cudaError_t e = launch_anp(m->cmp, tile_args(m), m->d_node_ptr, m->d_U, m->d_Ulo, (int)m->E, (int)m->N,
                                m->d_vparts, m->d_c1, m->d_pres, s);
     if (e != cudaSuccess) return e;
   }
+  ForceArgs a = force_args(m, advance);
+  if (tgt_src) {
+    a.tgt_src = tgt_src;
+    a.tgt_dst = m->d_tgt_stage;
+    a.n_tgt = (int)m->bc_dof.size();
+  }
   if (m->assembly == ASSEMBLY_TILES_TMA)
-    return launch_force_tma(m->elem_type, m->variant, m->cmp, m->anp, force_args(m, advance), tile_args(m),
-                            m->tma_grid, s);
+    return launch_force_tma(m->elem_type, m->variant, m->cmp, m->anp, a, tile_args(m), m->tma_grid, s);
   if (m->assembly == ASSEMBLY_TILES)
-    return launch_force_tiled(m->elem_type, m->variant, m->cmp, force_args(m, advance), tile_args(m),
-                              m->n_tiles, s);
-  return launch_force(m->elem_type, m->variant, m->cmp, force_args(m, advance), m->threads_force, s);
+    return launch_force_tiled(m->elem_type, m->variant, m->cmp, a, tile_args(m), m->n_tiles, s);
+  return launch_force(m->elem_type, m->variant, m->cmp, a, m->threads_force, s);
 }
 
 NodeArgs node_args(dj_mesh* m) {
@@ -1328,39 +1327,23 @@ dj_status dj_step_host(dj_mesh* m, const double* target, void* U_out, int out_f6
   DevState* st_map = m->h_state_map;
   const bool with_targets = target && nb;
   if (with_targets) {
-    // The node update reads this step's targets itself and stores them into
-    // its prescribed-node rows of the table: page-locked arrays through their
-    // device mapping (no copy, no wait on another stream, so the update keeps
-    // its programmatic launch behind the element forces), other host memory
-    // from a device copy made ahead of the step.  Non-finite entries are not
+    // The force kernel copies this step's targets from a page-locked caller
+    // array (through its device mapping, coalesced, beside its own work) into
+    // the device copy d_tgt_stage; other host memory is copied there before
+    // the step.  The update kernel reads the device copy and stores the
+    // targets into its prescribed-node rows of the table, so no scatter
+    // kernel and no wait on another stream sit between the two step kernels
+    // (the update keeps its programmatic launch).  Non-finite entries are not
     // applied (the previous target stays) and are reported after the step.
-    // A device copy of the targets, for the host's own copy of them, is made
-    // by a copy engine on a side stream (sync_host_targets reads it when the
-    // host copy is next needed).
-    if (!m->io_stream) {
-      CK(cudaStreamCreateWithFlags(&m->io_stream, cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&m->io_before, cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&m->io_done, cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&m->io_copied, cudaEventDisableTiming));
-    }
+    // The host's own copy of the targets is refreshed from the device copy
+    // when it is next needed (sync_host_targets).
     if (!m->d_tgt_stage) CK(cudaMalloc(&m->d_tgt_stage, nb * sizeof(double)));
-    const double* src = static_cast<const double*>(mapped_host(target));
-    if (!src) {
-      CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, st));
-      src = m->d_tgt_stage;
-    } else {
-      CK(cudaEventRecord(m->io_before, st));
-    }
-    CK(launch_force_any(m, 1, st));
+    const double* mapped = static_cast<const double*>(mapped_host(target));
+    if (!mapped) CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(launch_force_any(m, 1, st, mapped));
     NodeArgs na = node_args(m);
-    na.tgt = src;
-    CK(launch_node(NODE_UPDATE, m->cmp, na, st));
-    if (src != m->d_tgt_stage) {
-      CK(cudaStreamWaitEvent(m->io_stream, m->io_before, 0));
-      CK(cudaMemcpyAsync(m->d_tgt_stage, target, nb * sizeof(double), cudaMemcpyHostToDevice, m->io_stream));
-      CK(cudaEventRecord(m->io_done, m->io_stream));
-      CK(cudaStreamWaitEvent(st, m->io_done, 0));  // the device copy lands before the call returns
-    }
+    na.tgt = m->d_tgt_stage;
+    CK(launch_node(NODE_UPDATE_TGT, m->cmp, na, st));
     m->targets_on_device = true;
   } else {
     CK(launch_step(m, st, NODE_UPDATE));

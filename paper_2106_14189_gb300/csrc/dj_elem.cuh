@@ -285,6 +285,23 @@ __device__ __forceinline__ void advance_clock(const ForceArgs& a) {
   }
 }
 
+// The step's prescribed targets from the caller's page-locked array (read
+// coalesced over the host link, one value per thread, before the wait) into
+// the device copy the update kernel reads (stored after the wait, once the
+// previous update has completed).  A grid with fewer threads than targets
+// copies the rest in a loop.
+__device__ __forceinline__ double targets_load(const ForceArgs& a) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  return g < a.n_tgt ? a.tgt_src[g] : 0.0;
+}
+__device__ __forceinline__ void targets_store(const ForceArgs& a, double v) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= a.n_tgt) return;
+  a.tgt_dst[g] = v;
+  const int n = gridDim.x * blockDim.x;
+  for (int q = g + n; q < a.n_tgt; q += n) a.tgt_dst[q] = a.tgt_src[q];
+}
+
 __device__ __forceinline__ bool finite3(float x, float y, float z) {
   return isfinite(x) && isfinite(y) && isfinite(z);
 }

@@ -63,6 +63,12 @@ struct ForceArgs {
   long long ramp_steps;
   int ramp_kind;
   const float* pres;     // average nodal pressure: p_i of every node (else unused)
+  // the step's prescribed targets (host-driven steps): the caller's FP64
+  // array through its device mapping, copied by the launch into tgt_dst (the
+  // device copy the update kernel reads); n_tgt = 0: nothing to copy
+  const double* tgt_src;
+  double* tgt_dst;
+  int n_tgt;
 };
 
 // Adaptive dynamic relaxation (one per mesh, device memory).  The damping in
@@ -114,7 +120,7 @@ struct NodeArgs {
   const float* bm1_node;  // grouped meshes with damping: per-node b - 1 (else nullptr)
   DevState* st;           // ramp value (read), error flags (written)
   const AdrState* adr;    // adaptive modes: damping in use (else nullptr)
-  // NODE_UPDATE only: prescribed targets read from the caller's FP64 array
+  // NODE_UPDATE_TGT only: prescribed targets read from the caller's FP64 array
   // (a device copy, or page-locked host memory through its device mapping;
   // entry bc_entry[b].{x,y,z} of prescribed-node row b, -1 if that component
   // is free; .w the component mask) instead of the per-node table; a
@@ -158,7 +164,11 @@ enum { NODE_UPDATE = 0, NODE_UPDATE_RESID = 1, NODE_FORCE_ONLY = 2, NODE_RESID_O
        // adaptive dynamic relaxation: the update with the damping of AdrState;
        // at a check also the Rayleigh-quotient and interval sums against the
        // previous check's snapshot (U, F - R), which it then replaces
-       NODE_ADR = 4, NODE_ADR_RQ = 5 };
+       NODE_ADR = 4, NODE_ADR_RQ = 5,
+       // the update with this step's prescribed targets read from the
+       // caller's FP64 array (NodeArgs::tgt, required) and stored into the
+       // prescribed-node rows of the table
+       NODE_UPDATE_TGT = 6 };
 
 // Programmatic dependent launch: the kernels of a step may start while the
 // kernel before them in the stream finishes; each of them reads or writes what

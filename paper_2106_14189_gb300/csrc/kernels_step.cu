@@ -49,11 +49,13 @@ __global__ void __launch_bounds__(NE == 4 ? 256 : 128) force_slots_kernel(ForceA
       nid[4] = n1.x; nid[5] = n1.y; nid[6] = n1.z; nid[7] = n1.w;
     }
   }
+  const double tgt = targets_load(a);
   pdl_wait();  // U of the previous update; the slots are read by it
   // the next update kernel may start now: what it reads before its own wait
   // (U, V) is final once the previous update has completed
   pdl_launch_dependents();
   advance_clock(a);
+  targets_store(a, tgt);
   if (!valid) return;
   bool inv;
   if constexpr (NE == 8) {
@@ -110,7 +112,14 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   const int T = t.T;
   const int tile = WARP ? blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32 : blockIdx.x;
   const int tid = WARP ? threadIdx.x % 32 : threadIdx.x;
-  if (WARP && tile >= t.n_tiles) return;
+  if (WARP && tile >= t.n_tiles) {
+    if (a.n_tgt) {  // this thread's share of the targets' copy
+      const double tgt = targets_load(a);
+      pdl_wait();
+      targets_store(a, tgt);
+    }
+    return;
+  }
   float4* smem4 = WARP ? smem_all + (threadIdx.x / 32) * tile_smem_f4(NE, CMP, T, t.cap) : smem_all;
   const auto tile_sync = [] {
     if (WARP) __syncwarp();
@@ -161,9 +170,11 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
       lc[4] = v1.x; lc[5] = v1.y; lc[6] = v1.z; lc[7] = v1.w;
     }
   }
+  const double tgt = targets_load(a);
   pdl_wait();  // U of the previous update; the partials are read by it
   pdl_launch_dependents();  // see force_slots_kernel
   if (!WARP || threadIdx.x < 32) advance_clock(a);
+  targets_store(a, tgt);
   for (int q = tid; q < n_t; q += T) {
     const int gid = __ldg(t.tnodes + (size_t)tile * t.cap + q);
     sx[q] = __ldcs(t.xloc + (size_t)tile * t.cap + q);
@@ -218,7 +229,8 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
 template <int MODE, bool CMP>
 __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   constexpr bool ADR = MODE == NODE_ADR || MODE == NODE_ADR_RQ;
-  constexpr bool UPD = MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID || ADR;
+  constexpr bool TGT = MODE == NODE_UPDATE_TGT;
+  constexpr bool UPD = MODE == NODE_UPDATE || MODE == NODE_UPDATE_RESID || TGT || ADR;
   constexpr bool RESID = MODE == NODE_UPDATE_RESID || MODE == NODE_RESID_ONLY || MODE == NODE_ADR_RQ;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = i / SELL_C, lane = i % SELL_C;
@@ -246,9 +258,9 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   if (i < a.N) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
     if (a.node_ptr) {
-      // node-major partials: one contiguous run per node, ascending tile.  The
-      // first kBatch loads are issued together (most nodes have fewer
-      // partials), then added in the run's order
+      // node-major partials: one contiguous run per node, ascending tile.
+      // The first kBatch loads are issued together (most nodes have no
+      // more), the rest two at a time; all are added in the run's order
       constexpr int kBatch = 4;
       float4 f0[kBatch];
 #pragma unroll
@@ -261,11 +273,17 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
           fy += f0[k].y;
           fz += f0[k].z;
         }
-      for (int p = beg + kBatch; p < end; ++p) {
+      for (int p = beg + kBatch; p < end; p += 2) {
         const float4 f = __ldcs(a.slots + p);
+        const float4 g = p + 1 < end ? __ldcs(a.slots + p + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         fx += f.x;
         fy += f.y;
         fz += f.z;
+        if (p + 1 < end) {
+          fx += g.x;
+          fy += g.y;
+          fz += g.z;
+        }
       }
     } else {
       const int beg = __ldg(a.chunk_ptr + chunk), end = __ldg(a.chunk_ptr + chunk + 1);
@@ -331,28 +349,26 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
       int mask = 0;
       if (bc >= 0) {
         float tv[3];
-        if (MODE == NODE_UPDATE && a.tgt) {
-          // this step's targets from the caller's array (host memory through
-          // its mapping, or a device copy); the node's table row takes them
-          // for later steps.  A non-finite entry is not applied: the row's
-          // previous target stays and the step records ERR_BAD_TARGET.
+        if (TGT) {
+          // this step's targets (the device copy of the caller's array); the
+          // node's table row takes them for later steps.  A non-finite entry
+          // is not applied: the row's previous target stays and the step
+          // records ERR_BAD_TARGET.
           const int4 en = __ldg(a.bc_entry + bc);
           mask = en.w;
           const int ek[3] = {en.x, en.y, en.z};
+          double v[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) v[q] = ek[q] >= 0 ? a.tgt[ek[q]] : 0.0;  // loads issued together
           float4 row = a.bct[bc];
           float* rv[3] = {&row.x, &row.y, &row.z};
 #pragma unroll
           for (int q = 0; q < 3; ++q) {
-            tv[q] = *rv[q];
             if (ek[q] >= 0) {
-              const double v = a.tgt[ek[q]];
-              if (isfinite(v)) {
-                tv[q] = (float)v;
-                *rv[q] = tv[q];
-              } else {
-                atomicOr(&a.st->err_flags, ERR_BAD_TARGET);
-              }
+              if (isfinite(v[q])) *rv[q] = (float)v[q];
+              else atomicOr(&a.st->err_flags, ERR_BAD_TARGET);
             }
+            tv[q] = *rv[q];
           }
           const_cast<float4*>(a.bct)[bc] = row;
         } else {
@@ -653,6 +669,7 @@ cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
 
 cudaError_t launch_node(int mode, int cmp, const NodeArgs& a, cudaStream_t s) {
   if (mode == NODE_UPDATE) return launch_node_m<NODE_UPDATE>(cmp, a, s);
+  if (mode == NODE_UPDATE_TGT) return launch_node_m<NODE_UPDATE_TGT>(cmp, a, s);
   if (mode == NODE_ADR) return launch_node_m<NODE_ADR>(cmp, a, s);
   if (mode == NODE_ADR_RQ) return launch_node_m<NODE_ADR_RQ>(cmp, a, s);
   if (mode == NODE_UPDATE_RESID) return launch_node_m<NODE_UPDATE_RESID>(cmp, a, s);

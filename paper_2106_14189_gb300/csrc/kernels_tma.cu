@@ -152,10 +152,14 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     issue_tile<NE>(a, t, L, smem, &bars[0], first, first + stride);
     if (second) issue_tile<NE>(a, t, L, smem + stage_bytes, &bars[1], first + stride, first + 2 * stride);
   }
+  const double tgt = targets_load(a);
   pdl_wait();  // U of the previous update; the partials are read by it
   pdl_launch_dependents();
   advance_clock(a);
-  if (first >= t.n_tiles) return;
+  if (first >= t.n_tiles) {
+    targets_store(a, tgt);
+    return;
+  }
   // prologue: the first tile's nodes
   {
     const bool ok = mbar_wait(&bars[0], 0u);
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     const int* tn = reinterpret_cast<const int*>(sf4);
     const int n0 = __ldg(t.tile_ptr + first + 1) - __ldg(t.tile_ptr + first);
     gather_nodes<CMP, ANP>(a, tn, n0, su2, sl2, sp2, tid, T);
+    targets_store(a, tgt);  // the host read has landed by now
     async_wait_all();
     __syncthreads();
   }

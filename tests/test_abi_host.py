@@ -139,3 +139,46 @@ def test_symmetric_eigen_rejects_bad_input(lib):
     A[0, 1] = np.nan
     with pytest.raises(binding.DJError):
         binding.dj_symmetric_eigen(A)
+
+
+class _FakeMesh:
+    """Stands in for a Mesh in HostStep's host-side checks (no device)."""
+    h = None
+
+    def info(self):
+        return type("Info", (), {"n_bc_dofs": 6, "n_nodes": 4})()
+
+
+def test_host_step_checks_buffers_once(lib):
+    """HostStep validates types, layout and sizes when it binds the buffers
+    and keeps their addresses (the arrays are held)."""
+    m = _FakeMesh()
+    tgt, U = np.zeros(6), np.zeros((4, 3), dtype=np.float32)
+    hs = binding.HostStep(m, tgt, U)
+    assert hs._args[1] == tgt.ctypes.data and hs._args[2] == U.ctypes.data and hs._args[3] == 0
+    assert binding.HostStep(m, tgt, np.zeros((4, 3)))._args[3] == 1
+    assert binding.HostStep(m, None, None)._args[1:3] == (None, None)
+    bad = [
+        (np.zeros(5), U),                          # wrong number of targets
+        (np.zeros(6, dtype=np.float32), U),        # targets not float64
+        (np.zeros(12)[::2], U),                    # targets not contiguous
+        (tgt, np.zeros((4, 2), dtype=np.float32)),  # wrong output size
+        (tgt, np.zeros((4, 3), dtype=np.int32)),    # output neither float32 nor float64
+        (tgt, np.zeros((3, 4)).T),                 # output not C-contiguous
+    ]
+    for t, u in bad:
+        with pytest.raises(ValueError):
+            binding.HostStep(m, t, u)
+
+
+def test_host_address_cache_tells_reused_ids(lib):
+    """The address cache of dj_step_host returns a buffer's own address, also
+    after an earlier buffer with the same id has been freed."""
+    for _ in range(50):
+        a = np.zeros(1000)
+        assert binding._host_addr(a) == a.ctypes.data
+        assert binding._host_addr(a) == a.ctypes.data
+        del a
+    ro = np.zeros(8)
+    ro.flags.writeable = False
+    assert binding._host_addr(ro) == ro.ctypes.data

@@ -581,18 +581,34 @@ def test_full_size_brain_ellipsoid_sampled_nodes(B, prec):
     print(f"brain ellipsoid 0.8M T4 TI, precision {prec}: worst error / bound {worst:.2f} over 64 nodes")
 
 
+STEP_HOST_SCHEDULES = {
+    "tiles": dict(assembly=1),
+    "tiles-warp": dict(assembly=1, tile_size=32),
+    "slots": dict(assembly=0),
+    "bulk-copy": dict(assembly=2, tile_size=256),
+    # one block of 256 threads for 294 targets: the force kernel's copy loops
+    "bulk-copy-1-block": dict(assembly=2, tile_size=256, max_blocks=1),
+}
+
+
+@pytest.mark.parametrize("sched", sorted(STEP_HOST_SCHEDULES))
 @pytest.mark.parametrize("prec", [0, 1])
-def test_step_host_matches_separate_calls(B, prec):
+def test_step_host_matches_separate_calls(B, prec, sched):
     """dj_step_host (targets in, one step, displacements out, one
     synchronisation) gives bit for bit the trajectory of dj_mesh_update_bc_targets
-    + dj_step + dj_get_displacements, with page-locked and pageable buffers, and
-    its FP32 output is the FP64 output rounded once."""
+    + dj_step + dj_get_displacements, with page-locked and pageable buffers, on
+    every force schedule (each copies page-locked targets in its own way), and
+    its FP32 output is the FP64 output rounded once; HostStep (the bound form)
+    gives the same."""
     torch = pytest.importorskip("torch")
     p = W.cube_shear(W.TET4, 6, n_steps=40)
+    kw = dict(precision=prec, **STEP_HOST_SCHEDULES[sched])
     base = np.asarray(p.bc_target, dtype=np.float64)
     N = p.n_nodes
     ref, outs = [], {}
-    with B.Mesh(p, precision=prec) as m:
+    with B.Mesh(p, **kw) as m:
+        if sched == "bulk-copy-1-block":
+            assert m.info().grid == 1 and base.size > 256
         for k in range(25):
             B.dj_mesh_update_bc_targets(m.h, base * (0.5 + 0.02 * k))
             B.dj_step(m.h)
@@ -602,15 +618,28 @@ def test_step_host_matches_separate_calls(B, prec):
             tgt = torch.empty(base.size, dtype=torch.float64).pin_memory().numpy()
             U64 = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
             U32 = torch.empty((N, 3), dtype=torch.float32).pin_memory().numpy()
+            U64b = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
         else:
             tgt, U64, U32 = np.empty(base.size), np.empty((N, 3)), np.empty((N, 3), dtype=np.float32)
-        with B.Mesh(p, precision=prec) as m, B.Mesh(p, precision=prec) as m2:
+            U64b = np.empty((N, 3))
+        with B.Mesh(p, **kw) as m, B.Mesh(p, **kw) as m2, B.Mesh(p, **kw) as m3:
+            step3 = B.HostStep(m3, tgt, U64b)
             for k in range(25):
                 tgt[:] = base * (0.5 + 0.02 * k)
                 B.dj_step_host(m.h, tgt, U64)
                 B.dj_step_host(m2.h, tgt, U32)
+                step3()
                 assert np.array_equal(U64, ref[k]), (layout, k)
                 assert np.array_equal(U32, U64.astype(np.float32)), (layout, k)
+                assert np.array_equal(U64b, U64), (layout, k)
+            # the host's copy of the targets follows the device's (a new
+            # precomputation starts from the last targets)
+            B.dj_precompute(m.h, m.params)
+            B.dj_step(m.h)
+            B.dj_precompute(m2.h, m2.params)
+            B.dj_mesh_update_bc_targets(m2.h, tgt)
+            B.dj_step(m2.h)
+            assert np.array_equal(m.displacements(), m2.displacements()), layout
         outs[layout] = U64.copy()
     assert np.abs(outs["pinned"]).max() > 0
 
