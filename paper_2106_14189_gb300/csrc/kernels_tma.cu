@@ -211,9 +211,19 @@ __global__ void __launch_bounds__(256) force_tma_kernel(ForceArgs a, TileArgs t)
     if (e < a.E) {
       const auto ld = [&](int r) { return tab[r * T + tid]; };
       ElemConsts<FA, FB, MR, ANP> k;
-      int lc[NE];
+      int lc[NE];  // the element's local connectivity: one 8- or 16-byte load
+      if constexpr (NE == 4) {
+        const ushort4 v = reinterpret_cast<const ushort4*>(lconn)[tid];
+        lc[0] = v.x; lc[1] = v.y; lc[2] = v.z; lc[3] = v.w;
+      } else {
+        const uint4 v = reinterpret_cast<const uint4*>(lconn)[tid];
+        const unsigned w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-      for (int b = 0; b < NE; ++b) lc[b] = lconn[tid * NE + b];
+        for (int b = 0; b < 4; ++b) {
+          lc[2 * b] = (int)(w[b] & 0xffffu);
+          lc[2 * b + 1] = (int)(w[b] >> 16);
+        }
+      }
       k.load_geometric(ld, a);
       if constexpr (ANP) {  // mean nodal pressure times 0V / det 0J = 1 / 6
         float ps = sp[lc[0] >> 4];

@@ -581,13 +581,16 @@ def test_full_size_brain_ellipsoid_sampled_nodes(B, prec):
     print(f"brain ellipsoid 0.8M T4 TI, precision {prec}: worst error / bound {worst:.2f} over 64 nodes")
 
 
-STEP_HOST_SCHEDULES = {
-    "tiles": dict(assembly=1),
-    "tiles-warp": dict(assembly=1, tile_size=32),
-    "slots": dict(assembly=0),
-    "bulk-copy": dict(assembly=2, tile_size=256),
+STEP_HOST_SCHEDULES = {  # name: (element, mesh options)
+    "tiles": ("T4", dict(assembly=1)),
+    "tiles-warp": ("T4", dict(assembly=1, tile_size=32)),
+    "slots": ("T4", dict(assembly=0)),
+    "bulk-copy": ("T4", dict(assembly=2, tile_size=256)),
     # one block of 256 threads for 294 targets: the force kernel's copy loops
-    "bulk-copy-1-block": dict(assembly=2, tile_size=256, max_blocks=1),
+    "bulk-copy-1-block": ("T4", dict(assembly=2, tile_size=256, max_blocks=1)),
+    "bulk-copy-anp": ("T4", dict(assembly=2, tile_size=256, anp=1)),
+    "hex-bulk-copy": ("H8", dict(assembly=2, tile_size=64)),
+    "hex-slots": ("H8", dict(assembly=0)),
 }
 
 
@@ -601,14 +604,16 @@ def test_step_host_matches_separate_calls(B, prec, sched):
     its FP32 output is the FP64 output rounded once; HostStep (the bound form)
     gives the same."""
     torch = pytest.importorskip("torch")
-    p = W.cube_shear(W.TET4, 6, n_steps=40)
-    kw = dict(precision=prec, **STEP_HOST_SCHEDULES[sched])
+    elem, opts = STEP_HOST_SCHEDULES[sched]
+    p = W.cube_shear(W.TET4, 6, n_steps=40) if elem == "T4" else W.cube_shear(W.HEX8, 6, n_steps=40)
+    kw = dict(precision=prec, **opts)
     base = np.asarray(p.bc_target, dtype=np.float64)
     N = p.n_nodes
     ref, outs = [], {}
     with B.Mesh(p, **kw) as m:
         if sched == "bulk-copy-1-block":
             assert m.info().grid == 1 and base.size > 256
+        assert m.info().assembly == opts["assembly"]
         for k in range(25):
             B.dj_mesh_update_bc_targets(m.h, base * (0.5 + 0.02 * k))
             B.dj_step(m.h)
