@@ -4,8 +4,9 @@
 //      steps 1-4 (tJ, J, g_hat, invariants, Table 3 force), written to the
 //      element-force slots (slot = a * E_pad + e, so each store instruction of a
 //      warp is one contiguous 512-byte run).
-//  node_kernel<MODE>                one thread per node: deterministic gather of
-//      the node's slots (sliced ELL, fixed order), central-difference update
+//  node_kernel<MODE, CMP, SELL>     one thread per node: deterministic gather of
+//      the node's slots (sliced ELL, fixed order) or tile partials (node-major
+//      runs, ascending tile), central-difference update
 //      with mass-proportional damping (Eq. 13) and prescribed displacements;
 //      optional FP64 residual partial sums for dynamic relaxation.
 //
@@ -226,7 +227,10 @@ __global__ void __launch_bounds__(NE == 4 ? 512 : 256, (tiles_min_blocks<NE, FA,
   reduce_tile(sf4, li, lp, n_t, tid, T, [&](int q, float4 f) { t.partials[__ldcs(pd + q)] = f; });
 }
 
-template <int MODE, bool CMP>
+// SELL: the slot assembly's sliced-ELL lists (a.node_ptr null), else the
+// tiled assembly's node-major partials (compiled apart: the batched slot
+// gather takes registers the partials' path does not need)
+template <int MODE, bool CMP, bool SELL>
 __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   constexpr bool ADR = MODE == NODE_ADR || MODE == NODE_ADR_RQ;
   constexpr bool TGT = MODE == NODE_UPDATE_TGT;
@@ -245,9 +249,12 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
     V = a.V[i];
     if (UPD) U = a.U[i];
     if (CMP && UPD) L = a.Ulo[i];
-    if (a.node_ptr) {
+    if (!SELL) {
       beg = __ldg(a.node_ptr + i);
       end = __ldg(a.node_ptr + i + 1);
+    } else {  // the node's chunk of the sliced-ELL slot lists
+      beg = __ldg(a.chunk_ptr + chunk);
+      end = __ldg(a.chunk_ptr + chunk + 1);
     }
   }
   pdl_wait();  // the forces of this step; U and V are read by the previous force kernel
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
   pdl_launch_dependents();
   if (i < a.N) {
     float fx = 0.f, fy = 0.f, fz = 0.f;
-    if (a.node_ptr) {
+    if (!SELL) {
       // node-major partials: one contiguous run per node, ascending tile.
       // The first kBatch loads are issued together (most nodes have no
       // more), the rest two at a time; all are added in the run's order
@@ -286,15 +293,24 @@ __global__ void __launch_bounds__(NODE_THREADS) node_kernel(NodeArgs a) {
         }
       }
     } else {
-      const int beg = __ldg(a.chunk_ptr + chunk), end = __ldg(a.chunk_ptr + chunk + 1);
-      for (int p = beg + lane; p < end; p += SELL_C) {
-        const int sid = __ldcs(a.sell + p);
-        if (sid >= 0) {
-          const float4 f = __ldcs(a.slots + sid);
-          fx += f.x;
-          fy += f.y;
-          fz += f.z;
-        }
+      // sliced ELL: the node's slot ids, kB at a time, then their slots,
+      // loads issued together and added in the list's order (-1: padding)
+      constexpr int kB = 4;
+      for (int p0 = beg + lane; p0 < end; p0 += kB * SELL_C) {
+        int sid[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k) sid[k] = p0 + k * SELL_C < end ? __ldcs(a.sell + p0 + k * SELL_C) : -1;
+        float4 f[kB];
+#pragma unroll
+        for (int k = 0; k < kB; ++k)
+          if (sid[k] >= 0) f[k] = __ldcs(a.slots + sid[k]);
+#pragma unroll
+        for (int k = 0; k < kB; ++k)
+          if (sid[k] >= 0) {
+            fx += f[k].x;
+            fy += f[k].y;
+            fz += f[k].z;
+          }
       }
     }
     if (a.R) {
@@ -661,8 +677,12 @@ cudaError_t launch_force_tiled(int elem_type, int variant, int cmp, const ForceA
 template <int MODE>
 cudaError_t launch_node_m(int cmp, const NodeArgs& a, cudaStream_t s) {
   const int grid = (a.N + NODE_THREADS - 1) / NODE_THREADS;
-  cudaError_t e = cmp ? launch_pdl(node_kernel<MODE, true>, dim3(grid), dim3(NODE_THREADS), 0, s, a)
-                      : launch_pdl(node_kernel<MODE, false>, dim3(grid), dim3(NODE_THREADS), 0, s, a);
+  const bool sell = a.node_ptr == nullptr;
+  cudaError_t e =
+      cmp ? (sell ? launch_pdl(node_kernel<MODE, true, true>, dim3(grid), dim3(NODE_THREADS), 0, s, a)
+                  : launch_pdl(node_kernel<MODE, true, false>, dim3(grid), dim3(NODE_THREADS), 0, s, a))
+          : (sell ? launch_pdl(node_kernel<MODE, false, true>, dim3(grid), dim3(NODE_THREADS), 0, s, a)
+                  : launch_pdl(node_kernel<MODE, false, false>, dim3(grid), dim3(NODE_THREADS), 0, s, a));
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
