@@ -627,16 +627,19 @@ def test_step_host_matches_separate_calls(B, prec, sched):
         else:
             tgt, U64, U32 = np.empty(base.size), np.empty((N, 3)), np.empty((N, 3), dtype=np.float32)
             U64b = np.empty((N, 3))
-        with B.Mesh(p, **kw) as m, B.Mesh(p, **kw) as m2, B.Mesh(p, **kw) as m3:
+        with B.Mesh(p, **kw) as m, B.Mesh(p, **kw) as m2, B.Mesh(p, **kw) as m3, B.Mesh(p, **kw) as m4:
             step3 = B.HostStep(m3, tgt, U64b)
             for k in range(25):
                 tgt[:] = base * (0.5 + 0.02 * k)
                 B.dj_step_host(m.h, tgt, U64)
                 B.dj_step_host(m2.h, tgt, U32)
                 step3()
+                B.dj_step_host(m4.h, tgt, None)  # no read-back
                 assert np.array_equal(U64, ref[k]), (layout, k)
                 assert np.array_equal(U32, U64.astype(np.float32)), (layout, k)
                 assert np.array_equal(U64b, U64), (layout, k)
+            assert np.array_equal(m4.displacements(), ref[-1]), layout
+            assert m.info().step == m4.info().step == 25
             # the host's copy of the targets follows the device's (a new
             # precomputation starts from the last targets)
             B.dj_precompute(m.h, m.params)
