@@ -113,6 +113,15 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def profile_for(workload_name, assembly, dominant):
+    """The committed ncu summary of the dominant kernel of this schedule, if any."""
+    known = {("tet4_cube59", 2, "force"): "profiles/force_tma_tet4_nh_cube59.md",
+             ("tet4_cube59", 2, "update"): "profiles/node_update_tet4_cube59.md",
+             ("hex8_cube64", 0, "force"): "profiles/force_slots_hex8_nh_cube64.md",
+             ("hex8_cube64", 0, "update"): "profiles/force_slots_hex8_nh_cube64.md"}
+    return known.get((workload_name, assembly, dominant))
+
+
 def measured_peak():
     try:
         d = json.load(open(PEAKS_FILE))
@@ -866,8 +875,7 @@ def main():
                 "kernel": ("element force (" + {0: "slots", 1: "tiles", 2: "tiles, bulk-copy pipeline"}[minfo.assembly] + ")")
                 if dominant == "force" else "node gather-update",
                 "peak_source": peak_kind,
-                "profile": "profiles/force_tma_tet4_nh_cube59.md" if dominant == "force"
-                           else "profiles/node_update_tet4_cube59.md",
+                "profile": profile_for(args.workload, minfo.assembly, dominant),
                 "algorithmic_bytes_per_launch": bytes_dom,
                 "step": {"bytes_per_element_update": (force_bytes + update_bytes) / E,
                          "achieved_gbs": (force_bytes + update_bytes) / (ms_max * 1e-3 / args.steps) / 1e9},
