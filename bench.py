@@ -304,6 +304,9 @@ def run_reference(args, world, rank):
     rate, _, _ = oracle_rate(probe, 5)
     # process-parallel efficiency is taken as one half for sizing only
     per_step_elems = rate * max(1.0, 0.5 * cores) * budget_s / max(1, args.steps + args.warmup)
+    # at most 2.5M elements (a few GB of host memory in the oracle): a run of
+    # very few steps then takes less than the budget instead of more memory
+    per_step_elems = min(per_step_elems, 2.5e6)
     if args.workload.startswith("tet4"):
         n = max(2, int(round((per_step_elems / 6.0) ** (1 / 3))))
         sample = W.cube_shear(W.TET4, n, n_steps=5000)
