@@ -13,6 +13,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cmath>
 #include <cstdarg>
@@ -328,6 +329,69 @@ void build_sell(const std::vector<int>& ptr, const std::vector<int>& idx, long l
     const long long c = i / SELL_C, lane = i % SELL_C;
     for (int j = 0; j < ptr[i + 1] - ptr[i]; ++j) sell[chunk_ptr[c] + j * SELL_C + lane] = idx[ptr[i] + j];
   }
+}
+
+// Shared-memory positions of a tile's nodes.  The element phase reads the
+// staged U and reference coordinates of each element's nodes with 16-byte
+// loads; eight consecutive lanes (elements) share a wavefront when the
+// distinct positions they touch fall in distinct groups of four banks
+// (position mod 8), and each extra node in a group costs one more.  The
+// groups are given greedily: nodes in descending record count, each to the
+// group, among those with room left, that adds the fewest such conflicts
+// over the eight-element blocks that read it; within a group the nodes keep
+// descending record count.  `lnode` holds the local node (index into the
+// tile's sorted node list) of record (e, b), e < n_el; the result maps that
+// index to a position in [0, n_t).  Only the layout changes: every node's
+// sum keeps its order of additions.
+std::vector<int> bank_positions(int n_t, const std::vector<int>& lnode, int n_el, int ne,
+                                const std::vector<int>& deg) {
+  constexpr int G = 8, W = 8;  // bank groups of a 16-byte load; lanes of one wavefront
+  const int n_sets = (n_el + W - 1) / W * ne;
+  // the distinct nodes of each (eight-element block, local node b) set, and
+  // the sets of each node
+  std::vector<std::array<int, W>> setn(n_sets);
+  std::vector<int> setsz(n_sets, 0), ptr(n_t + 1, 0);
+  for (int qd = 0; qd * W < n_el; ++qd)
+    for (int b = 0; b < ne; ++b) {
+      const int si = qd * ne + b;
+      for (int j = 0; j < W && qd * W + j < n_el; ++j) {
+        const int k = lnode[(size_t)(qd * W + j) * ne + b];
+        if (std::find(setn[si].begin(), setn[si].begin() + setsz[si], k) == setn[si].begin() + setsz[si]) {
+          setn[si][setsz[si]++] = k;
+          ptr[k + 1]++;
+        }
+      }
+    }
+  for (int k = 0; k < n_t; ++k) ptr[k + 1] += ptr[k];
+  std::vector<int> memb(ptr[n_t]), fill(ptr.begin(), ptr.end() - 1);
+  for (int si = 0; si < n_sets; ++si)
+    for (int q = 0; q < setsz[si]; ++q) memb[fill[setn[si][q]]++] = si;
+  std::vector<std::array<int, G>> cnt(n_sets);
+  for (auto& c : cnt) c.fill(0);
+  std::vector<int> mx(n_sets, 0), room(G, 0), grp(n_t, 0), order(n_t);
+  for (int p = 0; p < n_t; ++p) room[p % G]++;
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return deg[x] > deg[y]; });
+  for (int k : order) {
+    int best = -1, best_add = INT_MAX;
+    for (int g = 0; g < G; ++g) {
+      if (!room[g]) continue;
+      int add = 0;
+      for (int q = ptr[k]; q < ptr[k + 1]; ++q) add += cnt[memb[q]][g] + 1 > mx[memb[q]] ? 1 : 0;
+      if (add < best_add) best_add = add, best = g;
+    }
+    grp[k] = best;
+    room[best]--;
+    for (int q = ptr[k]; q < ptr[k + 1]; ++q) mx[memb[q]] = std::max(mx[memb[q]], ++cnt[memb[q]][best]);
+  }
+  // positions g, g + 8, ... of each group, in descending record count
+  std::vector<int> pos(n_t), next(G);
+  for (int g = 0; g < G; ++g) next[g] = g;
+  for (int k : order) {
+    pos[k] = next[grp[k]];
+    next[grp[k]] += G;
+  }
+  return pos;
 }
 
 ForceArgs force_args(dj_mesh* m, int advance) {
@@ -807,15 +871,17 @@ dj_status dj_precompute(dj_mesh* m, const dj_params* p, double* dt_out) {
       smax = std::max(smax, n_t);
       tile_ptr[t + 1] = tile_ptr[t] + n_t;
       tile_x0[t] = loc[0];
-      // local node order: descending record count (ties by node id), so that
-      // the lanes of a warp in the tile reduction walk lists of similar length
-      std::vector<int> deg(n_t, 0), ord(n_t), pos(n_t);
+      // local node positions: chosen against the shared-memory bank conflicts
+      // of the element phase's node loads (bank_positions)
+      std::vector<int> deg(n_t, 0), lnode((size_t)(e1 - e0) * ne), ord(n_t);
       for (long long e = e0; e < e1; ++e)
-        for (int b = 0; b < ne; ++b)
-          deg[std::lower_bound(loc.begin(), loc.end(), cn[e * ne + b]) - loc.begin()]++;
-      for (int k = 0; k < n_t; ++k) ord[k] = k;
-      std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return deg[x] > deg[y]; });
-      for (int k = 0; k < n_t; ++k) pos[ord[k]] = k;
+        for (int b = 0; b < ne; ++b) {
+          const int k = (int)(std::lower_bound(loc.begin(), loc.end(), cn[e * ne + b]) - loc.begin());
+          lnode[(size_t)(e - e0) * ne + b] = k;
+          deg[k]++;
+        }
+      const std::vector<int> pos = bank_positions(n_t, lnode, (int)(e1 - e0), ne, deg);
+      for (int k = 0; k < n_t; ++k) ord[pos[k]] = k;
       // local connectivity and the per-node slot lists (ascending element, then local node)
       std::vector<int> kcnt(n_t + 1, 0);
       for (long long e = e0; e < e1; ++e)
