@@ -924,11 +924,11 @@ def main():
                     t_e2e += time.perf_counter() - t0
             val, _ = replica_throughput(E * n_e2e, t_e2e * 1e3, dist, device="cuda")
             # bytes that cross the host link per step: the FP64 targets (read by
-            # the library's kernel from the page-locked array), U and the 48-byte
+            # the library's kernel from the page-locked array), U and the 40-byte
             # device state read with it
             res[name] = {"value": val, "unit": "element-updates/s", "ms_per_step": t_e2e * 1e3 / n_e2e,
                          "h2d_bytes_per_step": int(targets.nbytes),
-                         "d2h_bytes_per_step": int(U_host.nbytes + 48), "steps": n_e2e}
+                         "d2h_bytes_per_step": int(U_host.nbytes + 40), "steps": n_e2e}
         e2e = dict(res["f32"])
         e2e["call"] = ("dj_step_host through binding.HostStep (targets in, one step, FP32 displacements out, "
                        "one synchronisation)")
